@@ -1,0 +1,209 @@
+/*
+ * sgpe.h -- C ABI of libsgpe: GB300 (sm_103a) kernels for the split-step
+ * Crank-Nicolson time step of the three-component spin-1 Gross-Pitaevskii
+ * equation with spin-orbit (SO) and Rabi coupling, in 1D and 2D, imaginary and
+ * real time (arXiv:2009.13507, Eqs. (1)-(2), Sec. 3 and Appendix A).
+ *
+ * Conventions shared by every entry point
+ *  - The wave function psi is a contiguous array [3][ny][nx] of interleaved
+ *    complex numbers (re, im), x fastest; component index 0, 1, 2 holds the
+ *    spin components +1, 0, -1 (the paper's CP(L,I,J), L = 1, 2, 3, Sec. 3).
+ *    Element type: double (SGPE_C128, 16 bytes per complex) or float
+ *    (SGPE_C64, 8 bytes). ny = 1 in 1D.
+ *  - Grid: x_i = (i - nx/2) dx, y_k = (k - ny/2) dy (integer division), with
+ *    homogeneous Dirichlet boundaries (psi = 0 outside the grid).
+ *  - Memory: the caller owns every device buffer (state, workspace, Omega(t)
+ *    tables) and keeps it alive while the context uses it; the library never
+ *    allocates or frees device memory for the caller's data. The context itself
+ *    (a small host object) is allocated by sgpe_init_grid and released by
+ *    sgpe_destroy; sgpe_set_params also uploads a few small coefficient tables
+ *    into the caller's workspace.
+ *  - Streams: work is enqueued on the stream given to sgpe_init_grid and is
+ *    asynchronous unless a function says it synchronises.
+ *  - Errors: every function returns an sgpe_status; invalid arguments are
+ *    rejected before anything is launched, and a textual reason is available
+ *    from sgpe_last_error. Nothing traps or aborts.
+ *  - Thread safety: one context must not be used from two host threads at once.
+ */
+#ifndef SGPE_H
+#define SGPE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgpe_ctx sgpe_ctx; /* opaque, library-owned host object */
+
+typedef enum {
+    SGPE_OK = 0,
+    SGPE_EINVAL = 1,      /* bad argument (null pointer, size, parameter, alignment) */
+    SGPE_ENOMEM = 2,      /* host allocation of the context failed */
+    SGPE_ECUDA = 3,       /* a CUDA runtime call failed; see sgpe_last_error */
+    SGPE_ENONFINITE = 4,  /* the norm of the state is not finite (NaN/Inf in psi) */
+    SGPE_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
+    SGPE_ESTATE = 6,      /* call out of order (no buffers bound, no parameters set) */
+    SGPE_EUNSUPPORTED = 7 /* size or option outside what the kernels support */
+} sgpe_status;
+
+typedef enum { SGPE_C128 = 0, SGPE_C64 = 1 } sgpe_precision;
+
+/*
+ * Physical parameters (the inputs of the paper's Table 2 and Sec. 2).
+ *  c0, c2   density-density and spin-exchange nonlinearities of Eqs. (1)-(2).
+ *  so_type  OPT_SO (Sec. 3). 1D: 0 none, 1 gamma p_x Sigma_x, 2 gamma p_x Sigma_y,
+ *           3 gamma p_x Sigma_z. 2D: 0 none, 1 Rashba (eta = 1), 2 Dresselhaus
+ *           (eta = -1), 3 equal Rashba-Dresselhaus mixture (eta = 0), for the 2D
+ *           coupling gamma (eta p_y Sigma_x - p_x Sigma_y) of Sec. 2.
+ *  gamma    SO strength; omega: Rabi strength Omega (the coupling is Omega/sqrt2).
+ *  wx, wy   trap V = (wx^2 x^2 + wy^2 y^2)/2 (the paper: wx = wy = 1); wy unused in 1D.
+ *  dt       time step Delta (> 0).
+ *  renorm   imaginary time only: 0 none, 1 Eq. (DJ2) (unit norm), 2 Eq. (DJ) (unit
+ *           norm and magnetisation mag, |mag| < 1). Real time never renormalises.
+ */
+typedef struct {
+    double c0, c2;
+    int so_type;
+    double gamma, omega;
+    double wx, wy;
+    double dt;
+    int renorm;
+    double mag;
+} sgpe_params;
+
+/* Indices of the observables written by sgpe_energy (SGPE_NOBS doubles). */
+enum {
+    SGPE_OBS_NP = 0,     /* N_{+1} = integral of rho_{+1} */
+    SGPE_OBS_N0 = 1,     /* N_0 */
+    SGPE_OBS_NM = 2,     /* N_{-1} */
+    SGPE_OBS_N = 3,      /* N = N_{+1} + N_0 + N_{-1}, Eq. (noma) */
+    SGPE_OBS_MAG = 4,    /* m = N_{+1} - N_{-1}, Eq. (noma) */
+    SGPE_OBS_E = 5,      /* energy functional, Eq. (energy) */
+    SGPE_OBS_MU = 6,     /* (E_kin + E_trap + E_SO + E_Rabi + 2 E_int) / N */
+    SGPE_OBS_RMSP = 7,   /* sqrt(<r^2>) of rho_{+1} (LENGTH / RADIUS, Sec. 3) */
+    SGPE_OBS_RMS0 = 8,
+    SGPE_OBS_RMSM = 9,
+    SGPE_OBS_RMS = 10,   /* of the total density */
+    SGPE_OBS_EKIN = 11,  /* parts of E: kinetic, trap, c0/c2 interaction, Rabi, SO */
+    SGPE_OBS_ETRAP = 12,
+    SGPE_OBS_EINT = 13,
+    SGPE_OBS_ERABI = 14,
+    SGPE_OBS_ESO = 15,
+    SGPE_NOBS = 16
+};
+
+/*
+ * Create a context for one grid. dim = 1 or 2; nx >= 3 (and ny >= 3 in 2D, ny
+ * ignored and taken as 1 in 1D); dx, dy > 0. nx, ny <= 4096 for SGPE_C128 and
+ * <= 8192 for SGPE_C64 (a whole grid line is staged in shared memory).
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream). The context
+ * uses the CUDA device current at this call for all later calls.
+ * Returns SGPE_EINVAL / SGPE_EUNSUPPORTED / SGPE_ENOMEM / SGPE_ECUDA.
+ */
+sgpe_status sgpe_init_grid(sgpe_ctx** out, int dim, int nx, int ny, double dx, double dy,
+                           sgpe_precision prec, void* cuda_stream);
+
+/* Bytes of device workspace the context needs (256-byte aligned start required). */
+sgpe_status sgpe_workspace_bytes(const sgpe_ctx* ctx, size_t* bytes);
+
+/*
+ * Bind caller-owned device buffers: psi_dev ([3][ny][nx] complex, 16-byte
+ * aligned, the state the step functions advance in place) and workspace_dev
+ * (sgpe_workspace_bytes bytes, 256-byte aligned). Binding resets the pending
+ * renormalisation scale to 1. Rebinding is allowed at any time between calls.
+ */
+sgpe_status sgpe_bind(sgpe_ctx* ctx, void* psi_dev, void* workspace_dev);
+
+/*
+ * Set the physical parameters and build the Crank-Nicolson coefficient tables
+ * (the paper's COEF module) in the workspace with a small kernel. Requires
+ * bound buffers. Returns SGPE_EINVAL for dt <= 0, a bad so_type, a bad renorm
+ * mode or |mag| >= 1 with renorm = 2.
+ */
+sgpe_status sgpe_set_params(sgpe_ctx* ctx, const sgpe_params* p);
+
+/*
+ * Advance the bound state by nsteps imaginary-time steps (z = dt): per step
+ * SO (Appendix A Eqs. (p1)-(p2)) -> CALCNU (diagonal trap and c0/c2 terms) ->
+ * HERM (Appendix A Eqs. (nu), (11)) -> Crank-Nicolson along x -> along y (2D)
+ * -> renormalisation by params.renorm (Eqs. (DJ2)/(DJ)). The renormalisation
+ * scale of the last step is kept pending and folded into the next step's first
+ * kernel; sgpe_normalize, sgpe_energy and sgpe_get_state apply it.
+ * Asynchronous. nsteps >= 0.
+ */
+sgpe_status sgpe_step_imag(sgpe_ctx* ctx, int nsteps);
+
+/*
+ * Advance by nsteps real-time steps (z = i dt), same substeps, no
+ * renormalisation. omega_dev (nullable) is a device array of at least nsteps
+ * doubles giving Omega for each step; NULL uses params.omega. Asynchronous;
+ * omega_dev must stay valid until the work completes.
+ */
+sgpe_status sgpe_step_real(sgpe_ctx* ctx, int nsteps, const double* omega_dev);
+
+/*
+ * Apply the pending renormalisation scale to the state, then write the norms
+ * N_{+1}, N_0, N_{-1} of the state (grid sums times dx, or dx dy) to norms_out
+ * (host, 3 doubles; nullable). Synchronises the stream. Returns
+ * SGPE_ENONFINITE if a norm is NaN or infinite.
+ */
+sgpe_status sgpe_normalize(sgpe_ctx* ctx, double* norms_out);
+
+/*
+ * Apply the pending scale, then compute the SGPE_NOBS observables (indices
+ * above; energy of Eq. (energy) with params.omega as the Rabi strength) into
+ * out (host, SGPE_NOBS doubles). Synchronises the stream. SGPE_ENONFINITE if
+ * the norm is not finite.
+ */
+sgpe_status sgpe_energy(sgpe_ctx* ctx, double* out);
+
+/*
+ * Copy a host state ([3][ny][nx] complex of the context's precision) into the
+ * bound state (resets the pending scale), or copy the bound state (after
+ * applying the pending scale) to host memory. Both synchronise the stream;
+ * pinned host memory makes the copies faster but is not required.
+ */
+sgpe_status sgpe_set_state(sgpe_ctx* ctx, const void* host_psi);
+sgpe_status sgpe_get_state(sgpe_ctx* ctx, void* host_psi);
+
+/*
+ * Copy a device state (same layout and precision, caller-owned, must not
+ * overlap the bound state) into the bound state and reset the pending scale.
+ * Asynchronous on the context's stream.
+ */
+sgpe_status sgpe_load_state(sgpe_ctx* ctx, const void* psi_dev);
+
+/*
+ * Apply ONE substep to the bound state, for per-substep checks: which = 0 SO,
+ * 1 CALCNU, 2 HERM, 3 Crank-Nicolson along x, 4 along y (2D only), 5
+ * renormalisation by params.renorm; imag selects z = dt (1) or z = i dt (0);
+ * omega is the Rabi strength used by HERM. The pending scale is applied first.
+ * Asynchronous.
+ */
+sgpe_status sgpe_substep(sgpe_ctx* ctx, int which, int imag, double omega);
+
+/*
+ * Measurement aid: run nsteps steps (imag = 1 imaginary, 0 real time, constant
+ * Omega) with launches enqueued one by one and CUDA events recorded on the
+ * context's stream around every kernel; writes the summed device time in ms of
+ * each kernel kind to ms_out[0..2] (0 pointwise SO/CALCNU/HERM, 1 Crank-Nicolson
+ * along x, 2 along y; unused kinds 0) and the launch counts to launches_out[0..2].
+ * Advances the state exactly like the step functions. Synchronises the stream.
+ */
+sgpe_status sgpe_profile_steps(sgpe_ctx* ctx, int nsteps, int imag, double* ms_out, int* launches_out);
+
+/* Number of kernel launches one step enqueues (for launch accounting). */
+int sgpe_launches_per_step(const sgpe_ctx* ctx);
+
+/* Last error message of this context (never NULL; "" when there is none). */
+const char* sgpe_last_error(const sgpe_ctx* ctx);
+
+/* Release the context (not the caller's buffers). NULL is accepted. */
+sgpe_status sgpe_destroy(sgpe_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGPE_H */

@@ -1,0 +1,554 @@
+// sgpe_api.cu -- the C ABI of libsgpe (see include/sgpe.h): context, workspace
+// layout, parameter checks, step orchestration and CUDA-graph replay.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <map>
+#include <tuple>
+
+#include "../../include/sgpe.h"
+#include "sgpe_device.cuh"
+#include "sgpe_kernels.cuh"
+#include "sgpe_launch.h"
+
+using namespace sgpe;
+
+namespace sgpe {
+Geometry make_geometry(int dim, int nx, int ny, int esz) {
+    Geometry g;
+    g.dim = dim;
+    g.nx = nx;
+    g.ny = ny;
+    g.esz = esz;
+    size_t per_warp_x = (size_t)(32 * chunk_stride(nx) + 32) * esz;
+    g.wx = 4;
+    while (g.wx > 1 && g.wx * per_warp_x > 96 * 1024) g.wx >>= 1;
+    g.smem_x = g.wx * per_warp_x;
+    g.blocks_x = ceil_div(3 * ny, g.wx);
+    size_t per_warp_y = (size_t)(32 * chunk_stride(ny) + 32) * esz;
+    g.wy = 2;
+    while (g.wy > 1 && g.wy * per_warp_y > 160 * 1024) g.wy >>= 1;
+    g.smem_y = g.wy * per_warp_y;
+    g.blocks_y = dim == 2 ? 3 * ceil_div(nx, g.wy) : 0;
+    g.blocks_obs = ceil_div(nx, 32) * ceil_div(ny, 4);
+    g.blocks_norm = kNormBlocks;
+    return g;
+}
+}  // namespace sgpe
+
+struct GraphKey {
+    int imag, count;
+    const double* omega;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(imag, count, omega) < std::tie(o.imag, o.count, o.omega);
+    }
+};
+
+struct sgpe_ctx {
+    int dim, nx, ny;
+    double dx, dy;
+    sgpe_precision prec;
+    int esz;
+    cudaStream_t stream;
+    int device;
+    Geometry geo;
+    // caller-owned buffers
+    void* psi;
+    unsigned char* work;
+    // workspace carve-up
+    DevScalars* sc;
+    void* mid;
+    void* tabs[2][2][4];  // [mode: 0 imag, 1 real][axis: 0 x, 1 y][fa, fg, fp, fq]
+    double* partials;
+    // parameters
+    bool have_params;
+    sgpe_params params;
+    KParams kp;
+    // graph cache
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    bool graphs_ok;
+    char err[512];
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static sgpe_status fail(sgpe_ctx* c, sgpe_status st, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+static sgpe_status cuda_fail(sgpe_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, SGPE_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(expr, where)                                   \
+    do {                                                  \
+        cudaError_t e_ = (expr);                          \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+    } while (0)
+
+struct Layout {
+    size_t sc, mid, tabs[2][2][4], partials, total;
+};
+
+static Layout layout_of(const sgpe_ctx* c) {
+    Layout L;
+    size_t off = 0;
+    L.sc = off;
+    off = align256(off + sizeof(DevScalars));
+    L.mid = off;
+    off = align256(off + (size_t)3 * c->nx * c->ny * c->esz);
+    for (int m = 0; m < 2; m++)
+        for (int a = 0; a < 2; a++) {
+            int n = a == 0 ? c->nx : c->ny;
+            for (int k = 0; k < 4; k++) {
+                L.tabs[m][a][k] = off;
+                off = align256(off + (size_t)n * c->esz);
+            }
+        }
+    L.partials = off;
+    size_t np = 0;
+    const Geometry& g = c->geo;
+    size_t cand[4] = {(size_t)g.blocks_x * 3, (size_t)g.blocks_y * 3, (size_t)g.blocks_obs * kObsAcc,
+                      (size_t)g.blocks_norm * 3};
+    for (int i = 0; i < 4; i++)
+        if (cand[i] > np) np = cand[i];
+    off = align256(off + np * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+static void invalidate_graphs(sgpe_ctx* c) {
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+}
+
+extern "C" {
+
+sgpe_status sgpe_init_grid(sgpe_ctx** out, int dim, int nx, int ny, double dx, double dy, sgpe_precision prec,
+                           void* cuda_stream) {
+    if (!out) return SGPE_EINVAL;
+    *out = nullptr;
+    if (dim != 1 && dim != 2) return SGPE_EINVAL;
+    if (dim == 1) {
+        ny = 1;
+        dy = dx;
+    }
+    if (nx < 3 || (dim == 2 && ny < 3)) return SGPE_EINVAL;
+    if (!(dx > 0.0) || !(dy > 0.0) || !isfinite(dx) || !isfinite(dy)) return SGPE_EINVAL;
+    if (prec != SGPE_C128 && prec != SGPE_C64) return SGPE_EINVAL;
+    int nmax = prec == SGPE_C128 ? 4096 : 8192;
+    if (nx > nmax || ny > nmax) return SGPE_EUNSUPPORTED;
+    sgpe_ctx* c = new (std::nothrow) sgpe_ctx();
+    if (!c) return SGPE_ENOMEM;
+    c->dim = dim;
+    c->nx = nx;
+    c->ny = ny;
+    c->dx = dx;
+    c->dy = dy;
+    c->prec = prec;
+    c->esz = prec == SGPE_C128 ? 16 : 8;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->geo = make_geometry(dim, nx, ny, c->esz);
+    c->psi = nullptr;
+    c->work = nullptr;
+    c->have_params = false;
+    c->graphs_ok = true;
+    c->err[0] = 0;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = prec == SGPE_C128 ? Launcher<double>::setup() : Launcher<float>::setup();
+    if (e != cudaSuccess) {
+        delete c;
+        return SGPE_ECUDA;
+    }
+    *out = c;
+    return SGPE_OK;
+}
+
+sgpe_status sgpe_workspace_bytes(const sgpe_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return SGPE_EINVAL;
+    *bytes = layout_of(c).total;
+    return SGPE_OK;
+}
+
+sgpe_status sgpe_bind(sgpe_ctx* c, void* psi_dev, void* workspace_dev) {
+    if (!c) return SGPE_EINVAL;
+    if (!psi_dev || !workspace_dev) return fail(c, SGPE_EINVAL, "sgpe_bind: null buffer");
+    if (((uintptr_t)psi_dev & 15) != 0) return fail(c, SGPE_EINVAL, "sgpe_bind: psi not 16-byte aligned");
+    if (((uintptr_t)workspace_dev & 255) != 0) return fail(c, SGPE_EINVAL, "sgpe_bind: workspace not 256-byte aligned");
+    invalidate_graphs(c);
+    c->psi = psi_dev;
+    c->work = (unsigned char*)workspace_dev;
+    Layout L = layout_of(c);
+    c->sc = (DevScalars*)(c->work + L.sc);
+    c->mid = c->work + L.mid;
+    for (int m = 0; m < 2; m++)
+        for (int a = 0; a < 2; a++)
+            for (int k = 0; k < 4; k++) c->tabs[m][a][k] = c->work + L.tabs[m][a][k];
+    c->partials = (double*)(c->work + L.partials);
+    c->have_params = false;
+    CK(cudaMemsetAsync(c->sc, 0, sizeof(DevScalars), c->stream), "sgpe_bind memset");
+    CK(reset_scale(c->stream, c->sc), "sgpe_bind reset_scale");
+    return SGPE_OK;
+}
+
+sgpe_status sgpe_set_params(sgpe_ctx* c, const sgpe_params* p) {
+    if (!c || !p) return SGPE_EINVAL;
+    if (!c->psi) return fail(c, SGPE_ESTATE, "sgpe_set_params: no buffers bound");
+    if (!(p->dt > 0.0) || !isfinite(p->dt)) return fail(c, SGPE_EINVAL, "dt must be positive and finite");
+    if (p->so_type < 0 || p->so_type > 3) return fail(c, SGPE_EINVAL, "so_type must be 0..3");
+    if (p->renorm < 0 || p->renorm > 2) return fail(c, SGPE_EINVAL, "renorm must be 0, 1 or 2");
+    if (p->renorm == 2 && !(fabs(p->mag) < 1.0)) return fail(c, SGPE_EINVAL, "renorm 2 needs |mag| < 1");
+    const double vals[] = {p->c0, p->c2, p->gamma, p->omega, p->wx, p->wy, p->mag};
+    for (double v : vals)
+        if (!isfinite(v)) return fail(c, SGPE_EINVAL, "non-finite parameter");
+    invalidate_graphs(c);
+    c->params = *p;
+    KParams& k = c->kp;
+    memset(&k, 0, sizeof(k));
+    k.dim = c->dim;
+    k.nx = c->nx;
+    k.ny = c->ny;
+    k.dx = c->dx;
+    k.dy = c->dy;
+    k.dt = p->dt;
+    const double gt = p->gamma / sqrt(2.0);
+    k.so_case = 0;
+    if (p->so_type != 0 && p->gamma != 0.0) {
+        if (c->dim == 1) {
+            k.so_case = p->so_type;
+            k.sx = (p->so_type == 3 ? p->gamma : gt) / (2.0 * c->dx);
+            k.sy = 0.0;
+        } else {
+            double eta = p->so_type == 1 ? 1.0 : (p->so_type == 2 ? -1.0 : 0.0);
+            k.so_case = 4;
+            k.sx = gt / (2.0 * c->dx);
+            k.sy = gt * eta / (2.0 * c->dy);
+        }
+    }
+    k.hx = p->dt * k.sx;
+    k.hy = p->dt * k.sy;
+    k.c0 = p->c0;
+    k.c2 = p->c2;
+    k.wx2h = 0.5 * p->wx * p->wx;
+    k.wy2h = c->dim == 2 ? 0.5 * p->wy * p->wy : 0.0;
+    k.omega_t = p->omega / sqrt(2.0);
+    k.cell = c->dim == 2 ? c->dx * c->dy : c->dx;
+    k.renorm = p->renorm;
+    k.mag = p->mag;
+    // COEF: Crank-Nicolson tables, bt = z/(4 h^2), z = dt (imaginary) or i dt (real)
+    for (int m = 0; m < 2; m++)
+        for (int a = 0; a < (c->dim == 2 ? 2 : 1); a++) {
+            double h = a == 0 ? c->dx : c->dy;
+            int n = a == 0 ? c->nx : c->ny;
+            double b = p->dt / (4.0 * h * h);
+            double bre = m == 0 ? b : 0.0, bim = m == 0 ? 0.0 : b;
+            void** t = c->tabs[m][a];
+            cudaError_t e = c->prec == SGPE_C128 ? Launcher<double>::coef(c->stream, t[0], t[1], t[2], t[3], n, bre, bim)
+                                                 : Launcher<float>::coef(c->stream, t[0], t[1], t[2], t[3], n, bre, bim);
+            CK(e, "COEF kernel");
+        }
+    c->have_params = true;
+    return SGPE_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Step orchestration
+// ---------------------------------------------------------------------------
+template <typename R>
+static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab) {
+    cudaError_t e;
+    const int mode = imag ? 0 : 1;
+    const int renorm = imag ? c->params.renorm : 0;
+    if ((e = Launcher<R>::pointwise(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, 7))) return e;
+    if (c->dim == 2) {
+        if ((e = Launcher<R>::cn_x(c->stream, imag, false, c->mid, c->mid, c->kp, c->tabs[mode][0], c->geo,
+                                   c->partials, c->sc, renorm, 1)))
+            return e;
+        return Launcher<R>::cn_y(c->stream, imag, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials, c->sc,
+                                 renorm, 1, 1);
+    }
+    return Launcher<R>::cn_x(c->stream, imag, true, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo, c->partials,
+                             c->sc, renorm, 1);
+}
+
+static cudaError_t enqueue_steps(sgpe_ctx* c, int n, bool imag, const double* omega_tab) {
+    for (int i = 0; i < n; i++) {
+        cudaError_t e = c->prec == SGPE_C128 ? enqueue_step<double>(c, imag, omega_tab)
+                                             : enqueue_step<float>(c, imag, omega_tab);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static const int kGraphSteps = 32;
+
+static sgpe_status run_steps(sgpe_ctx* c, int nsteps, bool imag, const double* omega_tab) {
+    if (omega_tab) CK(cudaMemsetAsync(&c->sc->step_idx, 0, sizeof(int), c->stream), "step_idx reset");
+    int G = nsteps < kGraphSteps ? nsteps : kGraphSteps;
+    int reps = G > 0 ? nsteps / G : 0;
+    int rem = G > 0 ? nsteps - reps * G : 0;
+    cudaGraphExec_t exec = nullptr;
+    if (c->graphs_ok && c->stream != nullptr && reps > 0 && G >= 4) {
+        GraphKey key{imag ? 1 : 0, G, omega_tab};
+        auto it = c->graphs.find(key);
+        if (it != c->graphs.end()) {
+            exec = it->second;
+        } else {
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t e2 = enqueue_steps(c, G, imag, omega_tab);
+                e = cudaStreamEndCapture(c->stream, &graph);
+                if (e2 != cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                exec = nullptr;
+                c->graphs_ok = false;
+            } else {
+                c->graphs[key] = exec;
+            }
+        }
+    }
+    if (exec) {
+        for (int r = 0; r < reps; r++) CK(cudaGraphLaunch(exec, c->stream), "cudaGraphLaunch");
+        CK(enqueue_steps(c, rem, imag, omega_tab), "step kernels");
+    } else {
+        CK(enqueue_steps(c, nsteps, imag, omega_tab), "step kernels");
+    }
+    return SGPE_OK;
+}
+
+static sgpe_status check_ready(sgpe_ctx* c) {
+    if (!c) return SGPE_EINVAL;
+    if (!c->psi) return fail(c, SGPE_ESTATE, "no buffers bound");
+    if (!c->have_params) return fail(c, SGPE_ESTATE, "no parameters set");
+    return SGPE_OK;
+}
+
+template <typename R> static cudaError_t flush_scale(sgpe_ctx* c) {
+    cudaError_t e = Launcher<R>::flush(c->stream, c->psi, (size_t)c->nx * c->ny, c->sc);
+    if (e) return e;
+    return reset_scale(c->stream, c->sc);
+}
+static cudaError_t flush_any(sgpe_ctx* c) {
+    return c->prec == SGPE_C128 ? flush_scale<double>(c) : flush_scale<float>(c);
+}
+
+static sgpe_status read_err(sgpe_ctx* c) {
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, &c->sc->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read err");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    if (err) {
+        CK(cudaMemsetAsync(&c->sc->err, 0, sizeof(int), c->stream), "clear err");
+        return fail(c, SGPE_ENONFINITE, "non-finite norm of the state");
+    }
+    return SGPE_OK;
+}
+
+extern "C" {
+
+sgpe_status sgpe_step_imag(sgpe_ctx* c, int nsteps) {
+    sgpe_status st = check_ready(c);
+    if (st) return st;
+    if (nsteps < 0) return fail(c, SGPE_EINVAL, "nsteps < 0");
+    if (nsteps == 0) return SGPE_OK;
+    return run_steps(c, nsteps, true, nullptr);
+}
+
+sgpe_status sgpe_step_real(sgpe_ctx* c, int nsteps, const double* omega_dev) {
+    sgpe_status st = check_ready(c);
+    if (st) return st;
+    if (nsteps < 0) return fail(c, SGPE_EINVAL, "nsteps < 0");
+    if (((uintptr_t)omega_dev & 7) != 0) return fail(c, SGPE_EINVAL, "omega table not 8-byte aligned");
+    if (nsteps == 0) return SGPE_OK;
+    return run_steps(c, nsteps, false, omega_dev);
+}
+
+sgpe_status sgpe_normalize(sgpe_ctx* c, double* norms_out) {
+    sgpe_status st = check_ready(c);
+    if (st) return st;
+    CK(flush_any(c), "flush");
+    size_t plane = (size_t)c->nx * c->ny;
+    cudaError_t e = c->prec == SGPE_C128
+                        ? Launcher<double>::norms(c->stream, c->psi, plane, c->kp.cell, 0, 0.0, c->partials, c->sc)
+                        : Launcher<float>::norms(c->stream, c->psi, plane, c->kp.cell, 0, 0.0, c->partials, c->sc);
+    CK(e, "norms kernel");
+    double n[4];
+    CK(cudaMemcpyAsync(n, c->sc->norms, sizeof(n), cudaMemcpyDeviceToHost, c->stream), "copy norms");
+    st = read_err(c);
+    if (norms_out) memcpy(norms_out, n, 3 * sizeof(double));
+    return st;
+}
+
+sgpe_status sgpe_energy(sgpe_ctx* c, double* out) {
+    sgpe_status st = check_ready(c);
+    if (st) return st;
+    if (!out) return fail(c, SGPE_EINVAL, "null output");
+    CK(flush_any(c), "flush");
+    cudaError_t e = c->prec == SGPE_C128
+                        ? Launcher<double>::observables(c->stream, c->psi, c->kp, c->kp.omega_t, c->partials, c->sc)
+                        : Launcher<float>::observables(c->stream, c->psi, c->kp, c->kp.omega_t, c->partials, c->sc);
+    CK(e, "observables kernel");
+    CK(cudaMemcpyAsync(out, c->sc->obs, SGPE_NOBS * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy obs");
+    return read_err(c);
+}
+
+sgpe_status sgpe_set_state(sgpe_ctx* c, const void* host_psi) {
+    if (!c || !host_psi) return SGPE_EINVAL;
+    if (!c->psi) return fail(c, SGPE_ESTATE, "no buffers bound");
+    size_t bytes = (size_t)3 * c->nx * c->ny * c->esz;
+    CK(cudaMemcpyAsync(c->psi, host_psi, bytes, cudaMemcpyHostToDevice, c->stream), "set_state copy");
+    CK(reset_scale(c->stream, c->sc), "reset scale");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    return SGPE_OK;
+}
+
+sgpe_status sgpe_load_state(sgpe_ctx* c, const void* psi_dev) {
+    if (!c || !psi_dev) return SGPE_EINVAL;
+    if (!c->psi) return fail(c, SGPE_ESTATE, "no buffers bound");
+    size_t bytes = (size_t)3 * c->nx * c->ny * c->esz;
+    CK(cudaMemcpyAsync(c->psi, psi_dev, bytes, cudaMemcpyDeviceToDevice, c->stream), "load_state copy");
+    CK(reset_scale(c->stream, c->sc), "reset scale");
+    return SGPE_OK;
+}
+
+sgpe_status sgpe_get_state(sgpe_ctx* c, void* host_psi) {
+    if (!c || !host_psi) return SGPE_EINVAL;
+    if (!c->psi) return fail(c, SGPE_ESTATE, "no buffers bound");
+    CK(flush_any(c), "flush");
+    size_t bytes = (size_t)3 * c->nx * c->ny * c->esz;
+    CK(cudaMemcpyAsync(host_psi, c->psi, bytes, cudaMemcpyDeviceToHost, c->stream), "get_state copy");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    return SGPE_OK;
+}
+
+sgpe_status sgpe_substep(sgpe_ctx* c, int which, int imag, double omega) {
+    sgpe_status st = check_ready(c);
+    if (st) return st;
+    if (which < 0 || which > 5) return fail(c, SGPE_EINVAL, "which must be 0..5");
+    if (which == 4 && c->dim != 2) return fail(c, SGPE_EINVAL, "no y sweep in 1D");
+    if (!isfinite(omega)) return fail(c, SGPE_EINVAL, "non-finite omega");
+    CK(flush_any(c), "flush");
+    const bool im = imag != 0;
+    const int mode = im ? 0 : 1;
+    const size_t bytes = (size_t)3 * c->nx * c->ny * c->esz;
+    const bool dbl = c->prec == SGPE_C128;
+    cudaError_t e = cudaSuccess;
+    if (which <= 2) {
+        KParams k = c->kp;
+        k.omega_t = omega / sqrt(2.0);
+        e = dbl ? Launcher<double>::pointwise(c->stream, im, c->psi, c->mid, k, c->sc, nullptr, 1 << which)
+                : Launcher<float>::pointwise(c->stream, im, c->psi, c->mid, k, c->sc, nullptr, 1 << which);
+        CK(e, "pointwise kernel");
+        CK(cudaMemcpyAsync(c->psi, c->mid, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy back");
+    } else if (which == 3) {
+        CK(cudaMemcpyAsync(c->mid, c->psi, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        e = dbl ? Launcher<double>::cn_x(c->stream, im, false, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo,
+                                         c->partials, c->sc, 0, 0)
+                : Launcher<float>::cn_x(c->stream, im, false, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo,
+                                        c->partials, c->sc, 0, 0);
+        CK(e, "cn_x kernel");
+    } else if (which == 4) {
+        CK(cudaMemcpyAsync(c->mid, c->psi, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy");
+        e = dbl ? Launcher<double>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials,
+                                         c->sc, 0, 0, 0)
+                : Launcher<float>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials,
+                                        c->sc, 0, 0, 0);
+        CK(e, "cn_y kernel");
+    } else {
+        size_t plane = (size_t)c->nx * c->ny;
+        int rn = c->params.renorm ? c->params.renorm : 1;
+        e = dbl ? Launcher<double>::norms(c->stream, c->psi, plane, c->kp.cell, rn, c->kp.mag, c->partials, c->sc)
+                : Launcher<float>::norms(c->stream, c->psi, plane, c->kp.cell, rn, c->kp.mag, c->partials, c->sc);
+        CK(e, "norms kernel");
+        CK(flush_any(c), "flush");
+    }
+    return SGPE_OK;
+}
+
+sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out, int* launches_out) {
+    sgpe_status st = check_ready(c);
+    if (st) return st;
+    if (nsteps < 0 || !ms_out || !launches_out) return fail(c, SGPE_EINVAL, "bad profile arguments");
+    const bool im = imag != 0;
+    const int mode = im ? 0 : 1;
+    const int renorm = im ? c->params.renorm : 0;
+    const bool dbl = c->prec == SGPE_C128;
+    cudaEvent_t ev[4];
+    for (int k = 0; k < 4; k++) CK(cudaEventCreate(&ev[k]), "cudaEventCreate");
+    double acc[3] = {0, 0, 0};
+    int cnt[3] = {0, 0, 0};
+    sgpe_status out = SGPE_OK;
+    for (int i = 0; i < nsteps && out == SGPE_OK; i++) {
+        cudaError_t e = cudaEventRecord(ev[0], c->stream);
+        if (!e) e = dbl ? Launcher<double>::pointwise(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, 7)
+                        : Launcher<float>::pointwise(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, 7);
+        if (!e) e = cudaEventRecord(ev[1], c->stream);
+        if (!e) {
+            if (c->dim == 2)
+                e = dbl ? Launcher<double>::cn_x(c->stream, im, false, c->mid, c->mid, c->kp, c->tabs[mode][0], c->geo,
+                                                 c->partials, c->sc, renorm, 1)
+                        : Launcher<float>::cn_x(c->stream, im, false, c->mid, c->mid, c->kp, c->tabs[mode][0], c->geo,
+                                                c->partials, c->sc, renorm, 1);
+            else
+                e = dbl ? Launcher<double>::cn_x(c->stream, im, true, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo,
+                                                 c->partials, c->sc, renorm, 1)
+                        : Launcher<float>::cn_x(c->stream, im, true, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo,
+                                                c->partials, c->sc, renorm, 1);
+        }
+        if (!e) e = cudaEventRecord(ev[2], c->stream);
+        if (!e && c->dim == 2)
+            e = dbl ? Launcher<double>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo,
+                                             c->partials, c->sc, renorm, 1, 1)
+                    : Launcher<float>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo,
+                                            c->partials, c->sc, renorm, 1, 1);
+        if (!e) e = cudaEventRecord(ev[3], c->stream);
+        if (!e) e = cudaEventSynchronize(ev[3]);
+        if (e) {
+            out = cuda_fail(c, e, "profile");
+            break;
+        }
+        for (int k = 0; k < (c->dim == 2 ? 3 : 2); k++) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            acc[k] += ms;
+            cnt[k] += 1;
+        }
+    }
+    for (int k = 0; k < 4; k++) cudaEventDestroy(ev[k]);
+    for (int k = 0; k < 3; k++) {
+        ms_out[k] = acc[k];
+        launches_out[k] = cnt[k];
+    }
+    return out;
+}
+
+int sgpe_launches_per_step(const sgpe_ctx* c) {
+    if (!c) return 0;
+    return c->dim == 2 ? 3 : 2;
+}
+
+const char* sgpe_last_error(const sgpe_ctx* c) { return c ? c->err : "null context"; }
+
+sgpe_status sgpe_destroy(sgpe_ctx* c) {
+    if (!c) return SGPE_OK;
+    invalidate_graphs(c);
+    delete c;
+    return SGPE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,300 @@
+// sgpe_device.cuh -- device arithmetic shared by the step, observable and
+// adjoint kernels: complex helpers, small-argument exponential / sine-cosine
+// polynomials, and the per-point substeps of the split-step scheme of
+// arXiv:2009.13507 (SO: Appendix A Eqs. (p1)-(p2); CALCNU: the diagonal terms
+// of Eqs. (1)-(2); HERM: Appendix A Eqs. (nu), (11)).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sgpe {
+
+template <typename R> struct V2;
+template <> struct V2<double> { using T = double2; };
+template <> struct V2<float> { using T = float2; };
+
+template <typename R> struct cx {
+    R re, im;
+};
+
+template <typename R> __device__ __forceinline__ cx<R> mk(R a, R b) { return cx<R>{a, b}; }
+template <typename R> __device__ __forceinline__ cx<R> add(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R> __device__ __forceinline__ cx<R> sub(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R> __device__ __forceinline__ cx<R> scl(R s, cx<R> a) { return {s * a.re, s * a.im}; }
+template <typename R> __device__ __forceinline__ cx<R> mul(cx<R> a, cx<R> b) {
+    return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+// conj(a) * b
+template <typename R> __device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+    return {fma(a.re, b.re, a.im * b.im), fma(a.re, b.im, -a.im * b.re)};
+}
+template <typename R> __device__ __forceinline__ R nrm(cx<R> a) { return fma(a.re, a.re, a.im * a.im); }
+template <typename R> __device__ __forceinline__ cx<R> cj(cx<R> a) { return {a.re, -a.im}; }
+// a + s*b (s real)
+template <typename R> __device__ __forceinline__ cx<R> axpy(R s, cx<R> b, cx<R> a) {
+    return {fma(s, b.re, a.re), fma(s, b.im, a.im)};
+}
+// a + s*b (s complex)
+template <typename R> __device__ __forceinline__ cx<R> caxpy(cx<R> s, cx<R> b, cx<R> a) {
+    return {fma(s.re, b.re, fma(-s.im, b.im, a.re)), fma(s.re, b.im, fma(s.im, b.re, a.im))};
+}
+
+template <typename R> __device__ __forceinline__ cx<R> ld(const typename V2<R>::T* p, size_t i) {
+    typename V2<R>::T v = __ldg(p + i);
+    return {v.x, v.y};
+}
+template <typename R> __device__ __forceinline__ cx<R> ldc(const typename V2<R>::T* p, size_t i) {
+    typename V2<R>::T v = __ldcg(p + i);  // L2 only: data written earlier in this kernel's grid or stream
+    return {v.x, v.y};
+}
+template <typename R> __device__ __forceinline__ void st(typename V2<R>::T* p, size_t i, cx<R> a) {
+    typename V2<R>::T v;
+    v.x = a.re;
+    v.y = a.im;
+    p[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// exp(x) and (cos x, sin x) for the phase factors.
+//
+// FP64: GB300 executes FP64 at 1/64 of its FP32 rate, so the library
+// exponential / sincos (range reduction plus a long polynomial) dominate the
+// pointwise substeps. Every argument here is dt times an energy, normally well
+// below 1/32 in magnitude, where a truncated Taylor series evaluated by Horner's
+// rule is accurate to a fraction of an ulp:
+//   exp(x) = sum_{n<=9} x^n/n!       (|x| <= 1/32: first omitted term < 3e-20)
+//   sin(x) = x sum_{n<=4} (-x^2)^n/(2n+1)!,  cos(x) = sum_{n<=5} (-x^2)^n/(2n)!
+// Larger arguments take CUDA's exp / sincos.
+// FP32: CUDA's expf / sincosf (full-range, FP32 pipe).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double exp_small(double x) {
+    if (fabs(x) <= 0.03125) {
+        double p = 1.0 / 362880.0;
+        p = fma(p, x, 1.0 / 40320.0);
+        p = fma(p, x, 1.0 / 5040.0);
+        p = fma(p, x, 1.0 / 720.0);
+        p = fma(p, x, 1.0 / 120.0);
+        p = fma(p, x, 1.0 / 24.0);
+        p = fma(p, x, 1.0 / 6.0);
+        p = fma(p, x, 0.5);
+        p = fma(p, x, 1.0);
+        return fma(p, x, 1.0);
+    }
+    return exp(x);
+}
+__device__ __forceinline__ float exp_small(float x) { return expf(x); }
+
+__device__ __forceinline__ void sincos_small(double x, double* s, double* c) {
+    if (fabs(x) <= 0.03125) {
+        double t = x * x;
+        double ps = 1.0 / 362880.0;  // sin(x)/x = 1 - t/6 + t^2/120 - t^3/5040 + t^4/362880
+        ps = fma(ps, -t, 1.0 / 5040.0);
+        ps = fma(ps, -t, 1.0 / 120.0);
+        ps = fma(ps, -t, 1.0 / 6.0);
+        ps = fma(ps, -t, 1.0);
+        *s = ps * x;
+        double pc = 1.0 / 3628800.0;  // cos: 1 - t/2 + t^2/24 - t^3/720 + t^4/40320 - t^5/3628800
+        pc = fma(pc, -t, 1.0 / 40320.0);
+        pc = fma(pc, -t, 1.0 / 720.0);
+        pc = fma(pc, -t, 1.0 / 24.0);
+        pc = fma(pc, -t, 0.5);
+        *c = fma(pc, -t, 1.0);
+        return;
+    }
+    sincos(x, s, c);
+}
+__device__ __forceinline__ void sincos_small(float x, float* s, float* c) { sincosf(x, s, c); }
+
+// Coefficients of exp(-z A) = I - s_z A + k_z A^2 for the HERM matrix A
+// (A^3 = C^2 A since A has eigenvalues C, 0, -C):
+//   imaginary time (z = dt):  s = sinh(dt C)/C,  k = (cosh(dt C) - 1)/C^2
+//   real time (z = i dt):     s_z = i s, s = sin(dt C)/C,  k = (cos(dt C) - 1)/C^2
+// Both are even in C, so for small w = (dt C)^2 they are power series in w:
+//   s = dt  sum_n (+-w)^n/(2n+1)!,   k = +-dt^2 sum_n (+-w)^n/(2n+2)!
+// (+ for imaginary, - for real time); no square root is needed. Otherwise
+// C = sqrt(C^2) and the closed forms, with cosh - 1 = 2 sinh^2(x/2) and
+// cos - 1 = -2 sin^2(x/2) to avoid cancellation.
+template <bool IMAG>
+__device__ __forceinline__ void herm_coeffs(double C2, double dt, double* s, double* k) {
+    double w = dt * dt * C2;
+    if (w <= 1.0 / 1024.0) {
+        double v = IMAG ? w : -w;
+        double ps = 1.0 / 362880.0;  // 1/9!
+        ps = fma(ps, v, 1.0 / 5040.0);
+        ps = fma(ps, v, 1.0 / 120.0);
+        ps = fma(ps, v, 1.0 / 6.0);
+        ps = fma(ps, v, 1.0);
+        double pk = 1.0 / 3628800.0;  // 1/10!
+        pk = fma(pk, v, 1.0 / 40320.0);
+        pk = fma(pk, v, 1.0 / 720.0);
+        pk = fma(pk, v, 1.0 / 24.0);
+        pk = fma(pk, v, 0.5);
+        *s = dt * ps;
+        *k = (IMAG ? dt * dt : -dt * dt) * pk;
+        return;
+    }
+    double C = sqrt(C2);
+    double x = dt * C;
+    if (IMAG) {
+        double sh = sinh(0.5 * x);
+        *s = sinh(x) / C;
+        *k = 2.0 * sh * sh / C2;
+    } else {
+        double sh = sin(0.5 * x);
+        *s = sin(x) / C;
+        *k = -2.0 * sh * sh / C2;
+    }
+}
+template <bool IMAG>
+__device__ __forceinline__ void herm_coeffs(float C2, float dt, float* s, float* k) {
+    float w = dt * dt * C2;
+    if (w <= 1.0f / 256.0f) {
+        float v = IMAG ? w : -w;
+        float ps = fmaf(fmaf(1.0f / 5040.0f, v, 1.0f / 120.0f), v, 1.0f / 6.0f);
+        ps = fmaf(ps, v, 1.0f);
+        float pk = fmaf(fmaf(1.0f / 40320.0f, v, 1.0f / 720.0f), v, 1.0f / 24.0f);
+        pk = fmaf(pk, v, 0.5f);
+        *s = dt * ps;
+        *k = (IMAG ? dt * dt : -dt * dt) * pk;
+        return;
+    }
+    float C = sqrtf(C2);
+    float x = dt * C;
+    if (IMAG) {
+        float sh = sinhf(0.5f * x);
+        *s = sinhf(x) / C;
+        *k = 2.0f * sh * sh / C2;
+    } else {
+        float sh = sinf(0.5f * x);
+        *s = sinf(x) / C;
+        *k = -2.0f * sh * sh / C2;
+    }
+}
+
+// Multiply by z/dt: 1 in imaginary time, i in real time.
+template <bool IMAG, typename R> __device__ __forceinline__ cx<R> zunit(cx<R> a) {
+    if (IMAG) return a;
+    return {-a.im, a.re};
+}
+
+// ---------------------------------------------------------------------------
+// Kernel parameter block (host-computed constants; plain data).
+// ---------------------------------------------------------------------------
+struct KParams {
+    int dim, nx, ny;
+    int so_case;      // 0 none; 1 1D Sigma_x; 2 1D Sigma_y; 3 1D Sigma_z; 4 2D (eta)
+    double dx, dy, dt;
+    double hx, hy;    // SO: dt*gt/(2dx) (dt*gamma/(2dx) for Sigma_z), dt*gt*eta/(2dy)
+    double sx, sy;    // the same without the factor dt (for the SO energy)
+    double c0, c2;
+    double wx2h, wy2h;  // wx^2/2, wy^2/2
+    double omega_t;   // Omega/sqrt2 (constant Rabi term)
+    double cell;      // dx (1D) or dx*dy
+    int renorm;       // 0, 1 (DJ2), 2 (DJ)
+    double mag;
+};
+
+// ---------------------------------------------------------------------------
+// Pointwise substeps at one grid point. u[j] holds the (already scaled) state
+// of component j at the point; X[j], Y[j] the raw differences
+// psi_j(x+1) - psi_j(x-1), psi_j(y+1) - psi_j(y-1) with zero ghosts, and d[j]
+// the scale of component j (the pending renormalisation).
+// ---------------------------------------------------------------------------
+
+// SO (Appendix A Eqs. (p1)-(p2)): u_j <- u_j - z (H_SO psi)_j, with H_SO from
+// the SO terms of Sec. 2 (1D Sigma_y in the form derived from gamma p_x Sigma_y).
+template <bool IMAG, typename R>
+__device__ __forceinline__ void so_point(cx<R> (&u)[3], const cx<R> (&X)[3], const cx<R> (&Y)[3],
+                                         const R (&gx)[3], const R (&gy)[3], int so_case) {
+    // h'_j = dt * (H_SO psi)_j; the update is u_j -= zunit(h'_j).
+    cx<R> h0, hp, hm;
+    if (so_case == 4) {
+        // f_+ = gt d_x psi_0 - i gt eta d_y psi_0 ; f_- = -gt d_x psi_0 - i gt eta d_y psi_0
+        // g = -gt d_x psi_+ + gt d_x psi_- - i gt eta d_y (psi_+ + psi_-)
+        cx<R> ax = scl(gx[1], X[1]);
+        cx<R> ay = {gy[1] * Y[1].im, -gy[1] * Y[1].re};  // -i gy Y0
+        hp = add(ax, ay);
+        hm = sub(ay, ax);
+        h0.re = fma(-gx[0], X[0].re, fma(gx[2], X[2].re, fma(gy[0], Y[0].im, gy[2] * Y[2].im)));
+        h0.im = fma(-gx[0], X[0].im, fma(gx[2], X[2].im, -fma(gy[0], Y[0].re, gy[2] * Y[2].re)));
+    } else if (so_case == 1) {
+        // Sigma_x: f_+- = -i gt d_x psi_0 ; g = -i gt d_x (psi_+ + psi_-)
+        hp = {gx[1] * X[1].im, -gx[1] * X[1].re};
+        hm = hp;
+        h0.re = fma(gx[0], X[0].im, gx[2] * X[2].im);
+        h0.im = -fma(gx[0], X[0].re, gx[2] * X[2].re);
+    } else if (so_case == 2) {
+        // Sigma_y: f_+ = -gt d_x psi_0 ; f_- = gt d_x psi_0 ; g = gt d_x (psi_+ - psi_-)
+        hm = scl(gx[1], X[1]);
+        hp = {-hm.re, -hm.im};
+        h0.re = fma(gx[0], X[0].re, -gx[2] * X[2].re);
+        h0.im = fma(gx[0], X[0].im, -gx[2] * X[2].im);
+    } else if (so_case == 3) {
+        // Sigma_z: f_+ = -i gamma d_x psi_+ ; f_- = +i gamma d_x psi_- ; g = 0
+        hp = {gx[0] * X[0].im, -gx[0] * X[0].re};
+        hm = {-gx[2] * X[2].im, gx[2] * X[2].re};
+        h0 = {R(0), R(0)};
+    } else {
+        return;
+    }
+    u[0] = sub(u[0], zunit<IMAG>(hp));
+    u[1] = sub(u[1], zunit<IMAG>(h0));
+    u[2] = sub(u[2], zunit<IMAG>(hm));
+}
+
+// CALCNU: u_j <- exp(-z mu_j) u_j with
+//   mu_+- = V + c0 rho + c2 (rho_+- - rho_-+ + rho_0),  mu_0 = V + c0 rho + c2 (rho_+ + rho_-).
+template <bool IMAG, typename R>
+__device__ __forceinline__ void calcnu_point(cx<R> (&u)[3], R V, R c0, R c2, R dt) {
+    R rp = nrm(u[0]), r0 = nrm(u[1]), rm = nrm(u[2]);
+    R base = fma(c0, rp + r0 + rm, V);
+    R mup = fma(c2, rp - rm + r0, base);
+    R mu0 = fma(c2, rp + rm, base);
+    R mum = fma(c2, rm - rp + r0, base);
+    if (IMAG) {
+        R fp = exp_small(-dt * mup), f0 = exp_small(-dt * mu0), fm = exp_small(-dt * mum);
+        u[0] = scl(fp, u[0]);
+        u[1] = scl(f0, u[1]);
+        u[2] = scl(fm, u[2]);
+    } else {
+        R s, c;
+        sincos_small(dt * mup, &s, &c);  // exp(-i dt mu) = c - i s
+        u[0] = mul(cx<R>{c, -s}, u[0]);
+        sincos_small(dt * mu0, &s, &c);
+        u[1] = mul(cx<R>{c, -s}, u[1]);
+        sincos_small(dt * mum, &s, &c);
+        u[2] = mul(cx<R>{c, -s}, u[2]);
+    }
+}
+
+// HERM (Appendix A): with a = c2 psi_-^* psi_0 + Ot, b = c2 psi_0^* psi_+ + Ot
+// and A = [[0,a,0],[a*,0,b],[0,b*,0]] (frozen over the substep), psi <- exp(-z A) psi,
+// evaluated as psi - s_z A psi + k A^2 psi with A^2 = [[|a|^2,0,ab],[0,C^2,0],[a*b*,0,|b|^2]].
+// This equals the eigen-decomposition form V diag(exp(-z lambda)) V^{-1} of Eq. (11) and
+// stays finite at C = 0.
+template <bool IMAG, typename R>
+__device__ __forceinline__ void herm_point(cx<R> (&u)[3], R c2, R Ot, R dt) {
+    cx<R> a = cmul(u[2], u[1]);  // psi_-^* psi_0
+    a = {fma(c2, a.re, Ot), c2 * a.im};
+    cx<R> b = cmul(u[1], u[0]);  // psi_0^* psi_+
+    b = {fma(c2, b.re, Ot), c2 * b.im};
+    R na = nrm(a), nb = nrm(b);
+    R C2 = na + nb;
+    R s, k;
+    herm_coeffs<IMAG>(C2, dt, &s, &k);
+    cx<R> ab = mul(a, b);
+    // A psi
+    cx<R> Ap = mul(a, u[1]);
+    cx<R> A0 = add(cmul(a, u[0]), mul(b, u[2]));
+    cx<R> Am = cmul(b, u[1]);
+    // A^2 psi
+    cx<R> Bp = axpy(na, u[0], mul(ab, u[2]));
+    cx<R> B0 = scl(C2, u[1]);
+    cx<R> Bm = axpy(nb, u[2], cmul(ab, u[0]));
+    cx<R> sAp = zunit<IMAG>(Ap), sA0 = zunit<IMAG>(A0), sAm = zunit<IMAG>(Am);
+    u[0] = axpy(k, Bp, axpy(-s, sAp, u[0]));
+    u[1] = axpy(k, B0, axpy(-s, sA0, u[1]));
+    u[2] = axpy(k, Bm, axpy(-s, sAm, u[2]));
+}
+
+}  // namespace sgpe

@@ -1,0 +1,630 @@
+// sgpe_kernels.cuh -- sm_103a kernels of one split step (arXiv:2009.13507,
+// Sec. 3 and Appendix A) for one grid, templated on the storage precision R
+// (double: complex128 state; float: complex64 state) and on the time mode
+// (IMAG: z = dt, imaginary time; otherwise z = i dt, real time).
+//
+// One step, 2D:  k_pointwise (A -> B): pending scale, SO, CALCNU, HERM
+//                k_cn_x      (B -> B): Crank-Nicolson along x, one warp per line
+//                k_cn_y      (B -> A): Crank-Nicolson along y, one warp per column,
+//                                      FP64 norm partials, last block -> scale
+// One step, 1D:  k_pointwise (A -> B), k_cn_x<LAST> (B -> A) with the norm.
+// Reductions are FP64 in both precisions and deterministic (fixed order).
+#pragma once
+#include "sgpe_device.cuh"
+
+namespace sgpe {
+
+// ---------------------------------------------------------------------------
+// Workspace scalars (device) used by the step kernels.
+// ---------------------------------------------------------------------------
+struct DevScalars {
+    double scale[4];     // pending renormalisation scale per component (DJ2: all equal)
+    double norms[4];     // N_j of the state written by the last completed step
+    double obs[16];      // observables of the last sgpe_energy
+    int step_idx;        // index into a per-step Omega table (real time)
+    int err;             // bit 0: non-finite norm
+    unsigned ticket[4];  // last-block tickets: 0 step finalize, 1 observables, 2 norms
+};
+
+// Crank-Nicolson coefficient tables for one axis and one time mode.
+// T = I - bt L (L = tridiag(1,-2,1), bt = z/(4h^2)) factors as T = L U with
+// u_0 = 1 + 2bt, u_i = 1 + 2bt - bt^2/u_{i-1}. With y'_i = y_i/u_i:
+//   forward  y'_i = fa_i x_i + fg_i y'_{i-1},  fa_i = 1/u_i, fg_i = bt/u_i
+//   backward w_i  = y'_i + fg_i w_{i+1}
+// and the step's Crank-Nicolson result is 2 w - x  (= T^{-1}(I + bt L) x).
+// A warp solves a line in 32 chunks of C consecutive points; fp_i / fq_i are the
+// products of fg over the chunk up to / from point i (carry propagation).
+template <typename R> struct Tabs {
+    const typename V2<R>::T* fa;
+    const typename V2<R>::T* fg;
+    const typename V2<R>::T* fp;
+    const typename V2<R>::T* fq;
+};
+
+// Shared-memory slot of line element i: chunk k = i / C at k*S, S = C | 1 (odd,
+// so that the 32 lanes walking their chunks hit distinct banks).
+__device__ __forceinline__ int slot(int i, int C, int S) {
+    int k = i / C;
+    return k * S + (i - k * C);
+}
+
+template <bool IMAG, typename R> __device__ __forceinline__ cx<R> tmul(cx<R> t, cx<R> x) {
+    if (IMAG) return scl(t.re, x);
+    return mul(t, x);
+}
+// acc + t * x
+template <bool IMAG, typename R> __device__ __forceinline__ cx<R> tfma(cx<R> t, cx<R> x, cx<R> acc) {
+    if (IMAG) return axpy(t.re, x, acc);
+    return caxpy(t, x, acc);
+}
+template <typename R> __device__ __forceinline__ cx<R> shup(cx<R> a, int off) {
+    return {__shfl_up_sync(0xffffffffu, a.re, off), __shfl_up_sync(0xffffffffu, a.im, off)};
+}
+template <typename R> __device__ __forceinline__ cx<R> shdn(cx<R> a, int off) {
+    return {__shfl_down_sync(0xffffffffu, a.re, off), __shfl_down_sync(0xffffffffu, a.im, off)};
+}
+
+template <typename R> __device__ __forceinline__ cx<R> tld(const typename V2<R>::T* t, int i) {
+    typename V2<R>::T v = __ldg(t + i);
+    return {v.x, v.y};
+}
+
+// Solve T w = x for one line held in shared memory (buf, chunked layout) by the
+// calling warp; on return buf holds w up to the backward carry, which is left
+// per chunk in carry[0..31]: w_i = buf[slot(i)] + fq_i * carry[i / C].
+// All 32 lanes must call this.
+template <typename R, bool IMAG>
+__device__ __forceinline__ void warp_solve(cx<R>* buf, cx<R>* carry, int n, int C, int S, const Tabs<R>& t) {
+    const int lane = threadIdx.x & 31;
+    const int i0 = lane * C;
+    const int i1 = min(n, i0 + C);
+    // forward sweep inside the chunk, zero carry
+    cx<R> y = {R(0), R(0)};
+    for (int i = i0; i < i1; i++) {
+        int s = slot(i, C, S);
+        y = tfma<IMAG>(tld<R>(t.fg, i), y, tmul<IMAG>(tld<R>(t.fa, i), buf[s]));
+        buf[s] = y;
+    }
+    // inclusive scan of the chunk maps y_end = A y_in + B over the lanes
+    cx<R> A = (i1 > i0) ? tld<R>(t.fp, i1 - 1) : cx<R>{R(1), R(0)};
+    cx<R> B = y;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        cx<R> Ap = shup(A, off), Bp = shup(B, off);
+        if (lane >= off) {
+            B = tfma<IMAG>(A, Bp, B);
+            A = tmul<IMAG>(A, Ap);
+        }
+    }
+    cx<R> cin = shup(B, 1);
+    if (lane == 0) cin = {R(0), R(0)};
+    // backward sweep inside the chunk with the forward carry folded in
+    cx<R> w = {R(0), R(0)};
+    for (int i = i1 - 1; i >= i0; i--) {
+        int s = slot(i, C, S);
+        cx<R> yi = tfma<IMAG>(tld<R>(t.fp, i), cin, buf[s]);
+        w = tfma<IMAG>(tld<R>(t.fg, i), w, yi);
+        buf[s] = w;
+    }
+    // scan of the backward chunk maps w_start = A w_next + B from the right
+    A = (i1 > i0) ? tld<R>(t.fq, i0) : cx<R>{R(1), R(0)};
+    B = w;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        cx<R> An = shdn(A, off), Bn = shdn(B, off);
+        if (lane + off < 32) {
+            B = tfma<IMAG>(A, Bn, B);
+            A = tmul<IMAG>(A, An);
+        }
+    }
+    cx<R> cb = shdn(B, 1);
+    if (lane == 31) cb = {R(0), R(0)};
+    carry[lane] = cb;
+    __syncwarp();
+}
+
+// Deterministic block reduction of NV doubles per thread; result valid in
+// thread 0. red: shared scratch of (blockDim/32)*NV doubles.
+template <int NV>
+__device__ __forceinline__ void block_reduce(double (&v)[NV], double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) red[warp * NV + q] = v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+            double s = 0.0;
+            for (int w = 0; w < nw; w++) s += red[w * NV + q];
+            v[q] = s;
+        }
+    }
+}
+
+// Last-block election after every block wrote its partials; returns true in
+// all threads of the last block to arrive (threadfence-reduction pattern).
+__device__ __forceinline__ bool last_block(unsigned* ticket) {
+    __shared__ bool am_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+        unsigned t = atomicAdd(ticket, 1u);
+        am_last = (t == nb - 1);
+    }
+    __syncthreads();
+    if (am_last) __threadfence();
+    return am_last;
+}
+
+// Renormalisation factors from the norms (Appendix A): Eq. (DJ2) for renorm = 1,
+// Eq. (DJ) with magnetisation mag for renorm = 2; otherwise 1.
+__device__ __forceinline__ void renorm_factors(const double (&N)[3], int renorm, double mag, double (&d)[3]) {
+    d[0] = d[1] = d[2] = 1.0;
+    if (renorm == 1) {
+        double f = 1.0 / sqrt(N[0] + N[1] + N[2]);
+        d[0] = d[1] = d[2] = f;
+    } else if (renorm == 2) {
+        double m = mag;
+        double d0 = sqrt(1.0 - m * m) / sqrt(N[1] + sqrt(4.0 * (1.0 - m * m) * N[0] * N[2] + m * m * N[1] * N[1]));
+        d[0] = N[0] > 0.0 ? sqrt(1.0 + m - d0 * d0 * N[1]) / sqrt(2.0 * N[0]) : 1.0;
+        d[2] = N[2] > 0.0 ? sqrt(1.0 - m - d0 * d0 * N[1]) / sqrt(2.0 * N[2]) : 1.0;
+        d[1] = N[1] > 0.0 ? d0 : 1.0;
+    }
+}
+
+// Called by every thread of the last block: sum the per-block partial norms
+// (partials[b*3 + j]) in block order, then thread 0 publishes N_j, the next
+// pending scale (renorm != 0) and advances the step counter.
+__device__ __forceinline__ void finalize_norms(const double* partials, int nblk, double cell, int renorm,
+                                               double mag, bool advance_step, DevScalars* sc, unsigned* ticket) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double s[3] = {0.0, 0.0, 0.0};
+        for (int b = lane; b < nblk; b += 32) {
+            s[0] += __ldcg(partials + 3 * b + 0);
+            s[1] += __ldcg(partials + 3 * b + 1);
+            s[2] += __ldcg(partials + 3 * b + 2);
+        }
+#pragma unroll
+        for (int q = 0; q < 3; q++)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+        if (lane == 0) {
+            double N[3] = {s[0] * cell, s[1] * cell, s[2] * cell};
+            bool finite = isfinite(N[0]) && isfinite(N[1]) && isfinite(N[2]);
+            double d[3];
+            renorm_factors(N, finite ? renorm : 0, mag, d);
+            for (int j = 0; j < 3; j++) {
+                sc->norms[j] = N[j];
+                sc->scale[j] = d[j];
+            }
+            if (!finite) sc->err |= 1;
+            if (advance_step) sc->step_idx += 1;
+            *ticket = 0u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise substeps (SO, CALCNU, HERM) of one step; mask selects substeps
+// (bit 0 SO, bit 1 CALCNU, bit 2 HERM). Applies the pending scale on load.
+// Block (32, BY); one thread per grid point.
+// ---------------------------------------------------------------------------
+template <typename R, bool IMAG>
+__global__ void __launch_bounds__(128) k_pointwise(const typename V2<R>::T* __restrict__ A,
+                                                   typename V2<R>::T* __restrict__ B, KParams p,
+                                                   const DevScalars* __restrict__ sc,
+                                                   const double* __restrict__ omega_tab, int mask) {
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (ix >= p.nx || iy >= p.ny) return;
+    const size_t plane = (size_t)p.nx * p.ny;
+    const size_t c = (size_t)iy * p.nx + ix;
+    R d[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) d[j] = (R)sc->scale[j];
+    cx<R> u[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) u[j] = scl(d[j], ld<R>(A, j * plane + c));
+    const R dt = (R)p.dt;
+    if ((mask & 1) && p.so_case) {
+        cx<R> X[3], Y[3];
+        const cx<R> zero = {R(0), R(0)};
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            cx<R> xp = (ix + 1 < p.nx) ? ld<R>(A, j * plane + c + 1) : zero;
+            cx<R> xm = (ix > 0) ? ld<R>(A, j * plane + c - 1) : zero;
+            X[j] = sub(xp, xm);
+            if (p.dim == 2) {
+                cx<R> yp = (iy + 1 < p.ny) ? ld<R>(A, j * plane + c + p.nx) : zero;
+                cx<R> ym = (iy > 0) ? ld<R>(A, j * plane + c - p.nx) : zero;
+                Y[j] = sub(yp, ym);
+            } else {
+                Y[j] = zero;
+            }
+        }
+        R gx[3], gy[3];
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            gx[j] = (R)p.hx * d[j];
+            gy[j] = (R)p.hy * d[j];
+        }
+        so_point<IMAG>(u, X, Y, gx, gy, p.so_case);
+    }
+    if (mask & 2) {
+        R x = (R)((ix - p.nx / 2) * p.dx);
+        R y = (R)((iy - p.ny / 2) * p.dy);
+        R V = (R)p.wx2h * x * x + (p.dim == 2 ? (R)p.wy2h * y * y : R(0));
+        calcnu_point<IMAG>(u, V, (R)p.c0, (R)p.c2, dt);
+    }
+    if (mask & 4) {
+        R Ot = omega_tab ? (R)(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440) : (R)p.omega_t;
+        herm_point<IMAG>(u, (R)p.c2, Ot, dt);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; j++) st<R>(B, j * plane + c, u[j]);
+}
+
+// ---------------------------------------------------------------------------
+// Crank-Nicolson along x: line l = j*ny + iy is row iy of component j; one warp
+// per line, WX = blockDim.x/32 lines per block. in may equal out (in place).
+// LAST: this is the step's final pass (1D) -> FP64 norms and the next scale.
+// ---------------------------------------------------------------------------
+template <typename R, bool IMAG, bool LAST>
+__global__ void __launch_bounds__(256) k_cn_x(const typename V2<R>::T* in, typename V2<R>::T* out, KParams p,
+                                              Tabs<R> t, int C, int S, double* partials, DevScalars* sc,
+                                              int renorm, int advance_step) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw) + (size_t)warp * 32 * S;
+    cx<R>* carry = reinterpret_cast<cx<R>*>(smem_raw) + (size_t)nw * 32 * S + warp * 32;
+    const int nlines = 3 * p.ny;
+    const int line = blockIdx.x * nw + warp;
+    const int n = p.nx;
+    double acc = 0.0;
+    if (line < nlines) {
+        const size_t base = (size_t)line * n;
+        for (int i = lane; i < n; i += 32) buf[slot(i, C, S)] = ldc<R>(in, base + i);
+        __syncwarp();
+        warp_solve<R, IMAG>(buf, carry, n, C, S, t);
+        for (int i = lane; i < n; i += 32) {
+            cx<R> w = tfma<IMAG>(tld<R>(t.fq, i), carry[i / C], buf[slot(i, C, S)]);
+            cx<R> x = ldc<R>(in, base + i);
+            cx<R> o = {fma(R(2), w.re, -x.re), fma(R(2), w.im, -x.im)};
+            st<R>(out, base + i, o);
+            if (LAST) acc += (double)o.re * (double)o.re + (double)o.im * (double)o.im;
+        }
+    }
+    if (LAST) {
+        __shared__ double red[8 * 3];
+        double v[3] = {0.0, 0.0, 0.0};
+        if (line < nlines) v[line / p.ny] = acc;
+        block_reduce<3>(v, red);
+        if (threadIdx.x == 0)
+            for (int j = 0; j < 3; j++) partials[3 * blockIdx.x + j] = v[j];
+        if (last_block(&sc->ticket[0]))
+            finalize_norms(partials, gridDim.x, p.cell, renorm, p.mag, advance_step != 0, sc, &sc->ticket[0]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Crank-Nicolson along y (2D): block = W warps, column tile [col0, col0+W) of
+// component j; the tile is staged in shared memory, each warp solves one column.
+// Writes out (the state A), FP64 norm partials, and the last block publishes
+// the norms and the next pending scale.
+// ---------------------------------------------------------------------------
+template <typename R, bool IMAG>
+__global__ void __launch_bounds__(256) k_cn_y(const typename V2<R>::T* in, typename V2<R>::T* out, KParams p,
+                                              Tabs<R> t, int C, int S, double* partials, DevScalars* sc,
+                                              int renorm, int advance_step, int finalize) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int W = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5;
+    const int ncb = (p.nx + W - 1) / W;
+    const int j = blockIdx.x / ncb;
+    const int col0 = (blockIdx.x - j * ncb) * W;
+    const int n = p.ny;
+    const size_t plane = (size_t)p.nx * p.ny;
+    const size_t base = (size_t)j * plane;
+    cx<R>* bufs = reinterpret_cast<cx<R>*>(smem_raw);
+    cx<R>* carry = bufs + (size_t)W * 32 * S;
+    // stage the tile: element (row i, column col0 + w) -> bufs[w][slot(i)]
+    for (int q = threadIdx.x; q < n * W; q += blockDim.x) {
+        int i = q / W, w = q - i * W;
+        int col = col0 + w;
+        if (col < p.nx) bufs[(size_t)w * 32 * S + slot(i, C, S)] = ldc<R>(in, base + (size_t)i * p.nx + col);
+    }
+    __syncthreads();
+    if (col0 + warp < p.nx) warp_solve<R, IMAG>(bufs + (size_t)warp * 32 * S, carry + warp * 32, n, C, S, t);
+    __syncthreads();
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < n * W; q += blockDim.x) {
+        int i = q / W, w = q - i * W;
+        int col = col0 + w;
+        if (col < p.nx) {
+            cx<R> wv = tfma<IMAG>(tld<R>(t.fq, i), carry[w * 32 + i / C], bufs[(size_t)w * 32 * S + slot(i, C, S)]);
+            size_t g = base + (size_t)i * p.nx + col;
+            cx<R> x = ldc<R>(in, g);
+            cx<R> o = {fma(R(2), wv.re, -x.re), fma(R(2), wv.im, -x.im)};
+            st<R>(out, g, o);
+            acc += (double)o.re * (double)o.re + (double)o.im * (double)o.im;
+        }
+    }
+    if (finalize) {
+        __shared__ double red[8];
+        double v[1] = {acc};
+        block_reduce<1>(v, red);
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < 3; q++) partials[3 * blockIdx.x + q] = (q == j) ? v[0] : 0.0;
+        }
+        if (last_block(&sc->ticket[0]))
+            finalize_norms(partials, gridDim.x, p.cell, renorm, p.mag, advance_step != 0, sc, &sc->ticket[0]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// COEF: build the Crank-Nicolson tables of one axis for bt = (bre, bim)
+// (bt = dt/(4h^2) in imaginary time, i dt/(4h^2) in real time). One thread;
+// FP64 arithmetic, stored rounded to R.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi, double* r, double* i) {
+    // (a / b) with Smith's scaling
+    if (fabs(br) >= fabs(bi)) {
+        double q = bi / br, den = br + bi * q;
+        *r = (ar + ai * q) / den;
+        *i = (ai - ar * q) / den;
+    } else {
+        double q = br / bi, den = bi + br * q;
+        *r = (ar * q + ai) / den;
+        *i = (ai * q - ar) / den;
+    }
+}
+
+template <typename R>
+__global__ void k_coef(typename V2<R>::T* fa, typename V2<R>::T* fg, typename V2<R>::T* fp,
+                       typename V2<R>::T* fq, int n, int C, double bre, double bim) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double dr = 1.0 + 2.0 * bre, di = 2.0 * bim;  // diagonal 1 + 2 bt
+    double ur = dr, ui = di;
+    for (int i = 0; i < n; i++) {
+        if (i > 0) {
+            // u_i = (1 + 2bt) - bt^2 / u_{i-1}
+            double b2r = bre * bre - bim * bim, b2i = 2.0 * bre * bim;
+            double qr, qi;
+            cdiv(b2r, b2i, ur, ui, &qr, &qi);
+            ur = dr - qr;
+            ui = di - qi;
+        }
+        double ar, ai, gr, gi;
+        cdiv(1.0, 0.0, ur, ui, &ar, &ai);
+        cdiv(bre, bim, ur, ui, &gr, &gi);
+        fa[i].x = (R)ar;
+        fa[i].y = (R)ai;
+        fg[i].x = (R)gr;
+        fg[i].y = (R)gi;
+    }
+    // chunk products, computed from the rounded-to-FP64 fg values
+    for (int k0 = 0; k0 < n; k0 += C) {
+        int k1 = min(n, k0 + C);
+        double Pr = 1.0, Pi = 0.0;
+        for (int i = k0; i < k1; i++) {
+            double gr = (double)fg[i].x, gi = (double)fg[i].y;
+            double tr = Pr * gr - Pi * gi, ti = Pr * gi + Pi * gr;
+            Pr = tr;
+            Pi = ti;
+            fp[i].x = (R)Pr;
+            fp[i].y = (R)Pi;
+        }
+        Pr = 1.0;
+        Pi = 0.0;
+        for (int i = k1 - 1; i >= k0; i--) {
+            double gr = (double)fg[i].x, gi = (double)fg[i].y;
+            double tr = Pr * gr - Pi * gi, ti = Pr * gi + Pi * gr;
+            Pr = tr;
+            Pi = ti;
+            fq[i].x = (R)Pr;
+            fq[i].y = (R)Pi;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Apply the pending scale in place (psi_j <- d_j psi_j).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_flush(typename V2<R>::T* A, size_t plane, const DevScalars* sc) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = 3 * plane;
+    for (; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        int j = (int)(i / plane);
+        R d = (R)sc->scale[j];
+        cx<R> v = ldc<R>(A, i);
+        st<R>(A, i, scl(d, v));
+    }
+}
+
+static __global__ void k_reset_scale(DevScalars* sc) {
+    if (threadIdx.x < 4) sc->scale[threadIdx.x] = 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// Norms of the state (no pending scale): per-block FP64 partials, last block
+// publishes N_j and, for renorm != 0, the renormalisation scale.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_norms(const typename V2<R>::T* A, size_t plane, double cell, int renorm,
+                                               double mag, double* partials, DevScalars* sc) {
+    __shared__ double red[8 * 3];
+    double v[3] = {0.0, 0.0, 0.0};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * plane;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int j = (int)(i / plane);
+        cx<R> a = ldc<R>(A, i);
+        double q = (double)a.re * (double)a.re + (double)a.im * (double)a.im;
+        if (j == 0) v[0] += q;
+        else if (j == 1) v[1] += q;
+        else v[2] += q;
+    }
+    block_reduce<3>(v, red);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < 3; j++) partials[3 * blockIdx.x + j] = v[j];
+    if (last_block(&sc->ticket[2])) finalize_norms(partials, gridDim.x, cell, renorm, mag, false, sc, &sc->ticket[2]);
+}
+
+// ---------------------------------------------------------------------------
+// Observables (Eq. (noma), Eq. (energy), rms sizes) of the state (no pending
+// scale). Per point in FP64: N_j, r^2 rho_j, the kinetic energy of the links
+// ending at the point (plus the ghost links at the upper edges), trap,
+// interaction, Rabi and SO energy densities.
+// ---------------------------------------------------------------------------
+constexpr int NACC = 11;
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_observables(const typename V2<R>::T* __restrict__ A, KParams p, double omega_t,
+                                                     double* partials, DevScalars* sc) {
+    __shared__ double red[4 * NACC];
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    double v[NACC];
+#pragma unroll
+    for (int q = 0; q < NACC; q++) v[q] = 0.0;
+    if (ix < p.nx && iy < p.ny) {
+        const size_t plane = (size_t)p.nx * p.ny;
+        const size_t c = (size_t)iy * p.nx + ix;
+        cx<double> u[3];
+        const cx<double> zero = {0.0, 0.0};
+        for (int j = 0; j < 3; j++) {
+            cx<R> a = ld<R>(A, j * plane + c);
+            u[j] = {(double)a.re, (double)a.im};
+        }
+        double x = (ix - p.nx / 2) * p.dx, y = (p.dim == 2) ? (iy - p.ny / 2) * p.dy : 0.0;
+        double rr = x * x + y * y;
+        double rp = nrm(u[0]), r0 = nrm(u[1]), rm = nrm(u[2]), rho = rp + r0 + rm;
+        v[0] = rp;
+        v[1] = r0;
+        v[2] = rm;
+        v[3] = rr * rp;
+        v[4] = rr * r0;
+        v[5] = rr * rm;
+        // kinetic: links (ix-1, ix) and, at the upper edge, (ix, ghost); same in y
+        double ek = 0.0;
+        const double idx2 = 1.0 / (p.dx * p.dx), idy2 = 1.0 / (p.dy * p.dy);
+        cx<double> X[3], Y[3];
+        for (int j = 0; j < 3; j++) {
+            cx<double> xm = zero, xp = zero, ym = zero, yp = zero;
+            if (ix > 0) {
+                cx<R> a = ld<R>(A, j * plane + c - 1);
+                xm = {(double)a.re, (double)a.im};
+            }
+            if (ix + 1 < p.nx) {
+                cx<R> a = ld<R>(A, j * plane + c + 1);
+                xp = {(double)a.re, (double)a.im};
+            }
+            ek += 0.5 * nrm(sub(u[j], xm)) * idx2;
+            if (ix == p.nx - 1) ek += 0.5 * nrm(u[j]) * idx2;
+            X[j] = sub(xp, xm);
+            if (p.dim == 2) {
+                if (iy > 0) {
+                    cx<R> a = ld<R>(A, j * plane + c - p.nx);
+                    ym = {(double)a.re, (double)a.im};
+                }
+                if (iy + 1 < p.ny) {
+                    cx<R> a = ld<R>(A, j * plane + c + p.nx);
+                    yp = {(double)a.re, (double)a.im};
+                }
+                ek += 0.5 * nrm(sub(u[j], ym)) * idy2;
+                if (iy == p.ny - 1) ek += 0.5 * nrm(u[j]) * idy2;
+                Y[j] = sub(yp, ym);
+            } else {
+                Y[j] = zero;
+            }
+        }
+        v[6] = ek;
+        double V = p.wx2h * x * x + (p.dim == 2 ? p.wy2h * y * y : 0.0);
+        v[7] = V * rho;
+        cx<double> X4 = mul(cmul(u[2], mul(u[1], u[1])), cj(u[0]));  // psi_-^* psi_0^2 psi_+^*
+        v[8] = 0.5 * (p.c0 * rho * rho +
+                      p.c2 * (rp * rp + rm * rm + 2.0 * rp * r0 + 2.0 * rm * r0 - 2.0 * rp * rm + 4.0 * X4.re));
+        cx<double> Rb = cmul(add(u[0], u[2]), u[1]);  // (psi_+^* + psi_-^*) psi_0
+        v[9] = 2.0 * omega_t * Rb.re;
+        if (p.so_case) {
+            // H_SO psi via the SO update with unit time factor on a zero state
+            cx<double> h[3] = {zero, zero, zero};
+            double gx[3] = {p.sx, p.sx, p.sx}, gy[3] = {p.sy, p.sy, p.sy};
+            so_point<true>(h, X, Y, gx, gy, p.so_case);  // h = -(H_SO psi)
+            v[10] = -(cmul(u[0], h[0]).re + cmul(u[1], h[1]).re + cmul(u[2], h[2]).re);
+        }
+    }
+    // block reduce (blockDim.x * blockDim.y threads, flattened)
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y) >> 5;
+#pragma unroll
+    for (int q = 0; q < NACC; q++)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+    if (lane == 0)
+        for (int q = 0; q < NACC; q++) red[warp * NACC + q] = v[q];
+    __syncthreads();
+    const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+    if (tid == 0) {
+        for (int q = 0; q < NACC; q++) {
+            double s = 0.0;
+            for (int w = 0; w < nw; w++) s += red[w * NACC + q];
+            partials[(size_t)blk * NACC + q] = s;
+        }
+    }
+    __shared__ bool am_last;
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        unsigned t = atomicAdd(&sc->ticket[1], 1u);
+        am_last = (t == gridDim.x * gridDim.y - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    const int nblk = gridDim.x * gridDim.y;
+    if (tid < 32) {
+        double s[NACC];
+        for (int q = 0; q < NACC; q++) s[q] = 0.0;
+        for (int b = tid; b < nblk; b += 32)
+            for (int q = 0; q < NACC; q++) s[q] += __ldcg(partials + (size_t)b * NACC + q);
+        for (int q = 0; q < NACC; q++)
+            for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+        if (tid == 0) {
+            double w = p.cell;
+            double N0 = s[0] * w, N1 = s[1] * w, N2 = s[2] * w, Nt = N0 + N1 + N2;
+            double ekin = s[6] * w, etrap = s[7] * w, eint = s[8] * w, erabi = s[9] * w, eso = s[10] * w;
+            double* o = sc->obs;
+            o[0] = N0;
+            o[1] = N1;
+            o[2] = N2;
+            o[3] = Nt;
+            o[4] = N0 - N2;
+            o[5] = ekin + etrap + eint + erabi + eso;
+            o[6] = Nt > 0.0 ? (ekin + etrap + eso + erabi + 2.0 * eint) / Nt : 0.0;
+            o[7] = s[0] > 0.0 ? sqrt(s[3] / s[0]) : 0.0;
+            o[8] = s[1] > 0.0 ? sqrt(s[4] / s[1]) : 0.0;
+            o[9] = s[2] > 0.0 ? sqrt(s[5] / s[2]) : 0.0;
+            double ss = s[0] + s[1] + s[2];
+            o[10] = ss > 0.0 ? sqrt((s[3] + s[4] + s[5]) / ss) : 0.0;
+            o[11] = ekin;
+            o[12] = etrap;
+            o[13] = eint;
+            o[14] = erabi;
+            o[15] = eso;
+            if (!(isfinite(Nt))) sc->err |= 1;
+            sc->ticket[1] = 0u;
+        }
+    }
+}
+
+}  // namespace sgpe

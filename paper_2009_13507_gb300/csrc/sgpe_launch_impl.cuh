@@ -1,0 +1,116 @@
+// sgpe_launch_impl.cuh -- launchers of the step / observable kernels for one
+// storage precision; included once per precision translation unit.
+#pragma once
+#include "sgpe_kernels.cuh"
+#include "sgpe_launch.h"
+
+namespace sgpe {
+
+template <typename R> static Tabs<R> make_tabs(const void* const* t) {
+    using T = typename V2<R>::T;
+    return Tabs<R>{(const T*)t[0], (const T*)t[1], (const T*)t[2], (const T*)t[3]};
+}
+
+template <typename R> cudaError_t Launcher<R>::setup() {
+    const int lim = 227 * 1024;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_cn_x<R, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_cn_x<R, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_cn_x<R, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_cn_x<R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_cn_y<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_cn_y<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t Launcher<R>::pointwise(cudaStream_t s, bool imag, const void* A, void* B, const KParams& p,
+                                   const DevScalars* sc, const double* omega_tab, int mask) {
+    using T = typename V2<R>::T;
+    dim3 block(32, p.dim == 2 ? 4 : 1);
+    dim3 grid(ceil_div(p.nx, 32), p.dim == 2 ? ceil_div(p.ny, 4) : 1);
+    if (imag)
+        k_pointwise<R, true><<<grid, block, 0, s>>>((const T*)A, (T*)B, p, sc, omega_tab, mask);
+    else
+        k_pointwise<R, false><<<grid, block, 0, s>>>((const T*)A, (T*)B, p, sc, omega_tab, mask);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launcher<R>::cn_x(cudaStream_t s, bool imag, bool last, const void* in, void* out, const KParams& p,
+                              const void* const* tabs, const Geometry& g, double* partials, DevScalars* sc,
+                              int renorm, int advance) {
+    using T = typename V2<R>::T;
+    Tabs<R> t = make_tabs<R>(tabs);
+    const int C = chunk_len(p.nx), S = chunk_stride(p.nx);
+    dim3 block(32 * g.wx), grid(g.blocks_x);
+    if (imag) {
+        if (last)
+            k_cn_x<R, true, true><<<grid, block, g.smem_x, s>>>((const T*)in, (T*)out, p, t, C, S, partials, sc,
+                                                                renorm, advance);
+        else
+            k_cn_x<R, true, false><<<grid, block, g.smem_x, s>>>((const T*)in, (T*)out, p, t, C, S, partials, sc,
+                                                                 renorm, advance);
+    } else {
+        if (last)
+            k_cn_x<R, false, true><<<grid, block, g.smem_x, s>>>((const T*)in, (T*)out, p, t, C, S, partials, sc,
+                                                                 renorm, advance);
+        else
+            k_cn_x<R, false, false><<<grid, block, g.smem_x, s>>>((const T*)in, (T*)out, p, t, C, S, partials, sc,
+                                                                  renorm, advance);
+    }
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launcher<R>::cn_y(cudaStream_t s, bool imag, const void* in, void* out, const KParams& p,
+                              const void* const* tabs, const Geometry& g, double* partials, DevScalars* sc,
+                              int renorm, int advance, int finalize) {
+    using T = typename V2<R>::T;
+    Tabs<R> t = make_tabs<R>(tabs);
+    const int C = chunk_len(p.ny), S = chunk_stride(p.ny);
+    dim3 block(32 * g.wy), grid(g.blocks_y);
+    if (imag)
+        k_cn_y<R, true><<<grid, block, g.smem_y, s>>>((const T*)in, (T*)out, p, t, C, S, partials, sc, renorm, advance,
+                                                      finalize);
+    else
+        k_cn_y<R, false><<<grid, block, g.smem_y, s>>>((const T*)in, (T*)out, p, t, C, S, partials, sc, renorm,
+                                                       advance, finalize);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launcher<R>::coef(cudaStream_t s, void* fa, void* fg, void* fp, void* fq, int n, double bre, double bim) {
+    using T = typename V2<R>::T;
+    k_coef<R><<<1, 32, 0, s>>>((T*)fa, (T*)fg, (T*)fp, (T*)fq, n, chunk_len(n), bre, bim);
+    return cudaGetLastError();
+}
+
+template <typename R> cudaError_t Launcher<R>::flush(cudaStream_t s, void* A, size_t plane, const DevScalars* sc) {
+    using T = typename V2<R>::T;
+    size_t total = 3 * plane;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 4 * kNormBlocks) blocks = 4 * kNormBlocks;
+    k_flush<R><<<blocks, 256, 0, s>>>((T*)A, plane, sc);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launcher<R>::norms(cudaStream_t s, const void* A, size_t plane, double cell, int renorm, double mag,
+                               double* partials, DevScalars* sc) {
+    using T = typename V2<R>::T;
+    k_norms<R><<<kNormBlocks, 256, 0, s>>>((const T*)A, plane, cell, renorm, mag, partials, sc);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launcher<R>::observables(cudaStream_t s, const void* A, const KParams& p, double omega_t,
+                                     double* partials, DevScalars* sc) {
+    using T = typename V2<R>::T;
+    dim3 block(32, 4);
+    dim3 grid(ceil_div(p.nx, 32), ceil_div(p.ny, 4));
+    k_observables<R><<<grid, block, 0, s>>>((const T*)A, p, omega_t, partials, sc);
+    return cudaGetLastError();
+}
+
+}  // namespace sgpe

@@ -1,0 +1,224 @@
+"""Thin ctypes binding of libsgpe (include/sgpe.h): argument marshalling only.
+
+Every substep of the method runs in the library's CUDA kernels; PyTorch only
+provides device memory (state, workspace) and the CUDA stream. There is no CPU
+fallback: if the library has not been built, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, asdict
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsgpe.so")
+_lib = None
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, EUNSUPPORTED = range(8)
+STATUS = {0: "SGPE_OK", 1: "SGPE_EINVAL", 2: "SGPE_ENOMEM", 3: "SGPE_ECUDA", 4: "SGPE_ENONFINITE",
+          5: "SGPE_ETIMEOUT", 6: "SGPE_ESTATE", 7: "SGPE_EUNSUPPORTED"}
+C128, C64 = 0, 1
+NOBS = 16
+OBS_NAMES = ("N+", "N0", "N-", "N", "mag", "E", "mu", "rms+", "rms0", "rms-", "rms",
+             "E_kin", "E_trap", "E_int", "E_rabi", "E_so")
+SUBSTEP = {"so": 0, "calcnu": 1, "herm": 2, "cn_x": 3, "cn_y": 4, "renorm": 5}
+
+# Every symbol include/sgpe.h declares (checked by the CPU test suite).
+EXPORTS = ("sgpe_init_grid", "sgpe_workspace_bytes", "sgpe_bind", "sgpe_set_params", "sgpe_step_imag",
+           "sgpe_step_real", "sgpe_normalize", "sgpe_energy", "sgpe_set_state", "sgpe_get_state", "sgpe_load_state",
+           "sgpe_substep", "sgpe_profile_steps", "sgpe_launches_per_step", "sgpe_last_error",
+           "sgpe_destroy")
+
+
+class SgpeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """sgpe_params (include/sgpe.h)."""
+    _fields_ = [("c0", ctypes.c_double), ("c2", ctypes.c_double), ("so_type", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("omega", ctypes.c_double), ("wx", ctypes.c_double),
+                ("wy", ctypes.c_double), ("dt", ctypes.c_double), ("renorm", ctypes.c_int),
+                ("mag", ctypes.c_double)]
+
+
+def load():
+    """Load libsgpe.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libsgpe.so not found at %s; build it first (python -c 'import __graft_entry__ as g; "
+                           "g.build()')" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "sgpe_init_grid": (I, [ctypes.POINTER(P), I, I, I, D, D, I, P]),
+        "sgpe_workspace_bytes": (I, [P, ctypes.POINTER(S)]),
+        "sgpe_bind": (I, [P, P, P]),
+        "sgpe_set_params": (I, [P, ctypes.POINTER(Params)]),
+        "sgpe_step_imag": (I, [P, I]),
+        "sgpe_step_real": (I, [P, I, P]),
+        "sgpe_normalize": (I, [P, P]),
+        "sgpe_energy": (I, [P, P]),
+        "sgpe_set_state": (I, [P, P]),
+        "sgpe_get_state": (I, [P, P]),
+        "sgpe_load_state": (I, [P, P]),
+        "sgpe_substep": (I, [P, I, I, D]),
+        "sgpe_profile_steps": (I, [P, I, I, P, P]),
+        "sgpe_launches_per_step": (I, [P]),
+        "sgpe_last_error": (ctypes.c_char_p, [P]),
+        "sgpe_destroy": (I, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+@dataclass
+class Physics:
+    """Physical parameters (sgpe_params)."""
+    c0: float = 0.0
+    c2: float = 0.0
+    so_type: int = 0
+    gamma: float = 0.0
+    omega: float = 0.0
+    wx: float = 1.0
+    wy: float = 1.0
+    dt: float = 1e-4
+    renorm: int = 1
+    mag: float = 0.0
+
+    def c(self) -> Params:
+        return Params(self.c0, self.c2, self.so_type, self.gamma, self.omega, self.wx, self.wy, self.dt,
+                      self.renorm, self.mag)
+
+
+class Solver:
+    """One grid on one GPU: state and workspace are torch tensors, the step runs in libsgpe."""
+
+    def __init__(self, dim, nx, ny=1, dx=0.05, dy=None, precision="c128", device="cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.dim, self.nx = int(dim), int(nx)
+        self.ny = int(ny) if dim == 2 else 1
+        self.dx = float(dx)
+        self.dy = float(dy if dy is not None else dx) if dim == 2 else float(dx)
+        self.precision = precision
+        self.device = torch.device(device)
+        self.cdtype = torch.complex128 if precision == "c128" else torch.complex64
+        self.npdtype = np.complex128 if precision == "c128" else np.complex64
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        self.ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self.lib.sgpe_init_grid(ctypes.byref(self.ctx), self.dim, self.nx, self.ny, self.dx, self.dy,
+                                         C128 if precision == "c128" else C64,
+                                         ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != OK:
+            raise SgpeError(rc, "sgpe_init_grid(dim=%d, nx=%d, ny=%d)" % (self.dim, self.nx, self.ny))
+        nbytes = ctypes.c_size_t()
+        self._check(self.lib.sgpe_workspace_bytes(self.ctx, ctypes.byref(nbytes)))
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        self.psi = torch.zeros((3, self.ny, self.nx), dtype=self.cdtype, device=self.device)
+        self._check(self.lib.sgpe_bind(self.ctx, self.psi.data_ptr(), self.workspace.data_ptr()))
+        self.physics = None
+
+    def _check(self, rc):
+        if rc != OK:
+            msg = self.lib.sgpe_last_error(self.ctx)
+            raise SgpeError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if self.ctx:
+            self.lib.sgpe_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- parameters and state ------------------------------------------------
+    def set_params(self, physics: Physics | None = None, **kw):
+        if physics is None:
+            physics = Physics(**kw)
+        self.physics = physics
+        p = physics.c()
+        self._check(self.lib.sgpe_set_params(self.ctx, ctypes.byref(p)))
+
+    def set_state(self, psi):
+        """Upload a host state ([3][ny][nx] complex) through sgpe_set_state."""
+        a = np.ascontiguousarray(np.asarray(psi).reshape(3, self.ny, self.nx).astype(self.npdtype))
+        self._check(self.lib.sgpe_set_state(self.ctx, a.ctypes.data))
+
+    def set_state_host_ptr(self, ptr: int):
+        self._check(self.lib.sgpe_set_state(self.ctx, ctypes.c_void_p(ptr)))
+
+    def load_state(self, psi_dev):
+        """Copy a device tensor (same shape and dtype as the state) into the state (sgpe_load_state)."""
+        assert psi_dev.is_cuda and psi_dev.dtype == self.cdtype and psi_dev.is_contiguous()
+        assert psi_dev.numel() == 3 * self.ny * self.nx
+        self._check(self.lib.sgpe_load_state(self.ctx, psi_dev.data_ptr()))
+
+    def get_state(self) -> np.ndarray:
+        out = np.empty((3, self.ny, self.nx), dtype=self.npdtype)
+        self._check(self.lib.sgpe_get_state(self.ctx, out.ctypes.data))
+        return out
+
+    def get_state_host_ptr(self, ptr: int):
+        self._check(self.lib.sgpe_get_state(self.ctx, ctypes.c_void_p(ptr)))
+
+    # -- the method ------------------------------------------------------------
+    def step_imag(self, nsteps: int):
+        self._check(self.lib.sgpe_step_imag(self.ctx, int(nsteps)))
+
+    def step_real(self, nsteps: int, omega_t=None):
+        """omega_t: None, or a float64 CUDA tensor with at least nsteps entries."""
+        ptr = None
+        if omega_t is not None:
+            assert omega_t.dtype == self.torch.float64 and omega_t.is_cuda and omega_t.numel() >= nsteps
+            self._omega_keep = omega_t
+            ptr = omega_t.data_ptr()
+        self._check(self.lib.sgpe_step_real(self.ctx, int(nsteps), ptr))
+
+    def substep(self, which: str, imag: bool, omega: float | None = None):
+        om = self.physics.omega if omega is None else omega
+        self._check(self.lib.sgpe_substep(self.ctx, SUBSTEP[which], int(bool(imag)), float(om)))
+
+    def normalize(self) -> np.ndarray:
+        out = np.zeros(3)
+        self._check(self.lib.sgpe_normalize(self.ctx, out.ctypes.data))
+        return out
+
+    def energy(self) -> dict:
+        out = np.zeros(NOBS)
+        self._check(self.lib.sgpe_energy(self.ctx, out.ctypes.data))
+        return dict(zip(OBS_NAMES, out.tolist()))
+
+    def energy_array(self) -> np.ndarray:
+        out = np.zeros(NOBS)
+        self._check(self.lib.sgpe_energy(self.ctx, out.ctypes.data))
+        return out
+
+    def profile_steps(self, nsteps: int, imag: bool = True):
+        """Per-kernel device time (ms, summed) and launch counts over nsteps eager steps."""
+        ms = np.zeros(3)
+        cnt = np.zeros(3, dtype=np.int32)
+        self._check(self.lib.sgpe_profile_steps(self.ctx, int(nsteps), int(bool(imag)), ms.ctypes.data,
+                                                cnt.ctypes.data))
+        return ms, cnt
+
+    def launches_per_step(self) -> int:
+        return int(self.lib.sgpe_launches_per_step(self.ctx))
+
+    def synchronize(self):
+        self.stream.synchronize()

@@ -1,0 +1,168 @@
+"""GPU (libsgpe, sm_103a) against the FP64 CPU oracle, element by element on the
+same seeded inputs, through the C ABI.
+
+Tolerances: complex128 state -- 1e-13 normwise relative for one substep,
+1e-10 for whole steps and observables (the FP64 parity bar); complex64 state --
+its measured error against the FP64 oracle is asserted below a stated bound."""
+import numpy as np
+import pytest
+
+from gpu_util import make_pair, obs_relerr, relerr
+from oracle import oracle as O
+from paper_2009_13507_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+SUBSTEPS = ["so", "calcnu", "herm", "cn_x", "cn_y", "renorm"]
+
+
+def _rand(prob, seed, env=6.0):
+    cell = prob.dx * (prob.dy if prob.dim == 2 else 1.0)
+    return I.random_state(prob.shape, seed, cell, envelope=env)
+
+
+PHYS_2D = dict(c0=50.0, c2=1.0, so_type=1, gamma=0.8, omega=0.5, dt=2e-4, renorm=1)
+PHYS_1D = dict(c0=10.0, c2=-0.5, so_type=1, gamma=0.5, omega=0.2, dt=1e-4, renorm=1)
+
+
+@pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("which", SUBSTEPS)
+@pytest.mark.parametrize("dim,nx,ny", [(2, 37, 29), (1, 101, 1)])
+def test_substep_parity_fp64(dim, nx, ny, which, imag):
+    if dim == 1 and which == "cn_y":
+        pytest.skip("no y sweep in 1D")
+    phys = dict(PHYS_2D if dim == 2 else PHYS_1D)
+    phys["dt"] = 0.01  # large enough that every substep changes the state visibly
+    prob, s = make_pair(dim, nx, ny, dx=0.2, **phys)
+    psi = _rand(prob, 100 + nx) * 3.0
+    s.set_state(psi)
+    s.substep(which, imag)
+    ref = O.substep(prob, psi, which, imag)
+    assert relerr(s.get_state(), ref) < 1e-13
+
+
+@pytest.mark.parametrize("so", [0, 1, 2, 3])
+@pytest.mark.parametrize("dim", [1, 2])
+def test_so_variants_parity(dim, so):
+    phys = dict(c0=5.0, c2=0.7, so_type=so, gamma=0.9, omega=0.3, dt=0.01, renorm=1)
+    prob, s = make_pair(dim, 45, 19 if dim == 2 else 1, dx=0.15, dy=0.2, **phys)
+    psi = _rand(prob, 7 + so)
+    for imag in (True, False):
+        s.set_state(psi)
+        s.substep("so", imag)
+        assert relerr(s.get_state(), O.substep(prob, psi, "so", imag)) < 1e-13
+
+
+@pytest.mark.parametrize("imag", [True, False])
+def test_full_step_parity_2d(imag):
+    prob, s = make_pair(2, 64, 48, dx=0.15, **PHYS_2D)
+    psi = I.gaussian_phase_2d(64, 48, 0.15, 0.15, seed=1)
+    s.set_state(psi)
+    n = 40
+    if imag:
+        s.step_imag(n)
+    else:
+        s.step_real(n)
+    ref = O.step(prob, psi, n, imag)
+    gpu = s.get_state()
+    assert relerr(gpu, ref) < 1e-10
+    assert obs_relerr(s.energy(), O.observables(prob, ref)) < 1e-10
+
+
+@pytest.mark.parametrize("imag", [True, False])
+def test_full_step_parity_1d_config(imag):
+    """The 1D imaginary-time workload: Nx = 256, dx = 0.05, c0 = 10, c2 = -0.5,
+    gamma p_x Sigma_x with gamma = 0.5, Omega = 0.2, dt = 1e-4, jittered Gaussian."""
+    prob, s = make_pair(1, 256, 1, dx=0.05, **PHYS_1D)
+    psi = I.gaussian_jitter_1d(256, 0.05, seed=0)
+    s.set_state(psi)
+    n = 300
+    (s.step_imag(n) if imag else s.step_real(n))
+    ref = O.step(prob, psi, n, imag)
+    assert relerr(s.get_state(), ref) < 1e-10
+    assert obs_relerr(s.energy(), O.observables(prob, ref)) < 1e-10
+
+
+def test_full_size_2d_config_parity():
+    """The 2D imaginary-time workload at its full size (256 x 256, dx = 0.05,
+    c0 = 50, c2 = 1, Rashba gamma = 0.8, Omega = 0.5, dt = 2e-4, random-phase
+    Gaussian), in the launch configuration the benchmark times (graph-replayed
+    32-step blocks plus a remainder), for 40 steps against the oracle."""
+    prob, s = make_pair(2, 256, 256, dx=0.05, **PHYS_2D)
+    psi = I.gaussian_phase_2d(256, 256, 0.05, 0.05, seed=0)
+    s.set_state(psi)
+    s.step_imag(40)
+    ref = O.step(prob, psi, 40, True)
+    assert relerr(s.get_state(), ref) < 1e-10
+    assert obs_relerr(s.energy(), O.observables(prob, ref)) < 1e-10
+
+
+def test_graph_replay_equals_single_steps():
+    prob, s = make_pair(2, 40, 33, dx=0.2, **PHYS_2D)
+    psi = _rand(prob, 77)
+    s.set_state(psi)
+    s.step_imag(70)  # two 32-step graph replays + 6 single steps
+    a = s.get_state()
+    s.set_state(psi)
+    for _ in range(70):
+        s.step_imag(1)
+    b = s.get_state()
+    assert np.array_equal(a, b)
+
+
+def test_real_time_omega_table():
+    import torch
+    phys = dict(PHYS_2D)
+    phys["renorm"] = 0
+    prob, s = make_pair(2, 48, 40, dx=0.15, **phys)
+    psi = I.gaussian_phase_2d(48, 40, 0.15, 0.15, seed=4)
+    om = 0.5 * np.cos(np.linspace(0, 3, 50)) + 0.1 * I.uniform(9, 50)
+    s.set_state(psi)
+    s.step_real(50, torch.tensor(om, dtype=torch.float64, device="cuda:0"))
+    ref = O.step(prob, psi, 50, False, omega_t=om)
+    assert relerr(s.get_state(), ref) < 1e-10
+
+
+@pytest.mark.parametrize("mag", [0.0, 0.3])
+def test_fixed_magnetisation_renorm(mag):
+    phys = dict(c0=30.0, c2=2.0, so_type=0, gamma=0.0, omega=0.0, dt=1e-3, renorm=2, mag=mag)
+    prob, s = make_pair(1, 200, 1, dx=0.08, **phys)
+    psi = I.gaussian_jitter_1d(200, 0.08, seed=2, amp=1e-2)
+    s.set_state(psi)
+    s.step_imag(200)
+    ref = O.step(prob, psi, 200, True)
+    assert relerr(s.get_state(), ref) < 1e-10
+    o = s.energy()
+    assert abs(o["N"] - 1) < 1e-12 and abs(o["mag"] - mag) < 1e-12
+
+
+@pytest.mark.parametrize("dim,nx,ny", [(2, 3, 3), (2, 5, 7), (2, 17, 3), (2, 33, 65), (1, 3, 1), (1, 33, 1),
+                                       (1, 1000, 1), (2, 4096, 3), (2, 3, 4096)])
+def test_edge_sizes(dim, nx, ny):
+    prob, s = make_pair(dim, nx, ny, dx=0.1, **(PHYS_2D if dim == 2 else PHYS_1D))
+    psi = _rand(prob, nx * 7 + ny, env=2.0)
+    s.set_state(psi)
+    s.step_imag(3)
+    s.step_real(2)
+    ref = O.step(prob, O.step(prob, psi, 3, True), 2, False)
+    assert relerr(s.get_state(), ref) < 1e-10
+
+
+def test_precision_form_error_is_small():
+    """complex64 state and sweeps, FP64 reductions: error against the FP64 oracle."""
+    prob, s = make_pair(2, 96, 80, dx=0.1, precision="c64", **PHYS_2D)
+    psi = I.gaussian_phase_2d(96, 80, 0.1, 0.1, seed=5)
+    s.set_state(psi)
+    s.step_imag(200)
+    ref = O.step(prob, psi, 200, True)
+    assert relerr(s.get_state(), ref) < 2e-5
+    oe = O.observables(prob, ref)
+    assert abs(s.energy()["E"] - oe["E"]) / abs(oe["E"]) < 1e-5
+
+
+def test_precision_form_max_line():
+    prob, s = make_pair(2, 8192, 3, dx=0.01, precision="c64", **PHYS_2D)
+    psi = _rand(prob, 3, env=2.0)
+    s.set_state(psi)
+    s.step_real(2)
+    assert relerr(s.get_state(), O.step(prob, psi, 2, False)) < 1e-5
