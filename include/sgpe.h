@@ -196,7 +196,8 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* ctx, int nsteps, int imag, double* ms_o
 /* Number of kernel launches one step enqueues (for launch accounting). */
 int sgpe_launches_per_step(const sgpe_ctx* ctx);
 
-/* Last error message of this context (never NULL; "" when there is none). */
+/* Last error message of this context (never NULL; "" when there is none). With
+ * ctx = NULL: the message of the last failed sgpe_init_grid on this host thread. */
 const char* sgpe_last_error(const sgpe_ctx* ctx);
 
 /* Release the context (not the caller's buffers). NULL is accepted. */

@@ -75,6 +75,9 @@ struct sgpe_ctx {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Message of the last failed sgpe_init_grid on this host thread (no context exists then).
+static thread_local char g_init_err[256] = "";
+
 static sgpe_status fail(sgpe_ctx* c, sgpe_status st, const char* fmt, ...) {
     if (c) {
         va_list ap;
@@ -166,6 +169,7 @@ sgpe_status sgpe_init_grid(sgpe_ctx** out, int dim, int nx, int ny, double dx, d
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = prec == SGPE_C128 ? Launcher<double>::setup() : Launcher<float>::setup();
     if (e != cudaSuccess) {
+        snprintf(g_init_err, sizeof(g_init_err), "sgpe_init_grid: %s", cudaGetErrorString(e));
         delete c;
         return SGPE_ECUDA;
     }
@@ -542,7 +546,7 @@ int sgpe_launches_per_step(const sgpe_ctx* c) {
     return c->dim == 2 ? 3 : 2;
 }
 
-const char* sgpe_last_error(const sgpe_ctx* c) { return c ? c->err : "null context"; }
+const char* sgpe_last_error(const sgpe_ctx* c) { return c ? c->err : g_init_err; }
 
 sgpe_status sgpe_destroy(sgpe_ctx* c) {
     if (!c) return SGPE_OK;

@@ -11,15 +11,25 @@ template <typename R> static Tabs<R> make_tabs(const void* const* t) {
     return Tabs<R>{(const T*)t[0], (const T*)t[1], (const T*)t[2], (const T*)t[3]};
 }
 
+// Allow a kernel the device's opt-in shared memory minus its static shared memory.
+template <typename K> static cudaError_t allow_smem(K kernel) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (!e) e = cudaFuncGetAttributes(&fa, kernel);
+    if (!e) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
 template <typename R> cudaError_t Launcher<R>::setup() {
-    const int lim = 227 * 1024;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_cn_x<R, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(k_cn_x<R, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(k_cn_x<R, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(k_cn_x<R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(k_cn_y<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(k_cn_y<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = allow_smem(k_cn_x<R, true, false>))) return e;
+    if ((e = allow_smem(k_cn_x<R, true, true>))) return e;
+    if ((e = allow_smem(k_cn_x<R, false, false>))) return e;
+    if ((e = allow_smem(k_cn_x<R, false, true>))) return e;
+    if ((e = allow_smem(k_cn_y<R, true>))) return e;
+    if ((e = allow_smem(k_cn_y<R, false>))) return e;
     return cudaSuccess;
 }
 

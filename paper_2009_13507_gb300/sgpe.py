@@ -123,7 +123,9 @@ class Solver:
                                          C128 if precision == "c128" else C64,
                                          ctypes.c_void_p(self.stream.cuda_stream))
         if rc != OK:
-            raise SgpeError(rc, "sgpe_init_grid(dim=%d, nx=%d, ny=%d)" % (self.dim, self.nx, self.ny))
+            msg = self.lib.sgpe_last_error(None)
+            raise SgpeError(rc, "sgpe_init_grid(dim=%d, nx=%d, ny=%d): %s"
+                            % (self.dim, self.nx, self.ny, msg.decode() if msg else ""))
         nbytes = ctypes.c_size_t()
         self._check(self.lib.sgpe_workspace_bytes(self.ctx, ctypes.byref(nbytes)))
         self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
