@@ -193,6 +193,33 @@ sgpe_status sgpe_substep(sgpe_ctx* ctx, int which, int imag, double omega);
  */
 sgpe_status sgpe_profile_steps(sgpe_ctx* ctx, int nsteps, int imag, double* ms_out, int* launches_out);
 
+/*
+ * sgpe_observables_noalloc -- the SGPE_NOBS observables of sgpe_energy for a
+ * state given by pointer, without a context and without any device memory from
+ * the caller beyond its input and output. The paper has no counterpart: this is
+ * a service for callers that cannot allocate device memory (a host framework
+ * that owns every allocation through its own pool, a plug-in that only sees the
+ * buffers it is handed, a latency-critical loop that must not allocate).
+ *  psi_dev  device state [3][ny][nx] complex of precision prec (16-byte aligned);
+ *           it is read as it is (no pending renormalisation scale exists here).
+ *  obs_dev  device output, SGPE_NOBS doubles (8-byte aligned), same indices as
+ *           sgpe_energy; written asynchronously on cuda_stream.
+ *  p        physics (c0, c2, so_type, gamma, omega, wx, wy used; dt ignored).
+ * Scratch: a static 1 MiB device array inside the library, present on every
+ * GPU that loads the library until the process exits. Grids needing more
+ * reduction blocks than it holds (ceil(nx/32)*ceil(ny/4) > 11912, roughly more
+ * than 1.5 million points) are rejected with SGPE_EUNSUPPORTED before anything
+ * is launched; sgpe_last_error(NULL) then says why. No call allocates or frees
+ * device memory. The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture. All calls share the one array, so calls whose work overlaps on the
+ * GPU (other streams, other host threads) race: order them on one stream.
+ * Returns SGPE_EINVAL for null or misaligned pointers or bad parameters,
+ * SGPE_ECUDA if a CUDA call fails. Asynchronous.
+ */
+sgpe_status sgpe_observables_noalloc(const void* psi_dev, int dim, int nx, int ny, double dx, double dy,
+                                     sgpe_precision prec, const sgpe_params* p, double* obs_dev, void* cuda_stream);
+
 /* Number of kernel launches one step enqueues (for launch accounting). */
 int sgpe_launches_per_step(const sgpe_ctx* ctx);
 

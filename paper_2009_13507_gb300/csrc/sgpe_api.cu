@@ -78,6 +78,10 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Message of the last failed sgpe_init_grid on this host thread (no context exists then).
 static thread_local char g_init_err[256] = "";
 
+namespace sgpe {
+void set_thread_error(const char* msg) { snprintf(g_init_err, sizeof(g_init_err), "%s", msg); }
+}  // namespace sgpe
+
 static sgpe_status fail(sgpe_ctx* c, sgpe_status st, const char* fmt, ...) {
     if (c) {
         va_list ap;

@@ -46,4 +46,7 @@ template <typename R> struct Launcher {
 
 cudaError_t reset_scale(cudaStream_t s, DevScalars* sc);
 
+// Store the message that sgpe_last_error(NULL) returns on this host thread.
+void set_thread_error(const char* msg);
+
 }  // namespace sgpe

@@ -28,8 +28,8 @@ SUBSTEP = {"so": 0, "calcnu": 1, "herm": 2, "cn_x": 3, "cn_y": 4, "renorm": 5}
 # Every symbol include/sgpe.h declares (checked by the CPU test suite).
 EXPORTS = ("sgpe_init_grid", "sgpe_workspace_bytes", "sgpe_bind", "sgpe_set_params", "sgpe_step_imag",
            "sgpe_step_real", "sgpe_normalize", "sgpe_energy", "sgpe_set_state", "sgpe_get_state", "sgpe_load_state",
-           "sgpe_substep", "sgpe_profile_steps", "sgpe_launches_per_step", "sgpe_last_error",
-           "sgpe_destroy")
+           "sgpe_substep", "sgpe_profile_steps", "sgpe_observables_noalloc", "sgpe_launches_per_step",
+           "sgpe_last_error", "sgpe_destroy")
 
 
 class SgpeError(RuntimeError):
@@ -70,6 +70,7 @@ def load():
         "sgpe_load_state": (I, [P, P]),
         "sgpe_substep": (I, [P, I, I, D]),
         "sgpe_profile_steps": (I, [P, I, I, P, P]),
+        "sgpe_observables_noalloc": (I, [P, I, I, I, D, D, I, ctypes.POINTER(Params), P, P]),
         "sgpe_launches_per_step": (I, [P]),
         "sgpe_last_error": (ctypes.c_char_p, [P]),
         "sgpe_destroy": (I, [P]),
