@@ -46,6 +46,9 @@ POINTWISE_FLOPS = 263
 # Nominal FP64 rate: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 1.259
 CPU_SAMPLE_STEPS = 300
+# DRAM bytes (read + write) of one k_pointwise<double> launch on this workload in an ncu capture
+# (cold L2): None whenever the kernel changed after the capture.
+POINTWISE_TRAFFIC_BYTES = 3191296
 
 
 def _dist():
@@ -278,7 +281,7 @@ def main():
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "alu", "kernel": "k_pointwise<double> (SO+CALCNU+HERM)",
                      "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": POINTWISE_TRAFFIC_BYTES,
                      "peak_source": "nominal FP64: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (measured 1.20 at 1995 MHz)",
                      "flops_per_point": POINTWISE_FLOPS, "avg_launch_ms": pw_ms},
         "kernels": {"avg_ms": kavg, "share": share, "dominant": dom},
