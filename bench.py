@@ -231,8 +231,8 @@ def main():
     reset(solver, psi0_dev)
     kms, kcnt = solver.profile_steps(NSTEPS, True)
     e_prof = solver.energy_array()
-    names = ["pointwise", "cn_x", "cn_y"]
-    kavg = {names[i]: kms[i] / max(int(kcnt[i]), 1) for i in range(3)}
+    names = ["pointwise", "cn_x", "cn_y", "finalize"]
+    kavg = {names[i]: kms[i] / max(int(kcnt[i]), 1) for i in range(4)}
     dom = max(names, key=lambda n: kavg[n])
     share = {n: kms[i] / kms.sum() for i, n in enumerate(names)}
     pw_ms = kavg["pointwise"]

@@ -187,8 +187,9 @@ sgpe_status sgpe_substep(sgpe_ctx* ctx, int which, int imag, double omega);
  * Measurement aid: run nsteps steps (imag = 1 imaginary, 0 real time, constant
  * Omega) with launches enqueued one by one and CUDA events recorded on the
  * context's stream around every kernel; writes the summed device time in ms of
- * each kernel kind to ms_out[0..2] (0 pointwise SO/CALCNU/HERM, 1 Crank-Nicolson
- * along x, 2 along y; unused kinds 0) and the launch counts to launches_out[0..2].
+ * each kernel kind to ms_out[0..3] (0 pointwise SO/CALCNU/HERM, 1 Crank-Nicolson
+ * along x, 2 along y, 3 end-of-step norm reduction and renormalisation scale;
+ * unused kinds 0) and the launch counts to launches_out[0..3].
  * Advances the state exactly like the step functions. Synchronises the stream.
  */
 sgpe_status sgpe_profile_steps(sgpe_ctx* ctx, int nsteps, int imag, double* ms_out, int* launches_out);

@@ -23,16 +23,20 @@ Geometry make_geometry(int dim, int nx, int ny, int esz) {
     g.nx = nx;
     g.ny = ny;
     g.esz = esz;
+    // x sweep: register kernel (4 lines per block) up to kRegMaxN points, else shared-memory kernel
+    g.reg_x = nx <= kRegMaxN;
     size_t per_warp_x = (size_t)(32 * chunk_stride(nx) + 32) * esz;
     g.wx = 4;
-    while (g.wx > 1 && g.wx * per_warp_x > 96 * 1024) g.wx >>= 1;
-    g.smem_x = g.wx * per_warp_x;
-    g.blocks_x = ceil_div(3 * ny, g.wx);
+    while (!g.reg_x && g.wx > 1 && g.wx * per_warp_x > 96 * 1024) g.wx >>= 1;
+    g.smem_x = g.reg_x ? 0 : g.wx * per_warp_x;
+    g.blocks_x = g.reg_x ? 3 * ny : ceil_div(3 * ny, g.wx);
+    // y sweep: register kernel (4 columns per block, 2 per warp), else shared-memory kernel
+    g.reg_y = ny <= kRegMaxN;
     size_t per_warp_y = (size_t)(32 * chunk_stride(ny) + 32) * esz;
     g.wy = 2;
-    while (g.wy > 1 && g.wy * per_warp_y > 160 * 1024) g.wy >>= 1;
-    g.smem_y = g.wy * per_warp_y;
-    g.blocks_y = dim == 2 ? 3 * ceil_div(nx, g.wy) : 0;
+    while (!g.reg_y && g.wy > 1 && g.wy * per_warp_y > 160 * 1024) g.wy >>= 1;
+    g.smem_y = g.reg_y ? 0 : g.wy * per_warp_y;
+    g.blocks_y = dim == 2 ? 3 * ceil_div(nx, g.reg_y ? cny_cols_per_warp(chunk_len(ny)) : g.wy) : 0;
     g.blocks_obs = ceil_div(nx, 32) * ceil_div(ny, 4);
     g.blocks_norm = kNormBlocks;
     return g;
@@ -118,7 +122,7 @@ static Layout layout_of(const sgpe_ctx* c) {
             int n = a == 0 ? c->nx : c->ny;
             for (int k = 0; k < 4; k++) {
                 L.tabs[m][a][k] = off;
-                off = align256(off + (size_t)n * c->esz);
+                off = align256(off + (size_t)table_len(n) * c->esz);
             }
         }
     L.partials = off;
@@ -248,6 +252,8 @@ sgpe_status sgpe_set_params(sgpe_ctx* c, const sgpe_params* p) {
     k.c2 = p->c2;
     k.wx2h = 0.5 * p->wx * p->wx;
     k.wy2h = c->dim == 2 ? 0.5 * p->wy * p->wy : 0.0;
+    k.vx = k.wx2h * c->dx * c->dx;
+    k.vy = k.wy2h * c->dy * c->dy;
     k.omega_t = p->omega / sqrt(2.0);
     k.cell = c->dim == 2 ? c->dx * c->dy : c->dx;
     k.renorm = p->renorm;
@@ -283,11 +289,15 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
         if ((e = Launcher<R>::cn_x(c->stream, imag, false, c->mid, c->mid, c->kp, c->tabs[mode][0], c->geo,
                                    c->partials, c->sc, renorm, 1)))
             return e;
-        return Launcher<R>::cn_y(c->stream, imag, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials, c->sc,
-                                 renorm, 1, 1);
+        if ((e = Launcher<R>::cn_y(c->stream, imag, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials,
+                                   c->sc, renorm, 1, 1)))
+            return e;
+        return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 1, c->sc);
     }
-    return Launcher<R>::cn_x(c->stream, imag, true, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo, c->partials,
-                             c->sc, renorm, 1);
+    if ((e = Launcher<R>::cn_x(c->stream, imag, true, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo, c->partials,
+                               c->sc, renorm, 1)))
+        return e;
+    return finalize_step(c->stream, c->partials, c->geo.blocks_x, c->kp.cell, renorm, c->kp.mag, 1, c->sc);
 }
 
 static cudaError_t enqueue_steps(sgpe_ctx* c, int n, bool imag, const double* omega_tab) {
@@ -496,49 +506,61 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
     const int mode = im ? 0 : 1;
     const int renorm = im ? c->params.renorm : 0;
     const bool dbl = c->prec == SGPE_C128;
-    cudaEvent_t ev[4];
-    for (int k = 0; k < 4; k++) CK(cudaEventCreate(&ev[k]), "cudaEventCreate");
-    double acc[3] = {0, 0, 0};
-    int cnt[3] = {0, 0, 0};
+    // kinds: 0 pointwise, 1 CN along x, 2 CN along y, 3 end-of-step norm / scale
+    // Steps are enqueued in batches of kBatch with their events and synchronised
+    // once per batch, so the intervals measure the GPU, not host submission.
+    const int kBatch = 64;
+    cudaEvent_t evs[kBatch][5];
+    for (int b = 0; b < kBatch; b++)
+        for (int k = 0; k < 5; k++) CK(cudaEventCreate(&evs[b][k]), "cudaEventCreate");
+    double acc[4] = {0, 0, 0, 0};
+    int cnt[4] = {0, 0, 0, 0};
+    const bool two = c->dim == 2;
     sgpe_status out = SGPE_OK;
-    for (int i = 0; i < nsteps && out == SGPE_OK; i++) {
-        cudaError_t e = cudaEventRecord(ev[0], c->stream);
+    for (int i0 = 0; i0 < nsteps && out == SGPE_OK; i0 += kBatch) {
+      const int nb = nsteps - i0 < kBatch ? nsteps - i0 : kBatch;
+      cudaError_t e = cudaSuccess;
+      for (int bi = 0; bi < nb && !e; bi++) {
+        cudaEvent_t* ev = evs[bi];
+        e = cudaEventRecord(ev[0], c->stream);
         if (!e) e = dbl ? Launcher<double>::pointwise(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, 7)
                         : Launcher<float>::pointwise(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, 7);
         if (!e) e = cudaEventRecord(ev[1], c->stream);
-        if (!e) {
-            if (c->dim == 2)
-                e = dbl ? Launcher<double>::cn_x(c->stream, im, false, c->mid, c->mid, c->kp, c->tabs[mode][0], c->geo,
-                                                 c->partials, c->sc, renorm, 1)
-                        : Launcher<float>::cn_x(c->stream, im, false, c->mid, c->mid, c->kp, c->tabs[mode][0], c->geo,
-                                                c->partials, c->sc, renorm, 1);
-            else
-                e = dbl ? Launcher<double>::cn_x(c->stream, im, true, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo,
-                                                 c->partials, c->sc, renorm, 1)
-                        : Launcher<float>::cn_x(c->stream, im, true, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo,
-                                                c->partials, c->sc, renorm, 1);
-        }
+        void* xout = two ? c->mid : c->psi;
+        if (!e)
+            e = dbl ? Launcher<double>::cn_x(c->stream, im, !two, c->mid, xout, c->kp, c->tabs[mode][0], c->geo,
+                                             c->partials, c->sc, renorm, 1)
+                    : Launcher<float>::cn_x(c->stream, im, !two, c->mid, xout, c->kp, c->tabs[mode][0], c->geo,
+                                            c->partials, c->sc, renorm, 1);
         if (!e) e = cudaEventRecord(ev[2], c->stream);
-        if (!e && c->dim == 2)
+        if (!e && two)
             e = dbl ? Launcher<double>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo,
                                              c->partials, c->sc, renorm, 1, 1)
                     : Launcher<float>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo,
                                             c->partials, c->sc, renorm, 1, 1);
         if (!e) e = cudaEventRecord(ev[3], c->stream);
-        if (!e) e = cudaEventSynchronize(ev[3]);
-        if (e) {
-            out = cuda_fail(c, e, "profile");
-            break;
-        }
-        for (int k = 0; k < (c->dim == 2 ? 3 : 2); k++) {
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
-            acc[k] += ms;
-            cnt[k] += 1;
-        }
+        if (!e)
+            e = finalize_step(c->stream, c->partials, two ? c->geo.blocks_y : c->geo.blocks_x, c->kp.cell, renorm,
+                              c->kp.mag, 1, c->sc);
+        if (!e) e = cudaEventRecord(ev[4], c->stream);
+      }
+      if (!e) e = cudaEventSynchronize(evs[nb - 1][4]);
+      if (e) {
+          out = cuda_fail(c, e, "profile");
+          break;
+      }
+      for (int bi = 0; bi < nb; bi++)
+          for (int k = 0; k < 4; k++) {
+              if (k == 2 && !two) continue;
+              float ms = 0.f;
+              cudaEventElapsedTime(&ms, evs[bi][k], evs[bi][k + 1]);
+              acc[k] += ms;
+              cnt[k] += 1;
+          }
     }
-    for (int k = 0; k < 4; k++) cudaEventDestroy(ev[k]);
-    for (int k = 0; k < 3; k++) {
+    for (int b = 0; b < kBatch; b++)
+        for (int k = 0; k < 5; k++) cudaEventDestroy(evs[b][k]);
+    for (int k = 0; k < 4; k++) {
         ms_out[k] = acc[k];
         launches_out[k] = cnt[k];
     }
@@ -547,7 +569,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
 
 int sgpe_launches_per_step(const sgpe_ctx* c) {
     if (!c) return 0;
-    return c->dim == 2 ? 3 : 2;
+    return c->dim == 2 ? 4 : 3;
 }
 
 const char* sgpe_last_error(const sgpe_ctx* c) { return c ? c->err : g_init_err; }

@@ -1,0 +1,170 @@
+// sgpe_cn.cuh -- Crank-Nicolson sweeps (Sec. 3, LU / LUX / LUY) with each
+// lane's chunk of a line held in registers; compile-time chunk length C.
+//
+// A line of n points is split into 32 chunks of C = next_pow2(ceil(n/32))
+// points (n <= 1024); lane l owns points [lC, lC + C). The coefficient tables
+// are padded to 32*C entries with zeros beyond n, and points beyond n load as
+// zero, so a ragged line needs no special case: the recurrences stay at zero
+// past the end and the chunk products there vanish.
+//
+// One warp per block: the FP64 sweeps are bound by the FP64 pipe of each SM,
+// so the work is cut into as many equal blocks as there are lines (x) or
+// column pairs (y) for an even spread over the 152 SMs.
+#pragma once
+#include "sgpe_kernels.cuh"
+
+namespace sgpe {
+
+// Solve T w = x for the lane's chunk v (in: x, out: w), all 32 lanes together.
+template <typename R, bool IMAG, int C>
+__device__ __forceinline__ void solve_chunk(cx<R> (&v)[C], const Tabs<R>& t, int i0) {
+    const int lane = threadIdx.x & 31;
+    cx<R> y = {R(0), R(0)};
+#pragma unroll
+    for (int m = 0; m < C; m++) {
+        y = tfma<IMAG>(tld<R>(t.fg, i0 + m), y, tmul<IMAG>(tld<R>(t.fa, i0 + m), v[m]));
+        v[m] = y;
+    }
+    cx<R> A = tld<R>(t.fp, i0 + C - 1), B = y;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        cx<R> Ap = shup(A, off), Bp = shup(B, off);
+        if (lane >= off) {
+            B = tfma<IMAG>(A, Bp, B);
+            A = tmul<IMAG>(A, Ap);
+        }
+    }
+    cx<R> cin = shup(B, 1);
+    if (lane == 0) cin = {R(0), R(0)};
+    cx<R> w = {R(0), R(0)};
+#pragma unroll
+    for (int m = C - 1; m >= 0; m--) {
+        cx<R> yi = tfma<IMAG>(tld<R>(t.fp, i0 + m), cin, v[m]);
+        w = tfma<IMAG>(tld<R>(t.fg, i0 + m), w, yi);
+        v[m] = w;
+    }
+    A = tld<R>(t.fq, i0);
+    B = w;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        cx<R> An = shdn(A, off), Bn = shdn(B, off);
+        if (lane + off < 32) {
+            B = tfma<IMAG>(A, Bn, B);
+            A = tmul<IMAG>(A, An);
+        }
+    }
+    cx<R> cb = shdn(B, 1);
+    if (lane == 31) cb = {R(0), R(0)};
+#pragma unroll
+    for (int m = 0; m < C; m++) v[m] = tfma<IMAG>(tld<R>(t.fq, i0 + m), cb, v[m]);
+}
+
+// Columns per warp of the y sweep and whether a lane keeps its input chunk in
+// registers (small chunks) or reloads it for the final 2w - x (large chunks).
+template <int C> struct CnShape {
+    static constexpr int K = C <= 8 ? 2 : 1;
+    static constexpr bool KEEP = C <= 8;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// CN along x: block = one warp = one line (line = j*ny + iy). With partials
+// non-null the block writes the FP64 norm of its output line to
+// partials[3*line + j] (zeros for the other components).
+// ---------------------------------------------------------------------------
+template <typename R, bool IMAG, int C>
+__global__ void __launch_bounds__(32) k_cnx_reg(const typename V2<R>::T* in, typename V2<R>::T* out, KParams p,
+                                                Tabs<R> t, double* partials) {
+    constexpr bool KEEP = CnShape<C>::KEEP;
+    const int lane = threadIdx.x;
+    const int line = blockIdx.x;
+    const int n = p.nx;
+    const int i0 = lane * C;
+    const cx<R> zero = {R(0), R(0)};
+    const size_t base = (size_t)line * n;
+    cx<R> x[KEEP ? C : 1], v[C];
+#pragma unroll
+    for (int m = 0; m < C; m++) {
+        v[m] = (i0 + m < n) ? ldc<R>(in, base + i0 + m) : zero;
+        if (KEEP) x[m] = v[m];
+    }
+    solve_chunk<R, IMAG, C>(v, t, i0);
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m < C; m++) {
+        if (i0 + m < n) {
+            cx<R> xm = KEEP ? x[m] : ldc<R>(in, base + i0 + m);
+            cx<R> o = {fma(R(2), v[m].re, -xm.re), fma(R(2), v[m].im, -xm.im)};
+            st<R>(out, base + i0 + m, o);
+            acc += (double)o.re * (double)o.re + (double)o.im * (double)o.im;
+        }
+    }
+    if (partials) {
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            const int j = line / p.ny;
+            for (int q = 0; q < 3; q++) partials[3 * line + q] = (q == j) ? acc : 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CN along y: block = one warp solving K adjacent columns of one component
+// (K = 2 for small chunks: a lane's chunk rows then load 32 contiguous bytes
+// per row in FP64). Norm partials as for the x sweep, one slot per block.
+// ---------------------------------------------------------------------------
+template <typename R, bool IMAG, int C>
+__global__ void __launch_bounds__(32) k_cny_reg(const typename V2<R>::T* in, typename V2<R>::T* out, KParams p,
+                                                Tabs<R> t, double* partials) {
+    constexpr int K = CnShape<C>::K;
+    constexpr bool KEEP = CnShape<C>::KEEP;
+    const int lane = threadIdx.x;
+    const int ncb = (p.nx + K - 1) / K;
+    const int j = blockIdx.x / ncb;
+    const int col = (blockIdx.x - j * ncb) * K;
+    const int n = p.ny;
+    const int i0 = lane * C;
+    const size_t base = (size_t)j * p.nx * p.ny;
+    const cx<R> zero = {R(0), R(0)};
+    cx<R> x[K][KEEP ? C : 1], v[K][C];
+#pragma unroll
+    for (int m = 0; m < C; m++) {
+        const bool ok = i0 + m < n;
+        size_t g = base + (size_t)(i0 + m) * p.nx + col;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            v[k][m] = (ok && col + k < p.nx) ? ldc<R>(in, g + k) : zero;
+            if (KEEP) x[k][m] = v[k][m];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) solve_chunk<R, IMAG, C>(v[k], t, i0);
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m < C; m++) {
+        if (i0 + m < n) {
+            size_t g = base + (size_t)(i0 + m) * p.nx + col;
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                if (col + k < p.nx) {
+                    cx<R> xm = KEEP ? x[k][m] : ldc<R>(in, g + k);
+                    cx<R> o = {fma(R(2), v[k][m].re, -xm.re), fma(R(2), v[k][m].im, -xm.im)};
+                    st<R>(out, g + k, o);
+                    acc += (double)o.re * (double)o.re + (double)o.im * (double)o.im;
+                }
+            }
+        }
+    }
+    if (partials) {
+        acc = warp_sum(acc);
+        if (lane == 0)
+            for (int q = 0; q < 3; q++) partials[3 * blockIdx.x + q] = (q == j) ? acc : 0.0;
+    }
+}
+
+}  // namespace sgpe

@@ -57,21 +57,25 @@ template <typename R> __device__ __forceinline__ void st(typename V2<R>::T* p, s
 // ---------------------------------------------------------------------------
 // exp(x) and (cos x, sin x) for the phase factors.
 //
-// FP64: GB300 executes FP64 at 1/64 of its FP32 rate, so the library
-// exponential / sincos (range reduction plus a long polynomial) dominate the
-// pointwise substeps. Every argument here is dt times an energy, normally well
-// below 1/32 in magnitude, where a truncated Taylor series evaluated by Horner's
-// rule is accurate to a fraction of an ulp:
-//   exp(x) = sum_{n<=9} x^n/n!       (|x| <= 1/32: first omitted term < 3e-20)
-//   sin(x) = x sum_{n<=4} (-x^2)^n/(2n+1)!,  cos(x) = sum_{n<=5} (-x^2)^n/(2n)!
-// Larger arguments take CUDA's exp / sincos.
+// FP64: GB300 executes FP64 at about 1/60 of its FP32 rate, so the library
+// exponential / sincos (range reduction plus a long polynomial) would dominate
+// the pointwise substeps. Every argument here is dt times an energy, normally
+// below 1/64 in magnitude, where a truncated Taylor series evaluated by
+// Horner's rule is accurate to well under an ulp:
+//   exp(x) = sum_{n<=7} x^n/n!        (|x| <= 2^-6: first omitted term < 9e-20)
+//   sin(x) = x sum_{n<=3} (-x^2)^n/(2n+1)!   (omitted < 1e-20)
+//   cos(x) = sum_{n<=4} (-x^2)^n/(2n)!       (omitted < 3e-25)
+// Larger arguments take CUDA's exp / sincos. The range test reads the high
+// word of the double on the integer pipe: |x| < 2^-6 iff (hi & 0x7fffffff) < 0x3F900000.
 // FP32: CUDA's expf / sincosf (full-range, FP32 pipe).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ bool small_arg(double x) {
+    return (unsigned)(__double2hiint(x) & 0x7fffffff) < 0x3F900000u;  // |x| < 2^-6
+}
+
 __device__ __forceinline__ double exp_small(double x) {
-    if (fabs(x) <= 0.03125) {
-        double p = 1.0 / 362880.0;
-        p = fma(p, x, 1.0 / 40320.0);
-        p = fma(p, x, 1.0 / 5040.0);
+    if (small_arg(x)) {
+        double p = 1.0 / 5040.0;
         p = fma(p, x, 1.0 / 720.0);
         p = fma(p, x, 1.0 / 120.0);
         p = fma(p, x, 1.0 / 24.0);
@@ -85,16 +89,14 @@ __device__ __forceinline__ double exp_small(double x) {
 __device__ __forceinline__ float exp_small(float x) { return expf(x); }
 
 __device__ __forceinline__ void sincos_small(double x, double* s, double* c) {
-    if (fabs(x) <= 0.03125) {
+    if (small_arg(x)) {
         double t = x * x;
-        double ps = 1.0 / 362880.0;  // sin(x)/x = 1 - t/6 + t^2/120 - t^3/5040 + t^4/362880
-        ps = fma(ps, -t, 1.0 / 5040.0);
+        double ps = 1.0 / 5040.0;  // sin(x)/x = 1 - t/6 + t^2/120 - t^3/5040
         ps = fma(ps, -t, 1.0 / 120.0);
         ps = fma(ps, -t, 1.0 / 6.0);
         ps = fma(ps, -t, 1.0);
         *s = ps * x;
-        double pc = 1.0 / 3628800.0;  // cos: 1 - t/2 + t^2/24 - t^3/720 + t^4/40320 - t^5/3628800
-        pc = fma(pc, -t, 1.0 / 40320.0);
+        double pc = 1.0 / 40320.0;  // cos(x) = 1 - t/2 + t^2/24 - t^3/720 + t^4/40320
         pc = fma(pc, -t, 1.0 / 720.0);
         pc = fma(pc, -t, 1.0 / 24.0);
         pc = fma(pc, -t, 0.5);
@@ -116,7 +118,16 @@ __device__ __forceinline__ void sincos_small(float x, float* s, float* c) { sinc
 // cos - 1 = -2 sin^2(x/2) to avoid cancellation.
 template <bool IMAG>
 __device__ __forceinline__ void herm_coeffs(double C2, double dt, double* s, double* k) {
-    double w = dt * dt * C2;
+    double w = dt * dt * C2;  // >= 0
+    if ((unsigned)__double2hiint(w) < 0x3EB00000u) {
+        // w < 2^-20: three terms each (first omitted terms < 2e-22 relative)
+        double v = IMAG ? w : -w;
+        double ps = fma(fma(v, 1.0 / 120.0, 1.0 / 6.0), v, 1.0);
+        double pk = fma(fma(v, 1.0 / 720.0, 1.0 / 24.0), v, 0.5);
+        *s = dt * ps;
+        *k = (IMAG ? dt * dt : -dt * dt) * pk;
+        return;
+    }
     if (w <= 1.0 / 1024.0) {
         double v = IMAG ? w : -w;
         double ps = 1.0 / 362880.0;  // 1/9!
@@ -188,6 +199,7 @@ struct KParams {
     double sx, sy;    // the same without the factor dt (for the SO energy)
     double c0, c2;
     double wx2h, wy2h;  // wx^2/2, wy^2/2
+    double vx, vy;      // wx^2 dx^2/2, wy^2 dy^2/2 (trap per squared grid index)
     double omega_t;   // Omega/sqrt2 (constant Rabi term)
     double cell;      // dx (1D) or dx*dy
     int renorm;       // 0, 1 (DJ2), 2 (DJ)

@@ -4,6 +4,12 @@
 namespace sgpe {
 template struct Launcher<double>;
 
+cudaError_t finalize_step(cudaStream_t s, const double* partials, int nblk, double cell, int renorm, double mag,
+                          int advance, DevScalars* sc) {
+    k_finalize<<<1, 256, 0, s>>>(partials, nblk, cell, renorm, mag, advance, sc);
+    return cudaGetLastError();
+}
+
 cudaError_t reset_scale(cudaStream_t s, DevScalars* sc) {
     k_reset_scale<<<1, 32, 0, s>>>(sc);
     return cudaGetLastError();

@@ -260,9 +260,9 @@ __global__ void __launch_bounds__(128) k_pointwise(const typename V2<R>::T* __re
         so_point<IMAG>(u, X, Y, gx, gy, p.so_case);
     }
     if (mask & 2) {
-        R x = (R)((ix - p.nx / 2) * p.dx);
-        R y = (R)((iy - p.ny / 2) * p.dy);
-        R V = (R)p.wx2h * x * x + (p.dim == 2 ? (R)p.wy2h * y * y : R(0));
+        // V = wx^2 x^2/2 + wy^2 y^2/2 with x = kx dx: kx^2 is an exact integer
+        const int kx = ix - p.nx / 2, ky = iy - p.ny / 2;
+        R V = (R)p.vx * (R)(kx * kx) + (p.dim == 2 ? (R)p.vy * (R)(ky * ky) : R(0));
         calcnu_point<IMAG>(u, V, (R)p.c0, (R)p.c2, dt);
     }
     if (mask & 4) {
@@ -310,8 +310,6 @@ __global__ void __launch_bounds__(256) k_cn_x(const typename V2<R>::T* in, typen
         block_reduce<3>(v, red);
         if (threadIdx.x == 0)
             for (int j = 0; j < 3; j++) partials[3 * blockIdx.x + j] = v[j];
-        if (last_block(&sc->ticket[0]))
-            finalize_norms(partials, gridDim.x, p.cell, renorm, p.mag, advance_step != 0, sc, &sc->ticket[0]);
     }
 }
 
@@ -365,8 +363,36 @@ __global__ void __launch_bounds__(256) k_cn_y(const typename V2<R>::T* in, typen
         if (threadIdx.x == 0) {
             for (int q = 0; q < 3; q++) partials[3 * blockIdx.x + q] = (q == j) ? v[0] : 0.0;
         }
-        if (last_block(&sc->ticket[0]))
-            finalize_norms(partials, gridDim.x, p.cell, renorm, p.mag, advance_step != 0, sc, &sc->ticket[0]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// End of a step: one block sums the per-block partial norms of the step's last
+// sweep (partials[3b + j], fixed order), publishes N_j, the next pending scale
+// (Eq. (DJ2) / (DJ) for renorm != 0, else 1) and advances the step counter.
+// ---------------------------------------------------------------------------
+static __global__ void __launch_bounds__(256) k_finalize(const double* partials, int nblk, double cell, int renorm,
+                                                  double mag, int advance_step, DevScalars* sc) {
+    __shared__ double red[8 * 3];
+    double s[3] = {0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        s[0] += __ldcg(partials + 3 * b + 0);
+        s[1] += __ldcg(partials + 3 * b + 1);
+        s[2] += __ldcg(partials + 3 * b + 2);
+    }
+    block_reduce<3>(s, red);
+    if (threadIdx.x == 0) {
+        double N[3] = {s[0] * cell, s[1] * cell, s[2] * cell};
+        bool finite = isfinite(N[0]) && isfinite(N[1]) && isfinite(N[2]);
+        double d[3];
+        renorm_factors(N, finite ? renorm : 0, mag, d);
+        for (int j = 0; j < 3; j++) {
+            sc->norms[j] = N[j];
+            sc->scale[j] = d[j];
+        }
+        if (!finite) sc->err |= 1;
+        if (advance_step) sc->step_idx += 1;
     }
 }
 
@@ -388,11 +414,18 @@ __device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi,
     }
 }
 
+// Tables have 32*C entries; entries past n are zero (fa = fg = 0, hence the
+// chunk products vanish there too).
 template <typename R>
 __global__ void k_coef(typename V2<R>::T* fa, typename V2<R>::T* fg, typename V2<R>::T* fp,
                        typename V2<R>::T* fq, int n, int C, double bre, double bim) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double dr = 1.0 + 2.0 * bre, di = 2.0 * bim;  // diagonal 1 + 2 bt
+    const int len = 32 * C;
+    for (int i = n; i < len; i++) {
+        fa[i].x = fa[i].y = (R)0;
+        fg[i].x = fg[i].y = (R)0;
+    }
     double ur = dr, ui = di;
     for (int i = 0; i < n; i++) {
         if (i > 0) {
@@ -412,8 +445,8 @@ __global__ void k_coef(typename V2<R>::T* fa, typename V2<R>::T* fg, typename V2
         fg[i].y = (R)gi;
     }
     // chunk products, computed from the rounded-to-FP64 fg values
-    for (int k0 = 0; k0 < n; k0 += C) {
-        int k1 = min(n, k0 + C);
+    for (int k0 = 0; k0 < len; k0 += C) {
+        int k1 = k0 + C;
         double Pr = 1.0, Pi = 0.0;
         for (int i = k0; i < k1; i++) {
             double gr = (double)fg[i].x, gi = (double)fg[i].y;

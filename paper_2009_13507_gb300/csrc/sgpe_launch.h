@@ -11,15 +11,30 @@ struct DevScalars;
 
 // Launch geometry shared by the API layer (buffer sizing) and the launchers.
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
-inline int chunk_len(int n) { return ceil_div(n, 32); }
+// Chunk length of a line of n points split over the 32 lanes of a warp: the
+// next power of two of ceil(n/32) for n <= 1024 (register kernels, compile-time
+// chunk), ceil(n/32) above (shared-memory kernels).
+constexpr int kRegMaxN = 1024;
+inline int chunk_len(int n) {
+    int c = ceil_div(n, 32);
+    if (n > kRegMaxN) return c;
+    int p = 1;
+    while (p < c) p <<= 1;
+    return p;
+}
 inline int chunk_stride(int n) { return chunk_len(n) | 1; }
+// Entries of each coefficient table of an n-point axis (padded with zeros past n).
+inline int table_len(int n) { return 32 * chunk_len(n); }
+// Columns per warp of the register y sweep (must match CnShape<C>::K).
+inline int cny_cols_per_warp(int C) { return C <= 8 ? 2 : 1; }
 constexpr int kObsAcc = 11;
 constexpr int kNormBlocks = 304;
 
 struct Geometry {
     int dim, nx, ny, esz;
     int wx;  // warps (lines) per block of the x sweep
-    int wy;  // warps (columns) per block of the y sweep
+    int wy;  // warps (columns) per block of the y sweep (shared-memory kernel)
+    bool reg_x, reg_y;  // register-chunk kernels (lines of at most kRegMaxN points)
     size_t smem_x, smem_y;
     int blocks_x, blocks_y, blocks_obs, blocks_norm;
 };
@@ -30,6 +45,8 @@ template <typename R> struct Launcher {
     static cudaError_t setup();
     static cudaError_t pointwise(cudaStream_t s, bool imag, const void* A, void* B, const KParams& p,
                                  const DevScalars* sc, const double* omega_tab, int mask);
+    // cn_x / cn_y write per-block FP64 norm partials when last / finalize is set
+    // (the step's final sweep); finalize_step then reduces them.
     static cudaError_t cn_x(cudaStream_t s, bool imag, bool last, const void* in, void* out, const KParams& p,
                             const void* const* tabs, const Geometry& g, double* partials, DevScalars* sc, int renorm,
                             int advance);
@@ -45,6 +62,11 @@ template <typename R> struct Launcher {
 };
 
 cudaError_t reset_scale(cudaStream_t s, DevScalars* sc);
+
+// End of a step: reduce the last sweep's nblk norm partials, publish N_j and the
+// next pending scale, advance the step counter (one block).
+cudaError_t finalize_step(cudaStream_t s, const double* partials, int nblk, double cell, int renorm, double mag,
+                          int advance, DevScalars* sc);
 
 // Store the message that sgpe_last_error(NULL) returns on this host thread.
 void set_thread_error(const char* msg);

@@ -1,6 +1,7 @@
 // sgpe_launch_impl.cuh -- launchers of the step / observable kernels for one
 // storage precision; included once per precision translation unit.
 #pragma once
+#include "sgpe_cn.cuh"
 #include "sgpe_kernels.cuh"
 #include "sgpe_launch.h"
 
@@ -9,6 +10,50 @@ namespace sgpe {
 template <typename R> static Tabs<R> make_tabs(const void* const* t) {
     using T = typename V2<R>::T;
     return Tabs<R>{(const T*)t[0], (const T*)t[1], (const T*)t[2], (const T*)t[3]};
+}
+
+template <typename R, int C>
+static void cnx_reg_c(bool imag, dim3 grid, cudaStream_t s, const typename V2<R>::T* in, typename V2<R>::T* out,
+                      const KParams& p, const Tabs<R>& t, double* partials) {
+    if (imag)
+        k_cnx_reg<R, true, C><<<grid, 32, 0, s>>>(in, out, p, t, partials);
+    else
+        k_cnx_reg<R, false, C><<<grid, 32, 0, s>>>(in, out, p, t, partials);
+}
+
+template <typename R>
+static void launch_cnx_reg(int C, bool imag, dim3 grid, cudaStream_t s, const typename V2<R>::T* in,
+                           typename V2<R>::T* out, const KParams& p, const Tabs<R>& t, double* partials) {
+    switch (C) {
+        case 1: cnx_reg_c<R, 1>(imag, grid, s, in, out, p, t, partials); break;
+        case 2: cnx_reg_c<R, 2>(imag, grid, s, in, out, p, t, partials); break;
+        case 4: cnx_reg_c<R, 4>(imag, grid, s, in, out, p, t, partials); break;
+        case 8: cnx_reg_c<R, 8>(imag, grid, s, in, out, p, t, partials); break;
+        case 16: cnx_reg_c<R, 16>(imag, grid, s, in, out, p, t, partials); break;
+        default: cnx_reg_c<R, 32>(imag, grid, s, in, out, p, t, partials); break;
+    }
+}
+
+template <typename R, int C>
+static void cny_reg_c(bool imag, dim3 grid, cudaStream_t s, const typename V2<R>::T* in, typename V2<R>::T* out,
+                      const KParams& p, const Tabs<R>& t, double* partials) {
+    if (imag)
+        k_cny_reg<R, true, C><<<grid, 32, 0, s>>>(in, out, p, t, partials);
+    else
+        k_cny_reg<R, false, C><<<grid, 32, 0, s>>>(in, out, p, t, partials);
+}
+
+template <typename R>
+static void launch_cny_reg(int C, bool imag, dim3 grid, cudaStream_t s, const typename V2<R>::T* in,
+                           typename V2<R>::T* out, const KParams& p, const Tabs<R>& t, double* partials) {
+    switch (C) {
+        case 1: cny_reg_c<R, 1>(imag, grid, s, in, out, p, t, partials); break;
+        case 2: cny_reg_c<R, 2>(imag, grid, s, in, out, p, t, partials); break;
+        case 4: cny_reg_c<R, 4>(imag, grid, s, in, out, p, t, partials); break;
+        case 8: cny_reg_c<R, 8>(imag, grid, s, in, out, p, t, partials); break;
+        case 16: cny_reg_c<R, 16>(imag, grid, s, in, out, p, t, partials); break;
+        default: cny_reg_c<R, 32>(imag, grid, s, in, out, p, t, partials); break;
+    }
 }
 
 // Allow a kernel the device's opt-in shared memory minus its static shared memory.
@@ -53,6 +98,10 @@ cudaError_t Launcher<R>::cn_x(cudaStream_t s, bool imag, bool last, const void* 
     using T = typename V2<R>::T;
     Tabs<R> t = make_tabs<R>(tabs);
     const int C = chunk_len(p.nx), S = chunk_stride(p.nx);
+    if (g.reg_x) {
+        launch_cnx_reg<R>(C, imag, dim3(g.blocks_x), s, (const T*)in, (T*)out, p, t, last ? partials : nullptr);
+        return cudaGetLastError();
+    }
     dim3 block(32 * g.wx), grid(g.blocks_x);
     if (imag) {
         if (last)
@@ -79,6 +128,10 @@ cudaError_t Launcher<R>::cn_y(cudaStream_t s, bool imag, const void* in, void* o
     using T = typename V2<R>::T;
     Tabs<R> t = make_tabs<R>(tabs);
     const int C = chunk_len(p.ny), S = chunk_stride(p.ny);
+    if (g.reg_y) {
+        launch_cny_reg<R>(C, imag, dim3(g.blocks_y), s, (const T*)in, (T*)out, p, t, finalize ? partials : nullptr);
+        return cudaGetLastError();
+    }
     dim3 block(32 * g.wy), grid(g.blocks_y);
     if (imag)
         k_cn_y<R, true><<<grid, block, g.smem_y, s>>>((const T*)in, (T*)out, p, t, C, S, partials, sc, renorm, advance,

@@ -214,8 +214,8 @@ class Solver:
 
     def profile_steps(self, nsteps: int, imag: bool = True):
         """Per-kernel device time (ms, summed) and launch counts over nsteps eager steps."""
-        ms = np.zeros(3)
-        cnt = np.zeros(3, dtype=np.int32)
+        ms = np.zeros(4)
+        cnt = np.zeros(4, dtype=np.int32)
         self._check(self.lib.sgpe_profile_steps(self.ctx, int(nsteps), int(bool(imag)), ms.ctypes.data,
                                                 cnt.ctypes.data))
         return ms, cnt
