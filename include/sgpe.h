@@ -221,6 +221,69 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* ctx, int nsteps, int imag, double* ms_o
 sgpe_status sgpe_observables_noalloc(const void* psi_dev, int dim, int nx, int ny, double dx, double dy,
                                      sgpe_precision prec, const sgpe_params* p, double* obs_dev, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batched form: many independent grids advanced together by the split step of
+ * Sec. 3 (same substeps and readings as a single grid), each with its own size
+ * and physical parameters, in grouped launches (one per kernel kind and chunk
+ * length, covering every instance) replayed from CUDA graphs.
+ * ------------------------------------------------------------------------ */
+typedef struct sgpe_batch sgpe_batch; /* opaque, library-owned host object */
+
+/* One instance: dim 1 or 2, nx (and ny in 2D) in [3, 1024], dx (dy) > 0, params. */
+typedef struct {
+    int dim, nx, ny;
+    double dx, dy;
+    sgpe_params params;
+} sgpe_instance;
+
+/*
+ * Create a batch of n instances (copied). All states share one precision.
+ * Errors: SGPE_EINVAL (bad grid or parameters; sgpe_last_error(NULL) names the
+ * instance), SGPE_EUNSUPPORTED (a line longer than 1024 points), SGPE_ENOMEM.
+ */
+sgpe_status sgpe_batch_create(sgpe_batch** out, int n, const sgpe_instance* inst, sgpe_precision prec,
+                              void* cuda_stream);
+
+/* Total complex elements of the batch state and bytes of its workspace. */
+sgpe_status sgpe_batch_sizes(const sgpe_batch* b, size_t* state_elems, size_t* workspace_bytes);
+
+/* Element offset of each instance's [3][ny][nx] state in the batch state (n entries). */
+sgpe_status sgpe_batch_offsets(const sgpe_batch* b, size_t* offsets);
+
+/*
+ * Bind the caller-owned batch state (state_elems complex elements, 16-byte
+ * aligned) and workspace (256-byte aligned); uploads the work lists and builds
+ * every instance's Crank-Nicolson tables. Synchronises the stream.
+ */
+sgpe_status sgpe_batch_bind(sgpe_batch* b, void* psi_dev, void* workspace_dev);
+
+/* Copy a device batch state (same layout) into the bound state; resets the pending scales. Async. */
+sgpe_status sgpe_batch_load_state(sgpe_batch* b, const void* psi_dev);
+
+/* nsteps imaginary-time (with each instance's renorm) or real-time steps of every instance. Async. */
+sgpe_status sgpe_batch_step_imag(sgpe_batch* b, int nsteps);
+sgpe_status sgpe_batch_step_real(sgpe_batch* b, int nsteps);
+
+/*
+ * Apply the pending scales, then write each instance's SGPE_NOBS observables
+ * to out[i * SGPE_NOBS ...] (host, n * SGPE_NOBS doubles). Synchronises.
+ * SGPE_ENONFINITE if an instance's norm is not finite.
+ */
+sgpe_status sgpe_batch_energy(sgpe_batch* b, double* out);
+
+/*
+ * Choose the warps per block of the two sweeps (1, 2 or 4 each) by timing
+ * nsteps imaginary-time steps per candidate with CUDA events; writes the
+ * choice to choice[0..1] (nullable). Advances the bound state by 9 * (nsteps + 1)
+ * steps: tune before loading the state to be advanced. Synchronises.
+ */
+sgpe_status sgpe_batch_autotune(sgpe_batch* b, int nsteps, int* choice);
+
+/* Kernel launches per batched step; last error of a batch; release (not the buffers). */
+int sgpe_batch_launches_per_step(const sgpe_batch* b);
+const char* sgpe_batch_last_error(const sgpe_batch* b);
+sgpe_status sgpe_batch_destroy(sgpe_batch* b);
+
 /* Number of kernel launches one step enqueues (for launch accounting). */
 int sgpe_launches_per_step(const sgpe_ctx* ctx);
 

@@ -260,16 +260,20 @@ void orc_norms(const orc_params* p, const cplx* psi, double N[3]) {
  * d_j = 1/sqrt(N_0 + N_+ + N_-), or with Eq. (DJ) for fixed magnetisation m:
  *   d_0 = sqrt(1-m^2) / sqrt(N_0 + sqrt(4(1-m^2) N_+ N_- + m^2 N_0^2)),
  *   d_{+-} = sqrt(1 +- m - d_0^2 N_0) / sqrt(2 N_{+-}).
- * A component with N_j = 0 is left as it is (d_j has no value there).
+ * A component with N_j = 0 is left as it is (d_j has no value there), and so
+ * is a state whose norm is zero.
  */
 void orc_renorm(const orc_params* p, cplx* psi) {
     double N[3], d[3];
     orc_norms(p, psi, N);
+    if (!(N[0] + N[1] + N[2] > 0.0)) return;
     if (p->renorm == 1) {
         d[0] = d[1] = d[2] = 1.0 / sqrt(N[0] + N[1] + N[2]);
     } else if (p->renorm == 2) {
         double m = p->mag;
-        d[1] = sqrt(1.0 - m * m) / sqrt(N[1] + sqrt(4.0 * (1.0 - m * m) * N[0] * N[2] + m * m * N[1] * N[1]));
+        double den = N[1] + sqrt(4.0 * (1.0 - m * m) * N[0] * N[2] + m * m * N[1] * N[1]);
+        if (!(den > 0.0)) return;
+        d[1] = sqrt(1.0 - m * m) / sqrt(den);
         d[0] = N[0] > 0.0 ? sqrt(1.0 + m - d[1] * d[1] * N[1]) / sqrt(2.0 * N[0]) : 1.0;
         d[2] = N[2] > 0.0 ? sqrt(1.0 - m - d[1] * d[1] * N[1]) / sqrt(2.0 * N[2]) : 1.0;
         if (!(N[1] > 0.0)) d[1] = 1.0;

@@ -142,6 +142,57 @@ static void invalidate_graphs(sgpe_ctx* c) {
     c->graphs.clear();
 }
 
+namespace sgpe {
+const char* check_params(const sgpe_params* p) {
+    if (!(p->dt > 0.0) || !isfinite(p->dt)) return "dt must be positive and finite";
+    if (p->so_type < 0 || p->so_type > 3) return "so_type must be 0..3";
+    if (p->renorm < 0 || p->renorm > 2) return "renorm must be 0, 1 or 2";
+    if (p->renorm == 2 && !(fabs(p->mag) < 1.0)) return "renorm 2 needs |mag| < 1";
+    const double vals[] = {p->c0, p->c2, p->gamma, p->omega, p->wx, p->wy, p->mag};
+    for (double v : vals)
+        if (!isfinite(v)) return "non-finite parameter";
+    return nullptr;
+}
+
+KParams make_kparams(int dim, int nx, int ny, double dx, double dy, const sgpe_params* p) {
+    KParams k;
+    memset(&k, 0, sizeof(k));
+    k.dim = dim;
+    k.nx = nx;
+    k.ny = ny;
+    k.dx = dx;
+    k.dy = dy;
+    k.dt = p->dt;
+    const double gt = p->gamma / sqrt(2.0);
+    k.so_case = 0;
+    if (p->so_type != 0 && p->gamma != 0.0) {
+        if (dim == 1) {
+            k.so_case = p->so_type;
+            k.sx = (p->so_type == 3 ? p->gamma : gt) / (2.0 * dx);
+            k.sy = 0.0;
+        } else {
+            double eta = p->so_type == 1 ? 1.0 : (p->so_type == 2 ? -1.0 : 0.0);
+            k.so_case = 4;
+            k.sx = gt / (2.0 * dx);
+            k.sy = gt * eta / (2.0 * dy);
+        }
+    }
+    k.hx = p->dt * k.sx;
+    k.hy = p->dt * k.sy;
+    k.c0 = p->c0;
+    k.c2 = p->c2;
+    k.wx2h = 0.5 * p->wx * p->wx;
+    k.wy2h = dim == 2 ? 0.5 * p->wy * p->wy : 0.0;
+    k.vx = k.wx2h * dx * dx;
+    k.vy = k.wy2h * dy * dy;
+    k.omega_t = p->omega / sqrt(2.0);
+    k.cell = dim == 2 ? dx * dy : dx;
+    k.renorm = p->renorm;
+    k.mag = p->mag;
+    return k;
+}
+}  // namespace sgpe
+
 extern "C" {
 
 sgpe_status sgpe_init_grid(sgpe_ctx** out, int dim, int nx, int ny, double dx, double dy, sgpe_precision prec,
@@ -215,49 +266,10 @@ sgpe_status sgpe_bind(sgpe_ctx* c, void* psi_dev, void* workspace_dev) {
 sgpe_status sgpe_set_params(sgpe_ctx* c, const sgpe_params* p) {
     if (!c || !p) return SGPE_EINVAL;
     if (!c->psi) return fail(c, SGPE_ESTATE, "sgpe_set_params: no buffers bound");
-    if (!(p->dt > 0.0) || !isfinite(p->dt)) return fail(c, SGPE_EINVAL, "dt must be positive and finite");
-    if (p->so_type < 0 || p->so_type > 3) return fail(c, SGPE_EINVAL, "so_type must be 0..3");
-    if (p->renorm < 0 || p->renorm > 2) return fail(c, SGPE_EINVAL, "renorm must be 0, 1 or 2");
-    if (p->renorm == 2 && !(fabs(p->mag) < 1.0)) return fail(c, SGPE_EINVAL, "renorm 2 needs |mag| < 1");
-    const double vals[] = {p->c0, p->c2, p->gamma, p->omega, p->wx, p->wy, p->mag};
-    for (double v : vals)
-        if (!isfinite(v)) return fail(c, SGPE_EINVAL, "non-finite parameter");
+    if (const char* why = check_params(p)) return fail(c, SGPE_EINVAL, "%s", why);
     invalidate_graphs(c);
     c->params = *p;
-    KParams& k = c->kp;
-    memset(&k, 0, sizeof(k));
-    k.dim = c->dim;
-    k.nx = c->nx;
-    k.ny = c->ny;
-    k.dx = c->dx;
-    k.dy = c->dy;
-    k.dt = p->dt;
-    const double gt = p->gamma / sqrt(2.0);
-    k.so_case = 0;
-    if (p->so_type != 0 && p->gamma != 0.0) {
-        if (c->dim == 1) {
-            k.so_case = p->so_type;
-            k.sx = (p->so_type == 3 ? p->gamma : gt) / (2.0 * c->dx);
-            k.sy = 0.0;
-        } else {
-            double eta = p->so_type == 1 ? 1.0 : (p->so_type == 2 ? -1.0 : 0.0);
-            k.so_case = 4;
-            k.sx = gt / (2.0 * c->dx);
-            k.sy = gt * eta / (2.0 * c->dy);
-        }
-    }
-    k.hx = p->dt * k.sx;
-    k.hy = p->dt * k.sy;
-    k.c0 = p->c0;
-    k.c2 = p->c2;
-    k.wx2h = 0.5 * p->wx * p->wx;
-    k.wy2h = c->dim == 2 ? 0.5 * p->wy * p->wy : 0.0;
-    k.vx = k.wx2h * c->dx * c->dx;
-    k.vy = k.wy2h * c->dy * c->dy;
-    k.omega_t = p->omega / sqrt(2.0);
-    k.cell = c->dim == 2 ? c->dx * c->dy : c->dx;
-    k.renorm = p->renorm;
-    k.mag = p->mag;
+    c->kp = make_kparams(c->dim, c->nx, c->ny, c->dx, c->dy, p);
     // COEF: Crank-Nicolson tables, bt = z/(4 h^2), z = dt (imaginary) or i dt (real)
     for (int m = 0; m < 2; m++)
         for (int a = 0; a < (c->dim == 2 ? 2 : 1); a++) {
@@ -431,6 +443,7 @@ sgpe_status sgpe_set_state(sgpe_ctx* c, const void* host_psi) {
     size_t bytes = (size_t)3 * c->nx * c->ny * c->esz;
     CK(cudaMemcpyAsync(c->psi, host_psi, bytes, cudaMemcpyHostToDevice, c->stream), "set_state copy");
     CK(reset_scale(c->stream, c->sc), "reset scale");
+    CK(cudaMemsetAsync(&c->sc->err, 0, sizeof(int), c->stream), "clear err");
     CK(cudaStreamSynchronize(c->stream), "sync");
     return SGPE_OK;
 }
@@ -441,6 +454,7 @@ sgpe_status sgpe_load_state(sgpe_ctx* c, const void* psi_dev) {
     size_t bytes = (size_t)3 * c->nx * c->ny * c->esz;
     CK(cudaMemcpyAsync(c->psi, psi_dev, bytes, cudaMemcpyDeviceToDevice, c->stream), "load_state copy");
     CK(reset_scale(c->stream, c->sc), "reset scale");
+    CK(cudaMemsetAsync(&c->sc->err, 0, sizeof(int), c->stream), "clear err");
     return SGPE_OK;
 }
 

@@ -1,0 +1,624 @@
+// sgpe_batch.cu -- batched form: many independent grids (1D and 2D, uneven
+// sizes, uneven physical parameters) advanced together by the same split step
+// (arXiv:2009.13507, Sec. 3 and Appendix A) in grouped launches replayed from
+// CUDA graphs. Every launch covers all instances through device work lists:
+//   pointwise   one block per 128-point tile of any instance
+//   CN along x  one warp per line; one launch per chunk length C (the
+//               register kernels are compiled per C)
+//   CN along y  one warp per column pair (2D instances), one launch per C
+//   finalize    one block per instance (norms, renormalisation scale)
+// Warps per block of the two sweeps are chosen by sgpe_batch_autotune.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "../../include/sgpe.h"
+#include "sgpe_cn.cuh"
+#include "sgpe_kernels.cuh"
+#include "sgpe_launch.h"
+
+namespace sgpe {
+
+// Device descriptor of one instance.
+struct BInst {
+    KParams p;
+    long long off;  // element offset of the instance state in the batch state (and mid) buffers
+    long long tab;  // element offset of the instance CN tables in the table pool
+    int lenx, leny; // table lengths per axis
+    int slot0;      // first partial-norm slot of the instance's final sweep
+    int nslot;
+    int tile0;      // first pointwise / observable tile
+    int ntile;
+};
+
+// Tables of an instance: [mode 0 imag, 1 real][axis x, y][fa, fg, fp, fq].
+template <typename R>
+__device__ __forceinline__ Tabs<R> inst_tabs(const typename V2<R>::T* pool, const BInst& I, int mode, int axis) {
+    const typename V2<R>::T* b = pool + I.tab + (long long)mode * 4 * (I.lenx + I.leny);
+    const int len = axis == 0 ? I.lenx : I.leny;
+    if (axis == 1) b += 4 * I.lenx;
+    return Tabs<R>{b, b + len, b + 2 * len, b + 3 * len};
+}
+
+// Tile t of an instance: 2D tiles are 32 x 4 points, 1D tiles 128 points.
+__device__ __forceinline__ void tile_point(const KParams& p, int t, int* ix, int* iy) {
+    if (p.dim == 2) {
+        const int ntx = (p.nx + 31) / 32;
+        *ix = (t % ntx) * 32 + (threadIdx.x & 31);
+        *iy = (t / ntx) * 4 + (threadIdx.x >> 5);
+    } else {
+        *ix = t * 128 + threadIdx.x;
+        *iy = 0;
+    }
+}
+
+template <typename R, bool IMAG>
+__global__ void __launch_bounds__(128) kb_pointwise(const typename V2<R>::T* __restrict__ A,
+                                                    typename V2<R>::T* __restrict__ B, const BInst* __restrict__ insts,
+                                                    const int2* __restrict__ tiles, const DevScalars* __restrict__ scs) {
+    const int2 tl = tiles[blockIdx.x];
+    const BInst& I = insts[tl.x];
+    int ix, iy;
+    tile_point(I.p, tl.y, &ix, &iy);
+    if (ix >= I.p.nx || iy >= I.p.ny) return;
+    pointwise_at<R, IMAG>(A + I.off, B + I.off, I.p, scs[tl.x].scale, (R)I.p.omega_t, ix, iy, 7);
+}
+
+// Work entry of the x sweep: (instance, line, partial slot or -1).
+template <typename R, bool IMAG, int C>
+__global__ void kb_cnx(typename V2<R>::T* A, typename V2<R>::T* B, const BInst* __restrict__ insts,
+                       const typename V2<R>::T* __restrict__ pool, const int4* __restrict__ work, int nwork,
+                       double* partials) {
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= nwork) return;  // whole warp
+    const int4 e = work[w];
+    const BInst& I = insts[e.x];
+    const Tabs<R> t = inst_tabs<R>(pool, I, IMAG ? 0 : 1, 0);
+    typename V2<R>::T* out = (I.p.dim == 2 ? B : A) + I.off;
+    cnx_line<R, IMAG, C>(B + I.off, out, I.p, t, e.y, e.z >= 0 ? partials + 3 * e.z : nullptr);
+}
+
+// Work entry of the y sweep: (instance, component, first column, partial slot).
+template <typename R, bool IMAG, int C>
+__global__ void kb_cny(typename V2<R>::T* A, const typename V2<R>::T* B, const BInst* __restrict__ insts,
+                       const typename V2<R>::T* __restrict__ pool, const int4* __restrict__ work, int nwork,
+                       double* partials) {
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= nwork) return;
+    const int4 e = work[w];
+    const BInst& I = insts[e.x];
+    const Tabs<R> t = inst_tabs<R>(pool, I, IMAG ? 0 : 1, 1);
+    cny_cols<R, IMAG, C>(B + I.off, A + I.off, I.p, t, e.y, e.z, partials + 3 * e.w);
+}
+
+// One block per instance: sum its partial slots in order, publish norms and the
+// next pending scale (imaginary time with renorm != 0), advance its step count.
+__global__ void __launch_bounds__(128) kb_finalize(const BInst* __restrict__ insts, const double* partials,
+                                                   DevScalars* scs, int imag) {
+    __shared__ double red[4 * 3];
+    const BInst& I = insts[blockIdx.x];
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < I.nslot; b += blockDim.x) {
+        const double* q = partials + 3 * (I.slot0 + b);
+        s[0] += __ldcg(q + 0);
+        s[1] += __ldcg(q + 1);
+        s[2] += __ldcg(q + 2);
+    }
+    block_reduce<3>(s, red);
+    if (threadIdx.x == 0) {
+        DevScalars* sc = scs + blockIdx.x;
+        double N[3] = {s[0] * I.p.cell, s[1] * I.p.cell, s[2] * I.p.cell};
+        bool finite = isfinite(N[0]) && isfinite(N[1]) && isfinite(N[2]);
+        double d[3];
+        renorm_factors(N, (finite && imag) ? I.p.renorm : 0, I.p.mag, d);
+        for (int j = 0; j < 3; j++) {
+            sc->norms[j] = N[j];
+            sc->scale[j] = d[j];
+        }
+        if (!finite) sc->err |= 1;
+        sc->step_idx += 1;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) kb_flush(typename V2<R>::T* A, const BInst* __restrict__ insts,
+                                                const int2* __restrict__ tiles, const DevScalars* __restrict__ scs) {
+    const int2 tl = tiles[blockIdx.x];
+    const BInst& I = insts[tl.x];
+    int ix, iy;
+    tile_point(I.p, tl.y, &ix, &iy);
+    if (ix >= I.p.nx || iy >= I.p.ny) return;
+    const size_t plane = (size_t)I.p.nx * I.p.ny, c = (size_t)iy * I.p.nx + ix;
+    for (int j = 0; j < 3; j++) {
+        typename V2<R>::T* a = A + I.off + j * plane + c;
+        cx<R> v = ldc<R>(A + I.off, j * plane + c);
+        st<R>(a, 0, scl((R)scs[tl.x].scale[j], v));
+    }
+}
+
+__global__ void kb_reset(DevScalars* scs, int n, int clear_err) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        for (int j = 0; j < 4; j++) scs[i].scale[j] = 1.0;
+    if (i < n && clear_err) scs[i].err = 0;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) kb_obs_tiles(const typename V2<R>::T* __restrict__ A,
+                                                    const BInst* __restrict__ insts, const int2* __restrict__ tiles,
+                                                    double* partials) {
+    __shared__ double red[4 * NACC];
+    const int2 tl = tiles[blockIdx.x];
+    const BInst& I = insts[tl.x];
+    int ix, iy;
+    tile_point(I.p, tl.y, &ix, &iy);
+    double v[NACC];
+    for (int q = 0; q < NACC; q++) v[q] = 0.0;
+    if (ix < I.p.nx && iy < I.p.ny) obs_point<R>(A + I.off, I.p, I.p.omega_t, ix, iy, v);
+    block_reduce<NACC>(v, red);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < NACC; q++) partials[(size_t)blockIdx.x * NACC + q] = v[q];
+}
+
+__global__ void __launch_bounds__(128) kb_obs_final(const BInst* __restrict__ insts, const double* partials,
+                                                    DevScalars* scs) {
+    __shared__ double red[4 * NACC];
+    const BInst& I = insts[blockIdx.x];
+    double s[NACC];
+    for (int q = 0; q < NACC; q++) s[q] = 0.0;
+    for (int b = threadIdx.x; b < I.ntile; b += blockDim.x)
+        for (int q = 0; q < NACC; q++) s[q] += __ldcg(partials + (size_t)(I.tile0 + b) * NACC + q);
+    block_reduce<NACC>(s, red);
+    if (threadIdx.x == 0) obs_finish(s, I.p.cell, scs[blockIdx.x].obs, &scs[blockIdx.x].err);
+}
+
+}  // namespace sgpe
+
+using namespace sgpe;
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct BGraphKey {
+    int imag, count;
+    bool operator<(const BGraphKey& o) const { return imag != o.imag ? imag < o.imag : count < o.count; }
+};
+
+struct sgpe_batch {
+    int n;
+    sgpe_precision prec;
+    int esz;
+    cudaStream_t stream;
+    std::vector<sgpe_instance> inst;
+    std::vector<BInst> hinst;
+    std::vector<int2> tiles;
+    std::map<int, std::vector<int4>> cnx, cny;  // work lists by chunk length
+    size_t state_elems;
+    long long tab_elems;
+    int nslots;
+    // workspace layout (byte offsets)
+    size_t o_inst, o_sc, o_tiles, o_part, o_tab, o_mid, total;
+    std::map<int, size_t> o_cnx, o_cny;
+    // bound buffers
+    void* psi;
+    unsigned char* work;
+    // launch shape (warps per block of the x / y sweeps)
+    int wx, wy;
+    std::map<BGraphKey, cudaGraphExec_t> graphs;
+    bool graphs_ok;
+    char err[512];
+};
+
+static sgpe_status bfail(sgpe_batch* b, sgpe_status st, const char* fmt, ...) {
+    if (b) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(b->err, sizeof(b->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define BCK(expr, where)                                                                   \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess) return bfail(b, SGPE_ECUDA, "%s: %s", where, cudaGetErrorString(e_)); \
+    } while (0)
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static void binvalidate(sgpe_batch* b) {
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+// Enqueue one step for all instances.
+template <typename R, bool IMAG>
+static cudaError_t benqueue_step(sgpe_batch* b) {
+    using T = typename V2<R>::T;
+    T* A = (T*)b->psi;
+    T* B = (T*)(b->work + b->o_mid);
+    const BInst* I = (const BInst*)(b->work + b->o_inst);
+    DevScalars* sc = (DevScalars*)(b->work + b->o_sc);
+    const int2* tiles = (const int2*)(b->work + b->o_tiles);
+    double* part = (double*)(b->work + b->o_part);
+    const T* pool = (const T*)(b->work + b->o_tab);
+    kb_pointwise<R, IMAG><<<(unsigned)b->tiles.size(), 128, 0, b->stream>>>(A, B, I, tiles, sc);
+    for (auto& kv : b->cnx) {
+        const int4* w = (const int4*)(b->work + b->o_cnx[kv.first]);
+        int nw = (int)kv.second.size();
+        dim3 grid((nw + b->wx - 1) / b->wx), block(32 * b->wx);
+        switch (kv.first) {
+            case 1: kb_cnx<R, IMAG, 1><<<grid, block, 0, b->stream>>>(A, B, I, pool, w, nw, part); break;
+            case 2: kb_cnx<R, IMAG, 2><<<grid, block, 0, b->stream>>>(A, B, I, pool, w, nw, part); break;
+            case 4: kb_cnx<R, IMAG, 4><<<grid, block, 0, b->stream>>>(A, B, I, pool, w, nw, part); break;
+            case 8: kb_cnx<R, IMAG, 8><<<grid, block, 0, b->stream>>>(A, B, I, pool, w, nw, part); break;
+            case 16: kb_cnx<R, IMAG, 16><<<grid, block, 0, b->stream>>>(A, B, I, pool, w, nw, part); break;
+            default: kb_cnx<R, IMAG, 32><<<grid, block, 0, b->stream>>>(A, B, I, pool, w, nw, part); break;
+        }
+    }
+    for (auto& kv : b->cny) {
+        const int4* w = (const int4*)(b->work + b->o_cny[kv.first]);
+        int nw = (int)kv.second.size();
+        dim3 grid((nw + b->wy - 1) / b->wy), block(32 * b->wy);
+        switch (kv.first) {
+            case 1: kb_cny<R, IMAG, 1><<<grid, block, 0, b->stream>>>(A, B, I, pool, w, nw, part); break;
+            case 2: kb_cny<R, IMAG, 2><<<grid, block, 0, b->stream>>>(A, B, I, pool, w, nw, part); break;
+            case 4: kb_cny<R, IMAG, 4><<<grid, block, 0, b->stream>>>(A, B, I, pool, w, nw, part); break;
+            case 8: kb_cny<R, IMAG, 8><<<grid, block, 0, b->stream>>>(A, B, I, pool, w, nw, part); break;
+            case 16: kb_cny<R, IMAG, 16><<<grid, block, 0, b->stream>>>(A, B, I, pool, w, nw, part); break;
+            default: kb_cny<R, IMAG, 32><<<grid, block, 0, b->stream>>>(A, B, I, pool, w, nw, part); break;
+        }
+    }
+    kb_finalize<<<b->n, 128, 0, b->stream>>>(I, part, sc, IMAG ? 1 : 0);
+    return cudaGetLastError();
+}
+
+static cudaError_t benqueue_steps(sgpe_batch* b, int n, bool imag) {
+    for (int i = 0; i < n; i++) {
+        cudaError_t e;
+        if (b->prec == SGPE_C128)
+            e = imag ? benqueue_step<double, true>(b) : benqueue_step<double, false>(b);
+        else
+            e = imag ? benqueue_step<float, true>(b) : benqueue_step<float, false>(b);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static sgpe_status brun(sgpe_batch* b, int nsteps, bool imag) {
+    const int G = nsteps < 32 ? nsteps : 32;
+    const int reps = G > 0 ? nsteps / G : 0, rem = G > 0 ? nsteps - reps * G : 0;
+    cudaGraphExec_t exec = nullptr;
+    if (b->graphs_ok && b->stream != nullptr && reps > 0 && G >= 4) {
+        BGraphKey key{imag ? 1 : 0, G};
+        auto it = b->graphs.find(key);
+        if (it != b->graphs.end()) {
+            exec = it->second;
+        } else {
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t e2 = benqueue_steps(b, G, imag);
+                e = cudaStreamEndCapture(b->stream, &g);
+                if (e2 != cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                exec = nullptr;
+                b->graphs_ok = false;
+            } else {
+                b->graphs[key] = exec;
+            }
+        }
+    }
+    if (exec) {
+        for (int r = 0; r < reps; r++) BCK(cudaGraphLaunch(exec, b->stream), "cudaGraphLaunch");
+        BCK(benqueue_steps(b, rem, imag), "batch step kernels");
+    } else {
+        BCK(benqueue_steps(b, nsteps, imag), "batch step kernels");
+    }
+    return SGPE_OK;
+}
+
+template <typename R> static cudaError_t bflush(sgpe_batch* b) {
+    using T = typename V2<R>::T;
+    const BInst* I = (const BInst*)(b->work + b->o_inst);
+    DevScalars* sc = (DevScalars*)(b->work + b->o_sc);
+    const int2* tiles = (const int2*)(b->work + b->o_tiles);
+    kb_flush<R><<<(unsigned)b->tiles.size(), 128, 0, b->stream>>>((T*)b->psi, I, tiles, sc);
+    kb_reset<<<(b->n + 127) / 128, 128, 0, b->stream>>>(sc, b->n, 0);
+    return cudaGetLastError();
+}
+
+extern "C" {
+
+sgpe_status sgpe_batch_create(sgpe_batch** out, int n, const sgpe_instance* inst, sgpe_precision prec,
+                              void* cuda_stream) {
+    if (!out) return SGPE_EINVAL;
+    *out = nullptr;
+    if (n < 1 || !inst) {
+        set_thread_error("sgpe_batch_create: need n >= 1 instances");
+        return SGPE_EINVAL;
+    }
+    if (prec != SGPE_C128 && prec != SGPE_C64) return SGPE_EINVAL;
+    for (int i = 0; i < n; i++) {
+        const sgpe_instance& q = inst[i];
+        int ny = q.dim == 1 ? 1 : q.ny;
+        double dy = q.dim == 1 ? q.dx : q.dy;
+        if ((q.dim != 1 && q.dim != 2) || q.nx < 3 || (q.dim == 2 && ny < 3) || !(q.dx > 0.0) || !(dy > 0.0) ||
+            !isfinite(q.dx) || !isfinite(dy)) {
+            char m[128];
+            snprintf(m, sizeof(m), "sgpe_batch_create: instance %d has an invalid grid", i);
+            set_thread_error(m);
+            return SGPE_EINVAL;
+        }
+        if (q.nx > kRegMaxN || ny > kRegMaxN) {
+            char m[128];
+            snprintf(m, sizeof(m), "sgpe_batch_create: instance %d: lines longer than %d points", i, kRegMaxN);
+            set_thread_error(m);
+            return SGPE_EUNSUPPORTED;
+        }
+        if (const char* why = check_params(&q.params)) {
+            char m[160];
+            snprintf(m, sizeof(m), "sgpe_batch_create: instance %d: %s", i, why);
+            set_thread_error(m);
+            return SGPE_EINVAL;
+        }
+    }
+    sgpe_batch* b = new (std::nothrow) sgpe_batch();
+    if (!b) return SGPE_ENOMEM;
+    b->n = n;
+    b->prec = prec;
+    b->esz = prec == SGPE_C128 ? 16 : 8;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->inst.assign(inst, inst + n);
+    b->psi = nullptr;
+    b->work = nullptr;
+    b->wx = 1;
+    b->wy = 1;
+    b->graphs_ok = true;
+    b->err[0] = 0;
+    long long off = 0, tab = 0;
+    int slot = 0;
+    for (int i = 0; i < n; i++) {
+        sgpe_instance q = inst[i];
+        if (q.dim == 1) {
+            q.ny = 1;
+            q.dy = q.dx;
+        }
+        BInst I;
+        memset(&I, 0, sizeof(I));
+        I.p = make_kparams(q.dim, q.nx, q.ny, q.dx, q.dy, &q.params);
+        I.off = off;
+        off += ((long long)3 * q.nx * q.ny + 63) / 64 * 64;
+        I.lenx = table_len(q.nx);
+        I.leny = q.dim == 2 ? table_len(q.ny) : 0;
+        I.tab = tab;
+        tab += 2LL * 4 * (I.lenx + I.leny);
+        I.tile0 = (int)b->tiles.size();
+        I.ntile = q.dim == 2 ? ceil_div(q.nx, 32) * ceil_div(q.ny, 4) : ceil_div(q.nx, 128);
+        for (int t = 0; t < I.ntile; t++) b->tiles.push_back(make_int2(i, t));
+        const int Cx = chunk_len(q.nx);
+        I.slot0 = slot;
+        if (q.dim == 1) {
+            I.nslot = 3;
+            for (int l = 0; l < 3; l++) b->cnx[Cx].push_back(make_int4(i, l, slot + l, 0));
+            slot += 3;
+        } else {
+            for (int l = 0; l < 3 * q.ny; l++) b->cnx[Cx].push_back(make_int4(i, l, -1, 0));
+            const int Cy = chunk_len(q.ny);
+            const int K = cny_cols_per_warp(Cy);
+            int cnt = 0;
+            for (int j = 0; j < 3; j++)
+                for (int col = 0; col < q.nx; col += K) b->cny[Cy].push_back(make_int4(i, j, col, slot + cnt++));
+            I.nslot = cnt;
+            slot += cnt;
+        }
+        b->hinst.push_back(I);
+    }
+    b->state_elems = (size_t)off;
+    b->tab_elems = tab;
+    b->nslots = slot;
+    size_t o = 0;
+    b->o_inst = o;
+    o = al256(o + sizeof(BInst) * n);
+    b->o_sc = o;
+    o = al256(o + sizeof(DevScalars) * n);
+    b->o_tiles = o;
+    o = al256(o + sizeof(int2) * b->tiles.size());
+    for (auto& kv : b->cnx) {
+        b->o_cnx[kv.first] = o;
+        o = al256(o + sizeof(int4) * kv.second.size());
+    }
+    for (auto& kv : b->cny) {
+        b->o_cny[kv.first] = o;
+        o = al256(o + sizeof(int4) * kv.second.size());
+    }
+    b->o_part = o;
+    size_t np = std::max((size_t)3 * b->nslots, (size_t)NACC * b->tiles.size());
+    o = al256(o + sizeof(double) * np);
+    b->o_tab = o;
+    o = al256(o + (size_t)b->esz * b->tab_elems);
+    b->o_mid = o;
+    o = al256(o + (size_t)b->esz * b->state_elems);
+    b->total = o;
+    *out = b;
+    return SGPE_OK;
+}
+
+sgpe_status sgpe_batch_sizes(const sgpe_batch* b, size_t* state_elems, size_t* workspace_bytes) {
+    if (!b) return SGPE_EINVAL;
+    if (state_elems) *state_elems = b->state_elems;
+    if (workspace_bytes) *workspace_bytes = b->total;
+    return SGPE_OK;
+}
+
+sgpe_status sgpe_batch_offsets(const sgpe_batch* b, size_t* offsets) {
+    if (!b || !offsets) return SGPE_EINVAL;
+    for (int i = 0; i < b->n; i++) offsets[i] = (size_t)b->hinst[i].off;
+    return SGPE_OK;
+}
+
+sgpe_status sgpe_batch_bind(sgpe_batch* b, void* psi_dev, void* workspace_dev) {
+    if (!b) return SGPE_EINVAL;
+    if (!psi_dev || !workspace_dev) return bfail(b, SGPE_EINVAL, "sgpe_batch_bind: null buffer");
+    if (((uintptr_t)psi_dev & 15) || ((uintptr_t)workspace_dev & 255))
+        return bfail(b, SGPE_EINVAL, "sgpe_batch_bind: psi must be 16-byte and workspace 256-byte aligned");
+    binvalidate(b);
+    b->psi = psi_dev;
+    b->work = (unsigned char*)workspace_dev;
+    cudaStream_t s = b->stream;
+    BCK(cudaMemcpyAsync(b->work + b->o_inst, b->hinst.data(), sizeof(BInst) * b->n, cudaMemcpyHostToDevice, s), "copy");
+    BCK(cudaMemsetAsync(b->work + b->o_sc, 0, sizeof(DevScalars) * b->n, s), "memset");
+    BCK(cudaMemcpyAsync(b->work + b->o_tiles, b->tiles.data(), sizeof(int2) * b->tiles.size(), cudaMemcpyHostToDevice,
+                        s), "copy");
+    for (auto& kv : b->cnx)
+        BCK(cudaMemcpyAsync(b->work + b->o_cnx[kv.first], kv.second.data(), sizeof(int4) * kv.second.size(),
+                            cudaMemcpyHostToDevice, s), "copy");
+    for (auto& kv : b->cny)
+        BCK(cudaMemcpyAsync(b->work + b->o_cny[kv.first], kv.second.data(), sizeof(int4) * kv.second.size(),
+                            cudaMemcpyHostToDevice, s), "copy");
+    DevScalars* sc = (DevScalars*)(b->work + b->o_sc);
+    kb_reset<<<(b->n + 127) / 128, 128, 0, s>>>(sc, b->n, 1);
+    BCK(cudaGetLastError(), "reset");
+    // COEF for every instance, both time modes and axes
+    for (int i = 0; i < b->n; i++) {
+        const BInst& I = b->hinst[i];
+        for (int m = 0; m < 2; m++)
+            for (int a = 0; a < I.p.dim; a++) {
+                const int len = a == 0 ? I.lenx : I.leny;
+                const int nn = a == 0 ? I.p.nx : I.p.ny;
+                const double h = a == 0 ? I.p.dx : I.p.dy;
+                long long base = I.tab + (long long)m * 4 * (I.lenx + I.leny) + (a == 1 ? 4LL * I.lenx : 0);
+                unsigned char* t = b->work + b->o_tab + (size_t)b->esz * base;
+                double bt = I.p.dt / (4.0 * h * h);
+                double bre = m == 0 ? bt : 0.0, bim = m == 0 ? 0.0 : bt;
+                size_t L = (size_t)b->esz * len;
+                cudaError_t e = b->prec == SGPE_C128
+                                    ? Launcher<double>::coef(s, t, t + L, t + 2 * L, t + 3 * L, nn, bre, bim)
+                                    : Launcher<float>::coef(s, t, t + L, t + 2 * L, t + 3 * L, nn, bre, bim);
+                BCK(e, "COEF kernel");
+            }
+    }
+    BCK(cudaStreamSynchronize(s), "sync");  // host work lists must outlive the copies
+    return SGPE_OK;
+}
+
+sgpe_status sgpe_batch_load_state(sgpe_batch* b, const void* psi_dev) {
+    if (!b || !psi_dev) return SGPE_EINVAL;
+    if (!b->psi) return bfail(b, SGPE_ESTATE, "no buffers bound");
+    BCK(cudaMemcpyAsync(b->psi, psi_dev, (size_t)b->esz * b->state_elems, cudaMemcpyDeviceToDevice, b->stream),
+        "load_state");
+    kb_reset<<<(b->n + 127) / 128, 128, 0, b->stream>>>((DevScalars*)(b->work + b->o_sc), b->n, 1);
+    BCK(cudaGetLastError(), "reset");
+    return SGPE_OK;
+}
+
+sgpe_status sgpe_batch_step_imag(sgpe_batch* b, int nsteps) {
+    if (!b) return SGPE_EINVAL;
+    if (!b->psi) return bfail(b, SGPE_ESTATE, "no buffers bound");
+    if (nsteps < 0) return bfail(b, SGPE_EINVAL, "nsteps < 0");
+    return nsteps ? brun(b, nsteps, true) : SGPE_OK;
+}
+
+sgpe_status sgpe_batch_step_real(sgpe_batch* b, int nsteps) {
+    if (!b) return SGPE_EINVAL;
+    if (!b->psi) return bfail(b, SGPE_ESTATE, "no buffers bound");
+    if (nsteps < 0) return bfail(b, SGPE_EINVAL, "nsteps < 0");
+    return nsteps ? brun(b, nsteps, false) : SGPE_OK;
+}
+
+sgpe_status sgpe_batch_energy(sgpe_batch* b, double* out) {
+    if (!b || !out) return SGPE_EINVAL;
+    if (!b->psi) return bfail(b, SGPE_ESTATE, "no buffers bound");
+    BCK(b->prec == SGPE_C128 ? bflush<double>(b) : bflush<float>(b), "flush");
+    const BInst* I = (const BInst*)(b->work + b->o_inst);
+    const int2* tiles = (const int2*)(b->work + b->o_tiles);
+    double* part = (double*)(b->work + b->o_part);
+    DevScalars* sc = (DevScalars*)(b->work + b->o_sc);
+    if (b->prec == SGPE_C128)
+        kb_obs_tiles<double><<<(unsigned)b->tiles.size(), 128, 0, b->stream>>>((const double2*)b->psi, I, tiles, part);
+    else
+        kb_obs_tiles<float><<<(unsigned)b->tiles.size(), 128, 0, b->stream>>>((const float2*)b->psi, I, tiles, part);
+    kb_obs_final<<<b->n, 128, 0, b->stream>>>(I, part, sc);
+    BCK(cudaGetLastError(), "observables");
+    std::vector<DevScalars> h(b->n);
+    BCK(cudaMemcpyAsync(h.data(), sc, sizeof(DevScalars) * b->n, cudaMemcpyDeviceToHost, b->stream), "copy");
+    BCK(cudaStreamSynchronize(b->stream), "sync");
+    int bad = -1;
+    for (int i = 0; i < b->n; i++) {
+        memcpy(out + (size_t)SGPE_NOBS * i, h[i].obs, SGPE_NOBS * sizeof(double));
+        if (h[i].err && bad < 0) bad = i;
+    }
+    if (bad >= 0) {
+        for (int i = 0; i < b->n; i++) BCK(cudaMemsetAsync(&sc[i].err, 0, sizeof(int), b->stream), "clear err");
+        return bfail(b, SGPE_ENONFINITE, "instance %d: non-finite norm", bad);
+    }
+    return SGPE_OK;
+}
+
+sgpe_status sgpe_batch_autotune(sgpe_batch* b, int nsteps, int* choice) {
+    if (!b) return SGPE_EINVAL;
+    if (!b->psi) return bfail(b, SGPE_ESTATE, "no buffers bound");
+    if (nsteps < 1) return bfail(b, SGPE_EINVAL, "nsteps < 1");
+    const int cand[3] = {1, 2, 4};
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0), "event");
+    BCK(cudaEventCreate(&e1), "event");
+    float best = 1e30f;
+    int bx = 1, by = 1;
+    for (int ix = 0; ix < 3; ix++)
+        for (int iy = 0; iy < 3; iy++) {
+            b->wx = cand[ix];
+            b->wy = cand[iy];
+            binvalidate(b);
+            BCK(benqueue_steps(b, 1, true), "warm-up");
+            BCK(cudaEventRecord(e0, b->stream), "event");
+            BCK(benqueue_steps(b, nsteps, true), "tune steps");
+            BCK(cudaEventRecord(e1, b->stream), "event");
+            BCK(cudaEventSynchronize(e1), "sync");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bx = cand[ix];
+                by = cand[iy];
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->wx = bx;
+    b->wy = by;
+    binvalidate(b);
+    kb_reset<<<(b->n + 127) / 128, 128, 0, b->stream>>>((DevScalars*)(b->work + b->o_sc), b->n, 1);
+    BCK(cudaStreamSynchronize(b->stream), "sync");
+    if (choice) {
+        choice[0] = bx;
+        choice[1] = by;
+    }
+    return SGPE_OK;
+}
+
+int sgpe_batch_launches_per_step(const sgpe_batch* b) {
+    if (!b) return 0;
+    return 2 + (int)b->cnx.size() + (int)b->cny.size();
+}
+
+const char* sgpe_batch_last_error(const sgpe_batch* b) { return b ? b->err : "null batch"; }
+
+sgpe_status sgpe_batch_destroy(sgpe_batch* b) {
+    if (!b) return SGPE_OK;
+    binvalidate(b);
+    delete b;
+    return SGPE_OK;
+}
+
+}  // extern "C"

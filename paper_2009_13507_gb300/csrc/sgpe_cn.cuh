@@ -77,12 +77,13 @@ __device__ __forceinline__ double warp_sum(double v) {
 // non-null the block writes the FP64 norm of its output line to
 // partials[3*line + j] (zeros for the other components).
 // ---------------------------------------------------------------------------
+// One x line of one grid by the calling warp; part (nullable): the 3 partial
+// slots of this line (norm of the output line in slot j, zeros elsewhere).
 template <typename R, bool IMAG, int C>
-__global__ void __launch_bounds__(32) k_cnx_reg(const typename V2<R>::T* in, typename V2<R>::T* out, KParams p,
-                                                Tabs<R> t, double* partials) {
+__device__ __forceinline__ void cnx_line(const typename V2<R>::T* in, typename V2<R>::T* out, const KParams& p,
+                                         const Tabs<R>& t, int line, double* part) {
     constexpr bool KEEP = CnShape<C>::KEEP;
-    const int lane = threadIdx.x;
-    const int line = blockIdx.x;
+    const int lane = threadIdx.x & 31;
     const int n = p.nx;
     const int i0 = lane * C;
     const cx<R> zero = {R(0), R(0)};
@@ -104,13 +105,19 @@ __global__ void __launch_bounds__(32) k_cnx_reg(const typename V2<R>::T* in, typ
             acc += (double)o.re * (double)o.re + (double)o.im * (double)o.im;
         }
     }
-    if (partials) {
+    if (part) {
         acc = warp_sum(acc);
         if (lane == 0) {
             const int j = line / p.ny;
-            for (int q = 0; q < 3; q++) partials[3 * line + q] = (q == j) ? acc : 0.0;
+            for (int q = 0; q < 3; q++) part[q] = (q == j) ? acc : 0.0;
         }
     }
+}
+
+template <typename R, bool IMAG, int C>
+__global__ void __launch_bounds__(32) k_cnx_reg(const typename V2<R>::T* in, typename V2<R>::T* out, KParams p,
+                                                Tabs<R> t, double* partials) {
+    cnx_line<R, IMAG, C>(in, out, p, t, blockIdx.x, partials ? partials + 3 * blockIdx.x : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -118,15 +125,14 @@ __global__ void __launch_bounds__(32) k_cnx_reg(const typename V2<R>::T* in, typ
 // (K = 2 for small chunks: a lane's chunk rows then load 32 contiguous bytes
 // per row in FP64). Norm partials as for the x sweep, one slot per block.
 // ---------------------------------------------------------------------------
+// Columns [col, col + K) of component j of one grid by the calling warp; part
+// (nullable) as for cnx_line.
 template <typename R, bool IMAG, int C>
-__global__ void __launch_bounds__(32) k_cny_reg(const typename V2<R>::T* in, typename V2<R>::T* out, KParams p,
-                                                Tabs<R> t, double* partials) {
+__device__ __forceinline__ void cny_cols(const typename V2<R>::T* in, typename V2<R>::T* out, const KParams& p,
+                                         const Tabs<R>& t, int j, int col, double* part) {
     constexpr int K = CnShape<C>::K;
     constexpr bool KEEP = CnShape<C>::KEEP;
-    const int lane = threadIdx.x;
-    const int ncb = (p.nx + K - 1) / K;
-    const int j = blockIdx.x / ncb;
-    const int col = (blockIdx.x - j * ncb) * K;
+    const int lane = threadIdx.x & 31;
     const int n = p.ny;
     const int i0 = lane * C;
     const size_t base = (size_t)j * p.nx * p.ny;
@@ -160,11 +166,21 @@ __global__ void __launch_bounds__(32) k_cny_reg(const typename V2<R>::T* in, typ
             }
         }
     }
-    if (partials) {
+    if (part) {
         acc = warp_sum(acc);
         if (lane == 0)
-            for (int q = 0; q < 3; q++) partials[3 * blockIdx.x + q] = (q == j) ? acc : 0.0;
+            for (int q = 0; q < 3; q++) part[q] = (q == j) ? acc : 0.0;
     }
+}
+
+template <typename R, bool IMAG, int C>
+__global__ void __launch_bounds__(32) k_cny_reg(const typename V2<R>::T* in, typename V2<R>::T* out, KParams p,
+                                                Tabs<R> t, double* partials) {
+    constexpr int K = CnShape<C>::K;
+    const int ncb = (p.nx + K - 1) / K;
+    const int j = blockIdx.x / ncb;
+    const int col = (blockIdx.x - j * ncb) * K;
+    cny_cols<R, IMAG, C>(in, out, p, t, j, col, partials ? partials + 3 * blockIdx.x : nullptr);
 }
 
 }  // namespace sgpe

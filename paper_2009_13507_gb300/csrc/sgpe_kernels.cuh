@@ -168,12 +168,15 @@ __device__ __forceinline__ bool last_block(unsigned* ticket) {
 // Eq. (DJ) with magnetisation mag for renorm = 2; otherwise 1.
 __device__ __forceinline__ void renorm_factors(const double (&N)[3], int renorm, double mag, double (&d)[3]) {
     d[0] = d[1] = d[2] = 1.0;
+    if (!(N[0] + N[1] + N[2] > 0.0)) return;  // a zero state has no normalisation: left as it is
     if (renorm == 1) {
         double f = 1.0 / sqrt(N[0] + N[1] + N[2]);
         d[0] = d[1] = d[2] = f;
     } else if (renorm == 2) {
         double m = mag;
-        double d0 = sqrt(1.0 - m * m) / sqrt(N[1] + sqrt(4.0 * (1.0 - m * m) * N[0] * N[2] + m * m * N[1] * N[1]));
+        double den = N[1] + sqrt(4.0 * (1.0 - m * m) * N[0] * N[2] + m * m * N[1] * N[1]);
+        if (!(den > 0.0)) return;
+        double d0 = sqrt(1.0 - m * m) / sqrt(den);
         d[0] = N[0] > 0.0 ? sqrt(1.0 + m - d0 * d0 * N[1]) / sqrt(2.0 * N[0]) : 1.0;
         d[2] = N[2] > 0.0 ? sqrt(1.0 - m - d0 * d0 * N[1]) / sqrt(2.0 * N[2]) : 1.0;
         d[1] = N[1] > 0.0 ? d0 : 1.0;
@@ -218,19 +221,18 @@ __device__ __forceinline__ void finalize_norms(const double* partials, int nblk,
 // (bit 0 SO, bit 1 CALCNU, bit 2 HERM). Applies the pending scale on load.
 // Block (32, BY); one thread per grid point.
 // ---------------------------------------------------------------------------
+// The pointwise substeps at grid point (ix, iy) of the state A (one grid),
+// written to B; scale: the pending renormalisation scale per component; Ot the
+// Rabi coupling Omega/sqrt2 of this step.
 template <typename R, bool IMAG>
-__global__ void __launch_bounds__(128) k_pointwise(const typename V2<R>::T* __restrict__ A,
-                                                   typename V2<R>::T* __restrict__ B, KParams p,
-                                                   const DevScalars* __restrict__ sc,
-                                                   const double* __restrict__ omega_tab, int mask) {
-    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
-    if (ix >= p.nx || iy >= p.ny) return;
+__device__ __forceinline__ void pointwise_at(const typename V2<R>::T* __restrict__ A,
+                                             typename V2<R>::T* __restrict__ B, const KParams& p,
+                                             const double* scale, R Ot, int ix, int iy, int mask) {
     const size_t plane = (size_t)p.nx * p.ny;
     const size_t c = (size_t)iy * p.nx + ix;
     R d[3];
 #pragma unroll
-    for (int j = 0; j < 3; j++) d[j] = (R)sc->scale[j];
+    for (int j = 0; j < 3; j++) d[j] = (R)scale[j];
     cx<R> u[3];
 #pragma unroll
     for (int j = 0; j < 3; j++) u[j] = scl(d[j], ld<R>(A, j * plane + c));
@@ -265,12 +267,21 @@ __global__ void __launch_bounds__(128) k_pointwise(const typename V2<R>::T* __re
         R V = (R)p.vx * (R)(kx * kx) + (p.dim == 2 ? (R)p.vy * (R)(ky * ky) : R(0));
         calcnu_point<IMAG>(u, V, (R)p.c0, (R)p.c2, dt);
     }
-    if (mask & 4) {
-        R Ot = omega_tab ? (R)(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440) : (R)p.omega_t;
-        herm_point<IMAG>(u, (R)p.c2, Ot, dt);
-    }
+    if (mask & 4) herm_point<IMAG>(u, (R)p.c2, Ot, dt);
 #pragma unroll
     for (int j = 0; j < 3; j++) st<R>(B, j * plane + c, u[j]);
+}
+
+template <typename R, bool IMAG>
+__global__ void __launch_bounds__(128) k_pointwise(const typename V2<R>::T* __restrict__ A,
+                                                   typename V2<R>::T* __restrict__ B, KParams p,
+                                                   const DevScalars* __restrict__ sc,
+                                                   const double* __restrict__ omega_tab, int mask) {
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (ix >= p.nx || iy >= p.ny) return;
+    const R Ot = omega_tab ? (R)(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440) : (R)p.omega_t;
+    pointwise_at<R, IMAG>(A, B, p, sc->scale, Ot, ix, iy, mask);
 }
 
 // ---------------------------------------------------------------------------
@@ -520,16 +531,11 @@ __global__ void __launch_bounds__(256) k_norms(const typename V2<R>::T* A, size_
 // ---------------------------------------------------------------------------
 constexpr int NACC = 11;
 
+// The FP64 observable densities of grid point (ix, iy) of one grid, added to v.
 template <typename R>
-__global__ void __launch_bounds__(128) k_observables(const typename V2<R>::T* __restrict__ A, KParams p, double omega_t,
-                                                     double* partials, DevScalars* sc) {
-    __shared__ double red[4 * NACC];
-    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
-    double v[NACC];
-#pragma unroll
-    for (int q = 0; q < NACC; q++) v[q] = 0.0;
-    if (ix < p.nx && iy < p.ny) {
+__device__ __forceinline__ void obs_point(const typename V2<R>::T* __restrict__ A, const KParams& p, double omega_t,
+                                          int ix, int iy, double (&v)[NACC]) {
+    {
         const size_t plane = (size_t)p.nx * p.ny;
         const size_t c = (size_t)iy * p.nx + ix;
         cx<double> u[3];
@@ -596,6 +602,42 @@ __global__ void __launch_bounds__(128) k_observables(const typename V2<R>::T* __
             v[10] = -(cmul(u[0], h[0]).re + cmul(u[1], h[1]).re + cmul(u[2], h[2]).re);
         }
     }
+}
+
+// The SGPE_NOBS observables from the grid sums s (obs_point summed over the grid).
+__device__ __forceinline__ void obs_finish(const double (&s)[NACC], double w, double* o, int* err) {
+    double N0 = s[0] * w, N1 = s[1] * w, N2 = s[2] * w, Nt = N0 + N1 + N2;
+    double ekin = s[6] * w, etrap = s[7] * w, eint = s[8] * w, erabi = s[9] * w, eso = s[10] * w;
+    o[0] = N0;
+    o[1] = N1;
+    o[2] = N2;
+    o[3] = Nt;
+    o[4] = N0 - N2;
+    o[5] = ekin + etrap + eint + erabi + eso;
+    o[6] = Nt > 0.0 ? (ekin + etrap + eso + erabi + 2.0 * eint) / Nt : 0.0;
+    o[7] = s[0] > 0.0 ? sqrt(s[3] / s[0]) : 0.0;
+    o[8] = s[1] > 0.0 ? sqrt(s[4] / s[1]) : 0.0;
+    o[9] = s[2] > 0.0 ? sqrt(s[5] / s[2]) : 0.0;
+    double ss = s[0] + s[1] + s[2];
+    o[10] = ss > 0.0 ? sqrt((s[3] + s[4] + s[5]) / ss) : 0.0;
+    o[11] = ekin;
+    o[12] = etrap;
+    o[13] = eint;
+    o[14] = erabi;
+    o[15] = eso;
+    if (!(isfinite(Nt))) *err |= 1;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_observables(const typename V2<R>::T* __restrict__ A, KParams p, double omega_t,
+                                                     double* partials, DevScalars* sc) {
+    __shared__ double red[4 * NACC];
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    double v[NACC];
+#pragma unroll
+    for (int q = 0; q < NACC; q++) v[q] = 0.0;
+    if (ix < p.nx && iy < p.ny) obs_point<R>(A, p, omega_t, ix, iy, v);
     // block reduce (blockDim.x * blockDim.y threads, flattened)
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y) >> 5;
@@ -633,28 +675,7 @@ __global__ void __launch_bounds__(128) k_observables(const typename V2<R>::T* __
         for (int q = 0; q < NACC; q++)
             for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
         if (tid == 0) {
-            double w = p.cell;
-            double N0 = s[0] * w, N1 = s[1] * w, N2 = s[2] * w, Nt = N0 + N1 + N2;
-            double ekin = s[6] * w, etrap = s[7] * w, eint = s[8] * w, erabi = s[9] * w, eso = s[10] * w;
-            double* o = sc->obs;
-            o[0] = N0;
-            o[1] = N1;
-            o[2] = N2;
-            o[3] = Nt;
-            o[4] = N0 - N2;
-            o[5] = ekin + etrap + eint + erabi + eso;
-            o[6] = Nt > 0.0 ? (ekin + etrap + eso + erabi + 2.0 * eint) / Nt : 0.0;
-            o[7] = s[0] > 0.0 ? sqrt(s[3] / s[0]) : 0.0;
-            o[8] = s[1] > 0.0 ? sqrt(s[4] / s[1]) : 0.0;
-            o[9] = s[2] > 0.0 ? sqrt(s[5] / s[2]) : 0.0;
-            double ss = s[0] + s[1] + s[2];
-            o[10] = ss > 0.0 ? sqrt((s[3] + s[4] + s[5]) / ss) : 0.0;
-            o[11] = ekin;
-            o[12] = etrap;
-            o[13] = eint;
-            o[14] = erabi;
-            o[15] = eso;
-            if (!(isfinite(Nt))) sc->err |= 1;
+            obs_finish(s, p.cell, sc->obs, &sc->err);
             sc->ticket[1] = 0u;
         }
     }

@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "../../include/sgpe.h"
+#include "sgpe_device.cuh"
+
 namespace sgpe {
 
 struct KParams;
@@ -67,6 +70,11 @@ cudaError_t reset_scale(cudaStream_t s, DevScalars* sc);
 // next pending scale, advance the step counter (one block).
 cudaError_t finalize_step(cudaStream_t s, const double* partials, int nblk, double cell, int renorm, double mag,
                           int advance, DevScalars* sc);
+
+// Validation of sgpe_params (nullptr when valid, else the reason) and the kernel
+// constants of one grid.
+const char* check_params(const sgpe_params* p);
+KParams make_kparams(int dim, int nx, int ny, double dx, double dy, const sgpe_params* p);
 
 // Store the message that sgpe_last_error(NULL) returns on this host thread.
 void set_thread_error(const char* msg);

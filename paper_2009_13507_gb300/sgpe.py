@@ -29,7 +29,10 @@ SUBSTEP = {"so": 0, "calcnu": 1, "herm": 2, "cn_x": 3, "cn_y": 4, "renorm": 5}
 EXPORTS = ("sgpe_init_grid", "sgpe_workspace_bytes", "sgpe_bind", "sgpe_set_params", "sgpe_step_imag",
            "sgpe_step_real", "sgpe_normalize", "sgpe_energy", "sgpe_set_state", "sgpe_get_state", "sgpe_load_state",
            "sgpe_substep", "sgpe_profile_steps", "sgpe_observables_noalloc", "sgpe_launches_per_step",
-           "sgpe_last_error", "sgpe_destroy")
+           "sgpe_last_error", "sgpe_destroy",
+           "sgpe_batch_create", "sgpe_batch_sizes", "sgpe_batch_offsets", "sgpe_batch_bind",
+           "sgpe_batch_load_state", "sgpe_batch_step_imag", "sgpe_batch_step_real", "sgpe_batch_energy",
+           "sgpe_batch_autotune", "sgpe_batch_launches_per_step", "sgpe_batch_last_error", "sgpe_batch_destroy")
 
 
 class SgpeError(RuntimeError):
@@ -74,6 +77,18 @@ def load():
         "sgpe_launches_per_step": (I, [P]),
         "sgpe_last_error": (ctypes.c_char_p, [P]),
         "sgpe_destroy": (I, [P]),
+        "sgpe_batch_create": (I, [ctypes.POINTER(P), I, P, I, P]),
+        "sgpe_batch_sizes": (I, [P, ctypes.POINTER(S), ctypes.POINTER(S)]),
+        "sgpe_batch_offsets": (I, [P, P]),
+        "sgpe_batch_bind": (I, [P, P, P]),
+        "sgpe_batch_load_state": (I, [P, P]),
+        "sgpe_batch_step_imag": (I, [P, I]),
+        "sgpe_batch_step_real": (I, [P, I]),
+        "sgpe_batch_energy": (I, [P, P]),
+        "sgpe_batch_autotune": (I, [P, I, P]),
+        "sgpe_batch_launches_per_step": (I, [P]),
+        "sgpe_batch_last_error": (ctypes.c_char_p, [P]),
+        "sgpe_batch_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -170,6 +185,7 @@ class Solver:
         """Copy a device tensor (same shape and dtype as the state) into the state (sgpe_load_state)."""
         assert psi_dev.is_cuda and psi_dev.dtype == self.cdtype and psi_dev.is_contiguous()
         assert psi_dev.numel() == 3 * self.ny * self.nx
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
         self._check(self.lib.sgpe_load_state(self.ctx, psi_dev.data_ptr()))
 
     def get_state(self) -> np.ndarray:
@@ -225,3 +241,112 @@ class Solver:
 
     def synchronize(self):
         self.stream.synchronize()
+
+
+class Instance(ctypes.Structure):
+    """sgpe_instance (include/sgpe.h)."""
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double),
+                ("dy", ctypes.c_double), ("params", Params)]
+
+
+class BatchSolver:
+    """Many independent grids advanced together (sgpe_batch_*); state and workspace are torch tensors."""
+
+    def __init__(self, instances, precision="c128", device="cuda:0", stream=None):
+        """instances: list of dicts with dim, nx, ny, dx, dy and the Physics fields."""
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.precision = precision
+        self.device = torch.device(device)
+        self.cdtype = torch.complex128 if precision == "c128" else torch.complex64
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        self.specs = []
+        arr = (Instance * len(instances))()
+        for i, d in enumerate(instances):
+            dim = int(d["dim"])
+            phys = Physics(**{k: d[k] for k in Physics.__dataclass_fields__ if k in d})
+            nx, ny = int(d["nx"]), (int(d.get("ny", 1)) if dim == 2 else 1)
+            dx = float(d.get("dx", 0.05))
+            dy = float(d.get("dy", dx)) if dim == 2 else dx
+            arr[i] = Instance(dim, nx, ny, dx, dy, phys.c())
+            self.specs.append(dict(dim=dim, nx=nx, ny=ny, dx=dx, dy=dy, physics=phys))
+        self.n = len(instances)
+        self.b = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self.lib.sgpe_batch_create(ctypes.byref(self.b), self.n, ctypes.cast(arr, ctypes.c_void_p),
+                                            C128 if precision == "c128" else C64,
+                                            ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != OK:
+            msg = self.lib.sgpe_last_error(None)
+            raise SgpeError(rc, msg.decode() if msg else "sgpe_batch_create")
+        ne, nb = ctypes.c_size_t(), ctypes.c_size_t()
+        self._check(self.lib.sgpe_batch_sizes(self.b, ctypes.byref(ne), ctypes.byref(nb)))
+        offs = np.zeros(self.n, dtype=np.uint64)
+        self._check(self.lib.sgpe_batch_offsets(self.b, offs.ctypes.data))
+        self.offsets = [int(o) for o in offs]
+        self.psi = torch.zeros(int(ne.value), dtype=self.cdtype, device=self.device)
+        self.workspace = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        self._check(self.lib.sgpe_batch_bind(self.b, self.psi.data_ptr(), self.workspace.data_ptr()))
+
+    def _check(self, rc):
+        if rc != OK:
+            msg = self.lib.sgpe_batch_last_error(self.b)
+            raise SgpeError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if self.b:
+            self.lib.sgpe_batch_destroy(self.b)
+            self.b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def view(self, i):
+        """Instance i's state as a [3][ny][nx] view of the batch state tensor."""
+        s = self.specs[i]
+        n = 3 * s["ny"] * s["nx"]
+        return self.psi[self.offsets[i]:self.offsets[i] + n].view(3, s["ny"], s["nx"])
+
+    def pack(self, states):
+        """Batch state tensor (device) holding the given per-instance host states."""
+        out = self.torch.zeros_like(self.psi)
+        for i, st in enumerate(states):
+            s = self.specs[i]
+            n = 3 * s["ny"] * s["nx"]
+            out[self.offsets[i]:self.offsets[i] + n] = self.torch.from_numpy(
+                np.ascontiguousarray(np.asarray(st).reshape(-1))).to(self.cdtype).to(self.device)
+        return out
+
+    def load_state(self, psi_dev):
+        assert psi_dev.shape == self.psi.shape and psi_dev.dtype == self.cdtype
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+        self._check(self.lib.sgpe_batch_load_state(self.b, psi_dev.data_ptr()))
+
+    def step_imag(self, nsteps):
+        self._check(self.lib.sgpe_batch_step_imag(self.b, int(nsteps)))
+
+    def step_real(self, nsteps):
+        self._check(self.lib.sgpe_batch_step_real(self.b, int(nsteps)))
+
+    def energy(self) -> np.ndarray:
+        """(n, NOBS) observables; applies the pending scales to the state."""
+        out = np.zeros((self.n, NOBS))
+        self._check(self.lib.sgpe_batch_energy(self.b, out.ctypes.data))
+        return out
+
+    def states(self):
+        """Host copies of every instance's state (call energy() first to apply pending scales)."""
+        self.stream.synchronize()
+        return [self.view(i).cpu().numpy() for i in range(self.n)]
+
+    def autotune(self, nsteps=4):
+        ch = np.zeros(2, dtype=np.int32)
+        self._check(self.lib.sgpe_batch_autotune(self.b, int(nsteps), ch.ctypes.data))
+        return int(ch[0]), int(ch[1])
+
+    def launches_per_step(self):
+        return int(self.lib.sgpe_batch_launches_per_step(self.b))
