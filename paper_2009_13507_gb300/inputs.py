@@ -83,6 +83,17 @@ def random_state(shape, seed: int, cell: float, envelope: float = 0.0) -> np.nda
     return _unit(psi.astype(np.complex128), cell)
 
 
+def gaussian_target(nx: int, ny: int, dx: float, dy: float, seed: int) -> np.ndarray:
+    """[ny][nx] float64 target density: a Gaussian of width w ~ U[0.8, 1.2] centred at
+    (x0, y0) ~ U[-0.5, 0.5]^2 (y0 = 0 in 1D, ny = 1), normalised to unit integral."""
+    u = uniform(seed, 3)
+    w, x0, y0 = 0.8 + 0.4 * u[0], u[1] - 0.5, (u[2] - 0.5 if ny > 1 else 0.0)
+    x = grid_x(nx, dx)[None, :]
+    y = grid_x(ny, dy)[:, None] if ny > 1 else np.zeros((1, 1))
+    rho = np.exp(-((x - x0) ** 2 + (y - y0) ** 2) / (w * w))
+    return rho / (rho.sum() * dx * (dy if ny > 1 else 1.0))
+
+
 def batch_table(seed: int, n1d: int = 32, n2d: int = 32):
     """Instance table of a batched workload: n1d 1D instances with nx ~ U{128..1024},
     n2d 2D instances n x n with n ~ U{128..384}; per instance
