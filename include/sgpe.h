@@ -222,6 +222,37 @@ sgpe_status sgpe_observables_noalloc(const void* psi_dev, int dim, int nx, int n
                                      sgpe_precision prec, const sgpe_params* p, double* obs_dev, void* cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * Differentiation form: gradient of the final-density loss
+ *     L = dx dy sum_r (rho_N(r) - rho_tgt(r))^2,  rho = sum_j |psi_j|^2,
+ * after nsteps real-time steps (Sec. 3, z = i dt) from the bound state, with
+ * respect to the per-step Rabi strengths Omega_n and the trap frequencies
+ * (wx, wy) of V = (wx^2 x^2 + wy^2 y^2)/2, by a hand-written adjoint of the
+ * discrete propagator (the exact reverse of every substep) with a state
+ * checkpoint every checkpoint_every steps and recomputation in between.
+ * ------------------------------------------------------------------------ */
+
+/* Bytes of the caller-owned adjoint workspace for nsteps and checkpoint_every. */
+sgpe_status sgpe_adjoint_workspace_bytes(const sgpe_ctx* ctx, int nsteps, int checkpoint_every, size_t* bytes);
+
+/*
+ * Run nsteps real-time steps from the bound state (which ends as psi_N; a
+ * pending renormalisation scale is applied first), with Omega_n from
+ * omega_dev (device, nsteps doubles) and the other parameters from
+ * sgpe_set_params; then compute L and its gradient.
+ *  rho_target_dev  device [ny][nx] doubles (the target density).
+ *  adj_workspace   device, sgpe_adjoint_workspace_bytes bytes, 256-byte aligned.
+ *  loss_out        host, 1 double (nullable); dw_out host, 2 doubles dL/dwx,
+ *                  dL/dwy (nullable; dL/dwy = 0 in 1D).
+ *  domega_dev      device, nsteps doubles: dL/dOmega_n.
+ * Reductions are FP64 in both precisions. Synchronises the stream.
+ * SGPE_ESTATE without bound buffers or parameters; SGPE_EINVAL for bad sizes,
+ * null or misaligned pointers.
+ */
+sgpe_status sgpe_adjoint_loss_grad(sgpe_ctx* ctx, int nsteps, const double* omega_dev, const double* rho_target_dev,
+                                   int checkpoint_every, void* adj_workspace, double* loss_out, double* domega_dev,
+                                   double* dw_out);
+
+/* ------------------------------------------------------------------------
  * Batched form: many independent grids advanced together by the split step of
  * Sec. 3 (same substeps and readings as a single grid), each with its own size
  * and physical parameters, in grouped launches (one per kernel kind and chunk

@@ -1,0 +1,443 @@
+// sgpe_adjoint.cu -- hand-written adjoint of the real-time split step
+// (arXiv:2009.13507, Sec. 3 and Appendix A) for the gradient of
+//     L = dx dy sum_r (rho_N(r) - rho_tgt(r))^2,   rho = sum_j |psi_j|^2,
+// with respect to the per-step Rabi strengths Omega_n and the trap
+// frequencies (wx, wy), by checkpoint-and-recompute.
+//
+// Gradient convention: g = dL/dRe(psi) + i dL/dIm(psi), so dL = Re(conj(g) dpsi).
+// One forward step is psi_{n+1} = CNy CNx HERM_n CALCNU SO (psi_n). Backwards:
+//   CN along y and x are complex-linear maps M with M^H = the same sweep with
+//   dt -> -dt (tables of bt = -i dt/(4h^2)); SO is I - i dt H_SO with H_SO
+//   Hermitian, so its adjoint is the SO substep with dt -> -dt; CALCNU and HERM
+//   are non-holomorphic (they depend on |psi|^2 and conj(psi)) and get explicit
+//   reverse passes below, recomputing their inputs from the stored psi_n.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/sgpe.h"
+#include "sgpe_cn.cuh"
+#include "sgpe_kernels.cuh"
+#include "sgpe_launch.h"
+
+namespace sgpe {
+
+// d s/d C^2 and d k/d C^2 of the real-time HERM coefficients
+// s = sin(dt C)/C, k = (cos(dt C) - 1)/C^2 (series in v = -(dt C)^2 when small).
+template <typename R> __device__ __forceinline__ void herm_coeff_derivs(R C2, R dt, R* ds, R* dk) {
+    R w = dt * dt * C2;
+    if (w <= R(1.0 / 1024.0)) {
+        R v = -w;
+        // s  = dt sum v^n/(2n+1)!    -> ds/dC2 = -dt^3 sum_{n>=1} n v^{n-1}/(2n+1)!
+        // k  = -dt^2 sum v^n/(2n+2)! -> dk/dC2 = dt^4 sum_{n>=1} n v^{n-1}/(2n+2)!
+        R ps = fma(fma(fma(R(4.0 / 362880.0), v, R(3.0 / 5040.0)), v, R(2.0 / 120.0)), v, R(1.0 / 6.0));
+        R pk = fma(fma(fma(R(4.0 / 3628800.0), v, R(3.0 / 40320.0)), v, R(2.0 / 720.0)), v, R(1.0 / 24.0));
+        *ds = -dt * dt * dt * ps;
+        *dk = dt * dt * dt * dt * pk;
+        return;
+    }
+    R C = sqrt(C2), x = dt * C;
+    R sn = sin(x), cs = cos(x);
+    *ds = (x * cs - sn) / (R(2) * C2 * C);
+    *dk = (-x * sn - R(2) * (cs - R(1))) / (R(2) * C2 * C2);
+}
+
+template <typename R> __device__ __forceinline__ R re_cmul(cx<R> a, cx<R> b) {  // Re(conj(a) b)
+    return fma(a.re, b.re, a.im * b.im);
+}
+template <typename R> __device__ __forceinline__ R im_cmul(cx<R> a, cx<R> b) {  // Im(conj(a) b)
+    return fma(a.re, b.im, -a.im * b.re);
+}
+
+// Reverse pass of HERM (real time): u is the HERM input, g holds the gradient
+// w.r.t. its output on entry and w.r.t. its input on exit; returns dL/dOt.
+template <typename R>
+__device__ __forceinline__ R herm_adjoint(const cx<R> (&u)[3], cx<R> (&g)[3], R c2, R Ot, R dt) {
+    const cx<R> p = u[0], z = u[1], m = u[2];
+    cx<R> a = cmul(m, z);
+    a = {fma(c2, a.re, Ot), c2 * a.im};
+    cx<R> b = cmul(z, p);
+    b = {fma(c2, b.re, Ot), c2 * b.im};
+    const R na = nrm(a), nb = nrm(b), C2 = na + nb;
+    R s, k, ds, dk;
+    herm_coeffs<false>(C2, dt, &s, &k);
+    herm_coeff_derivs<R>(C2, dt, &ds, &dk);
+    const cx<R> Ap = mul(a, z), A0 = add(cmul(a, p), mul(b, m)), Am = cmul(b, z);
+    const cx<R> ab = mul(a, b);
+    const cx<R> Bp = axpy(na, p, mul(ab, m)), B0 = scl(C2, z), Bm = axpy(nb, m, cmul(ab, p));
+    const cx<R> gP = g[0], gZ = g[1], gM = g[2];
+    cx<R> gp = gP, gz = gZ, gm = gM;
+    // P = p - i s Ap + k Bp (and likewise Z, M)
+    R gs = im_cmul(gP, Ap) + im_cmul(gZ, A0) + im_cmul(gM, Am);
+    R gk = re_cmul(gP, Bp) + re_cmul(gZ, B0) + re_cmul(gM, Bm);
+    const cx<R> is = {R(0), s};
+    const cx<R> gAp = mul(is, gP), gA0 = mul(is, gZ), gAm = mul(is, gM);
+    const cx<R> gBp = scl(k, gP), gB0 = scl(k, gZ), gBm = scl(k, gM);
+    // Bp = na p + ab m
+    gp = axpy(na, gBp, gp);
+    R gna = re_cmul(gBp, p);
+    cx<R> gab = cmul(m, gBp);
+    gm = add(gm, cmul(ab, gBp));
+    // B0 = C2 z
+    gz = axpy(C2, gB0, gz);
+    R gC2 = re_cmul(gB0, z);
+    // Bm = conj(ab) p + nb m
+    gp = add(gp, mul(ab, gBm));
+    gab = add(gab, mul(p, cj(gBm)));
+    gm = axpy(nb, gBm, gm);
+    R gnb = re_cmul(gBm, m);
+    // Ap = a z
+    cx<R> ga = cmul(z, gAp);
+    gz = add(gz, cmul(a, gAp));
+    // A0 = conj(a) p + b m
+    ga = add(ga, mul(p, cj(gA0)));
+    gp = add(gp, mul(a, gA0));
+    cx<R> gb = cmul(m, gA0);
+    gm = add(gm, cmul(b, gA0));
+    // Am = conj(b) z
+    gb = add(gb, mul(z, cj(gAm)));
+    gz = add(gz, mul(b, gAm));
+    // ab = a b
+    ga = add(ga, cmul(b, gab));
+    gb = add(gb, cmul(a, gab));
+    // s(C2), k(C2); C2 = |a|^2 + |b|^2
+    gC2 = fma(gs, ds, fma(gk, dk, gC2));
+    gna += gC2;
+    gnb += gC2;
+    ga = axpy(R(2) * gna, a, ga);
+    gb = axpy(R(2) * gnb, b, gb);
+    // a = c2 conj(m) z + Ot ; b = c2 conj(z) p + Ot
+    gm = axpy(c2, mul(z, cj(ga)), gm);
+    gz = axpy(c2, mul(m, ga), gz);
+    gz = axpy(c2, mul(p, cj(gb)), gz);
+    gp = axpy(c2, mul(z, gb), gp);
+    g[0] = gp;
+    g[1] = gz;
+    g[2] = gm;
+    return ga.re + gb.re;
+}
+
+// Reverse pass of CALCNU (real time): u1 is the CALCNU input, g the gradient
+// w.r.t. its output on entry and w.r.t. u1 on exit; W = sum_j dt Im(conj(g_j) u2_j)
+// is returned for the trap gradient (dmu_j/dV = 1).
+template <typename R>
+__device__ __forceinline__ R calcnu_adjoint(const cx<R> (&u1)[3], cx<R> (&g)[3], R V, R c0, R c2, R dt) {
+    const R rp = nrm(u1[0]), r0 = nrm(u1[1]), rm = nrm(u1[2]);
+    const R base = fma(c0, rp + r0 + rm, V);
+    const R mu[3] = {fma(c2, rp - rm + r0, base), fma(c2, rp + rm, base), fma(c2, rm - rp + r0, base)};
+    R w[3];
+    cx<R> e[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        R s, c;
+        sincos_small(dt * mu[j], &s, &c);
+        e[j] = {c, -s};  // exp(-i dt mu_j)
+        const cx<R> u2 = mul(e[j], u1[j]);
+        w[j] = dt * im_cmul(g[j], u2);
+    }
+    const R cp = c0 + c2, cm = c0 - c2;
+    const R a[3] = {cp * w[0] + cp * w[1] + cm * w[2], cp * w[0] + c0 * w[1] + cp * w[2],
+                    cm * w[0] + cp * w[1] + cp * w[2]};
+#pragma unroll
+    for (int k = 0; k < 3; k++) g[k] = axpy(R(2) * a[k], u1[k], cmul(e[k], g[k]));
+    return w[0] + w[1] + w[2];
+}
+
+// Per point: recompute SO and CALCNU of psi_n, reverse HERM and CALCNU on g
+// (in place), and accumulate FP64 partial sums of dL/dOt and the trap sums.
+// Block 32 x 4, one point per thread.
+template <typename R>
+__global__ void __launch_bounds__(128) ka_pointwise(const typename V2<R>::T* __restrict__ psi,
+                                                    typename V2<R>::T* __restrict__ G, KParams p, double Ot,
+                                                    double* part) {
+    __shared__ double red[4 * 3];
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    double acc[3] = {0.0, 0.0, 0.0};  // dL/dOt, sum W wx x^2, sum W wy y^2
+    if (ix < p.nx && iy < p.ny) {
+        const size_t plane = (size_t)p.nx * p.ny, c = (size_t)iy * p.nx + ix;
+        const cx<R> zero = {R(0), R(0)};
+        cx<R> u[3];
+#pragma unroll
+        for (int j = 0; j < 3; j++) u[j] = ld<R>(psi, j * plane + c);
+        if (p.so_case) {
+            cx<R> X[3], Y[3];
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                cx<R> xp = (ix + 1 < p.nx) ? ld<R>(psi, j * plane + c + 1) : zero;
+                cx<R> xm = (ix > 0) ? ld<R>(psi, j * plane + c - 1) : zero;
+                X[j] = sub(xp, xm);
+                if (p.dim == 2) {
+                    cx<R> yp = (iy + 1 < p.ny) ? ld<R>(psi, j * plane + c + p.nx) : zero;
+                    cx<R> ym = (iy > 0) ? ld<R>(psi, j * plane + c - p.nx) : zero;
+                    Y[j] = sub(yp, ym);
+                } else {
+                    Y[j] = zero;
+                }
+            }
+            R gx[3] = {(R)p.hx, (R)p.hx, (R)p.hx}, gy[3] = {(R)p.hy, (R)p.hy, (R)p.hy};
+            so_point<false>(u, X, Y, gx, gy, p.so_case);
+        }
+        const int kx = ix - p.nx / 2, ky = iy - p.ny / 2;
+        const R V = (R)p.vx * (R)(kx * kx) + (p.dim == 2 ? (R)p.vy * (R)(ky * ky) : R(0));
+        const R dt = (R)p.dt;
+        cx<R> u2[3] = {u[0], u[1], u[2]};
+        calcnu_point<false>(u2, V, (R)p.c0, (R)p.c2, dt);
+        cx<R> g[3];
+#pragma unroll
+        for (int j = 0; j < 3; j++) g[j] = ld<R>(G, j * plane + c);
+        const R gOt = herm_adjoint<R>(u2, g, (R)p.c2, (R)Ot, dt);
+        const R W = calcnu_adjoint<R>(u, g, V, (R)p.c0, (R)p.c2, dt);
+#pragma unroll
+        for (int j = 0; j < 3; j++) st<R>(G, j * plane + c, g[j]);
+        acc[0] = (double)gOt;
+        // dV/dwx = wx x^2, dV/dwy = wy y^2
+        acc[1] = (double)W * p.wx * (double)(kx * kx) * p.dx * p.dx;
+        acc[2] = p.dim == 2 ? (double)W * p.wy * (double)(ky * ky) * p.dy * p.dy : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 3; q++)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+    if ((tid & 31) == 0)
+        for (int q = 0; q < 3; q++) red[(tid >> 5) * 3 + q] = acc[q];
+    __syncthreads();
+    if (tid == 0) {
+        const int nw = (blockDim.x * blockDim.y) >> 5;
+        const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+        for (int q = 0; q < 3; q++) {
+            double s = 0.0;
+            for (int w = 0; w < nw; w++) s += red[w * 3 + q];
+            part[3 * blk + q] = s;
+        }
+    }
+}
+
+// dL/dpsi of the final-density loss and the loss partial sums: g_j = 4 cell (rho - rho_tgt) psi_j.
+template <typename R>
+__global__ void __launch_bounds__(128) ka_loss(const typename V2<R>::T* __restrict__ psi,
+                                               const double* __restrict__ tgt, typename V2<R>::T* __restrict__ G,
+                                               KParams p, double* part) {
+    __shared__ double red[4];
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (ix < p.nx && iy < p.ny) {
+        const size_t plane = (size_t)p.nx * p.ny, c = (size_t)iy * p.nx + ix;
+        cx<R> u[3];
+        double rho = 0.0;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            u[j] = ld<R>(psi, j * plane + c);
+            rho += (double)u[j].re * (double)u[j].re + (double)u[j].im * (double)u[j].im;
+        }
+        const double d = rho - tgt[c];
+        acc = p.cell * d * d;
+        const R f = (R)(4.0 * p.cell * d);
+#pragma unroll
+        for (int j = 0; j < 3; j++) st<R>(G, j * plane + c, scl(f, u[j]));
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        const int nw = (blockDim.x * blockDim.y) >> 5;
+        double s = 0.0;
+        for (int w = 0; w < nw; w++) s += red[w];
+        part[blockIdx.y * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// One block: out[0] = sum of part[3b + 0] / sqrt2 (dL/dOmega_n) and dw[0..1] +=
+// sums of part[3b + 1..2]; with stride 1 (loss), out[0] = sum part[b].
+__global__ void __launch_bounds__(256) ka_reduce(const double* part, int nblk, int stride, double* out, double* dw) {
+    __shared__ double red[8 * 3];
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+        for (int q = 0; q < stride; q++) s[q] += part[(size_t)stride * b + q];
+    block_reduce<3>(s, red);
+    if (threadIdx.x == 0) {
+        if (stride == 1) {
+            out[0] = s[0];
+        } else {
+            out[0] = s[0] * 0.70710678118654752440;
+            dw[0] += s[1];
+            dw[1] += s[2];
+        }
+    }
+}
+
+}  // namespace sgpe
+
+using namespace sgpe;
+
+// ---------------------------------------------------------------------------
+// Host driver
+// ---------------------------------------------------------------------------
+namespace {
+
+struct AdjLayout {
+    size_t ckpt, seg, g, g2, part, scal, total;
+    int nck, K;
+};
+
+AdjLayout adj_layout(int nx, int ny, int esz, int nsteps, int K) {
+    AdjLayout L;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t st = al((size_t)3 * nx * ny * esz);
+    L.K = K;
+    L.nck = (nsteps + K - 1) / K;
+    size_t o = 0;
+    L.ckpt = o;
+    o += st * (size_t)(L.nck > 0 ? L.nck : 1);
+    L.seg = o;
+    o += st * (size_t)K;
+    L.g = o;
+    o += st;
+    L.g2 = o;
+    o += st;
+    L.part = o;
+    o = al(o + sizeof(double) * 3 * (size_t)ceil_div(nx, 32) * ceil_div(ny, 4));
+    L.scal = o;
+    o = al(o + sizeof(double) * 8);
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+// Internal context access (defined in sgpe_api.cu).
+namespace sgpe {
+struct CtxView {
+    int dim, nx, ny, esz;
+    bool dbl;
+    cudaStream_t stream;
+    void* psi;
+    void* mid;
+    DevScalars* sc;
+    const void* const* tabs_real;  // [axis][4], bt = i dt/(4h^2)
+    const void* const* tabs_adj;   // [axis][4], bt = -i dt/(4h^2)
+    const Geometry* geo;
+    KParams kp;
+    double* partials;
+    bool ready;
+};
+bool ctx_view(sgpe_ctx* c, CtxView* v);
+sgpe_status ctx_fail(sgpe_ctx* c, sgpe_status st, const char* msg);
+cudaError_t ctx_flush(sgpe_ctx* c);
+}  // namespace sgpe
+
+template <typename R>
+static cudaError_t adj_forward_step(const CtxView& v, const void* in, void* out, double omega) {
+    KParams k = v.kp;
+    k.omega_t = omega * 0.70710678118654752440;
+    cudaError_t e = Launcher<R>::pointwise(v.stream, false, in, v.mid, k, v.sc, nullptr, 7);
+    if (e) return e;
+    if (v.dim == 2) {
+        if ((e = Launcher<R>::cn_x(v.stream, false, false, v.mid, v.mid, k, v.tabs_real, *v.geo, v.partials, v.sc, 0,
+                                   0)))
+            return e;
+        return Launcher<R>::cn_y(v.stream, false, v.mid, out, k, v.tabs_real + 4, *v.geo, v.partials, v.sc, 0, 0, 0);
+    }
+    return Launcher<R>::cn_x(v.stream, false, false, v.mid, out, k, v.tabs_real, *v.geo, v.partials, v.sc, 0, 0);
+}
+
+template <typename R>
+static sgpe_status adj_run(sgpe_ctx* c, const CtxView& v, int nsteps, const double* omega_host, const double* tgt,
+                           int K, unsigned char* ws, double* loss_out, double* domega_dev, double* dw_out) {
+    using T = typename V2<R>::T;
+    const AdjLayout L = adj_layout(v.nx, v.ny, v.esz, nsteps, K);
+    const size_t st = (size_t)3 * v.nx * v.ny * v.esz;
+    const size_t sst = (st + 255) & ~(size_t)255;
+    cudaStream_t s = v.stream;
+    auto ckpt = [&](int i) { return (void*)(ws + L.ckpt + sst * i); };
+    auto seg = [&](int i) { return (void*)(ws + L.seg + sst * i); };
+    T* G = (T*)(ws + L.g);
+    T* G2 = (T*)(ws + L.g2);
+    double* part = (double*)(ws + L.part);
+    double* scal = (double*)(ws + L.scal);  // [0] loss, [1..2] dw
+    dim3 blk(32, 4), grd(ceil_div(v.nx, 32), ceil_div(v.ny, 4));
+    const int nblk = grd.x * grd.y;
+    cudaError_t e = cudaMemsetAsync(scal, 0, sizeof(double) * 8, s);
+    // forward with checkpoints: the bound state psi holds psi_0 and ends as psi_N
+    for (int n = 0; n < nsteps && !e; n++) {
+        if (n % K == 0) e = cudaMemcpyAsync(ckpt(n / K), v.psi, st, cudaMemcpyDeviceToDevice, s);
+        if (!e) e = adj_forward_step<R>(v, v.psi, v.psi, omega_host[n]);
+    }
+    // loss and its gradient at psi_N
+    if (!e) {
+        ka_loss<R><<<grd, blk, 0, s>>>((const T*)v.psi, tgt, G, v.kp, part);
+        ka_reduce<<<1, 256, 0, s>>>(part, nblk, 1, scal, nullptr);
+        e = cudaGetLastError();
+    }
+    KParams kneg = v.kp;  // SO with dt -> -dt
+    kneg.hx = -kneg.hx;
+    kneg.hy = -kneg.hy;
+    for (int sg = L.nck - 1; sg >= 0 && !e; sg--) {
+        const int s0 = sg * K, s1 = (s0 + K < nsteps) ? s0 + K : nsteps;
+        e = cudaMemcpyAsync(seg(0), ckpt(sg), st, cudaMemcpyDeviceToDevice, s);
+        for (int k2 = 0; k2 + 1 < s1 - s0 && !e; k2++) e = adj_forward_step<R>(v, seg(k2), seg(k2 + 1), omega_host[s0 + k2]);
+        for (int n = s1 - 1; n >= s0 && !e; n--) {
+            if (v.dim == 2)
+                e = Launcher<R>::cn_y(s, false, G, G, v.kp, v.tabs_adj + 4, *v.geo, v.partials, v.sc, 0, 0, 0);
+            if (!e) e = Launcher<R>::cn_x(s, false, false, G, G, v.kp, v.tabs_adj, *v.geo, v.partials, v.sc, 0, 0);
+            if (!e) {
+                ka_pointwise<R><<<grd, blk, 0, s>>>((const T*)seg(n - s0), G, v.kp, omega_host[n] * 0.70710678118654752440,
+                                                    part);
+                ka_reduce<<<1, 256, 0, s>>>(part, nblk, 3, domega_dev + n, scal + 1);
+                e = cudaGetLastError();
+            }
+            if (!e) e = Launcher<R>::pointwise(s, false, G, G2, kneg, v.sc, nullptr, 1);
+            T* t = G;
+            G = G2;
+            G2 = t;
+        }
+    }
+    double h[3] = {0, 0, 0};
+    if (!e) e = cudaMemcpyAsync(h, scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return ctx_fail(c, SGPE_ECUDA, cudaGetErrorString(e));
+    if (loss_out) *loss_out = h[0];
+    if (dw_out) {
+        dw_out[0] = h[1];
+        dw_out[1] = h[2];
+    }
+    return SGPE_OK;
+}
+
+extern "C" {
+
+sgpe_status sgpe_adjoint_workspace_bytes(const sgpe_ctx* c, int nsteps, int checkpoint_every, size_t* bytes) {
+    CtxView v;
+    if (!c || !bytes || nsteps < 1 || checkpoint_every < 1) return SGPE_EINVAL;
+    if (!ctx_view((sgpe_ctx*)c, &v)) return SGPE_ESTATE;
+    *bytes = adj_layout(v.nx, v.ny, v.esz, nsteps, checkpoint_every).total;
+    return SGPE_OK;
+}
+
+sgpe_status sgpe_adjoint_loss_grad(sgpe_ctx* c, int nsteps, const double* omega_dev, const double* rho_target_dev,
+                                   int checkpoint_every, void* adj_workspace, double* loss_out, double* domega_dev,
+                                   double* dw_out) {
+    if (!c) return SGPE_EINVAL;
+    CtxView v;
+    if (!ctx_view(c, &v) || !v.ready) return ctx_fail(c, SGPE_ESTATE, "adjoint: no buffers bound or no parameters");
+    if (nsteps < 1 || checkpoint_every < 1 || !omega_dev || !rho_target_dev || !adj_workspace || !domega_dev)
+        return ctx_fail(c, SGPE_EINVAL, "adjoint: bad arguments");
+    if (((uintptr_t)adj_workspace & 255) || ((uintptr_t)omega_dev & 7) || ((uintptr_t)rho_target_dev & 7) ||
+        ((uintptr_t)domega_dev & 7))
+        return ctx_fail(c, SGPE_EINVAL, "adjoint: misaligned buffer");
+    cudaError_t e = ctx_flush(c);  // apply any pending renormalisation: the forward starts at scale 1
+    std::vector<double> om(nsteps);
+    if (!e) e = cudaMemcpyAsync(om.data(), omega_dev, sizeof(double) * nsteps, cudaMemcpyDeviceToHost, v.stream);
+    if (!e) e = cudaStreamSynchronize(v.stream);
+    if (e) return ctx_fail(c, SGPE_ECUDA, cudaGetErrorString(e));
+    return v.dbl ? adj_run<double>(c, v, nsteps, om.data(), rho_target_dev, checkpoint_every,
+                                   (unsigned char*)adj_workspace, loss_out, domega_dev, dw_out)
+                 : adj_run<float>(c, v, nsteps, om.data(), rho_target_dev, checkpoint_every,
+                                  (unsigned char*)adj_workspace, loss_out, domega_dev, dw_out);
+}
+
+}  // extern "C"

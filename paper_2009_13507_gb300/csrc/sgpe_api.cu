@@ -65,7 +65,7 @@ struct sgpe_ctx {
     // workspace carve-up
     DevScalars* sc;
     void* mid;
-    void* tabs[2][2][4];  // [mode: 0 imag, 1 real][axis: 0 x, 1 y][fa, fg, fp, fq]
+    void* tabs[3][2][4];  // [mode: 0 imag, 1 real, 2 real with -dt (adjoint)][axis: 0 x, 1 y][fa, fg, fp, fq]
     double* partials;
     // parameters
     bool have_params;
@@ -107,7 +107,7 @@ static sgpe_status cuda_fail(sgpe_ctx* c, cudaError_t e, const char* where) {
     } while (0)
 
 struct Layout {
-    size_t sc, mid, tabs[2][2][4], partials, total;
+    size_t sc, mid, tabs[3][2][4], partials, total;
 };
 
 static Layout layout_of(const sgpe_ctx* c) {
@@ -117,7 +117,7 @@ static Layout layout_of(const sgpe_ctx* c) {
     off = align256(off + sizeof(DevScalars));
     L.mid = off;
     off = align256(off + (size_t)3 * c->nx * c->ny * c->esz);
-    for (int m = 0; m < 2; m++)
+    for (int m = 0; m < 3; m++)
         for (int a = 0; a < 2; a++) {
             int n = a == 0 ? c->nx : c->ny;
             for (int k = 0; k < 4; k++) {
@@ -186,6 +186,8 @@ KParams make_kparams(int dim, int nx, int ny, double dx, double dy, const sgpe_p
     k.vx = k.wx2h * dx * dx;
     k.vy = k.wy2h * dy * dy;
     k.omega_t = p->omega / sqrt(2.0);
+    k.wx = p->wx;
+    k.wy = dim == 2 ? p->wy : 0.0;
     k.cell = dim == 2 ? dx * dy : dx;
     k.renorm = p->renorm;
     k.mag = p->mag;
@@ -253,7 +255,7 @@ sgpe_status sgpe_bind(sgpe_ctx* c, void* psi_dev, void* workspace_dev) {
     Layout L = layout_of(c);
     c->sc = (DevScalars*)(c->work + L.sc);
     c->mid = c->work + L.mid;
-    for (int m = 0; m < 2; m++)
+    for (int m = 0; m < 3; m++)
         for (int a = 0; a < 2; a++)
             for (int k = 0; k < 4; k++) c->tabs[m][a][k] = c->work + L.tabs[m][a][k];
     c->partials = (double*)(c->work + L.partials);
@@ -270,13 +272,13 @@ sgpe_status sgpe_set_params(sgpe_ctx* c, const sgpe_params* p) {
     invalidate_graphs(c);
     c->params = *p;
     c->kp = make_kparams(c->dim, c->nx, c->ny, c->dx, c->dy, p);
-    // COEF: Crank-Nicolson tables, bt = z/(4 h^2), z = dt (imaginary) or i dt (real)
-    for (int m = 0; m < 2; m++)
+    // COEF: Crank-Nicolson tables, bt = z/(4 h^2), z = dt (imaginary), i dt (real), -i dt (adjoint)
+    for (int m = 0; m < 3; m++)
         for (int a = 0; a < (c->dim == 2 ? 2 : 1); a++) {
             double h = a == 0 ? c->dx : c->dy;
             int n = a == 0 ? c->nx : c->ny;
             double b = p->dt / (4.0 * h * h);
-            double bre = m == 0 ? b : 0.0, bim = m == 0 ? 0.0 : b;
+            double bre = m == 0 ? b : 0.0, bim = m == 0 ? 0.0 : (m == 1 ? b : -b);
             void** t = c->tabs[m][a];
             cudaError_t e = c->prec == SGPE_C128 ? Launcher<double>::coef(c->stream, t[0], t[1], t[2], t[3], n, bre, bim)
                                                  : Launcher<float>::coef(c->stream, t[0], t[1], t[2], t[3], n, bre, bim);
@@ -596,3 +598,45 @@ sgpe_status sgpe_destroy(sgpe_ctx* c) {
 }
 
 }  // extern "C"
+
+// Internal access for the adjoint translation unit.
+namespace sgpe {
+struct CtxView {
+    int dim, nx, ny, esz;
+    bool dbl;
+    cudaStream_t stream;
+    void* psi;
+    void* mid;
+    DevScalars* sc;
+    const void* const* tabs_real;
+    const void* const* tabs_adj;
+    const Geometry* geo;
+    KParams kp;
+    double* partials;
+    bool ready;
+};
+
+bool ctx_view(sgpe_ctx* c, CtxView* v) {
+    if (!c) return false;
+    v->dim = c->dim;
+    v->nx = c->nx;
+    v->ny = c->ny;
+    v->esz = c->esz;
+    v->dbl = c->prec == SGPE_C128;
+    v->stream = c->stream;
+    v->psi = c->psi;
+    v->mid = c->mid;
+    v->sc = c->sc;
+    v->tabs_real = (const void* const*)&c->tabs[1][0][0];
+    v->tabs_adj = (const void* const*)&c->tabs[2][0][0];
+    v->geo = &c->geo;
+    v->kp = c->kp;
+    v->partials = c->partials;
+    v->ready = c->psi != nullptr && c->have_params;
+    return true;
+}
+
+sgpe_status ctx_fail(sgpe_ctx* c, sgpe_status st, const char* msg) { return fail(c, st, "%s", msg); }
+
+cudaError_t ctx_flush(sgpe_ctx* c) { return flush_any(c); }
+}  // namespace sgpe

@@ -201,6 +201,7 @@ struct KParams {
     double wx2h, wy2h;  // wx^2/2, wy^2/2
     double vx, vy;      // wx^2 dx^2/2, wy^2 dy^2/2 (trap per squared grid index)
     double omega_t;   // Omega/sqrt2 (constant Rabi term)
+    double wx, wy;    // trap frequencies (for the trap gradient of the adjoint)
     double cell;      // dx (1D) or dx*dy
     int renorm;       // 0, 1 (DJ2), 2 (DJ)
     double mag;

@@ -29,7 +29,7 @@ SUBSTEP = {"so": 0, "calcnu": 1, "herm": 2, "cn_x": 3, "cn_y": 4, "renorm": 5}
 EXPORTS = ("sgpe_init_grid", "sgpe_workspace_bytes", "sgpe_bind", "sgpe_set_params", "sgpe_step_imag",
            "sgpe_step_real", "sgpe_normalize", "sgpe_energy", "sgpe_set_state", "sgpe_get_state", "sgpe_load_state",
            "sgpe_substep", "sgpe_profile_steps", "sgpe_observables_noalloc", "sgpe_launches_per_step",
-           "sgpe_last_error", "sgpe_destroy",
+           "sgpe_last_error", "sgpe_destroy", "sgpe_adjoint_workspace_bytes", "sgpe_adjoint_loss_grad",
            "sgpe_batch_create", "sgpe_batch_sizes", "sgpe_batch_offsets", "sgpe_batch_bind",
            "sgpe_batch_load_state", "sgpe_batch_step_imag", "sgpe_batch_step_real", "sgpe_batch_energy",
            "sgpe_batch_autotune", "sgpe_batch_launches_per_step", "sgpe_batch_last_error", "sgpe_batch_destroy")
@@ -77,6 +77,8 @@ def load():
         "sgpe_launches_per_step": (I, [P]),
         "sgpe_last_error": (ctypes.c_char_p, [P]),
         "sgpe_destroy": (I, [P]),
+        "sgpe_adjoint_workspace_bytes": (I, [P, I, I, ctypes.POINTER(S)]),
+        "sgpe_adjoint_loss_grad": (I, [P, I, P, P, I, P, P, P, P]),
         "sgpe_batch_create": (I, [ctypes.POINTER(P), I, P, I, P]),
         "sgpe_batch_sizes": (I, [P, ctypes.POINTER(S), ctypes.POINTER(S)]),
         "sgpe_batch_offsets": (I, [P, P]),
@@ -238,6 +240,57 @@ class Solver:
 
     def launches_per_step(self) -> int:
         return int(self.lib.sgpe_launches_per_step(self.ctx))
+
+    # -- differentiation form ----------------------------------------------------
+    def loss_grad(self, omega_t, rho_tgt, checkpoint_every=50):
+        """Run len(omega_t) real-time steps from the current state (which ends as
+        psi_N) and return (L, dL/dOmega (float64 CUDA tensor), (dL/dwx, dL/dwy))
+        for L = cell * sum (rho_N - rho_tgt)^2 (sgpe_adjoint_loss_grad)."""
+        torch = self.torch
+        om = torch.as_tensor(omega_t, dtype=torch.float64, device=self.device).contiguous()
+        tgt = torch.as_tensor(rho_tgt, dtype=torch.float64, device=self.device).reshape(self.ny, self.nx).contiguous()
+        n = int(om.numel())
+        nb = ctypes.c_size_t()
+        self._check(self.lib.sgpe_adjoint_workspace_bytes(self.ctx, n, int(checkpoint_every), ctypes.byref(nb)))
+        ws = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        dom = torch.zeros(n, dtype=torch.float64, device=self.device)
+        L = np.zeros(1)
+        dw = np.zeros(2)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        self._check(self.lib.sgpe_adjoint_loss_grad(self.ctx, n, om.data_ptr(), tgt.data_ptr(), int(checkpoint_every),
+                                                    ws.data_ptr(), L.ctypes.data, dom.data_ptr(), dw.ctypes.data))
+        return float(L[0]), dom, (float(dw[0]), float(dw[1]))
+
+
+def _rabi_trap_loss_function():
+    import torch
+
+    class RabiTrapLoss(torch.autograd.Function):
+        """L(Omega(t), wx, wy) = cell * sum (rho_N - rho_tgt)^2 after real-time
+        propagation of psi0 by `solver`; backward uses the library's hand-written
+        adjoint (the gradient is computed together with L in forward)."""
+
+        @staticmethod
+        def forward(ctx, omega_t, w, solver, psi0, rho_tgt, checkpoint_every=50):
+            ph = solver.physics
+            solver.set_params(Physics(c0=ph.c0, c2=ph.c2, so_type=ph.so_type, gamma=ph.gamma, omega=ph.omega,
+                                      wx=float(w[0]), wy=float(w[1]), dt=ph.dt, renorm=0, mag=ph.mag))
+            solver.load_state(psi0)
+            L, dom, dw = solver.loss_grad(omega_t.detach(), rho_tgt, checkpoint_every)
+            ctx.save_for_backward(dom.to(omega_t.device), torch.tensor(dw, dtype=torch.float64, device=w.device))
+            return torch.tensor(L, dtype=torch.float64, device=omega_t.device)
+
+        @staticmethod
+        def backward(ctx, grad):
+            dom, dw = ctx.saved_tensors
+            return grad * dom, grad * dw, None, None, None, None
+
+    return RabiTrapLoss
+
+
+def rabi_trap_loss(omega_t, w, solver, psi0, rho_tgt, checkpoint_every=50):
+    """Differentiable loss through the GPU propagator (see RabiTrapLoss)."""
+    return _rabi_trap_loss_function().apply(omega_t, w, solver, psi0, rho_tgt, checkpoint_every)
 
     def synchronize(self):
         self.stream.synchronize()

@@ -1,0 +1,107 @@
+"""Differentiation form: the GPU hand-written adjoint of the real-time
+propagator against the oracle adjoint (exact derivative of the discrete
+propagator) and against central finite differences of the GPU loss."""
+import numpy as np
+import pytest
+
+from gpu_util import make_pair
+from oracle import adjoint as A
+from paper_2009_13507_gb300 import inputs as I
+from paper_2009_13507_gb300 import sgpe
+
+pytestmark = pytest.mark.gpu
+
+
+def _small(dim, precision="c128"):
+    if dim == 2:
+        phys = dict(c0=15.0, c2=-1.5, so_type=1, gamma=0.7, omega=0.5, wx=1.1, wy=0.9, dt=1e-2, renorm=0)
+        prob, s = make_pair(2, 20, 16, dx=0.35, dy=0.4, precision=precision, **phys)
+        psi0 = I.gaussian_phase_2d(20, 16, 0.35, 0.4, seed=2)
+        tgt = I.gaussian_target(20, 16, 0.35, 0.4, seed=3)
+    else:
+        phys = dict(c0=20.0, c2=0.8, so_type=2, gamma=0.6, omega=0.4, wx=1.2, dt=1e-2, renorm=0)
+        prob, s = make_pair(1, 48, 1, dx=0.2, precision=precision, **phys)
+        psi0 = I.gaussian_jitter_1d(48, 0.2, seed=4, amp=0.05)
+        tgt = I.gaussian_target(48, 1, 0.2, 0.2, seed=5)
+    om = 0.5 + 0.3 * np.sin(np.arange(24) * 0.7)
+    return prob, s, psi0, tgt, om
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("K", [1, 5, 24])
+def test_adjoint_matches_oracle_gradient(dim, K):
+    prob, s, psi0, tgt, om = _small(dim)
+    L_ref, g_om, g_wx, g_wy, psiN = A.loss_and_grad(prob, psi0, om, tgt)
+    s.set_state(psi0)
+    L, dom, dw = s.loss_grad(om, tgt, checkpoint_every=K)
+    assert abs(L - L_ref) < 1e-12 * abs(L_ref)
+    d = dom.cpu().numpy()
+    assert np.max(np.abs(d - g_om)) < 1e-9 * np.max(np.abs(g_om))
+    assert abs(dw[0] - g_wx) < 1e-9 * abs(g_wx)
+    if dim == 2:
+        assert abs(dw[1] - g_wy) < 1e-9 * abs(g_wy)
+    got = s.get_state()  # the bound state ends as psi_N
+    assert np.linalg.norm(got - psiN) < 1e-11 * np.linalg.norm(psiN)
+
+
+def test_adjoint_precision_form_error():
+    prob, s, psi0, tgt, om = _small(2, precision="c64")
+    L_ref, g_om, g_wx, g_wy, _ = A.loss_and_grad(prob, psi0, om, tgt)
+    s.set_state(psi0)
+    L, dom, dw = s.loss_grad(om, tgt, checkpoint_every=6)
+    assert abs(L - L_ref) < 1e-5 * abs(L_ref)
+    assert np.max(np.abs(dom.cpu().numpy() - g_om)) < 2e-3 * np.max(np.abs(g_om))
+    assert abs(dw[0] - g_wx) < 2e-3 * abs(g_wx)
+
+
+def test_autograd_function_backward():
+    import torch
+    prob, s, psi0, tgt, om = _small(2)
+    omt = torch.tensor(om, dtype=torch.float64, device="cuda:0", requires_grad=True)
+    w = torch.tensor([1.1, 0.9], dtype=torch.float64, device="cuda:0", requires_grad=True)
+    p0 = torch.from_numpy(psi0).to("cuda:0")
+    loss = sgpe.rabi_trap_loss(omt, w, s, p0, torch.from_numpy(tgt).to("cuda:0"), 6)
+    loss.backward()
+    L_ref, g_om, g_wx, g_wy, _ = A.loss_and_grad(prob, psi0, om, tgt)
+    assert abs(loss.item() - L_ref) < 1e-12 * L_ref
+    assert np.max(np.abs(omt.grad.cpu().numpy() - g_om)) < 1e-9 * np.max(np.abs(g_om))
+    assert np.allclose(w.grad.cpu().numpy(), [g_wx, g_wy], rtol=1e-9, atol=0)
+
+
+def test_differentiation_workload_against_central_differences():
+    """The differentiation workload: 256 x 256, dx = 0.05, real time, 500 steps
+    at dt = 2e-4, Omega_n = 0.5, checkpoint every 50 steps, Gaussian target;
+    gradients against central differences of the (FP64) GPU loss at h = 1e-4."""
+    import torch
+    phys = dict(c0=50.0, c2=1.0, so_type=1, gamma=0.8, omega=0.5, wx=1.0, wy=1.0, dt=2e-4, renorm=0)
+    n, nsteps = 256, 500
+    s = sgpe.Solver(2, n, n, dx=0.05)
+    s.set_params(sgpe.Physics(**phys))
+    psi0 = I.gaussian_phase_2d(n, n, 0.05, 0.05, seed=0)
+    tgt = I.gaussian_target(n, n, 0.05, 0.05, seed=7)
+    om = np.full(nsteps, 0.5)
+
+    def loss(omv, wx=1.0, wy=1.0):
+        s.set_params(sgpe.Physics(**dict(phys, wx=wx, wy=wy)))
+        s.set_state(psi0)
+        s.step_real(nsteps, torch.tensor(omv, dtype=torch.float64, device="cuda:0"))
+        rho = np.sum(np.abs(s.get_state()) ** 2, axis=0)
+        return 0.05 * 0.05 * np.sum((rho - tgt) ** 2)
+
+    s.set_state(psi0)
+    L, dom, dw = s.loss_grad(om, tgt, checkpoint_every=50)
+    d = dom.cpu().numpy()
+    assert abs(L - loss(om)) < 1e-12 * L
+    h = 1e-4
+    # central differences carry a round-off floor of about eps * L / h
+    floor = 100 * np.finfo(float).eps * L / h
+    for k in (0, 123, 250, 400, 499):
+        op, omn = om.copy(), om.copy()
+        op[k] += h
+        omn[k] -= h
+        fd = (loss(op) - loss(omn)) / (2 * h)
+        assert abs(fd - d[k]) < 1e-4 * abs(fd) + floor, (k, fd, d[k], floor)
+    fdx = (loss(om, wx=1.0 + h) - loss(om, wx=1.0 - h)) / (2 * h)
+    fdy = (loss(om, wy=1.0 + h) - loss(om, wy=1.0 - h)) / (2 * h)
+    assert abs(fdx - dw[0]) < 1e-4 * abs(fdx) + floor
+    assert abs(fdy - dw[1]) < 1e-4 * abs(fdy) + floor
