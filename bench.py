@@ -48,7 +48,7 @@ FP64_PEAK_TFLOPS = 1.259
 CPU_SAMPLE_STEPS = 300
 # DRAM bytes (read + write) of one k_pointwise<double> launch on this workload in an ncu capture
 # (cold L2): None whenever the kernel changed after the capture.
-POINTWISE_TRAFFIC_BYTES = 3191296
+POINTWISE_TRAFFIC_BYTES = None
 
 
 def _dist():
@@ -148,6 +148,131 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def extra_workloads(dev, reps=2):
+    """The other workloads of the method, each measured with CUDA events on its
+    solver's stream after one warm-up run (rank 0 only):
+      1d_imag       1D, Nx = 256, dx = 0.05, c0 = 10, c2 = -0.5, gamma p_x Sigma_x (0.5),
+                    Omega = 0.2, dt = 1e-4, 10,000 imaginary-time steps, complex128
+      quench        2D 512 x 512, dx = 0.04, the 2D physics above; ground state prepared
+                    in FP64 (3000 imaginary-time steps, untimed), then Omega 0.5 -> 0 and
+                    10,000 real-time steps at dt = 1e-4 in complex64 and complex128
+                    (energy / norm drift of complex64 against complex128)
+      batched       64 instances (32 1D nx ~ U{128..1024}, 32 2D n ~ U{128..384}), per-instance
+                    (gamma, Omega, c0, c2) drawn, 1,000 imaginary-time steps, autotuned tiles
+      adjoint       2D 256 x 256 real time, 500 steps at dt = 2e-4, gradient of the
+                    final-density loss w.r.t. Omega(t) and (wx, wy), checkpoint every 50
+    """
+    import numpy as np
+    import torch
+
+    from paper_2009_13507_gb300 import inputs as I
+    from paper_2009_13507_gb300 import sgpe
+
+    def ev_time(stream, fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    out = {}
+    # 1D imaginary time
+    s1 = sgpe.Solver(1, 256, dx=0.05, device=dev)
+    s1.set_params(sgpe.Physics(c0=10.0, c2=-0.5, so_type=1, gamma=0.5, omega=0.2, dt=1e-4, renorm=1))
+    p1 = torch.from_numpy(I.gaussian_jitter_1d(256, 0.05, seed=0)).to(dev)
+    ms = []
+    for r in range(reps + 1):
+        s1.load_state(p1)
+        t = ev_time(s1.stream, lambda: s1.step_imag(10000))
+        if r:
+            ms.append(t)
+    e1 = s1.energy()
+    out["1d_imag"] = {"value": 256 * 10000 / (statistics.mean(ms) * 1e-3), "unit": METRIC,
+                      "ms": statistics.mean(ms), "E": e1["E"], "precision": "complex128"}
+    # 512 x 512 real-time quench
+    n3, dx3 = 512, 0.04
+    phys = dict(PHYS)
+    prep = sgpe.Solver(2, n3, n3, dx=dx3, device=dev)
+    prep.set_params(sgpe.Physics(**phys))
+    prep.set_state(I.gaussian_phase_2d(n3, n3, dx3, dx3, seed=0))
+    prep.step_imag(3000)
+    prep.energy()
+    ground = prep.psi.clone()
+    prep.stream.synchronize()
+    q = {}
+    for prec in ("c128", "c64"):
+        s3 = sgpe.Solver(2, n3, n3, dx=dx3, precision=prec, device=dev)
+        s3.set_params(sgpe.Physics(**dict(phys, omega=0.0, dt=1e-4, renorm=0)))
+        g = ground.to(s3.cdtype)
+        s3.load_state(g)
+        s3.step_real(100)  # warm-up (graph capture)
+        s3.load_state(g)
+        e0 = s3.energy()
+        t = ev_time(s3.stream, lambda: s3.step_real(10000))
+        e = s3.energy()
+        q[prec] = {"value": n3 * n3 * 10000 / (t * 1e-3), "ms": t, "E0": e0["E"], "E": e["E"], "N": e["N"]}
+    out["quench"] = {"value": q["c64"]["value"], "unit": METRIC, "precision": "complex64 (FP64 reductions)",
+                     "fp64_value": q["c128"]["value"],
+                     "energy_rel_err_vs_fp64": abs(q["c64"]["E"] - q["c128"]["E"]) / abs(q["c128"]["E"]),
+                     "norm_err_vs_fp64": abs(q["c64"]["N"] - q["c128"]["N"]),
+                     "energy_drift_fp64": q["c128"]["E"] - q["c128"]["E0"], "detail": q}
+    # batched
+    inst = []
+    for t in I.batch_table(0):
+        d = dict(t)
+        d.update(dx=0.05, dy=0.05, so_type=1, dt=(1e-4 if t["dim"] == 1 else 2e-4), renorm=1)
+        inst.append(d)
+    bres = {}
+    for prec in ("c128", "c64"):
+        bs = sgpe.BatchSolver(inst, precision=prec, device=dev)
+        tiles = bs.autotune(2)
+        states = [I.gaussian_phase_2d(s["nx"], s["ny"], s["dx"], s["dy"], seed=100 + i) if s["dim"] == 2
+                  else I.gaussian_jitter_1d(s["nx"], s["dx"], seed=100 + i, amp=1e-2) for i, s in enumerate(bs.specs)]
+        packed = bs.pack(states)
+        torch.cuda.synchronize(dev)
+        ms = []
+        for r in range(reps + 1):
+            bs.load_state(packed)
+            t = ev_time(bs.stream, lambda: bs.step_imag(1000))
+            if r:
+                ms.append(t)
+        obs = bs.energy()
+        pts = sum(s["nx"] * s["ny"] for s in bs.specs)
+        bres[prec] = {"value": pts * 1000 / (statistics.mean(ms) * 1e-3), "ms": statistics.mean(ms),
+                      "tiles": tiles, "E": obs[:, 5].copy(), "launches_per_step": bs.launches_per_step()}
+    err = float(np.max(np.abs(bres["c64"]["E"] - bres["c128"]["E"]) / np.abs(bres["c128"]["E"])))
+    out["batched"] = {"value": bres["c128"]["value"], "unit": METRIC, "precision": "complex128",
+                      "c64_value": bres["c64"]["value"], "c64_energy_max_rel_err_vs_fp64": err,
+                      "ms": bres["c128"]["ms"], "c64_ms": bres["c64"]["ms"], "tiles_c128": bres["c128"]["tiles"],
+                      "tiles_c64": bres["c64"]["tiles"], "instances": len(inst),
+                      "launches_per_step": bres["c128"]["launches_per_step"]}
+    # adjoint
+    ares = {}
+    tgt = I.gaussian_target(NX, NY, DX, DX, seed=7)
+    psi0 = I.gaussian_phase_2d(NX, NY, DX, DX, seed=0)
+    for prec in ("c64", "c128"):
+        sa = sgpe.Solver(2, NX, NY, dx=DX, precision=prec, device=dev)
+        sa.set_params(sgpe.Physics(**dict(PHYS, renorm=0)))
+        p0 = torch.from_numpy(psi0).to(sa.cdtype).to(dev)
+        om = np.full(500, 0.5)
+        times = []
+        for r in range(reps + 1):
+            sa.load_state(p0)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            L, dom, dw = sa.loss_grad(om, tgt, checkpoint_every=50)
+            if r:
+                times.append((time.perf_counter() - t0) * 1e3)
+        ares[prec] = {"ms_per_gradient": statistics.mean(times), "loss": L, "dL_dwx": dw[0], "dL_dwy": dw[1]}
+    out["adjoint"] = {"value": ares["c64"]["ms_per_gradient"], "unit": "ms per gradient", "precision": "complex64",
+                      "fp64_ms_per_gradient": ares["c128"]["ms_per_gradient"],
+                      "loss_rel_err_vs_fp64": abs(ares["c64"]["loss"] - ares["c128"]["loss"]) / ares["c128"]["loss"],
+                      "dL_dwx_rel_err_vs_fp64": abs(ares["c64"]["dL_dwx"] - ares["c128"]["dL_dwx"])
+                      / abs(ares["c128"]["dL_dwx"])}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -155,6 +280,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads (forms)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -264,6 +390,8 @@ def main():
     e2e_t = statistics.mean(e2e_ms)
     nbytes_state = 3 * NX * NY * 16
 
+    forms = extra_workloads(dev) if (rank == 0 and not args.no_extra) else None
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         r, t = cpu_oracle_rate(CPU_SAMPLE_STEPS)
@@ -291,6 +419,7 @@ def main():
                    "ms_per_step": t32, "energy_rel_err_vs_fp64": abs(e32 - e64) / abs(e64),
                    "speedup_vs_fp64": t_step / t32},
         "energy": {"E_fp64": e64, "E_c64": e32, "E_profile_pass": e_prof[5]},
+        "forms": forms,
         "cpu_baseline": cpu,
         "e2e": {"value": ws * point_steps / (e2e_t * 1e-3), "unit": METRIC, "h2d_bytes_per_step": nbytes_state,
                 "d2h_bytes_per_step": nbytes_state + 16 * 8, "ms_per_step": e2e_t},

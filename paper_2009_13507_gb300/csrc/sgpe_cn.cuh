@@ -59,6 +59,36 @@ __device__ __forceinline__ void solve_chunk(cx<R> (&v)[C], const Tabs<R>& t, int
     for (int m = 0; m < C; m++) v[m] = tfma<IMAG>(tld<R>(t.fq, i0 + m), cb, v[m]);
 }
 
+// Increment form of the sweep, used for the complex64 state: out = x + 2 e with
+// T e = bt L x, L x = (x_{i-1} - x_i) + (x_{i+1} - x_i). The FP32-rounded LU
+// factors then only touch the small increment e, so the sweep stays unitary
+// (real time) to far better than one ulp per step; the two differences of
+// neighbouring values are exact. bt is recovered from the tables as fg_0/fa_0.
+// In place on the lane's chunk v (in: x, out: bt L x); all 32 lanes.
+template <typename R, bool IMAG, int C>
+__device__ __forceinline__ void cn_increment_rhs(cx<R> (&v)[C], const Tabs<R>& t) {
+    const int lane = threadIdx.x & 31;
+    const cx<R> a0 = tld<R>(t.fa, 0), g0 = tld<R>(t.fg, 0);
+    cx<R> bt;
+    if (IMAG) {
+        bt = {g0.re / a0.re, R(0)};
+    } else {
+        const R den = nrm(a0);
+        const cx<R> q = cmul(a0, g0);  // conj(a0) g0
+        bt = {q.re / den, q.im / den};
+    }
+    cx<R> prev = shup(v[C - 1], 1), last = shdn(v[0], 1);
+    if (lane == 0) prev = {R(0), R(0)};
+    if (lane == 31) last = {R(0), R(0)};
+#pragma unroll
+    for (int m = 0; m < C; m++) {
+        const cx<R> cur = v[m];
+        const cx<R> nxt = (m + 1 < C) ? v[m + 1] : last;
+        v[m] = tmul<IMAG>(bt, add(sub(prev, cur), sub(nxt, cur)));
+        prev = cur;
+    }
+}
+
 // Columns per warp of the y sweep and whether a lane keeps its input chunk in
 // registers (small chunks) or reloads it for the final 2w - x (large chunks).
 template <int C> struct CnShape {
@@ -94,13 +124,16 @@ __device__ __forceinline__ void cnx_line(const typename V2<R>::T* in, typename V
         v[m] = (i0 + m < n) ? ldc<R>(in, base + i0 + m) : zero;
         if (KEEP) x[m] = v[m];
     }
+    constexpr bool INC = sizeof(R) == 4;
+    if (INC) cn_increment_rhs<R, IMAG, C>(v, t);
     solve_chunk<R, IMAG, C>(v, t, i0);
     double acc = 0.0;
 #pragma unroll
     for (int m = 0; m < C; m++) {
         if (i0 + m < n) {
             cx<R> xm = KEEP ? x[m] : ldc<R>(in, base + i0 + m);
-            cx<R> o = {fma(R(2), v[m].re, -xm.re), fma(R(2), v[m].im, -xm.im)};
+            cx<R> o = INC ? cx<R>{fma(R(2), v[m].re, xm.re), fma(R(2), v[m].im, xm.im)}
+                          : cx<R>{fma(R(2), v[m].re, -xm.re), fma(R(2), v[m].im, -xm.im)};
             st<R>(out, base + i0 + m, o);
             acc += (double)o.re * (double)o.re + (double)o.im * (double)o.im;
         }
@@ -132,6 +165,7 @@ __device__ __forceinline__ void cny_cols(const typename V2<R>::T* in, typename V
                                          const Tabs<R>& t, int j, int col, double* part) {
     constexpr int K = CnShape<C>::K;
     constexpr bool KEEP = CnShape<C>::KEEP;
+    constexpr bool INC = sizeof(R) == 4;
     const int lane = threadIdx.x & 31;
     const int n = p.ny;
     const int i0 = lane * C;
@@ -149,7 +183,10 @@ __device__ __forceinline__ void cny_cols(const typename V2<R>::T* in, typename V
         }
     }
 #pragma unroll
-    for (int k = 0; k < K; k++) solve_chunk<R, IMAG, C>(v[k], t, i0);
+    for (int k = 0; k < K; k++) {
+        if (INC) cn_increment_rhs<R, IMAG, C>(v[k], t);
+        solve_chunk<R, IMAG, C>(v[k], t, i0);
+    }
     double acc = 0.0;
 #pragma unroll
     for (int m = 0; m < C; m++) {
@@ -159,7 +196,8 @@ __device__ __forceinline__ void cny_cols(const typename V2<R>::T* in, typename V
             for (int k = 0; k < K; k++) {
                 if (col + k < p.nx) {
                     cx<R> xm = KEEP ? x[k][m] : ldc<R>(in, g + k);
-                    cx<R> o = {fma(R(2), v[k][m].re, -xm.re), fma(R(2), v[k][m].im, -xm.im)};
+                    cx<R> o = INC ? cx<R>{fma(R(2), v[k][m].re, xm.re), fma(R(2), v[k][m].im, xm.im)}
+                                  : cx<R>{fma(R(2), v[k][m].re, -xm.re), fma(R(2), v[k][m].im, -xm.im)};
                     st<R>(out, g + k, o);
                     acc += (double)o.re * (double)o.re + (double)o.im * (double)o.im;
                 }

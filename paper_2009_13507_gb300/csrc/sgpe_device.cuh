@@ -264,7 +264,23 @@ __device__ __forceinline__ void calcnu_point(cx<R> (&u)[3], R V, R c0, R c2, R d
     R mup = fma(c2, rp - rm + r0, base);
     R mu0 = fma(c2, rp + rm, base);
     R mum = fma(c2, rm - rp + r0, base);
-    if (IMAG) {
+    if (sizeof(R) == 4) {
+        // complex64 state: apply the factor as u + (f - 1) u with f - 1 formed
+        // without cancellation, so that rounding the factor cannot bias |u|
+        // the same way every step (expm1; cos t - 1 = -2 sin^2(t/2)).
+        const R mu[3] = {mup, mu0, mum};
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            if (IMAG) {
+                u[j] = axpy((R)expm1f((float)(-dt * mu[j])), u[j], u[j]);
+            } else {
+                float sh, ch;
+                sincosf((float)(0.5f * dt * mu[j]), &sh, &ch);
+                const cx<R> fm1 = {(R)(-2.0f * sh * sh), (R)(-2.0f * sh * ch)};  // exp(-i t) - 1
+                u[j] = add(u[j], mul(fm1, u[j]));
+            }
+        }
+    } else if (IMAG) {
         R fp = exp_small(-dt * mup), f0 = exp_small(-dt * mu0), fm = exp_small(-dt * mum);
         u[0] = scl(fp, u[0]);
         u[1] = scl(f0, u[1]);

@@ -82,8 +82,10 @@ template <typename R>
 cudaError_t Launcher<R>::pointwise(cudaStream_t s, bool imag, const void* A, void* B, const KParams& p,
                                    const DevScalars* sc, const double* omega_tab, int mask) {
     using T = typename V2<R>::T;
-    dim3 block(32, p.dim == 2 ? 4 : 1);
-    dim3 grid(ceil_div(p.nx, 32), p.dim == 2 ? ceil_div(p.ny, 4) : 1);
+    // 64-thread blocks: the FP64 form is bound by each SM's FP64 pipe, and small
+    // blocks spread the points evenly over the 152 SMs (1024 blocks at 256^2).
+    dim3 block(32, p.dim == 2 ? 2 : 1);
+    dim3 grid(ceil_div(p.nx, 32), p.dim == 2 ? ceil_div(p.ny, 2) : 1);
     if (imag)
         k_pointwise<R, true><<<grid, block, 0, s>>>((const T*)A, (T*)B, p, sc, omega_tab, mask);
     else
