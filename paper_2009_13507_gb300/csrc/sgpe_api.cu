@@ -36,7 +36,7 @@ Geometry make_geometry(int dim, int nx, int ny, int esz) {
     g.wy = 2;
     while (!g.reg_y && g.wy > 1 && g.wy * per_warp_y > 160 * 1024) g.wy >>= 1;
     g.smem_y = g.reg_y ? 0 : g.wy * per_warp_y;
-    g.blocks_y = dim == 2 ? 3 * ceil_div(nx, g.reg_y ? cny_cols_per_warp(chunk_len(ny)) : g.wy) : 0;
+    g.blocks_y = dim == 2 ? 3 * ceil_div(nx, g.reg_y ? cny_cols_per_warp(chunk_len(ny), esz) : g.wy) : 0;
     g.blocks_obs = ceil_div(nx, 32) * ceil_div(ny, 4);
     g.blocks_norm = kNormBlocks;
     return g;
@@ -311,7 +311,8 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
     if ((e = Launcher<R>::cn_x(c->stream, imag, true, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo, c->partials,
                                c->sc, renorm, 1)))
         return e;
-    return finalize_step(c->stream, c->partials, c->geo.blocks_x, c->kp.cell, renorm, c->kp.mag, 1, c->sc);
+    // 1D: one partial per line (3 lines)
+    return finalize_step(c->stream, c->partials, 3 * c->ny, c->kp.cell, renorm, c->kp.mag, 1, c->sc);
 }
 
 static cudaError_t enqueue_steps(sgpe_ctx* c, int n, bool imag, const double* omega_tab) {
@@ -556,7 +557,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
                                             c->partials, c->sc, renorm, 1, 1);
         if (!e) e = cudaEventRecord(ev[3], c->stream);
         if (!e)
-            e = finalize_step(c->stream, c->partials, two ? c->geo.blocks_y : c->geo.blocks_x, c->kp.cell, renorm,
+            e = finalize_step(c->stream, c->partials, two ? c->geo.blocks_y : 3 * c->ny, c->kp.cell, renorm,
                               c->kp.mag, 1, c->sc);
         if (!e) e = cudaEventRecord(ev[4], c->stream);
       }

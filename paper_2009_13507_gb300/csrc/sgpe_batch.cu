@@ -80,7 +80,7 @@ __global__ void kb_cnx(typename V2<R>::T* A, typename V2<R>::T* B, const BInst* 
     const BInst& I = insts[e.x];
     const Tabs<R> t = inst_tabs<R>(pool, I, IMAG ? 0 : 1, 0);
     typename V2<R>::T* out = (I.p.dim == 2 ? B : A) + I.off;
-    cnx_line<R, IMAG, C>(B + I.off, out, I.p, t, e.y, e.z >= 0 ? partials + 3 * e.z : nullptr);
+    cnx_line<R, IMAG, C>(B + I.off, out, I.p, t, e.y, e.z >= 0 ? partials + e.z : nullptr);
 }
 
 // Work entry of the y sweep: (instance, component, first column, partial slot).
@@ -93,7 +93,7 @@ __global__ void kb_cny(typename V2<R>::T* A, const typename V2<R>::T* B, const B
     const int4 e = work[w];
     const BInst& I = insts[e.x];
     const Tabs<R> t = inst_tabs<R>(pool, I, IMAG ? 0 : 1, 1);
-    cny_cols<R, IMAG, C>(B + I.off, A + I.off, I.p, t, e.y, e.z, partials + 3 * e.w);
+    cny_cols<R, IMAG, C>(B + I.off, A + I.off, I.p, t, e.y, e.z, partials + e.w);
 }
 
 // One block per instance: sum its partial slots in order, publish norms and the
@@ -103,11 +103,13 @@ __global__ void __launch_bounds__(128) kb_finalize(const BInst* __restrict__ ins
     __shared__ double red[4 * 3];
     const BInst& I = insts[blockIdx.x];
     double s[3] = {0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < I.nslot; b += blockDim.x) {
-        const double* q = partials + 3 * (I.slot0 + b);
-        s[0] += __ldcg(q + 0);
-        s[1] += __ldcg(q + 1);
-        s[2] += __ldcg(q + 2);
+    // slots of component j: [slot0 + j*m, slot0 + (j+1)*m)
+    const int m = I.nslot / 3;
+    for (int b = threadIdx.x; b < m; b += blockDim.x) {
+        const double* q = partials + I.slot0 + b;
+        s[0] += __ldcg(q);
+        s[1] += __ldcg(q + m);
+        s[2] += __ldcg(q + 2 * m);
     }
     block_reduce<3>(s, red);
     if (threadIdx.x == 0) {
@@ -415,7 +417,7 @@ sgpe_status sgpe_batch_create(sgpe_batch** out, int n, const sgpe_instance* inst
         } else {
             for (int l = 0; l < 3 * q.ny; l++) b->cnx[Cx].push_back(make_int4(i, l, -1, 0));
             const int Cy = chunk_len(q.ny);
-            const int K = cny_cols_per_warp(Cy);
+            const int K = cny_cols_per_warp(Cy, b->esz);
             int cnt = 0;
             for (int j = 0; j < 3; j++)
                 for (int col = 0; col < q.nx; col += K) b->cny[Cy].push_back(make_int4(i, j, col, slot + cnt++));

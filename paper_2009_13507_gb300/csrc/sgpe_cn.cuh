@@ -91,8 +91,10 @@ __device__ __forceinline__ void cn_increment_rhs(cx<R> (&v)[C], const Tabs<R>& t
 
 // Columns per warp of the y sweep and whether a lane keeps its input chunk in
 // registers (small chunks) or reloads it for the final 2w - x (large chunks).
-template <int C> struct CnShape {
-    static constexpr int K = C <= 8 ? 2 : 1;
+template <typename R, int C> struct CnShape {
+    // complex128: one column per warp (the FP64 sweep is latency-bound, more
+    // warps per SM help more than full 32-byte rows); complex64: two columns
+    static constexpr int K = (sizeof(R) == 4 && C <= 8) ? 2 : 1;
     static constexpr bool KEEP = C <= 8;
 };
 
@@ -104,15 +106,15 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // ---------------------------------------------------------------------------
 // CN along x: block = one warp = one line (line = j*ny + iy). With partials
-// non-null the block writes the FP64 norm of its output line to
-// partials[3*line + j] (zeros for the other components).
+// non-null the block writes the FP64 norm of its output line to partials[line]
+// (the lines of component j are contiguous).
 // ---------------------------------------------------------------------------
-// One x line of one grid by the calling warp; part (nullable): the 3 partial
-// slots of this line (norm of the output line in slot j, zeros elsewhere).
+// One x line of one grid by the calling warp; part (nullable): the partial
+// slot of this line (FP64 norm of the output line).
 template <typename R, bool IMAG, int C>
 __device__ __forceinline__ void cnx_line(const typename V2<R>::T* in, typename V2<R>::T* out, const KParams& p,
                                          const Tabs<R>& t, int line, double* part) {
-    constexpr bool KEEP = CnShape<C>::KEEP;
+    constexpr bool KEEP = CnShape<R, C>::KEEP;
     const int lane = threadIdx.x & 31;
     const int n = p.nx;
     const int i0 = lane * C;
@@ -140,17 +142,14 @@ __device__ __forceinline__ void cnx_line(const typename V2<R>::T* in, typename V
     }
     if (part) {
         acc = warp_sum(acc);
-        if (lane == 0) {
-            const int j = line / p.ny;
-            for (int q = 0; q < 3; q++) part[q] = (q == j) ? acc : 0.0;
-        }
+        if (lane == 0) *part = acc;
     }
 }
 
 template <typename R, bool IMAG, int C>
 __global__ void __launch_bounds__(32) k_cnx_reg(const typename V2<R>::T* in, typename V2<R>::T* out, KParams p,
                                                 Tabs<R> t, double* partials) {
-    cnx_line<R, IMAG, C>(in, out, p, t, blockIdx.x, partials ? partials + 3 * blockIdx.x : nullptr);
+    cnx_line<R, IMAG, C>(in, out, p, t, blockIdx.x, partials ? partials + blockIdx.x : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -163,8 +162,8 @@ __global__ void __launch_bounds__(32) k_cnx_reg(const typename V2<R>::T* in, typ
 template <typename R, bool IMAG, int C>
 __device__ __forceinline__ void cny_cols(const typename V2<R>::T* in, typename V2<R>::T* out, const KParams& p,
                                          const Tabs<R>& t, int j, int col, double* part) {
-    constexpr int K = CnShape<C>::K;
-    constexpr bool KEEP = CnShape<C>::KEEP;
+    constexpr int K = CnShape<R, C>::K;
+    constexpr bool KEEP = CnShape<R, C>::KEEP;
     constexpr bool INC = sizeof(R) == 4;
     const int lane = threadIdx.x & 31;
     const int n = p.ny;
@@ -206,19 +205,18 @@ __device__ __forceinline__ void cny_cols(const typename V2<R>::T* in, typename V
     }
     if (part) {
         acc = warp_sum(acc);
-        if (lane == 0)
-            for (int q = 0; q < 3; q++) part[q] = (q == j) ? acc : 0.0;
+        if (lane == 0) *part = acc;
     }
 }
 
 template <typename R, bool IMAG, int C>
 __global__ void __launch_bounds__(32) k_cny_reg(const typename V2<R>::T* in, typename V2<R>::T* out, KParams p,
                                                 Tabs<R> t, double* partials) {
-    constexpr int K = CnShape<C>::K;
+    constexpr int K = CnShape<R, C>::K;
     const int ncb = (p.nx + K - 1) / K;
     const int j = blockIdx.x / ncb;
     const int col = (blockIdx.x - j * ncb) * K;
-    cny_cols<R, IMAG, C>(in, out, p, t, j, col, partials ? partials + 3 * blockIdx.x : nullptr);
+    cny_cols<R, IMAG, C>(in, out, p, t, j, col, partials ? partials + blockIdx.x : nullptr);
 }
 
 }  // namespace sgpe

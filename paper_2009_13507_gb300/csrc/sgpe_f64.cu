@@ -6,7 +6,7 @@ template struct Launcher<double>;
 
 cudaError_t finalize_step(cudaStream_t s, const double* partials, int nblk, double cell, int renorm, double mag,
                           int advance, DevScalars* sc) {
-    k_finalize<<<1, 256, 0, s>>>(partials, nblk, cell, renorm, mag, advance, sc);
+    k_finalize<<<1, 96, 0, s>>>(partials, nblk / 3, cell, renorm, mag, advance, sc);
     return cudaGetLastError();
 }
 

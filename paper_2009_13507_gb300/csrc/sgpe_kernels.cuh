@@ -314,13 +314,11 @@ __global__ void __launch_bounds__(256) k_cn_x(const typename V2<R>::T* in, typen
             if (LAST) acc += (double)o.re * (double)o.re + (double)o.im * (double)o.im;
         }
     }
-    if (LAST) {
-        __shared__ double red[8 * 3];
-        double v[3] = {0.0, 0.0, 0.0};
-        if (line < nlines) v[line / p.ny] = acc;
-        block_reduce<3>(v, red);
-        if (threadIdx.x == 0)
-            for (int j = 0; j < 3; j++) partials[3 * blockIdx.x + j] = v[j];
+    if (LAST && line < nlines) {
+        // one partial per line; lines of component j are contiguous
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) partials[line] = acc;
     }
 }
 
@@ -371,36 +369,44 @@ __global__ void __launch_bounds__(256) k_cn_y(const typename V2<R>::T* in, typen
         __shared__ double red[8];
         double v[1] = {acc};
         block_reduce<1>(v, red);
-        if (threadIdx.x == 0) {
-            for (int q = 0; q < 3; q++) partials[3 * blockIdx.x + q] = (q == j) ? v[0] : 0.0;
-        }
+        if (threadIdx.x == 0) partials[blockIdx.x] = v[0];  // blocks of component j are contiguous
     }
 }
 
 // ---------------------------------------------------------------------------
-// End of a step: one block sums the per-block partial norms of the step's last
-// sweep (partials[3b + j], fixed order), publishes N_j, the next pending scale
-// (Eq. (DJ2) / (DJ) for renorm != 0, else 1) and advances the step counter.
+// End of a step: one block of 3 warps; warp j sums the m partial norms of
+// component j (partials[j*m .. j*m + m), fixed order), then thread 0 publishes
+// N_j, the next pending scale (Eq. (DJ2) / (DJ) for renorm != 0, else 1) and
+// advances the step counter. Few threads on purpose: the FP64 adds run on one
+// SM's FP64 pipe.
 // ---------------------------------------------------------------------------
-static __global__ void __launch_bounds__(256) k_finalize(const double* partials, int nblk, double cell, int renorm,
-                                                  double mag, int advance_step, DevScalars* sc) {
-    __shared__ double red[8 * 3];
-    double s[3] = {0.0, 0.0, 0.0};
-#pragma unroll 4
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-        s[0] += __ldcg(partials + 3 * b + 0);
-        s[1] += __ldcg(partials + 3 * b + 1);
-        s[2] += __ldcg(partials + 3 * b + 2);
+static __global__ void __launch_bounds__(96) k_finalize(const double* partials, int m, double cell, int renorm,
+                                                 double mag, int advance_step, DevScalars* sc) {
+    __shared__ double red[3];
+    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double* q = partials + (size_t)j * m;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int b = lane;
+    for (; b + 96 < m; b += 128) {
+        a0 += __ldcg(q + b);
+        a1 += __ldcg(q + b + 32);
+        a2 += __ldcg(q + b + 64);
+        a3 += __ldcg(q + b + 96);
     }
-    block_reduce<3>(s, red);
+    for (; b < m; b += 32) a0 += __ldcg(q + b);
+    double s = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) red[j] = s;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double N[3] = {s[0] * cell, s[1] * cell, s[2] * cell};
+        double N[3] = {red[0] * cell, red[1] * cell, red[2] * cell};
         bool finite = isfinite(N[0]) && isfinite(N[1]) && isfinite(N[2]);
         double d[3];
         renorm_factors(N, finite ? renorm : 0, mag, d);
-        for (int j = 0; j < 3; j++) {
-            sc->norms[j] = N[j];
-            sc->scale[j] = d[j];
+        for (int q3 = 0; q3 < 3; q3++) {
+            sc->norms[q3] = N[q3];
+            sc->scale[q3] = d[q3];
         }
         if (!finite) sc->err |= 1;
         if (advance_step) sc->step_idx += 1;

@@ -29,7 +29,7 @@ inline int chunk_stride(int n) { return chunk_len(n) | 1; }
 // Entries of each coefficient table of an n-point axis (padded with zeros past n).
 inline int table_len(int n) { return 32 * chunk_len(n); }
 // Columns per warp of the register y sweep (must match CnShape<C>::K).
-inline int cny_cols_per_warp(int C) { return C <= 8 ? 2 : 1; }
+inline int cny_cols_per_warp(int C, int esz) { return (esz == 8 && C <= 8) ? 2 : 1; }
 constexpr int kObsAcc = 11;
 constexpr int kNormBlocks = 304;
 
