@@ -25,6 +25,7 @@ Geometry make_geometry(int dim, int nx, int ny, int esz) {
     g.esz = esz;
     // x sweep: register kernel (4 lines per block) up to kRegMaxN points, else shared-memory kernel
     g.reg_x = nx <= kRegMaxN;
+    g.fused = dim == 2 && g.reg_x;
     size_t per_warp_x = (size_t)(32 * chunk_stride(nx) + 32) * esz;
     g.wx = 4;
     while (!g.reg_x && g.wx > 1 && g.wx * per_warp_x > 96 * 1024) g.wx >>= 1;
@@ -298,6 +299,14 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
     cudaError_t e;
     const int mode = imag ? 0 : 1;
     const int renorm = imag ? c->params.renorm : 0;
+    if (c->geo.fused) {
+        if ((e = Launcher<R>::pwx(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, c->tabs[mode][0])))
+            return e;
+        if ((e = Launcher<R>::cn_y(c->stream, imag, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials,
+                                   c->sc, renorm, 1, 1)))
+            return e;
+        return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 1, c->sc);
+    }
     if ((e = Launcher<R>::pointwise(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, 7))) return e;
     if (c->dim == 2) {
         if ((e = Launcher<R>::cn_x(c->stream, imag, false, c->mid, c->mid, c->kp, c->tabs[mode][0], c->geo,
@@ -523,7 +532,9 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
     const int mode = im ? 0 : 1;
     const int renorm = im ? c->params.renorm : 0;
     const bool dbl = c->prec == SGPE_C128;
-    // kinds: 0 pointwise, 1 CN along x, 2 CN along y, 3 end-of-step norm / scale
+    // kinds: 0 pointwise, 1 CN along x, 2 CN along y, 3 end-of-step norm / scale;
+    // with the fused 2D head, kind 0 is the fused pointwise + CN-x kernel and
+    // kind 1 has no launches.
     // Steps are enqueued in batches of kBatch with their events and synchronised
     // once per batch, so the intervals measure the GPU, not host submission.
     const int kBatch = 64;
@@ -533,6 +544,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
     double acc[4] = {0, 0, 0, 0};
     int cnt[4] = {0, 0, 0, 0};
     const bool two = c->dim == 2;
+    const bool fused = c->geo.fused;
     sgpe_status out = SGPE_OK;
     for (int i0 = 0; i0 < nsteps && out == SGPE_OK; i0 += kBatch) {
       const int nb = nsteps - i0 < kBatch ? nsteps - i0 : kBatch;
@@ -540,11 +552,15 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
       for (int bi = 0; bi < nb && !e; bi++) {
         cudaEvent_t* ev = evs[bi];
         e = cudaEventRecord(ev[0], c->stream);
-        if (!e) e = dbl ? Launcher<double>::pointwise(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, 7)
-                        : Launcher<float>::pointwise(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, 7);
+        if (!e && fused)
+            e = dbl ? Launcher<double>::pwx(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, c->tabs[mode][0])
+                    : Launcher<float>::pwx(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, c->tabs[mode][0]);
+        if (!e && !fused)
+            e = dbl ? Launcher<double>::pointwise(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, 7)
+                    : Launcher<float>::pointwise(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, 7);
         if (!e) e = cudaEventRecord(ev[1], c->stream);
         void* xout = two ? c->mid : c->psi;
-        if (!e)
+        if (!e && !fused)
             e = dbl ? Launcher<double>::cn_x(c->stream, im, !two, c->mid, xout, c->kp, c->tabs[mode][0], c->geo,
                                              c->partials, c->sc, renorm, 1)
                     : Launcher<float>::cn_x(c->stream, im, !two, c->mid, xout, c->kp, c->tabs[mode][0], c->geo,
@@ -568,7 +584,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
       }
       for (int bi = 0; bi < nb; bi++)
           for (int k = 0; k < 4; k++) {
-              if (k == 2 && !two) continue;
+              if ((k == 2 && !two) || (k == 1 && fused)) continue;
               float ms = 0.f;
               cudaEventElapsedTime(&ms, evs[bi][k], evs[bi][k + 1]);
               acc[k] += ms;
@@ -586,6 +602,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
 
 int sgpe_launches_per_step(const sgpe_ctx* c) {
     if (!c) return 0;
+    if (c->geo.fused) return 3;
     return c->dim == 2 ? 4 : 3;
 }
 

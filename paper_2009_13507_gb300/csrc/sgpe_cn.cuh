@@ -15,17 +15,49 @@
 
 namespace sgpe {
 
+// A lane's slice [i0, i0 + C) of one coefficient table: held in registers when
+// PRE (loaded once, up front, with the other loads of the kernel) or read from
+// global memory at each use.
+template <typename R, int C, bool PRE> struct ChunkTab {
+    cx<R> r[PRE ? C : 1];
+    const typename V2<R>::T* p;
+    __device__ __forceinline__ void init(const typename V2<R>::T* base, int i0) {
+        p = base + i0;
+        if (PRE) {
+#pragma unroll
+            for (int m = 0; m < C; m++) r[PRE ? m : 0] = tld<R>(p, m);
+        }
+    }
+    __device__ __forceinline__ cx<R> operator[](int m) const { return PRE ? r[PRE ? m : 0] : tld<R>(p, m); }
+};
+
+// Register-resident tables for small chunks, except FP64 real-time tables (complex, too many registers).
+template <typename R, bool IMAG, int C> struct TabPolicy {
+    static constexpr bool PRE = C <= 8 && (sizeof(R) == 4 || IMAG);
+};
+
+template <typename R, bool IMAG, int C> struct LaneTabs {
+    static constexpr bool PRE = TabPolicy<R, IMAG, C>::PRE;
+    ChunkTab<R, C, PRE> fa, fg, fp, fq;
+    __device__ __forceinline__ void init(const Tabs<R>& t, int i0) {
+        fa.init(t.fa, i0);
+        fg.init(t.fg, i0);
+        fp.init(t.fp, i0);
+        fq.init(t.fq, i0);
+    }
+};
+
 // Solve T w = x for the lane's chunk v (in: x, out: w), all 32 lanes together.
 template <typename R, bool IMAG, int C>
-__device__ __forceinline__ void solve_chunk(cx<R> (&v)[C], const Tabs<R>& t, int i0) {
+__device__ __forceinline__ void solve_chunk(cx<R> (&v)[C], const LaneTabs<R, IMAG, C>& t) {
     const int lane = threadIdx.x & 31;
     cx<R> y = {R(0), R(0)};
 #pragma unroll
     for (int m = 0; m < C; m++) {
-        y = tfma<IMAG>(tld<R>(t.fg, i0 + m), y, tmul<IMAG>(tld<R>(t.fa, i0 + m), v[m]));
+        y = tfma<IMAG>(t.fg[m], y, tmul<IMAG>(t.fa[m], v[m]));
         v[m] = y;
     }
-    cx<R> A = tld<R>(t.fp, i0 + C - 1), B = y;
+    cx<R> A = t.fp[C - 1], B = y;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         cx<R> Ap = shup(A, off), Bp = shup(B, off);
@@ -39,11 +71,11 @@ __device__ __forceinline__ void solve_chunk(cx<R> (&v)[C], const Tabs<R>& t, int
     cx<R> w = {R(0), R(0)};
 #pragma unroll
     for (int m = C - 1; m >= 0; m--) {
-        cx<R> yi = tfma<IMAG>(tld<R>(t.fp, i0 + m), cin, v[m]);
-        w = tfma<IMAG>(tld<R>(t.fg, i0 + m), w, yi);
+        cx<R> yi = tfma<IMAG>(t.fp[m], cin, v[m]);
+        w = tfma<IMAG>(t.fg[m], w, yi);
         v[m] = w;
     }
-    A = tld<R>(t.fq, i0);
+    A = t.fq[0];
     B = w;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -56,7 +88,7 @@ __device__ __forceinline__ void solve_chunk(cx<R> (&v)[C], const Tabs<R>& t, int
     cx<R> cb = shdn(B, 1);
     if (lane == 31) cb = {R(0), R(0)};
 #pragma unroll
-    for (int m = 0; m < C; m++) v[m] = tfma<IMAG>(tld<R>(t.fq, i0 + m), cb, v[m]);
+    for (int m = 0; m < C; m++) v[m] = tfma<IMAG>(t.fq[m], cb, v[m]);
 }
 
 // Increment form of the sweep, used for the complex64 state: out = x + 2 e with
@@ -109,35 +141,36 @@ __device__ __forceinline__ double warp_sum(double v) {
 // non-null the block writes the FP64 norm of its output line to partials[line]
 // (the lines of component j are contiguous).
 // ---------------------------------------------------------------------------
-// One x line of one grid by the calling warp; part (nullable): the partial
+// One x line of n points by the calling warp: input point i (i < n) comes from
+// load(i), output point i goes to out[base + i]; part (nullable): the partial
 // slot of this line (FP64 norm of the output line).
-template <typename R, bool IMAG, int C>
-__device__ __forceinline__ void cnx_line(const typename V2<R>::T* in, typename V2<R>::T* out, const KParams& p,
-                                         const Tabs<R>& t, int line, double* part) {
+template <typename R, bool IMAG, int C, typename Load>
+__device__ __forceinline__ void cnx_solve_line(Load load, typename V2<R>::T* out, size_t base, int n,
+                                               const Tabs<R>& t, double* part) {
     constexpr bool KEEP = CnShape<R, C>::KEEP;
     const int lane = threadIdx.x & 31;
-    const int n = p.nx;
     const int i0 = lane * C;
     const cx<R> zero = {R(0), R(0)};
-    const size_t base = (size_t)line * n;
+    LaneTabs<R, IMAG, C> lt;
+    lt.init(t, i0);
     cx<R> x[KEEP ? C : 1], v[C];
 #pragma unroll
     for (int m = 0; m < C; m++) {
-        v[m] = (i0 + m < n) ? ldc<R>(in, base + i0 + m) : zero;
+        v[m] = (i0 + m < n) ? load(i0 + m) : zero;
         if (KEEP) x[m] = v[m];
     }
     constexpr bool INC = sizeof(R) == 4;
     if (INC) cn_increment_rhs<R, IMAG, C>(v, t);
-    solve_chunk<R, IMAG, C>(v, t, i0);
+    solve_chunk<R, IMAG, C>(v, lt);
     double acc = 0.0;
 #pragma unroll
     for (int m = 0; m < C; m++) {
         if (i0 + m < n) {
-            cx<R> xm = KEEP ? x[m] : ldc<R>(in, base + i0 + m);
+            cx<R> xm = KEEP ? x[m] : load(i0 + m);
             cx<R> o = INC ? cx<R>{fma(R(2), v[m].re, xm.re), fma(R(2), v[m].im, xm.im)}
                           : cx<R>{fma(R(2), v[m].re, -xm.re), fma(R(2), v[m].im, -xm.im)};
             st<R>(out, base + i0 + m, o);
-            acc += (double)o.re * (double)o.re + (double)o.im * (double)o.im;
+            if (part) acc += (double)o.re * (double)o.re + (double)o.im * (double)o.im;
         }
     }
     if (part) {
@@ -146,10 +179,66 @@ __device__ __forceinline__ void cnx_line(const typename V2<R>::T* in, typename V
     }
 }
 
+// One x line of one grid (line = j*ny + iy) from global memory.
+template <typename R, bool IMAG, int C>
+__device__ __forceinline__ void cnx_line(const typename V2<R>::T* in, typename V2<R>::T* out, const KParams& p,
+                                         const Tabs<R>& t, int line, double* part) {
+    const size_t base = (size_t)line * p.nx;
+    cnx_solve_line<R, IMAG, C>([&](int i) { return ldc<R>(in, base + i); }, out, base, p.nx, t, part);
+}
+
 template <typename R, bool IMAG, int C>
 __global__ void __launch_bounds__(32) k_cnx_reg(const typename V2<R>::T* in, typename V2<R>::T* out, KParams p,
                                                 Tabs<R> t, double* partials) {
     cnx_line<R, IMAG, C>(in, out, p, t, blockIdx.x, partials ? partials + blockIdx.x : nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Fused head of a 2D step, one block per grid row iy (rows of at most 1024
+// points). All threads run the pointwise substeps (pending scale, SO, CALCNU,
+// HERM) of the row's points for the three components and stage the results in
+// shared memory in the lanes' chunk layout, each chunk padded to C + 1 entries
+// so that a lane's chunk reads are free of bank conflicts; then warp j solves
+// the Crank-Nicolson x line of component j from there and writes it to B.
+// Compared with separate pointwise and x-sweep kernels this saves one pass over
+// the state and one launch per step.
+// ---------------------------------------------------------------------------
+constexpr int kPwxThreads = 256;
+
+template <typename R, int C> constexpr size_t pwx_smem_bytes() {
+    return (size_t)3 * 32 * (C + 1) * sizeof(typename V2<R>::T);
+}
+
+template <typename R, bool IMAG, int C>
+__global__ void __launch_bounds__(kPwxThreads, C <= 8 ? 2 : 1)
+    k_pwx(const typename V2<R>::T* __restrict__ A, typename V2<R>::T* __restrict__ B, KParams p,
+          const DevScalars* __restrict__ sc, const double* __restrict__ omega_tab, Tabs<R> t) {
+    using T = typename V2<R>::T;
+    extern __shared__ __align__(16) unsigned char pwx_smem[];
+    T* row = reinterpret_cast<T*>(pwx_smem);
+    constexpr int S = 32 * (C + 1);  // staged entries per component
+    const int iy = blockIdx.x;
+    const int nx = p.nx;
+    const R Ot = omega_tab ? (R)(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440) : (R)p.omega_t;
+    for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
+        cx<R> u[3];
+        pointwise_point<R, IMAG>(A, p, sc->scale, Ot, ix, iy, 7, u);
+        const int slot = (ix / C) * (C + 1) + (ix % C);
+#pragma unroll
+        for (int j = 0; j < 3; j++) row[j * S + slot] = T{u[j].re, u[j].im};
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5;
+    if (warp < 3) {
+        const T* r = row + warp * S;
+        const size_t base = ((size_t)warp * p.ny + iy) * nx;
+        cnx_solve_line<R, IMAG, C>(
+            [&](int i) {
+                const T v = r[(i / C) * (C + 1) + (i % C)];
+                return cx<R>{v.x, v.y};
+            },
+            B, base, nx, t, nullptr);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -170,6 +259,8 @@ __device__ __forceinline__ void cny_cols(const typename V2<R>::T* in, typename V
     const int i0 = lane * C;
     const size_t base = (size_t)j * p.nx * p.ny;
     const cx<R> zero = {R(0), R(0)};
+    LaneTabs<R, IMAG, C> lt;
+    lt.init(t, i0);
     cx<R> x[K][KEEP ? C : 1], v[K][C];
 #pragma unroll
     for (int m = 0; m < C; m++) {
@@ -184,7 +275,7 @@ __device__ __forceinline__ void cny_cols(const typename V2<R>::T* in, typename V
 #pragma unroll
     for (int k = 0; k < K; k++) {
         if (INC) cn_increment_rhs<R, IMAG, C>(v[k], t);
-        solve_chunk<R, IMAG, C>(v[k], t, i0);
+        solve_chunk<R, IMAG, C>(v[k], lt);
     }
     double acc = 0.0;
 #pragma unroll

@@ -224,16 +224,16 @@ __device__ __forceinline__ void finalize_norms(const double* partials, int nblk,
 // The pointwise substeps at grid point (ix, iy) of the state A (one grid),
 // written to B; scale: the pending renormalisation scale per component; Ot the
 // Rabi coupling Omega/sqrt2 of this step.
+// pointwise_point returns the three updated values in u; pointwise_at stores them.
 template <typename R, bool IMAG>
-__device__ __forceinline__ void pointwise_at(const typename V2<R>::T* __restrict__ A,
-                                             typename V2<R>::T* __restrict__ B, const KParams& p,
-                                             const double* scale, R Ot, int ix, int iy, int mask) {
+__device__ __forceinline__ void pointwise_point(const typename V2<R>::T* __restrict__ A, const KParams& p,
+                                                const double* scale, R Ot, int ix, int iy, int mask,
+                                                cx<R> (&u)[3]) {
     const size_t plane = (size_t)p.nx * p.ny;
     const size_t c = (size_t)iy * p.nx + ix;
     R d[3];
 #pragma unroll
     for (int j = 0; j < 3; j++) d[j] = (R)scale[j];
-    cx<R> u[3];
 #pragma unroll
     for (int j = 0; j < 3; j++) u[j] = scl(d[j], ld<R>(A, j * plane + c));
     const R dt = (R)p.dt;
@@ -268,6 +268,16 @@ __device__ __forceinline__ void pointwise_at(const typename V2<R>::T* __restrict
         calcnu_point<IMAG>(u, V, (R)p.c0, (R)p.c2, dt);
     }
     if (mask & 4) herm_point<IMAG>(u, (R)p.c2, Ot, dt);
+}
+
+template <typename R, bool IMAG>
+__device__ __forceinline__ void pointwise_at(const typename V2<R>::T* __restrict__ A,
+                                             typename V2<R>::T* __restrict__ B, const KParams& p,
+                                             const double* scale, R Ot, int ix, int iy, int mask) {
+    const size_t plane = (size_t)p.nx * p.ny;
+    const size_t c = (size_t)iy * p.nx + ix;
+    cx<R> u[3];
+    pointwise_point<R, IMAG>(A, p, scale, Ot, ix, iy, mask, u);
 #pragma unroll
     for (int j = 0; j < 3; j++) st<R>(B, j * plane + c, u[j]);
 }

@@ -38,6 +38,7 @@ struct Geometry {
     int wx;  // warps (lines) per block of the x sweep
     int wy;  // warps (columns) per block of the y sweep (shared-memory kernel)
     bool reg_x, reg_y;  // register-chunk kernels (lines of at most kRegMaxN points)
+    bool fused;         // 2D with register x lines: pointwise + CN-x in one kernel
     size_t smem_x, smem_y;
     int blocks_x, blocks_y, blocks_obs, blocks_norm;
 };
@@ -48,6 +49,9 @@ template <typename R> struct Launcher {
     static cudaError_t setup();
     static cudaError_t pointwise(cudaStream_t s, bool imag, const void* A, void* B, const KParams& p,
                                  const DevScalars* sc, const double* omega_tab, int mask);
+    // Fused pointwise substeps + CN along x of a 2D grid (Geometry::fused): A -> B.
+    static cudaError_t pwx(cudaStream_t s, bool imag, const void* A, void* B, const KParams& p, const DevScalars* sc,
+                           const double* omega_tab, const void* const* tabs_x);
     // cn_x / cn_y write per-block FP64 norm partials when last / finalize is set
     // (the step's final sweep); finalize_step then reduces them.
     static cudaError_t cn_x(cudaStream_t s, bool imag, bool last, const void* in, void* out, const KParams& p,

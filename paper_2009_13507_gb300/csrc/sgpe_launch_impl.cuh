@@ -67,8 +67,35 @@ template <typename K> static cudaError_t allow_smem(K kernel) {
     return e;
 }
 
+template <typename R, bool IMAG, int C> static cudaError_t pwx_allow() {
+    return cudaFuncSetAttribute(k_pwx<R, IMAG, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pwx_smem_bytes<R, C>());
+}
+
+template <typename R, bool IMAG> static cudaError_t pwx_allow_all() {
+    cudaError_t e;
+    if ((e = pwx_allow<R, IMAG, 1>())) return e;
+    if ((e = pwx_allow<R, IMAG, 2>())) return e;
+    if ((e = pwx_allow<R, IMAG, 4>())) return e;
+    if ((e = pwx_allow<R, IMAG, 8>())) return e;
+    if ((e = pwx_allow<R, IMAG, 16>())) return e;
+    return pwx_allow<R, IMAG, 32>();
+}
+
+template <typename R, int C>
+static void pwx_c(bool imag, int rows, cudaStream_t s, const typename V2<R>::T* A, typename V2<R>::T* B,
+                  const KParams& p, const DevScalars* sc, const double* omega_tab, const Tabs<R>& t) {
+    const size_t smem = pwx_smem_bytes<R, C>();
+    if (imag)
+        k_pwx<R, true, C><<<rows, kPwxThreads, smem, s>>>(A, B, p, sc, omega_tab, t);
+    else
+        k_pwx<R, false, C><<<rows, kPwxThreads, smem, s>>>(A, B, p, sc, omega_tab, t);
+}
+
 template <typename R> cudaError_t Launcher<R>::setup() {
     cudaError_t e;
+    if ((e = pwx_allow_all<R, true>())) return e;
+    if ((e = pwx_allow_all<R, false>())) return e;
     if ((e = allow_smem(k_cn_x<R, true, false>))) return e;
     if ((e = allow_smem(k_cn_x<R, true, true>))) return e;
     if ((e = allow_smem(k_cn_x<R, false, false>))) return e;
@@ -90,6 +117,25 @@ cudaError_t Launcher<R>::pointwise(cudaStream_t s, bool imag, const void* A, voi
         k_pointwise<R, true><<<grid, block, 0, s>>>((const T*)A, (T*)B, p, sc, omega_tab, mask);
     else
         k_pointwise<R, false><<<grid, block, 0, s>>>((const T*)A, (T*)B, p, sc, omega_tab, mask);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launcher<R>::pwx(cudaStream_t s, bool imag, const void* A, void* B, const KParams& p,
+                             const DevScalars* sc, const double* omega_tab, const void* const* tabs_x) {
+    using T = typename V2<R>::T;
+    if (p.dim != 2 || p.nx > kRegMaxN) return cudaErrorInvalidValue;
+    Tabs<R> t = make_tabs<R>(tabs_x);
+    const T* a = (const T*)A;
+    T* b = (T*)B;
+    switch (chunk_len(p.nx)) {
+        case 1: pwx_c<R, 1>(imag, p.ny, s, a, b, p, sc, omega_tab, t); break;
+        case 2: pwx_c<R, 2>(imag, p.ny, s, a, b, p, sc, omega_tab, t); break;
+        case 4: pwx_c<R, 4>(imag, p.ny, s, a, b, p, sc, omega_tab, t); break;
+        case 8: pwx_c<R, 8>(imag, p.ny, s, a, b, p, sc, omega_tab, t); break;
+        case 16: pwx_c<R, 16>(imag, p.ny, s, a, b, p, sc, omega_tab, t); break;
+        default: pwx_c<R, 32>(imag, p.ny, s, a, b, p, sc, omega_tab, t); break;
+    }
     return cudaGetLastError();
 }
 
