@@ -43,11 +43,10 @@ METRIC = "point-steps/s"
 # HERM, imaginary time, 2D Rashba), counted from the formulas it evaluates
 # (FMA = 2 flops; exp by its degree-9 Taylor polynomial).
 POINTWISE_FLOPS = 263
-# Algorithmic FP64 flops per grid point of the Crank-Nicolson x sweep (three
+# Algorithmic FP64 flops per grid point of one Crank-Nicolson sweep (three
 # component lines; real tables in imaginary time): forward 6, backward 8,
-# carry fix-up 4, 2w - x 4 per component. The fused head kernel (pointwise +
-# CN-x) does POINTWISE_FLOPS + CNX_FLOPS per point.
-CNX_FLOPS = 66
+# carry fix-up 4, 2w - x 4 per component.
+CN_FLOPS = 66
 # Nominal FP64 rate: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 1.259
 CPU_SAMPLE_STEPS = 300
@@ -367,11 +366,11 @@ def main():
     kavg = {names[i]: kms[i] / max(int(kcnt[i]), 1) for i in range(4) if int(kcnt[i]) > 0}
     dom = max(kavg, key=lambda n: kavg[n])
     share = {n: kms[i] / kms.sum() for i, n in enumerate(names) if int(kcnt[i]) > 0}
-    pw_ms = kavg[names[0]]
-    head_flops = POINTWISE_FLOPS + (CNX_FLOPS if fused else 0)
-    head_name = ("k_pwx<double, imag, 8> (SO+CALCNU+HERM, CN-x)" if fused
-                 else "k_pointwise<double> (SO+CALCNU+HERM)")
-    achieved_tflops = head_flops * NX * NY / (pw_ms * 1e-3) / 1e12
+    dom_ms = kavg[names[0]]
+    dom_flops = POINTWISE_FLOPS + (CN_FLOPS if fused else 0)
+    dom_name = ("k_pwx<double, imag, 8> (SO+CALCNU+HERM, CN-x)" if fused
+                else "k_pointwise<double> (SO+CALCNU+HERM)")
+    achieved_tflops = dom_flops * NX * NY / (dom_ms * 1e-3) / 1e12
 
     # precision form (complex64 state, FP64 reductions) on the same workload
     s32 = sgpe.Solver(2, NX, NY, dx=DX, precision="c64", device=dev)
@@ -380,6 +379,9 @@ def main():
     ms32, en32, _ = timed_run(s32, psi0_dev32, args.steps, args.warmup)
     t32 = statistics.mean(ms32)
     e64, e32 = en64[-1][5], en32[-1][5]
+    reset(s32, psi0_dev32)
+    kms32, kcnt32 = s32.profile_steps(NSTEPS, True)
+    kavg32 = {names[i]: kms32[i] / max(int(kcnt32[i]), 1) for i in range(4) if int(kcnt32[i]) > 0}
 
     # end to end through the C ABI with host buffers: pinned host state in,
     # 2000 steps, observables and the final state out, copies inside the timed region
@@ -416,17 +418,17 @@ def main():
                    "grid": [NX, NY], "time_steps_per_bench_step": NSTEPS,
                    "l2": "flushed (256 MiB write) between benchmark steps; the 3 MiB state is L2-resident within a run",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "roofline": {"bound": "alu", "kernel": head_name,
+        "roofline": {"bound": "alu", "kernel": dom_name,
                      "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": HEAD_TRAFFIC_BYTES,
                      "peak_source": "nominal FP64: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (measured 1.20 at 1995 MHz)",
-                     "flops_per_point": head_flops, "avg_launch_ms": pw_ms},
+                     "flops_per_point": dom_flops, "avg_launch_ms": dom_ms},
         "kernels": {"avg_ms": kavg, "share": share, "dominant": dom},
         "hbm_view": {"algorithmic_bytes_per_point_step": 192,
                      "effective_GBps": value / ws * 192 / 1e9},
         "chosen": {"form": "complex64 state, FP64 reductions", "value": ws * point_steps / (t32 * 1e-3),
                    "ms_per_step": t32, "energy_rel_err_vs_fp64": abs(e32 - e64) / abs(e64),
-                   "speedup_vs_fp64": t_step / t32},
+                   "speedup_vs_fp64": t_step / t32, "kernels_avg_ms": kavg32},
         "energy": {"E_fp64": e64, "E_c64": e32, "E_profile_pass": e_prof[5]},
         "forms": forms,
         "cpu_baseline": cpu,

@@ -241,6 +241,9 @@ class Solver:
     def launches_per_step(self) -> int:
         return int(self.lib.sgpe_launches_per_step(self.ctx))
 
+    def synchronize(self):
+        self.stream.synchronize()
+
     # -- differentiation form ----------------------------------------------------
     def loss_grad(self, omega_t, rho_tgt, checkpoint_every=50):
         """Run len(omega_t) real-time steps from the current state (which ends as
@@ -291,9 +294,6 @@ def _rabi_trap_loss_function():
 def rabi_trap_loss(omega_t, w, solver, psi0, rho_tgt, checkpoint_every=50):
     """Differentiable loss through the GPU propagator (see RabiTrapLoss)."""
     return _rabi_trap_loss_function().apply(omega_t, w, solver, psi0, rho_tgt, checkpoint_every)
-
-    def synchronize(self):
-        self.stream.synchronize()
 
 
 class Instance(ctypes.Structure):
