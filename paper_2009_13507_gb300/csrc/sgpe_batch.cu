@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(128) kb_pointwise(const typename V2<R>::T* __r
     int ix, iy;
     tile_point(I.p, tl.y, &ix, &iy);
     if (ix >= I.p.nx || iy >= I.p.ny) return;
-    pointwise_at<R, IMAG>(A + I.off, B + I.off, I.p, scs[tl.x].scale, (R)I.p.omega_t, ix, iy, 7);
+    pointwise_at<R, IMAG>(A + I.off, B + I.off, I.p, scs + tl.x, pick<R>(I.p.omega_t, I.p.f_omega_t), ix, iy, 7);
 }
 
 // Work entry of the x sweep: (instance, line, partial slot or -1).
@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(128) kb_finalize(const BInst* __restrict__ ins
         for (int j = 0; j < 3; j++) {
             sc->norms[j] = N[j];
             sc->scale[j] = d[j];
+            sc->scale_f[j] = (float)d[j];
         }
         if (!finite) sc->err |= 1;
         sc->step_idx += 1;
@@ -146,7 +147,10 @@ __global__ void __launch_bounds__(128) kb_flush(typename V2<R>::T* A, const BIns
 __global__ void kb_reset(DevScalars* scs, int n, int clear_err) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n)
-        for (int j = 0; j < 4; j++) scs[i].scale[j] = 1.0;
+        for (int j = 0; j < 4; j++) {
+            scs[i].scale[j] = 1.0;
+            scs[i].scale_f[j] = 1.0f;
+        }
     if (i < n && clear_err) scs[i].err = 0;
 }
 
@@ -399,6 +403,7 @@ sgpe_status sgpe_batch_create(sgpe_batch** out, int n, const sgpe_instance* inst
         BInst I;
         memset(&I, 0, sizeof(I));
         I.p = make_kparams(q.dim, q.nx, q.ny, q.dx, q.dy, &q.params);
+        fill_f32(I.p);
         I.off = off;
         off += ((long long)3 * q.nx * q.ny + 63) / 64 * 64;
         I.lenx = table_len(q.nx);

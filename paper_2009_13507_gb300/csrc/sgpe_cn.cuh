@@ -130,6 +130,35 @@ template <typename R, int C> struct CnShape {
     static constexpr bool KEEP = C <= 8;
 };
 
+// Per-lane accumulator of |o|^2 over the lane's points for the FP64 norm
+// partials. complex64 state: each square is split exactly into p + e
+// (p = x*x, e = fma(x, x, -p)) and summed as an unevaluated FP32 pair
+// (Knuth's TwoSum for the high part, the rounding errors collected in the low
+// part): about 2^-44 relative, i.e. FP64-grade for the few dozen terms of a
+// lane, on the FP32 pipe instead of GB300's much slower FP64 pipe.
+template <typename R> struct NormAcc;
+template <> struct NormAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(cx<double> o) { s += o.re * o.re + o.im * o.im; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct NormAcc<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add1(float x) {
+        const float p = x * x;
+        const float e = fmaf(x, x, -p);
+        const float t = hi + p;
+        const float bp = t - hi;
+        lo += ((hi - (t - bp)) + (p - bp)) + e;
+        hi = t;
+    }
+    __device__ __forceinline__ void add(cx<float> o) {
+        add1(o.re);
+        add1(o.im);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -162,7 +191,7 @@ __device__ __forceinline__ void cnx_solve_line(Load load, typename V2<R>::T* out
     constexpr bool INC = sizeof(R) == 4;
     if (INC) cn_increment_rhs<R, IMAG, C>(v, t);
     solve_chunk<R, IMAG, C>(v, lt);
-    double acc = 0.0;
+    NormAcc<R> acc;
 #pragma unroll
     for (int m = 0; m < C; m++) {
         if (i0 + m < n) {
@@ -170,12 +199,12 @@ __device__ __forceinline__ void cnx_solve_line(Load load, typename V2<R>::T* out
             cx<R> o = INC ? cx<R>{fma(R(2), v[m].re, xm.re), fma(R(2), v[m].im, xm.im)}
                           : cx<R>{fma(R(2), v[m].re, -xm.re), fma(R(2), v[m].im, -xm.im)};
             st<R>(out, base + i0 + m, o);
-            if (part) acc += (double)o.re * (double)o.re + (double)o.im * (double)o.im;
+            if (part) acc.add(o);
         }
     }
     if (part) {
-        acc = warp_sum(acc);
-        if (lane == 0) *part = acc;
+        const double t = warp_sum(acc.value());
+        if (lane == 0) *part = t;
     }
 }
 
@@ -219,10 +248,11 @@ __global__ void __launch_bounds__(kPwxThreads, C <= 8 ? 2 : 1)
     constexpr int S = 32 * (C + 1);  // staged entries per component
     const int iy = blockIdx.x;
     const int nx = p.nx;
-    const R Ot = omega_tab ? (R)(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440) : (R)p.omega_t;
+    const R Ot = omega_tab ? (R)(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440)
+                           : pick<R>(p.omega_t, p.f_omega_t);
     for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
         cx<R> u[3];
-        pointwise_point<R, IMAG>(A, p, sc->scale, Ot, ix, iy, 7, u);
+        pointwise_point<R, IMAG>(A, p, sc, Ot, ix, iy, 7, u);
         const int slot = (ix / C) * (C + 1) + (ix % C);
 #pragma unroll
         for (int j = 0; j < 3; j++) row[j * S + slot] = T{u[j].re, u[j].im};
@@ -277,7 +307,7 @@ __device__ __forceinline__ void cny_cols(const typename V2<R>::T* in, typename V
         if (INC) cn_increment_rhs<R, IMAG, C>(v[k], t);
         solve_chunk<R, IMAG, C>(v[k], lt);
     }
-    double acc = 0.0;
+    NormAcc<R> acc;
 #pragma unroll
     for (int m = 0; m < C; m++) {
         if (i0 + m < n) {
@@ -289,14 +319,14 @@ __device__ __forceinline__ void cny_cols(const typename V2<R>::T* in, typename V
                     cx<R> o = INC ? cx<R>{fma(R(2), v[k][m].re, xm.re), fma(R(2), v[k][m].im, xm.im)}
                                   : cx<R>{fma(R(2), v[k][m].re, -xm.re), fma(R(2), v[k][m].im, -xm.im)};
                     st<R>(out, g + k, o);
-                    acc += (double)o.re * (double)o.re + (double)o.im * (double)o.im;
+                    if (part) acc.add(o);
                 }
             }
         }
     }
     if (part) {
-        acc = warp_sum(acc);
-        if (lane == 0) *part = acc;
+        const double t = warp_sum(acc.value());
+        if (lane == 0) *part = t;
     }
 }
 

@@ -205,7 +205,27 @@ struct KParams {
     double cell;      // dx (1D) or dx*dy
     int renorm;       // 0, 1 (DJ2), 2 (DJ)
     double mag;
+    // FP32 copies of the constants the pointwise substeps use, for the
+    // complex64 form (no FP64 -> FP32 conversion per grid point); filled by
+    // fill_f32 on the host just before a launch.
+    float f_dt, f_hx, f_hy, f_c0, f_c2, f_vx, f_vy, f_omega_t;
 };
+
+inline void fill_f32(KParams& k) {
+    k.f_dt = (float)k.dt;
+    k.f_hx = (float)k.hx;
+    k.f_hy = (float)k.hy;
+    k.f_c0 = (float)k.c0;
+    k.f_c2 = (float)k.c2;
+    k.f_vx = (float)k.vx;
+    k.f_vy = (float)k.vy;
+    k.f_omega_t = (float)k.omega_t;
+}
+
+// The constant in the arithmetic type R: d for double, its FP32 copy f for float.
+template <typename R> __device__ __forceinline__ R pick(double d, float f);
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
 // ---------------------------------------------------------------------------
 // Pointwise substeps at one grid point. u[j] holds the (already scaled) state

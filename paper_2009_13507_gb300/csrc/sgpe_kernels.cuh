@@ -19,6 +19,7 @@ namespace sgpe {
 // ---------------------------------------------------------------------------
 struct DevScalars {
     double scale[4];     // pending renormalisation scale per component (DJ2: all equal)
+    float scale_f[4];    // the same rounded to FP32 (read by the complex64 form)
     double norms[4];     // N_j of the state written by the last completed step
     double obs[16];      // observables of the last sgpe_energy
     int step_idx;        // index into a per-step Omega table (real time)
@@ -208,6 +209,7 @@ __device__ __forceinline__ void finalize_norms(const double* partials, int nblk,
             for (int j = 0; j < 3; j++) {
                 sc->norms[j] = N[j];
                 sc->scale[j] = d[j];
+                sc->scale_f[j] = (float)d[j];
             }
             if (!finite) sc->err |= 1;
             if (advance_step) sc->step_idx += 1;
@@ -227,16 +229,16 @@ __device__ __forceinline__ void finalize_norms(const double* partials, int nblk,
 // pointwise_point returns the three updated values in u; pointwise_at stores them.
 template <typename R, bool IMAG>
 __device__ __forceinline__ void pointwise_point(const typename V2<R>::T* __restrict__ A, const KParams& p,
-                                                const double* scale, R Ot, int ix, int iy, int mask,
+                                                const DevScalars* sc, R Ot, int ix, int iy, int mask,
                                                 cx<R> (&u)[3]) {
     const size_t plane = (size_t)p.nx * p.ny;
     const size_t c = (size_t)iy * p.nx + ix;
     R d[3];
 #pragma unroll
-    for (int j = 0; j < 3; j++) d[j] = (R)scale[j];
+    for (int j = 0; j < 3; j++) d[j] = pick<R>(sc->scale[j], sc->scale_f[j]);
 #pragma unroll
     for (int j = 0; j < 3; j++) u[j] = scl(d[j], ld<R>(A, j * plane + c));
-    const R dt = (R)p.dt;
+    const R dt = pick<R>(p.dt, p.f_dt);
     if ((mask & 1) && p.so_case) {
         cx<R> X[3], Y[3];
         const cx<R> zero = {R(0), R(0)};
@@ -256,28 +258,28 @@ __device__ __forceinline__ void pointwise_point(const typename V2<R>::T* __restr
         R gx[3], gy[3];
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            gx[j] = (R)p.hx * d[j];
-            gy[j] = (R)p.hy * d[j];
+            gx[j] = pick<R>(p.hx, p.f_hx) * d[j];
+            gy[j] = pick<R>(p.hy, p.f_hy) * d[j];
         }
         so_point<IMAG>(u, X, Y, gx, gy, p.so_case);
     }
     if (mask & 2) {
         // V = wx^2 x^2/2 + wy^2 y^2/2 with x = kx dx: kx^2 is an exact integer
         const int kx = ix - p.nx / 2, ky = iy - p.ny / 2;
-        R V = (R)p.vx * (R)(kx * kx) + (p.dim == 2 ? (R)p.vy * (R)(ky * ky) : R(0));
-        calcnu_point<IMAG>(u, V, (R)p.c0, (R)p.c2, dt);
+        R V = pick<R>(p.vx, p.f_vx) * (R)(kx * kx) + (p.dim == 2 ? pick<R>(p.vy, p.f_vy) * (R)(ky * ky) : R(0));
+        calcnu_point<IMAG>(u, V, pick<R>(p.c0, p.f_c0), pick<R>(p.c2, p.f_c2), dt);
     }
-    if (mask & 4) herm_point<IMAG>(u, (R)p.c2, Ot, dt);
+    if (mask & 4) herm_point<IMAG>(u, pick<R>(p.c2, p.f_c2), Ot, dt);
 }
 
 template <typename R, bool IMAG>
 __device__ __forceinline__ void pointwise_at(const typename V2<R>::T* __restrict__ A,
                                              typename V2<R>::T* __restrict__ B, const KParams& p,
-                                             const double* scale, R Ot, int ix, int iy, int mask) {
+                                             const DevScalars* sc, R Ot, int ix, int iy, int mask) {
     const size_t plane = (size_t)p.nx * p.ny;
     const size_t c = (size_t)iy * p.nx + ix;
     cx<R> u[3];
-    pointwise_point<R, IMAG>(A, p, scale, Ot, ix, iy, mask, u);
+    pointwise_point<R, IMAG>(A, p, sc, Ot, ix, iy, mask, u);
 #pragma unroll
     for (int j = 0; j < 3; j++) st<R>(B, j * plane + c, u[j]);
 }
@@ -290,8 +292,9 @@ __global__ void __launch_bounds__(128) k_pointwise(const typename V2<R>::T* __re
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int iy = blockIdx.y * blockDim.y + threadIdx.y;
     if (ix >= p.nx || iy >= p.ny) return;
-    const R Ot = omega_tab ? (R)(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440) : (R)p.omega_t;
-    pointwise_at<R, IMAG>(A, B, p, sc->scale, Ot, ix, iy, mask);
+    const R Ot = omega_tab ? (R)(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440)
+                           : pick<R>(p.omega_t, p.f_omega_t);
+    pointwise_at<R, IMAG>(A, B, p, sc, Ot, ix, iy, mask);
 }
 
 // ---------------------------------------------------------------------------
@@ -417,6 +420,7 @@ static __global__ void __launch_bounds__(96) k_finalize(const double* partials, 
         for (int q3 = 0; q3 < 3; q3++) {
             sc->norms[q3] = N[q3];
             sc->scale[q3] = d[q3];
+            sc->scale_f[q3] = (float)d[q3];
         }
         if (!finite) sc->err |= 1;
         if (advance_step) sc->step_idx += 1;
@@ -512,7 +516,10 @@ __global__ void k_flush(typename V2<R>::T* A, size_t plane, const DevScalars* sc
 }
 
 static __global__ void k_reset_scale(DevScalars* sc) {
-    if (threadIdx.x < 4) sc->scale[threadIdx.x] = 1.0;
+    if (threadIdx.x < 4) {
+        sc->scale[threadIdx.x] = 1.0;
+        sc->scale_f[threadIdx.x] = 1.0f;
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -113,10 +113,12 @@ cudaError_t Launcher<R>::pointwise(cudaStream_t s, bool imag, const void* A, voi
     // blocks spread the points evenly over the 152 SMs (1024 blocks at 256^2).
     dim3 block(32, p.dim == 2 ? 2 : 1);
     dim3 grid(ceil_div(p.nx, 32), p.dim == 2 ? ceil_div(p.ny, 2) : 1);
+    KParams q = p;
+    fill_f32(q);
     if (imag)
-        k_pointwise<R, true><<<grid, block, 0, s>>>((const T*)A, (T*)B, p, sc, omega_tab, mask);
+        k_pointwise<R, true><<<grid, block, 0, s>>>((const T*)A, (T*)B, q, sc, omega_tab, mask);
     else
-        k_pointwise<R, false><<<grid, block, 0, s>>>((const T*)A, (T*)B, p, sc, omega_tab, mask);
+        k_pointwise<R, false><<<grid, block, 0, s>>>((const T*)A, (T*)B, q, sc, omega_tab, mask);
     return cudaGetLastError();
 }
 
@@ -128,13 +130,15 @@ cudaError_t Launcher<R>::pwx(cudaStream_t s, bool imag, const void* A, void* B, 
     Tabs<R> t = make_tabs<R>(tabs_x);
     const T* a = (const T*)A;
     T* b = (T*)B;
+    KParams q = p;
+    fill_f32(q);
     switch (chunk_len(p.nx)) {
-        case 1: pwx_c<R, 1>(imag, p.ny, s, a, b, p, sc, omega_tab, t); break;
-        case 2: pwx_c<R, 2>(imag, p.ny, s, a, b, p, sc, omega_tab, t); break;
-        case 4: pwx_c<R, 4>(imag, p.ny, s, a, b, p, sc, omega_tab, t); break;
-        case 8: pwx_c<R, 8>(imag, p.ny, s, a, b, p, sc, omega_tab, t); break;
-        case 16: pwx_c<R, 16>(imag, p.ny, s, a, b, p, sc, omega_tab, t); break;
-        default: pwx_c<R, 32>(imag, p.ny, s, a, b, p, sc, omega_tab, t); break;
+        case 1: pwx_c<R, 1>(imag, p.ny, s, a, b, q, sc, omega_tab, t); break;
+        case 2: pwx_c<R, 2>(imag, p.ny, s, a, b, q, sc, omega_tab, t); break;
+        case 4: pwx_c<R, 4>(imag, p.ny, s, a, b, q, sc, omega_tab, t); break;
+        case 8: pwx_c<R, 8>(imag, p.ny, s, a, b, q, sc, omega_tab, t); break;
+        case 16: pwx_c<R, 16>(imag, p.ny, s, a, b, q, sc, omega_tab, t); break;
+        default: pwx_c<R, 32>(imag, p.ny, s, a, b, q, sc, omega_tab, t); break;
     }
     return cudaGetLastError();
 }
