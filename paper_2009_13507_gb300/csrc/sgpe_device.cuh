@@ -222,6 +222,15 @@ inline void fill_f32(KParams& k) {
     k.f_omega_t = (float)k.omega_t;
 }
 
+// Programmatic dependent launch (sm_90+). The step kernels are launched with
+// programmatic stream serialization, so a kernel's blocks may be scheduled
+// while its predecessor on the stream is still running: every such kernel
+// first lets its own successor launch (pdl_trigger), then waits until the
+// predecessor grid has completed and its writes are visible (pdl_wait) before
+// it touches any data the predecessor produces. Launched normally, both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // The constant in the arithmetic type R: d for double, its FP32 copy f for float.
 template <typename R> __device__ __forceinline__ R pick(double d, float f);
 template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }

@@ -6,8 +6,7 @@ template struct Launcher<double>;
 
 cudaError_t finalize_step(cudaStream_t s, const double* partials, int nblk, double cell, int renorm, double mag,
                           int advance, DevScalars* sc) {
-    k_finalize<<<1, 96, 0, s>>>(partials, nblk / 3, cell, renorm, mag, advance, sc);
-    return cudaGetLastError();
+    return launch_pdl(k_finalize, dim3(1), dim3(96), 0, s, partials, nblk / 3, cell, renorm, mag, advance, sc);
 }
 
 cudaError_t reset_scale(cudaStream_t s, DevScalars* sc) {

@@ -3,11 +3,15 @@
 // (double: complex128 state; float: complex64 state) and on the time mode
 // (IMAG: z = dt, imaginary time; otherwise z = i dt, real time).
 //
-// One step, 2D:  k_pointwise (A -> B): pending scale, SO, CALCNU, HERM
-//                k_cn_x      (B -> B): Crank-Nicolson along x, one warp per line
-//                k_cn_y      (B -> A): Crank-Nicolson along y, one warp per column,
-//                                      FP64 norm partials, last block -> scale
-// One step, 1D:  k_pointwise (A -> B), k_cn_x<LAST> (B -> A) with the norm.
+// One step, 2D with lines of at most 1024 points (sgpe_cn.cuh):
+//   k_pwx      (A -> B): pending scale, SO, CALCNU, HERM, then Crank-Nicolson
+//                        along x from shared memory, one block per row
+//   k_cny_reg  (B -> A): Crank-Nicolson along y, one warp per column (pair),
+//                        FP64 norm partials
+//   k_finalize         : norms, next pending scale, step counter
+// Longer lines: k_pointwise and the shared-memory sweeps k_cn_x / k_cn_y below.
+// One step, 1D: k_pointwise (A -> B), the x sweep (B -> A) with norm partials,
+// k_finalize.
 // Reductions are FP64 in both precisions and deterministic (fixed order).
 #pragma once
 #include "sgpe_device.cuh"
@@ -291,6 +295,7 @@ __global__ void __launch_bounds__(128) k_pointwise(const typename V2<R>::T* __re
                                                    const double* __restrict__ omega_tab, int mask) {
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    pdl_wait();
     if (ix >= p.nx || iy >= p.ny) return;
     const R Ot = omega_tab ? (R)(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440)
                            : pick<R>(p.omega_t, p.f_omega_t);
@@ -398,6 +403,8 @@ static __global__ void __launch_bounds__(96) k_finalize(const double* partials, 
     __shared__ double red[3];
     const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double* q = partials + (size_t)j * m;
+    pdl_trigger();  // one small block: the next step's first kernel may launch now
+    pdl_wait();
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     int b = lane;
     for (; b + 96 < m; b += 128) {

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <utility>
+
 #include "../../include/sgpe.h"
 #include "sgpe_device.cuh"
 
@@ -11,6 +13,25 @@ namespace sgpe {
 
 struct KParams;
 struct DevScalars;
+
+// Launch a step kernel with programmatic stream serialization: its blocks may
+// be scheduled before the previous kernel on the stream completes; the kernel
+// itself waits (pdl_wait) before reading what that kernel wrote.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Launch geometry shared by the API layer (buffer sizing) and the launchers.
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }

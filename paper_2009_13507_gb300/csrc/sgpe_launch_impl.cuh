@@ -16,9 +16,9 @@ template <typename R, int C>
 static void cnx_reg_c(bool imag, dim3 grid, cudaStream_t s, const typename V2<R>::T* in, typename V2<R>::T* out,
                       const KParams& p, const Tabs<R>& t, double* partials) {
     if (imag)
-        k_cnx_reg<R, true, C><<<grid, 32, 0, s>>>(in, out, p, t, partials);
+        launch_pdl(k_cnx_reg<R, true, C>, grid, dim3(32), 0, s, in, out, p, t, partials);
     else
-        k_cnx_reg<R, false, C><<<grid, 32, 0, s>>>(in, out, p, t, partials);
+        launch_pdl(k_cnx_reg<R, false, C>, grid, dim3(32), 0, s, in, out, p, t, partials);
 }
 
 template <typename R>
@@ -38,9 +38,9 @@ template <typename R, int C>
 static void cny_reg_c(bool imag, dim3 grid, cudaStream_t s, const typename V2<R>::T* in, typename V2<R>::T* out,
                       const KParams& p, const Tabs<R>& t, double* partials) {
     if (imag)
-        k_cny_reg<R, true, C><<<grid, 32, 0, s>>>(in, out, p, t, partials);
+        launch_pdl(k_cny_reg<R, true, C>, grid, dim3(32), 0, s, in, out, p, t, partials);
     else
-        k_cny_reg<R, false, C><<<grid, 32, 0, s>>>(in, out, p, t, partials);
+        launch_pdl(k_cny_reg<R, false, C>, grid, dim3(32), 0, s, in, out, p, t, partials);
 }
 
 template <typename R>
@@ -87,9 +87,9 @@ static void pwx_c(bool imag, int rows, cudaStream_t s, const typename V2<R>::T* 
                   const KParams& p, const DevScalars* sc, const double* omega_tab, const Tabs<R>& t) {
     const size_t smem = pwx_smem_bytes<R, C>();
     if (imag)
-        k_pwx<R, true, C><<<rows, kPwxThreads, smem, s>>>(A, B, p, sc, omega_tab, t);
+        launch_pdl(k_pwx<R, true, C>, dim3(rows), dim3(kPwxThreads), smem, s, A, B, p, sc, omega_tab, t);
     else
-        k_pwx<R, false, C><<<rows, kPwxThreads, smem, s>>>(A, B, p, sc, omega_tab, t);
+        launch_pdl(k_pwx<R, false, C>, dim3(rows), dim3(kPwxThreads), smem, s, A, B, p, sc, omega_tab, t);
 }
 
 template <typename R> cudaError_t Launcher<R>::setup() {
@@ -116,9 +116,9 @@ cudaError_t Launcher<R>::pointwise(cudaStream_t s, bool imag, const void* A, voi
     KParams q = p;
     fill_f32(q);
     if (imag)
-        k_pointwise<R, true><<<grid, block, 0, s>>>((const T*)A, (T*)B, q, sc, omega_tab, mask);
+        launch_pdl(k_pointwise<R, true>, grid, block, 0, s, (const T*)A, (T*)B, q, sc, omega_tab, mask);
     else
-        k_pointwise<R, false><<<grid, block, 0, s>>>((const T*)A, (T*)B, q, sc, omega_tab, mask);
+        launch_pdl(k_pointwise<R, false>, grid, block, 0, s, (const T*)A, (T*)B, q, sc, omega_tab, mask);
     return cudaGetLastError();
 }
 
