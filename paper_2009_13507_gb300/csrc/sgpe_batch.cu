@@ -403,7 +403,7 @@ sgpe_status sgpe_batch_create(sgpe_batch** out, int n, const sgpe_instance* inst
         BInst I;
         memset(&I, 0, sizeof(I));
         I.p = make_kparams(q.dim, q.nx, q.ny, q.dx, q.dy, &q.params);
-        fill_f32(I.p);
+        fill_derived(I.p);
         I.off = off;
         off += ((long long)3 * q.nx * q.ny + 63) / 64 * 64;
         I.lenx = table_len(q.nx);

@@ -61,10 +61,10 @@ template <typename R> __device__ __forceinline__ void st(typename V2<R>::T* p, s
 // exponential / sincos (range reduction plus a long polynomial) would dominate
 // the pointwise substeps. Every argument here is dt times an energy, normally
 // below 1/64 in magnitude, where a truncated Taylor series evaluated by
-// Horner's rule is accurate to well under an ulp:
-//   exp(x) = sum_{n<=7} x^n/n!        (|x| <= 2^-6: first omitted term < 9e-20)
+// Horner's rule is accurate to under an ulp:
+//   exp(x) = sum_{n<=6} x^n/n!   (|x| <= 2^-6: first omitted term < 4.5e-17, 0.2 ulp of 1)
 //   sin(x) = x sum_{n<=3} (-x^2)^n/(2n+1)!   (omitted < 1e-20)
-//   cos(x) = sum_{n<=4} (-x^2)^n/(2n)!       (omitted < 3e-25)
+//   cos(x) = sum_{n<=3} (-x^2)^n/(2n)!       (omitted < 9e-20)
 // Larger arguments take CUDA's exp / sincos. The range test reads the high
 // word of the double on the integer pipe: |x| < 2^-6 iff (hi & 0x7fffffff) < 0x3F900000.
 // FP32: CUDA's expf / sincosf (full-range, FP32 pipe).
@@ -75,8 +75,7 @@ __device__ __forceinline__ bool small_arg(double x) {
 
 __device__ __forceinline__ double exp_small(double x) {
     if (small_arg(x)) {
-        double p = 1.0 / 5040.0;
-        p = fma(p, x, 1.0 / 720.0);
+        double p = 1.0 / 720.0;
         p = fma(p, x, 1.0 / 120.0);
         p = fma(p, x, 1.0 / 24.0);
         p = fma(p, x, 1.0 / 6.0);
@@ -96,8 +95,7 @@ __device__ __forceinline__ void sincos_small(double x, double* s, double* c) {
         ps = fma(ps, -t, 1.0 / 6.0);
         ps = fma(ps, -t, 1.0);
         *s = ps * x;
-        double pc = 1.0 / 40320.0;  // cos(x) = 1 - t/2 + t^2/24 - t^3/720 + t^4/40320
-        pc = fma(pc, -t, 1.0 / 720.0);
+        double pc = 1.0 / 720.0;  // cos(x) = 1 - t/2 + t^2/24 - t^3/720
         pc = fma(pc, -t, 1.0 / 24.0);
         pc = fma(pc, -t, 0.5);
         *c = fma(pc, -t, 1.0);
@@ -207,11 +205,27 @@ struct KParams {
     double mag;
     // FP32 copies of the constants the pointwise substeps use, for the
     // complex64 form (no FP64 -> FP32 conversion per grid point); filled by
-    // fill_f32 on the host just before a launch.
+    // fill_derived on the host just before a launch.
     float f_dt, f_hx, f_hy, f_c0, f_c2, f_vx, f_vy, f_omega_t;
+    // Derived FP64 constants of the complex128 pointwise substeps (fill_derived):
+    // dt folded into the CALCNU exponent coefficients and into the HERM series.
+    double n_c0, n_c2, n_vx, n_vy;  // -dt c0, -dt c2, -dt vx, -dt vy
+    double dt2;                     // dt^2
+    double hs[5], hk[5];            // dt/(2n+1)!, dt^2/(2n+2)!  (n = 0..4)
 };
 
-inline void fill_f32(KParams& k) {
+inline void fill_derived(KParams& k) {
+    k.n_c0 = -k.dt * k.c0;
+    k.n_c2 = -k.dt * k.c2;
+    k.n_vx = -k.dt * k.vx;
+    k.n_vy = -k.dt * k.vy;
+    k.dt2 = k.dt * k.dt;
+    double f = 1.0;  // (2n+1)!
+    for (int n = 0; n < 5; n++) {
+        if (n > 0) f *= (2.0 * n) * (2.0 * n + 1.0);
+        k.hs[n] = k.dt / f;
+        k.hk[n] = k.dt2 / (f * (2.0 * n + 2.0));
+    }
     k.f_dt = (float)k.dt;
     k.f_hx = (float)k.hx;
     k.f_hy = (float)k.hy;
@@ -325,13 +339,61 @@ __device__ __forceinline__ void calcnu_point(cx<R> (&u)[3], R V, R c0, R c2, R d
     }
 }
 
+// CALCNU for the complex128 state with dt folded into the coefficients
+// (KParams::n_*): Vn = -dt V, exponents x_j = -dt mu_j; imaginary time
+// u_j <- exp(x_j) u_j, real time u_j <- (cos x_j + i sin x_j) u_j = exp(-i dt mu_j) u_j.
+template <bool IMAG, typename R>
+__device__ __forceinline__ void calcnu_point_dt(cx<R> (&u)[3], R Vn, const KParams& p) {
+    R rp = nrm(u[0]), r0 = nrm(u[1]), rm = nrm(u[2]);
+    R base = fma((R)p.n_c0, rp + r0 + rm, Vn);
+    R x[3] = {fma((R)p.n_c2, rp - rm + r0, base), fma((R)p.n_c2, rp + rm, base), fma((R)p.n_c2, rm - rp + r0, base)};
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        if (IMAG) {
+            u[j] = scl(exp_small(x[j]), u[j]);
+        } else {
+            R s, c;
+            sincos_small(x[j], &s, &c);
+            u[j] = mul(cx<R>{c, s}, u[j]);
+        }
+    }
+}
+
+// HERM coefficients s, k (see herm_coeffs) from the dt-folded series constants
+// KParams::hs, hk: s = sum_n hs_n v^n, k = +-sum_n hk_n v^n, v = +-dt^2 C^2.
+template <bool IMAG>
+__device__ __forceinline__ void herm_coeffs_dt(double C2, const KParams& p, double* s, double* k) {
+    double w = p.dt2 * C2;  // >= 0
+    double v = IMAG ? w : -w;
+    if ((unsigned)__double2hiint(w) < 0x3EB00000u) {
+        // w < 2^-20: three terms each
+        *s = fma(fma(v, p.hs[2], p.hs[1]), v, p.hs[0]);
+        double pk = fma(fma(v, p.hk[2], p.hk[1]), v, p.hk[0]);
+        *k = IMAG ? pk : -pk;
+        return;
+    }
+    if (w <= 1.0 / 1024.0) {
+        double ps = p.hs[4], pk = p.hk[4];
+#pragma unroll
+        for (int n = 3; n >= 0; n--) {
+            ps = fma(ps, v, p.hs[n]);
+            pk = fma(pk, v, p.hk[n]);
+        }
+        *s = ps;
+        *k = IMAG ? pk : -pk;
+        return;
+    }
+    herm_coeffs<IMAG>(C2, p.dt, s, k);
+}
+
 // HERM (Appendix A): with a = c2 psi_-^* psi_0 + Ot, b = c2 psi_0^* psi_+ + Ot
 // and A = [[0,a,0],[a*,0,b],[0,b*,0]] (frozen over the substep), psi <- exp(-z A) psi,
 // evaluated as psi - s_z A psi + k A^2 psi with A^2 = [[|a|^2,0,ab],[0,C^2,0],[a*b*,0,|b|^2]].
 // This equals the eigen-decomposition form V diag(exp(-z lambda)) V^{-1} of Eq. (11) and
 // stays finite at C = 0.
+// kp (nullable): take s, k from the dt-folded constants (complex128 step).
 template <bool IMAG, typename R>
-__device__ __forceinline__ void herm_point(cx<R> (&u)[3], R c2, R Ot, R dt) {
+__device__ __forceinline__ void herm_point(cx<R> (&u)[3], R c2, R Ot, R dt, const KParams* kp = nullptr) {
     cx<R> a = cmul(u[2], u[1]);  // psi_-^* psi_0
     a = {fma(c2, a.re, Ot), c2 * a.im};
     cx<R> b = cmul(u[1], u[0]);  // psi_0^* psi_+
@@ -339,7 +401,14 @@ __device__ __forceinline__ void herm_point(cx<R> (&u)[3], R c2, R Ot, R dt) {
     R na = nrm(a), nb = nrm(b);
     R C2 = na + nb;
     R s, k;
-    herm_coeffs<IMAG>(C2, dt, &s, &k);
+    if (sizeof(R) == 8 && kp) {
+        double sd, kd;
+        herm_coeffs_dt<IMAG>((double)C2, *kp, &sd, &kd);
+        s = (R)sd;
+        k = (R)kd;
+    } else {
+        herm_coeffs<IMAG>(C2, dt, &s, &k);
+    }
     cx<R> ab = mul(a, b);
     // A psi
     cx<R> Ap = mul(a, u[1]);

@@ -260,20 +260,36 @@ __device__ __forceinline__ void pointwise_point(const typename V2<R>::T* __restr
             }
         }
         R gx[3], gy[3];
+        if (p.renorm != 2) {
+            // one scale for all components (DJ2, or none): the same products, formed once
+            const R g = pick<R>(p.hx, p.f_hx) * d[0], h = pick<R>(p.hy, p.f_hy) * d[0];
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-            gx[j] = pick<R>(p.hx, p.f_hx) * d[j];
-            gy[j] = pick<R>(p.hy, p.f_hy) * d[j];
+            for (int j = 0; j < 3; j++) {
+                gx[j] = g;
+                gy[j] = h;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                gx[j] = pick<R>(p.hx, p.f_hx) * d[j];
+                gy[j] = pick<R>(p.hy, p.f_hy) * d[j];
+            }
         }
         so_point<IMAG>(u, X, Y, gx, gy, p.so_case);
     }
     if (mask & 2) {
         // V = wx^2 x^2/2 + wy^2 y^2/2 with x = kx dx: kx^2 is an exact integer
         const int kx = ix - p.nx / 2, ky = iy - p.ny / 2;
-        R V = pick<R>(p.vx, p.f_vx) * (R)(kx * kx) + (p.dim == 2 ? pick<R>(p.vy, p.f_vy) * (R)(ky * ky) : R(0));
-        calcnu_point<IMAG>(u, V, pick<R>(p.c0, p.f_c0), pick<R>(p.c2, p.f_c2), dt);
+        if (sizeof(R) == 8) {
+            // complex128: -dt folded into the coefficients (exponent -dt mu directly)
+            R Vn = (R)p.n_vx * (R)(kx * kx) + (p.dim == 2 ? (R)p.n_vy * (R)(ky * ky) : R(0));
+            calcnu_point_dt<IMAG>(u, Vn, p);
+        } else {
+            R V = pick<R>(p.vx, p.f_vx) * (R)(kx * kx) + (p.dim == 2 ? pick<R>(p.vy, p.f_vy) * (R)(ky * ky) : R(0));
+            calcnu_point<IMAG>(u, V, pick<R>(p.c0, p.f_c0), pick<R>(p.c2, p.f_c2), dt);
+        }
     }
-    if (mask & 4) herm_point<IMAG>(u, pick<R>(p.c2, p.f_c2), Ot, dt);
+    if (mask & 4) herm_point<IMAG>(u, pick<R>(p.c2, p.f_c2), Ot, dt, &p);
 }
 
 template <typename R, bool IMAG>

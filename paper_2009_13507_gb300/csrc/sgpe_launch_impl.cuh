@@ -114,7 +114,7 @@ cudaError_t Launcher<R>::pointwise(cudaStream_t s, bool imag, const void* A, voi
     dim3 block(32, p.dim == 2 ? 2 : 1);
     dim3 grid(ceil_div(p.nx, 32), p.dim == 2 ? ceil_div(p.ny, 2) : 1);
     KParams q = p;
-    fill_f32(q);
+    fill_derived(q);
     if (imag)
         launch_pdl(k_pointwise<R, true>, grid, block, 0, s, (const T*)A, (T*)B, q, sc, omega_tab, mask);
     else
@@ -131,7 +131,7 @@ cudaError_t Launcher<R>::pwx(cudaStream_t s, bool imag, const void* A, void* B, 
     const T* a = (const T*)A;
     T* b = (T*)B;
     KParams q = p;
-    fill_f32(q);
+    fill_derived(q);
     switch (chunk_len(p.nx)) {
         case 1: pwx_c<R, 1>(imag, p.ny, s, a, b, q, sc, omega_tab, t); break;
         case 2: pwx_c<R, 2>(imag, p.ny, s, a, b, q, sc, omega_tab, t); break;
