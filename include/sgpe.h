@@ -8,8 +8,10 @@
  *  - The wave function psi is a contiguous array [3][ny][nx] of interleaved
  *    complex numbers (re, im), x fastest; component index 0, 1, 2 holds the
  *    spin components +1, 0, -1 (the paper's CP(L,I,J), L = 1, 2, 3, Sec. 3).
- *    Element type: double (SGPE_C128, 16 bytes per complex) or float
- *    (SGPE_C64, 8 bytes). ny = 1 in 1D.
+ *    Element type: double (SGPE_C128, 16 bytes per complex), float
+ *    (SGPE_C64, 8 bytes), or for SGPE_CDF four floats (re_hi, re_lo, im_hi,
+ *    im_lo; 16 bytes) holding each real part as the unevaluated sum hi + lo.
+ *    ny = 1 in 1D.
  *  - Grid: x_i = (i - nx/2) dx, y_k = (k - ny/2) dy (integer division), with
  *    homogeneous Dirichlet boundaries (psi = 0 outside the grid).
  *  - Memory: the caller owns every device buffer (state, workspace, Omega(t)
@@ -47,7 +49,21 @@ typedef enum {
     SGPE_EUNSUPPORTED = 7 /* size or option outside what the kernels support */
 } sgpe_status;
 
-typedef enum { SGPE_C128 = 0, SGPE_C64 = 1 } sgpe_precision;
+/*
+ * Arithmetic of the step:
+ *  SGPE_C128  complex128 state, FP64 arithmetic (the plain FP64 form).
+ *  SGPE_C64   complex64 state and sweeps, FP64 reductions (the precision form).
+ *  SGPE_CDF   "double-float": every real number is a pair of FP32 numbers
+ *             (about 48 significant bits), all step arithmetic on the FP32
+ *             pipe, reductions and the renormalisation in FP64. Results agree
+ *             with the complex128 form to ~1e-13; on GB300, whose FP64 rate is
+ *             ~1/60 of its FP32 rate, it is the fast FP64-accurate form.
+ *             sgpe_set_state / sgpe_get_state / sgpe_load_state take and
+ *             return complex128; the bound psi buffer holds the pair layout.
+ *             Not available for the batched and adjoint entry points
+ *             (SGPE_EUNSUPPORTED).
+ */
+typedef enum { SGPE_C128 = 0, SGPE_C64 = 1, SGPE_CDF = 2 } sgpe_precision;
 
 /*
  * Physical parameters (the inputs of the paper's Table 2 and Sec. 2).
@@ -96,7 +112,8 @@ enum {
 /*
  * Create a context for one grid. dim = 1 or 2; nx >= 3 (and ny >= 3 in 2D, ny
  * ignored and taken as 1 in 1D); dx, dy > 0. nx, ny <= 4096 for SGPE_C128 and
- * <= 8192 for SGPE_C64 (a whole grid line is staged in shared memory).
+ * SGPE_CDF and <= 8192 for SGPE_C64 (a whole grid line is staged in shared
+ * memory).
  * cuda_stream is a cudaStream_t (NULL = legacy default stream). The context
  * uses the CUDA device current at this call for all later calls.
  * Returns SGPE_EINVAL / SGPE_EUNSUPPORTED / SGPE_ENOMEM / SGPE_ECUDA.
@@ -168,9 +185,11 @@ sgpe_status sgpe_set_state(sgpe_ctx* ctx, const void* host_psi);
 sgpe_status sgpe_get_state(sgpe_ctx* ctx, void* host_psi);
 
 /*
- * Copy a device state (same layout and precision, caller-owned, must not
- * overlap the bound state) into the bound state and reset the pending scale.
- * Asynchronous on the context's stream.
+ * Copy a device state (caller-owned, must not overlap the bound state) into the
+ * bound state and reset the pending scale. Layout [3][ny][nx] complex of the
+ * context's precision: complex128 for SGPE_C128 and SGPE_CDF (split into the
+ * pair layout by a kernel), complex64 for SGPE_C64. Asynchronous on the
+ * context's stream.
  */
 sgpe_status sgpe_load_state(sgpe_ctx* ctx, const void* psi_dev);
 
@@ -201,7 +220,8 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* ctx, int nsteps, int imag, double* ms_o
  * a service for callers that cannot allocate device memory (a host framework
  * that owns every allocation through its own pool, a plug-in that only sees the
  * buffers it is handed, a latency-critical loop that must not allocate).
- *  psi_dev  device state [3][ny][nx] complex of precision prec (16-byte aligned);
+ *  psi_dev  device state [3][ny][nx] complex of precision prec (16-byte aligned;
+ *           for SGPE_CDF the pair layout of the bound state);
  *           it is read as it is (no pending renormalisation scale exists here).
  *  obs_dev  device output, SGPE_NOBS doubles (8-byte aligned), same indices as
  *           sgpe_energy; written asynchronously on cuda_stream.

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsgpe.so")
-SOURCES = ["sgpe_api.cu", "sgpe_f64.cu", "sgpe_f32.cu", "sgpe_static.cu", "sgpe_batch.cu", "sgpe_adjoint.cu"]
+SOURCES = ["sgpe_api.cu", "sgpe_f64.cu", "sgpe_f32.cu", "sgpe_cdf.cu", "sgpe_static.cu", "sgpe_batch.cu", "sgpe_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

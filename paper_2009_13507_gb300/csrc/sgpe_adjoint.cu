@@ -309,27 +309,6 @@ AdjLayout adj_layout(int nx, int ny, int esz, int nsteps, int K) {
 
 }  // namespace
 
-// Internal context access (defined in sgpe_api.cu).
-namespace sgpe {
-struct CtxView {
-    int dim, nx, ny, esz;
-    bool dbl;
-    cudaStream_t stream;
-    void* psi;
-    void* mid;
-    DevScalars* sc;
-    const void* const* tabs_real;  // [axis][4], bt = i dt/(4h^2)
-    const void* const* tabs_adj;   // [axis][4], bt = -i dt/(4h^2)
-    const Geometry* geo;
-    KParams kp;
-    double* partials;
-    bool ready;
-};
-bool ctx_view(sgpe_ctx* c, CtxView* v);
-sgpe_status ctx_fail(sgpe_ctx* c, sgpe_status st, const char* msg);
-cudaError_t ctx_flush(sgpe_ctx* c);
-}  // namespace sgpe
-
 template <typename R>
 static cudaError_t adj_forward_step(const CtxView& v, const void* in, void* out, double omega) {
     KParams k = v.kp;
@@ -424,6 +403,7 @@ sgpe_status sgpe_adjoint_loss_grad(sgpe_ctx* c, int nsteps, const double* omega_
     if (!c) return SGPE_EINVAL;
     CtxView v;
     if (!ctx_view(c, &v) || !v.ready) return ctx_fail(c, SGPE_ESTATE, "adjoint: no buffers bound or no parameters");
+    if (v.prec == SGPE_CDF) return ctx_fail(c, SGPE_EUNSUPPORTED, "adjoint: not available for SGPE_CDF");
     if (nsteps < 1 || checkpoint_every < 1 || !omega_dev || !rho_target_dev || !adj_workspace || !domega_dev)
         return ctx_fail(c, SGPE_EINVAL, "adjoint: bad arguments");
     if (((uintptr_t)adj_workspace & 255) || ((uintptr_t)omega_dev & 7) || ((uintptr_t)rho_target_dev & 7) ||

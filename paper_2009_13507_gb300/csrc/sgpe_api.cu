@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <map>
+#include <vector>
 #include <tuple>
 
 #include "../../include/sgpe.h"
@@ -43,6 +44,14 @@ Geometry make_geometry(int dim, int nx, int ny, int esz) {
     return g;
 }
 }  // namespace sgpe
+
+// Call f with a value of the arithmetic type of precision p (double, float or
+// the double-float pair).
+template <typename F> static auto with_prec(sgpe_precision p, F&& f) {
+    if (p == SGPE_C128) return f(double(0));
+    if (p == SGPE_C64) return f(float(0));
+    return f(df(0));
+}
 
 struct GraphKey {
     int imag, count;
@@ -209,8 +218,8 @@ sgpe_status sgpe_init_grid(sgpe_ctx** out, int dim, int nx, int ny, double dx, d
     }
     if (nx < 3 || (dim == 2 && ny < 3)) return SGPE_EINVAL;
     if (!(dx > 0.0) || !(dy > 0.0) || !isfinite(dx) || !isfinite(dy)) return SGPE_EINVAL;
-    if (prec != SGPE_C128 && prec != SGPE_C64) return SGPE_EINVAL;
-    int nmax = prec == SGPE_C128 ? 4096 : 8192;
+    if (prec != SGPE_C128 && prec != SGPE_C64 && prec != SGPE_CDF) return SGPE_EINVAL;
+    int nmax = prec == SGPE_C64 ? 8192 : 4096;
     if (nx > nmax || ny > nmax) return SGPE_EUNSUPPORTED;
     sgpe_ctx* c = new (std::nothrow) sgpe_ctx();
     if (!c) return SGPE_ENOMEM;
@@ -220,7 +229,7 @@ sgpe_status sgpe_init_grid(sgpe_ctx** out, int dim, int nx, int ny, double dx, d
     c->dx = dx;
     c->dy = dy;
     c->prec = prec;
-    c->esz = prec == SGPE_C128 ? 16 : 8;
+    c->esz = prec == SGPE_C64 ? 8 : 16;
     c->stream = (cudaStream_t)cuda_stream;
     c->geo = make_geometry(dim, nx, ny, c->esz);
     c->psi = nullptr;
@@ -229,7 +238,7 @@ sgpe_status sgpe_init_grid(sgpe_ctx** out, int dim, int nx, int ny, double dx, d
     c->graphs_ok = true;
     c->err[0] = 0;
     cudaError_t e = cudaGetDevice(&c->device);
-    if (e == cudaSuccess) e = prec == SGPE_C128 ? Launcher<double>::setup() : Launcher<float>::setup();
+    if (e == cudaSuccess) e = with_prec(prec, [](auto r) { return Launcher<decltype(r)>::setup(); });
     if (e != cudaSuccess) {
         snprintf(g_init_err, sizeof(g_init_err), "sgpe_init_grid: %s", cudaGetErrorString(e));
         delete c;
@@ -281,8 +290,7 @@ sgpe_status sgpe_set_params(sgpe_ctx* c, const sgpe_params* p) {
             double b = p->dt / (4.0 * h * h);
             double bre = m == 0 ? b : 0.0, bim = m == 0 ? 0.0 : (m == 1 ? b : -b);
             void** t = c->tabs[m][a];
-            cudaError_t e = c->prec == SGPE_C128 ? Launcher<double>::coef(c->stream, t[0], t[1], t[2], t[3], n, bre, bim)
-                                                 : Launcher<float>::coef(c->stream, t[0], t[1], t[2], t[3], n, bre, bim);
+            cudaError_t e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::coef(c->stream, t[0], t[1], t[2], t[3], n, bre, bim); });
             CK(e, "COEF kernel");
         }
     c->have_params = true;
@@ -326,8 +334,7 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
 
 static cudaError_t enqueue_steps(sgpe_ctx* c, int n, bool imag, const double* omega_tab) {
     for (int i = 0; i < n; i++) {
-        cudaError_t e = c->prec == SGPE_C128 ? enqueue_step<double>(c, imag, omega_tab)
-                                             : enqueue_step<float>(c, imag, omega_tab);
+        cudaError_t e = with_prec(c->prec, [&](auto r) { return enqueue_step<decltype(r)>(c, imag, omega_tab); });
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -387,7 +394,7 @@ template <typename R> static cudaError_t flush_scale(sgpe_ctx* c) {
     return reset_scale(c->stream, c->sc);
 }
 static cudaError_t flush_any(sgpe_ctx* c) {
-    return c->prec == SGPE_C128 ? flush_scale<double>(c) : flush_scale<float>(c);
+    return with_prec(c->prec, [&](auto r) { return flush_scale<decltype(r)>(c); });
 }
 
 static sgpe_status read_err(sgpe_ctx* c) {
@@ -425,9 +432,7 @@ sgpe_status sgpe_normalize(sgpe_ctx* c, double* norms_out) {
     if (st) return st;
     CK(flush_any(c), "flush");
     size_t plane = (size_t)c->nx * c->ny;
-    cudaError_t e = c->prec == SGPE_C128
-                        ? Launcher<double>::norms(c->stream, c->psi, plane, c->kp.cell, 0, 0.0, c->partials, c->sc)
-                        : Launcher<float>::norms(c->stream, c->psi, plane, c->kp.cell, 0, 0.0, c->partials, c->sc);
+    cudaError_t e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::norms(c->stream, c->psi, plane, c->kp.cell, 0, 0.0, c->partials, c->sc); });
     CK(e, "norms kernel");
     double n[4];
     CK(cudaMemcpyAsync(n, c->sc->norms, sizeof(n), cudaMemcpyDeviceToHost, c->stream), "copy norms");
@@ -441,18 +446,40 @@ sgpe_status sgpe_energy(sgpe_ctx* c, double* out) {
     if (st) return st;
     if (!out) return fail(c, SGPE_EINVAL, "null output");
     CK(flush_any(c), "flush");
-    cudaError_t e = c->prec == SGPE_C128
-                        ? Launcher<double>::observables(c->stream, c->psi, c->kp, c->kp.omega_t, c->partials, c->sc)
-                        : Launcher<float>::observables(c->stream, c->psi, c->kp, c->kp.omega_t, c->partials, c->sc);
+    cudaError_t e = with_prec(c->prec, [&](auto r) {
+        return Launcher<decltype(r)>::observables(c->stream, c->psi, c->kp, c->kp.omega_t, c->partials, c->sc);
+    });
     CK(e, "observables kernel");
     CK(cudaMemcpyAsync(out, c->sc->obs, SGPE_NOBS * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy obs");
     return read_err(c);
+}
+
+// complex128 <-> double-float layout (hi, lo per real part), on the host.
+static void cdf_split(const double* in, float* out, size_t nreal) {
+    for (size_t i = 0; i < nreal; i++) {
+        const df v = df_from(in[i]);
+        out[2 * i] = v.hi;
+        out[2 * i + 1] = v.lo;
+    }
+}
+static void cdf_join(const float* in, double* out, size_t nreal) {
+    for (size_t i = 0; i < nreal; i++) out[i] = (double)in[2 * i] + (double)in[2 * i + 1];
 }
 
 sgpe_status sgpe_set_state(sgpe_ctx* c, const void* host_psi) {
     if (!c || !host_psi) return SGPE_EINVAL;
     if (!c->psi) return fail(c, SGPE_ESTATE, "no buffers bound");
     size_t bytes = (size_t)3 * c->nx * c->ny * c->esz;
+    if (c->prec == SGPE_CDF) {
+        const size_t nreal = (size_t)6 * c->nx * c->ny;
+        std::vector<float> tmp(2 * nreal);
+        cdf_split((const double*)host_psi, tmp.data(), nreal);
+        CK(cudaMemcpyAsync(c->psi, tmp.data(), bytes, cudaMemcpyHostToDevice, c->stream), "set_state copy");
+        CK(reset_scale(c->stream, c->sc), "reset scale");
+        CK(cudaMemsetAsync(&c->sc->err, 0, sizeof(int), c->stream), "clear err");
+        CK(cudaStreamSynchronize(c->stream), "sync");  // tmp must outlive the copy
+        return SGPE_OK;
+    }
     CK(cudaMemcpyAsync(c->psi, host_psi, bytes, cudaMemcpyHostToDevice, c->stream), "set_state copy");
     CK(reset_scale(c->stream, c->sc), "reset scale");
     CK(cudaMemsetAsync(&c->sc->err, 0, sizeof(int), c->stream), "clear err");
@@ -464,7 +491,10 @@ sgpe_status sgpe_load_state(sgpe_ctx* c, const void* psi_dev) {
     if (!c || !psi_dev) return SGPE_EINVAL;
     if (!c->psi) return fail(c, SGPE_ESTATE, "no buffers bound");
     size_t bytes = (size_t)3 * c->nx * c->ny * c->esz;
-    CK(cudaMemcpyAsync(c->psi, psi_dev, bytes, cudaMemcpyDeviceToDevice, c->stream), "load_state copy");
+    if (c->prec == SGPE_CDF)
+        CK(cdf_from_c128(c->stream, psi_dev, c->psi, (size_t)3 * c->nx * c->ny), "load_state split");
+    else
+        CK(cudaMemcpyAsync(c->psi, psi_dev, bytes, cudaMemcpyDeviceToDevice, c->stream), "load_state copy");
     CK(reset_scale(c->stream, c->sc), "reset scale");
     CK(cudaMemsetAsync(&c->sc->err, 0, sizeof(int), c->stream), "clear err");
     return SGPE_OK;
@@ -475,6 +505,14 @@ sgpe_status sgpe_get_state(sgpe_ctx* c, void* host_psi) {
     if (!c->psi) return fail(c, SGPE_ESTATE, "no buffers bound");
     CK(flush_any(c), "flush");
     size_t bytes = (size_t)3 * c->nx * c->ny * c->esz;
+    if (c->prec == SGPE_CDF) {
+        const size_t nreal = (size_t)6 * c->nx * c->ny;
+        std::vector<float> tmp(2 * nreal);
+        CK(cudaMemcpyAsync(tmp.data(), c->psi, bytes, cudaMemcpyDeviceToHost, c->stream), "get_state copy");
+        CK(cudaStreamSynchronize(c->stream), "sync");
+        cdf_join(tmp.data(), (double*)host_psi, nreal);
+        return SGPE_OK;
+    }
     CK(cudaMemcpyAsync(host_psi, c->psi, bytes, cudaMemcpyDeviceToHost, c->stream), "get_state copy");
     CK(cudaStreamSynchronize(c->stream), "sync");
     return SGPE_OK;
@@ -490,34 +528,25 @@ sgpe_status sgpe_substep(sgpe_ctx* c, int which, int imag, double omega) {
     const bool im = imag != 0;
     const int mode = im ? 0 : 1;
     const size_t bytes = (size_t)3 * c->nx * c->ny * c->esz;
-    const bool dbl = c->prec == SGPE_C128;
     cudaError_t e = cudaSuccess;
     if (which <= 2) {
         KParams k = c->kp;
         k.omega_t = omega / sqrt(2.0);
-        e = dbl ? Launcher<double>::pointwise(c->stream, im, c->psi, c->mid, k, c->sc, nullptr, 1 << which)
-                : Launcher<float>::pointwise(c->stream, im, c->psi, c->mid, k, c->sc, nullptr, 1 << which);
+        e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::pointwise(c->stream, im, c->psi, c->mid, k, c->sc, nullptr, 1 << which); });
         CK(e, "pointwise kernel");
         CK(cudaMemcpyAsync(c->psi, c->mid, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy back");
     } else if (which == 3) {
         CK(cudaMemcpyAsync(c->mid, c->psi, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy");
-        e = dbl ? Launcher<double>::cn_x(c->stream, im, false, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo,
-                                         c->partials, c->sc, 0, 0)
-                : Launcher<float>::cn_x(c->stream, im, false, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo,
-                                        c->partials, c->sc, 0, 0);
+        e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::cn_x(c->stream, im, false, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo, c->partials, c->sc, 0, 0); });
         CK(e, "cn_x kernel");
     } else if (which == 4) {
         CK(cudaMemcpyAsync(c->mid, c->psi, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy");
-        e = dbl ? Launcher<double>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials,
-                                         c->sc, 0, 0, 0)
-                : Launcher<float>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials,
-                                        c->sc, 0, 0, 0);
+        e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials, c->sc, 0, 0, 0); });
         CK(e, "cn_y kernel");
     } else {
         size_t plane = (size_t)c->nx * c->ny;
         int rn = c->params.renorm ? c->params.renorm : 1;
-        e = dbl ? Launcher<double>::norms(c->stream, c->psi, plane, c->kp.cell, rn, c->kp.mag, c->partials, c->sc)
-                : Launcher<float>::norms(c->stream, c->psi, plane, c->kp.cell, rn, c->kp.mag, c->partials, c->sc);
+        e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::norms(c->stream, c->psi, plane, c->kp.cell, rn, c->kp.mag, c->partials, c->sc); });
         CK(e, "norms kernel");
         CK(flush_any(c), "flush");
     }
@@ -531,7 +560,6 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
     const bool im = imag != 0;
     const int mode = im ? 0 : 1;
     const int renorm = im ? c->params.renorm : 0;
-    const bool dbl = c->prec == SGPE_C128;
     // kinds: 0 pointwise, 1 CN along x, 2 CN along y, 3 end-of-step norm / scale;
     // with the fused 2D head, kind 0 is the fused pointwise + CN-x kernel and
     // kind 1 has no launches.
@@ -553,24 +581,16 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
         cudaEvent_t* ev = evs[bi];
         e = cudaEventRecord(ev[0], c->stream);
         if (!e && fused)
-            e = dbl ? Launcher<double>::pwx(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, c->tabs[mode][0])
-                    : Launcher<float>::pwx(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, c->tabs[mode][0]);
+            e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::pwx(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, c->tabs[mode][0]); });
         if (!e && !fused)
-            e = dbl ? Launcher<double>::pointwise(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, 7)
-                    : Launcher<float>::pointwise(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, 7);
+            e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::pointwise(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, 7); });
         if (!e) e = cudaEventRecord(ev[1], c->stream);
         void* xout = two ? c->mid : c->psi;
         if (!e && !fused)
-            e = dbl ? Launcher<double>::cn_x(c->stream, im, !two, c->mid, xout, c->kp, c->tabs[mode][0], c->geo,
-                                             c->partials, c->sc, renorm, 1)
-                    : Launcher<float>::cn_x(c->stream, im, !two, c->mid, xout, c->kp, c->tabs[mode][0], c->geo,
-                                            c->partials, c->sc, renorm, 1);
+            e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::cn_x(c->stream, im, !two, c->mid, xout, c->kp, c->tabs[mode][0], c->geo, c->partials, c->sc, renorm, 1); });
         if (!e) e = cudaEventRecord(ev[2], c->stream);
         if (!e && two)
-            e = dbl ? Launcher<double>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo,
-                                             c->partials, c->sc, renorm, 1, 1)
-                    : Launcher<float>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo,
-                                            c->partials, c->sc, renorm, 1, 1);
+            e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials, c->sc, renorm, 1, 1); });
         if (!e) e = cudaEventRecord(ev[3], c->stream);
         if (!e)
             e = finalize_step(c->stream, c->partials, two ? c->geo.blocks_y : 3 * c->ny, c->kp.cell, renorm,
@@ -619,21 +639,6 @@ sgpe_status sgpe_destroy(sgpe_ctx* c) {
 
 // Internal access for the adjoint translation unit.
 namespace sgpe {
-struct CtxView {
-    int dim, nx, ny, esz;
-    bool dbl;
-    cudaStream_t stream;
-    void* psi;
-    void* mid;
-    DevScalars* sc;
-    const void* const* tabs_real;
-    const void* const* tabs_adj;
-    const Geometry* geo;
-    KParams kp;
-    double* partials;
-    bool ready;
-};
-
 bool ctx_view(sgpe_ctx* c, CtxView* v) {
     if (!c) return false;
     v->dim = c->dim;
@@ -641,6 +646,7 @@ bool ctx_view(sgpe_ctx* c, CtxView* v) {
     v->ny = c->ny;
     v->esz = c->esz;
     v->dbl = c->prec == SGPE_C128;
+    v->prec = c->prec;
     v->stream = c->stream;
     v->psi = c->psi;
     v->mid = c->mid;

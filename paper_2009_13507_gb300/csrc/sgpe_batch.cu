@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(128) kb_pointwise(const typename V2<R>::T* __r
     int ix, iy;
     tile_point(I.p, tl.y, &ix, &iy);
     if (ix >= I.p.nx || iy >= I.p.ny) return;
-    pointwise_at<R, IMAG>(A + I.off, B + I.off, I.p, scs + tl.x, pick<R>(I.p.omega_t, I.p.f_omega_t), ix, iy, 7);
+    pointwise_at<R, IMAG>(A + I.off, B + I.off, I.p, scs + tl.x, kc<R>(I.p, KC_OMEGA), ix, iy, 7);
 }
 
 // Work entry of the x sweep: (instance, line, partial slot or -1).
@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(128) kb_finalize(const BInst* __restrict__ ins
             sc->norms[j] = N[j];
             sc->scale[j] = d[j];
             sc->scale_f[j] = (float)d[j];
+            sc->scale_l[j] = (float)(d[j] - (double)sc->scale_f[j]);
         }
         if (!finite) sc->err |= 1;
         sc->step_idx += 1;
@@ -150,6 +151,7 @@ __global__ void kb_reset(DevScalars* scs, int n, int clear_err) {
         for (int j = 0; j < 4; j++) {
             scs[i].scale[j] = 1.0;
             scs[i].scale_f[j] = 1.0f;
+            scs[i].scale_l[j] = 0.0f;
         }
     if (i < n && clear_err) scs[i].err = 0;
 }
@@ -354,6 +356,7 @@ sgpe_status sgpe_batch_create(sgpe_batch** out, int n, const sgpe_instance* inst
         set_thread_error("sgpe_batch_create: need n >= 1 instances");
         return SGPE_EINVAL;
     }
+    if (prec == SGPE_CDF) return SGPE_EUNSUPPORTED;
     if (prec != SGPE_C128 && prec != SGPE_C64) return SGPE_EINVAL;
     for (int i = 0; i < n; i++) {
         const sgpe_instance& q = inst[i];

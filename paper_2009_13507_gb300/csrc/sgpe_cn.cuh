@@ -142,6 +142,11 @@ template <> struct NormAcc<double> {
     __device__ __forceinline__ void add(cx<double> o) { s += o.re * o.re + o.im * o.im; }
     __device__ __forceinline__ double value() const { return s; }
 };
+template <> struct NormAcc<df> {
+    df s = df(0);
+    __device__ __forceinline__ void add(cx<df> o) { s = fma(o.re, o.re, fma(o.im, o.im, s)); }
+    __device__ __forceinline__ double value() const { return df_to(s); }
+};
 template <> struct NormAcc<float> {
     float hi = 0.0f, lo = 0.0f;
     __device__ __forceinline__ void add1(float x) {
@@ -189,7 +194,7 @@ __device__ __forceinline__ void cnx_solve_line(Load load, typename V2<R>::T* out
         if (KEEP) x[m] = v[m];
     }
     constexpr bool INC = sizeof(R) == 4;
-    if (INC) cn_increment_rhs<R, IMAG, C>(v, t);
+    if constexpr (INC) cn_increment_rhs<R, IMAG, C>(v, t);
     solve_chunk<R, IMAG, C>(v, lt);
     // complex64: only the stores remain, let the next step kernel launch (the
     // FP64 form measured faster with the implicit trigger at completion)
@@ -253,14 +258,14 @@ __global__ void __launch_bounds__(kPwxThreads, C <= 8 ? 2 : 1)
     const int iy = blockIdx.x;
     const int nx = p.nx;
     pdl_wait();
-    const R Ot = omega_tab ? (R)(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440)
-                           : pick<R>(p.omega_t, p.f_omega_t);
+    const R Ot = omega_tab ? to_r<R>(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440)
+                           : kc<R>(p, KC_OMEGA);
     for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
         cx<R> u[3];
         pointwise_point<R, IMAG>(A, p, sc, Ot, ix, iy, 7, u);
         const int slot = (ix / C) * (C + 1) + (ix % C);
 #pragma unroll
-        for (int j = 0; j < 3; j++) row[j * S + slot] = T{u[j].re, u[j].im};
+        for (int j = 0; j < 3; j++) row[j * S + slot] = pack(u[j]);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5;
@@ -269,8 +274,7 @@ __global__ void __launch_bounds__(kPwxThreads, C <= 8 ? 2 : 1)
         const size_t base = ((size_t)warp * p.ny + iy) * nx;
         cnx_solve_line<R, IMAG, C>(
             [&](int i) {
-                const T v = r[(i / C) * (C + 1) + (i % C)];
-                return cx<R>{v.x, v.y};
+                return unpack(r[(i / C) * (C + 1) + (i % C)]);
             },
             B, base, nx, t, nullptr);
     }
@@ -309,7 +313,7 @@ __device__ __forceinline__ void cny_cols(const typename V2<R>::T* in, typename V
     }
 #pragma unroll
     for (int k = 0; k < K; k++) {
-        if (INC) cn_increment_rhs<R, IMAG, C>(v[k], t);
+        if constexpr (INC) cn_increment_rhs<R, IMAG, C>(v[k], t);
         solve_chunk<R, IMAG, C>(v[k], lt);
     }
     // complex64: only the stores remain, let the next step kernel launch (the

@@ -7,15 +7,36 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sgpe_df.cuh"
+
 namespace sgpe {
 
+// Storage element of one complex number per arithmetic type R: complex128,
+// complex64, and the double-float pair (re.hi, re.lo, im.hi, im.lo).
 template <typename R> struct V2;
 template <> struct V2<double> { using T = double2; };
 template <> struct V2<float> { using T = float2; };
+template <> struct V2<df> { using T = float4; };
 
 template <typename R> struct cx {
     R re, im;
 };
+
+__device__ __forceinline__ cx<double> unpack(double2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ cx<float> unpack(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ cx<df> unpack(float4 v) { return {df(v.x, v.y), df(v.z, v.w)}; }
+__device__ __forceinline__ double2 pack(cx<double> a) { return make_double2(a.re, a.im); }
+__device__ __forceinline__ float2 pack(cx<float> a) { return make_float2(a.re, a.im); }
+__device__ __forceinline__ float4 pack(cx<df> a) { return make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
+
+// The value as a double (observables, norms: FP64 arithmetic).
+__device__ __forceinline__ double dbl(double x) { return x; }
+__device__ __forceinline__ double dbl(float x) { return (double)x; }
+__device__ __forceinline__ double dbl(df x) { return df_to(x); }
+// A double rounded to R (FP64 conversion: off the per-point path).
+template <typename R> __device__ __forceinline__ R to_r(double x) { return (R)x; }
+template <> __device__ __forceinline__ df to_r<df>(double x) { return df_from(x); }
+template <typename R> constexpr bool is_f32() { return sizeof(R) == 4; }
 
 template <typename R> __device__ __forceinline__ cx<R> mk(R a, R b) { return cx<R>{a, b}; }
 template <typename R> __device__ __forceinline__ cx<R> add(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
@@ -40,19 +61,12 @@ template <typename R> __device__ __forceinline__ cx<R> caxpy(cx<R> s, cx<R> b, c
 }
 
 template <typename R> __device__ __forceinline__ cx<R> ld(const typename V2<R>::T* p, size_t i) {
-    typename V2<R>::T v = __ldg(p + i);
-    return {v.x, v.y};
+    return unpack(__ldg(p + i));
 }
 template <typename R> __device__ __forceinline__ cx<R> ldc(const typename V2<R>::T* p, size_t i) {
-    typename V2<R>::T v = __ldcg(p + i);  // L2 only: data written earlier in this kernel's grid or stream
-    return {v.x, v.y};
+    return unpack(__ldcg(p + i));  // L2 only: data written earlier in this kernel's grid or stream
 }
-template <typename R> __device__ __forceinline__ void st(typename V2<R>::T* p, size_t i, cx<R> a) {
-    typename V2<R>::T v;
-    v.x = a.re;
-    v.y = a.im;
-    p[i] = v;
-}
+template <typename R> __device__ __forceinline__ void st(typename V2<R>::T* p, size_t i, cx<R> a) { p[i] = pack(a); }
 
 // ---------------------------------------------------------------------------
 // exp(x) and (cos x, sin x) for the phase factors.
@@ -203,38 +217,55 @@ struct KParams {
     double cell;      // dx (1D) or dx*dy
     int renorm;       // 0, 1 (DJ2), 2 (DJ)
     double mag;
-    // FP32 copies of the constants the pointwise substeps use, for the
-    // complex64 form (no FP64 -> FP32 conversion per grid point); filled by
-    // fill_derived on the host just before a launch.
-    float f_dt, f_hx, f_hy, f_c0, f_c2, f_vx, f_vy, f_omega_t;
-    // Derived FP64 constants of the complex128 pointwise substeps (fill_derived):
-    // dt folded into the CALCNU exponent coefficients and into the HERM series.
-    double n_c0, n_c2, n_vx, n_vy;  // -dt c0, -dt c2, -dt vx, -dt vy
-    double dt2;                     // dt^2
-    double hs[5], hk[5];            // dt/(2n+1)!, dt^2/(2n+2)!  (n = 0..4)
+    // Constants of the pointwise substeps in each arithmetic type (kc<R>):
+    // kd the FP64 value, kf its FP32 rounding, kl the FP32 rest kd - kf (the
+    // double-float low part); filled by fill_derived on the host before a
+    // launch, so no kernel converts a constant per grid point.
+    double kd[32];
+    float kf[32], kl[32];
 };
 
+// Indices into KParams::kd / kf / kl. NC0..NVY: -dt times c0, c2, vx, vy (dt
+// folded into the CALCNU exponent); HS0 + n, HK0 + n: the HERM series
+// coefficients dt/(2n+1)! and dt^2/(2n+2)!, n = 0..4.
+enum KC {
+    KC_DT, KC_HX, KC_HY, KC_C0, KC_C2, KC_VX, KC_VY, KC_OMEGA,
+    KC_NC0, KC_NC2, KC_NVX, KC_NVY, KC_DT2, KC_HS0, KC_HK0 = KC_HS0 + 5, KC_N = KC_HK0 + 5
+};
+static_assert(KC_N <= 32, "KParams constant table too small");
+
 inline void fill_derived(KParams& k) {
-    k.n_c0 = -k.dt * k.c0;
-    k.n_c2 = -k.dt * k.c2;
-    k.n_vx = -k.dt * k.vx;
-    k.n_vy = -k.dt * k.vy;
-    k.dt2 = k.dt * k.dt;
+    double* d = k.kd;
+    d[KC_DT] = k.dt;
+    d[KC_HX] = k.hx;
+    d[KC_HY] = k.hy;
+    d[KC_C0] = k.c0;
+    d[KC_C2] = k.c2;
+    d[KC_VX] = k.vx;
+    d[KC_VY] = k.vy;
+    d[KC_OMEGA] = k.omega_t;
+    d[KC_NC0] = -k.dt * k.c0;
+    d[KC_NC2] = -k.dt * k.c2;
+    d[KC_NVX] = -k.dt * k.vx;
+    d[KC_NVY] = -k.dt * k.vy;
+    d[KC_DT2] = k.dt * k.dt;
     double f = 1.0;  // (2n+1)!
     for (int n = 0; n < 5; n++) {
         if (n > 0) f *= (2.0 * n) * (2.0 * n + 1.0);
-        k.hs[n] = k.dt / f;
-        k.hk[n] = k.dt2 / (f * (2.0 * n + 2.0));
+        d[KC_HS0 + n] = k.dt / f;
+        d[KC_HK0 + n] = d[KC_DT2] / (f * (2.0 * n + 2.0));
     }
-    k.f_dt = (float)k.dt;
-    k.f_hx = (float)k.hx;
-    k.f_hy = (float)k.hy;
-    k.f_c0 = (float)k.c0;
-    k.f_c2 = (float)k.c2;
-    k.f_vx = (float)k.vx;
-    k.f_vy = (float)k.vy;
-    k.f_omega_t = (float)k.omega_t;
+    for (int i = 0; i < KC_N; i++) {
+        k.kf[i] = (float)d[i];
+        k.kl[i] = (float)(d[i] - (double)k.kf[i]);
+    }
 }
+
+// Constant i of the pointwise substeps in the arithmetic type R.
+template <typename R> __device__ __forceinline__ R kc(const KParams& p, int i);
+template <> __device__ __forceinline__ double kc<double>(const KParams& p, int i) { return p.kd[i]; }
+template <> __device__ __forceinline__ float kc<float>(const KParams& p, int i) { return p.kf[i]; }
+template <> __device__ __forceinline__ df kc<df>(const KParams& p, int i) { return df(p.kf[i], p.kl[i]); }
 
 // Programmatic dependent launch (sm_90+). The step kernels are launched with
 // programmatic stream serialization, so a kernel's blocks may be scheduled
@@ -245,10 +276,6 @@ inline void fill_derived(KParams& k) {
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-// The constant in the arithmetic type R: d for double, its FP32 copy f for float.
-template <typename R> __device__ __forceinline__ R pick(double d, float f);
-template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
-template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
 // ---------------------------------------------------------------------------
 // Pointwise substeps at one grid point. u[j] holds the (already scaled) state
@@ -345,8 +372,9 @@ __device__ __forceinline__ void calcnu_point(cx<R> (&u)[3], R V, R c0, R c2, R d
 template <bool IMAG, typename R>
 __device__ __forceinline__ void calcnu_point_dt(cx<R> (&u)[3], R Vn, const KParams& p) {
     R rp = nrm(u[0]), r0 = nrm(u[1]), rm = nrm(u[2]);
-    R base = fma((R)p.n_c0, rp + r0 + rm, Vn);
-    R x[3] = {fma((R)p.n_c2, rp - rm + r0, base), fma((R)p.n_c2, rp + rm, base), fma((R)p.n_c2, rm - rp + r0, base)};
+    const R nc0 = kc<R>(p, KC_NC0), nc2 = kc<R>(p, KC_NC2);
+    R base = fma(nc0, rp + r0 + rm, Vn);
+    R x[3] = {fma(nc2, rp - rm + r0, base), fma(nc2, rp + rm, base), fma(nc2, rm - rp + r0, base)};
 #pragma unroll
     for (int j = 0; j < 3; j++) {
         if (IMAG) {
@@ -361,29 +389,39 @@ __device__ __forceinline__ void calcnu_point_dt(cx<R> (&u)[3], R Vn, const KPara
 
 // HERM coefficients s, k (see herm_coeffs) from the dt-folded series constants
 // KParams::hs, hk: s = sum_n hs_n v^n, k = +-sum_n hk_n v^n, v = +-dt^2 C^2.
-template <bool IMAG>
-__device__ __forceinline__ void herm_coeffs_dt(double C2, const KParams& p, double* s, double* k) {
-    double w = p.dt2 * C2;  // >= 0
-    double v = IMAG ? w : -w;
-    if ((unsigned)__double2hiint(w) < 0x3EB00000u) {
+// w = dt^2 C^2 against 2^-20 and 1/1024 (the series ranges below).
+__device__ __forceinline__ bool w_tiny(double w) { return (unsigned)__double2hiint(w) < 0x3EB00000u; }
+__device__ __forceinline__ bool w_tiny(df w) { return w.hi < 9.5367431640625e-07f; }
+__device__ __forceinline__ bool w_small(double w) { return w <= 1.0 / 1024.0; }
+__device__ __forceinline__ bool w_small(df w) { return w.hi <= 1.0f / 1024.0f; }
+
+template <bool IMAG, typename R>
+__device__ __forceinline__ void herm_coeffs_dt(R C2, const KParams& p, R* s, R* k) {
+    R w = kc<R>(p, KC_DT2) * C2;  // >= 0
+    R v = IMAG ? w : -w;
+    if (w_tiny(w)) {
         // w < 2^-20: three terms each
-        *s = fma(fma(v, p.hs[2], p.hs[1]), v, p.hs[0]);
-        double pk = fma(fma(v, p.hk[2], p.hk[1]), v, p.hk[0]);
+        *s = fma(fma(v, kc<R>(p, KC_HS0 + 2), kc<R>(p, KC_HS0 + 1)), v, kc<R>(p, KC_HS0));
+        R pk = fma(fma(v, kc<R>(p, KC_HK0 + 2), kc<R>(p, KC_HK0 + 1)), v, kc<R>(p, KC_HK0));
         *k = IMAG ? pk : -pk;
         return;
     }
-    if (w <= 1.0 / 1024.0) {
-        double ps = p.hs[4], pk = p.hk[4];
+    if (w_small(w)) {
+        R ps = kc<R>(p, KC_HS0 + 4), pk = kc<R>(p, KC_HK0 + 4);
 #pragma unroll
         for (int n = 3; n >= 0; n--) {
-            ps = fma(ps, v, p.hs[n]);
-            pk = fma(pk, v, p.hk[n]);
+            ps = fma(ps, v, kc<R>(p, KC_HS0 + n));
+            pk = fma(pk, v, kc<R>(p, KC_HK0 + n));
         }
         *s = ps;
         *k = IMAG ? pk : -pk;
         return;
     }
-    herm_coeffs<IMAG>(C2, p.dt, s, k);
+    // rare: closed forms in FP64
+    double sd, kd;
+    herm_coeffs<IMAG>(dbl(C2), p.dt, &sd, &kd);
+    *s = to_r<R>(sd);
+    *k = to_r<R>(kd);
 }
 
 // HERM (Appendix A): with a = c2 psi_-^* psi_0 + Ot, b = c2 psi_0^* psi_+ + Ot
@@ -391,9 +429,10 @@ __device__ __forceinline__ void herm_coeffs_dt(double C2, const KParams& p, doub
 // evaluated as psi - s_z A psi + k A^2 psi with A^2 = [[|a|^2,0,ab],[0,C^2,0],[a*b*,0,|b|^2]].
 // This equals the eigen-decomposition form V diag(exp(-z lambda)) V^{-1} of Eq. (11) and
 // stays finite at C = 0.
-// kp (nullable): take s, k from the dt-folded constants (complex128 step).
+// kp: the kernel constants (complex128 and double-float take s, k from the
+// dt-folded series constants; complex64 evaluates them from dt).
 template <bool IMAG, typename R>
-__device__ __forceinline__ void herm_point(cx<R> (&u)[3], R c2, R Ot, R dt, const KParams* kp = nullptr) {
+__device__ __forceinline__ void herm_point(cx<R> (&u)[3], R c2, R Ot, R dt, const KParams* kp) {
     cx<R> a = cmul(u[2], u[1]);  // psi_-^* psi_0
     a = {fma(c2, a.re, Ot), c2 * a.im};
     cx<R> b = cmul(u[1], u[0]);  // psi_0^* psi_+
@@ -401,13 +440,10 @@ __device__ __forceinline__ void herm_point(cx<R> (&u)[3], R c2, R Ot, R dt, cons
     R na = nrm(a), nb = nrm(b);
     R C2 = na + nb;
     R s, k;
-    if (sizeof(R) == 8 && kp) {
-        double sd, kd;
-        herm_coeffs_dt<IMAG>((double)C2, *kp, &sd, &kd);
-        s = (R)sd;
-        k = (R)kd;
-    } else {
+    if constexpr (is_f32<R>()) {
         herm_coeffs<IMAG>(C2, dt, &s, &k);
+    } else {
+        herm_coeffs_dt<IMAG>(C2, *kp, &s, &k);
     }
     cx<R> ab = mul(a, b);
     // A psi

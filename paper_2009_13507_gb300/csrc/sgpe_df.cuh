@@ -1,0 +1,117 @@
+// sgpe_df.cuh -- "double-float" arithmetic: a real number held as the
+// unevaluated sum hi + lo of two FP32 numbers (|lo| <= ulp(hi)/2), about 48
+// significant bits, computed entirely on the FP32 pipe.
+//
+// Why: GB300 executes FP64 at about 1/60 of its FP32 rate (a warp's FP64
+// instruction occupies its SM sub-partition for ~64-80 cycles), so the
+// complex128 step is bound by the FP64 pipe. A double-float operation costs
+// 3-15 FP32 instructions, each one cycle per warp, which is several times
+// cheaper than one FP64 instruction while keeping the step's error near
+// 1e-13, far inside the 1e-10 FP64 parity bar.
+//
+// Building blocks (error-free transformations with FMA, after Dekker and
+// Knuth): two_sum gives s + e = a + b exactly; fast_two_sum the same when
+// |a| >= |b|; two_prod gives p + e = a * b exactly (e from one FMA).
+// Addition is the "sloppy" variant (error relative to |a| + |b|, adequate
+// here: no result of the step depends on a cancellation of large terms),
+// multiplication adds the two cross terms before renormalising.
+// The exponent range is FP32's; values below ~1e-38 flush towards zero and
+// lose their low part, which is far below anything the step resolves.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace sgpe {
+
+// The double-float fma below must not hide the built-in overloads inside this namespace.
+using ::fma;
+using ::fmaf;
+
+struct df {
+    float hi, lo;
+    __host__ __device__ df() {}
+    __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ explicit constexpr df(int v) : hi((float)v), lo(0.0f) {}
+};
+
+// Split a double into hi + lo (host or device; on the device it costs FP64
+// instructions, so kernels take precomputed pairs or compile-time constants).
+__host__ __device__ constexpr df df_from(double d) { return df((float)d, (float)(d - (double)(float)d)); }
+__host__ __device__ inline double df_to(df a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = a + b;
+    const float t = s - a;
+    return df(s, (a - (s - t)) + (b - t));
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return df(s, b - (s - a));
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+    const float p = a * b;
+    return df(p, fmaf(a, b, -p));
+}
+
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator+(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) {
+    df p = two_prod(a.hi, b.hi);
+    float e = fmaf(a.hi, b.lo, p.lo);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum(p.hi, e);
+}
+// a * b + c with one renormalisation of the product's cross terms folded into the sum
+__device__ __forceinline__ df fma(df a, df b, df c) {
+    df p = two_prod(a.hi, b.hi);
+    float e = fmaf(a.hi, b.lo, p.lo);
+    e = fmaf(a.lo, b.hi, e);
+    df s = two_sum(p.hi, c.hi);
+    return fast_two_sum(s.hi, s.lo + (e + c.lo));
+}
+
+__device__ __forceinline__ bool df_isfinite(df a) { return isfinite(a.hi); }
+
+// exp(x) for |x| < 2^-6 by its Taylor polynomial of degree 6 (first omitted
+// term x^7/7! < 2^-54, below the format's 2^-48), in double-float; other
+// arguments through FP64.
+__device__ __forceinline__ df exp_small(df x) {
+    if (fabsf(x.hi) < 0.015625f) {
+        constexpr df c[7] = {df_from(1.0 / 720.0), df_from(1.0 / 120.0), df_from(1.0 / 24.0), df_from(1.0 / 6.0),
+                             df(0.5f, 0.0f),       df(1.0f, 0.0f),       df(1.0f, 0.0f)};
+        df p = c[0];
+#pragma unroll
+        for (int n = 1; n < 7; n++) p = fma(p, x, c[n]);
+        return p;
+    }
+    return df_from(exp(df_to(x)));
+}
+
+// (sin x, cos x) for |x| < 2^-6 by Taylor polynomials in t = x^2 (sin to x^7,
+// cos to x^6: omitted terms below 2^-62 relative); other arguments through FP64.
+__device__ __forceinline__ void sincos_small(df x, df* s, df* c) {
+    if (fabsf(x.hi) < 0.015625f) {
+        const df mt = -(x * x);
+        // sin(x)/x = sum (-t)^n/(2n+1)!, cos(x) = sum (-t)^n/(2n)!, n = 3..0
+        constexpr df sc[4] = {df_from(1.0 / 5040.0), df_from(1.0 / 120.0), df_from(1.0 / 6.0), df(1.0f, 0.0f)};
+        constexpr df cc[4] = {df_from(1.0 / 720.0), df_from(1.0 / 24.0), df(0.5f, 0.0f), df(1.0f, 0.0f)};
+        df ps = sc[0], pc = cc[0];
+#pragma unroll
+        for (int n = 1; n < 4; n++) {
+            ps = fma(ps, mt, sc[n]);
+            pc = fma(pc, mt, cc[n]);
+        }
+        *s = ps * x;
+        *c = pc;
+        return;
+    }
+    double sd, cd;
+    sincos(df_to(x), &sd, &cd);
+    *s = df_from(sd);
+    *c = df_from(cd);
+}
+
+}  // namespace sgpe

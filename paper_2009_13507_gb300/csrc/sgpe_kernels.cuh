@@ -24,6 +24,7 @@ namespace sgpe {
 struct DevScalars {
     double scale[4];     // pending renormalisation scale per component (DJ2: all equal)
     float scale_f[4];    // the same rounded to FP32 (read by the complex64 form)
+    float scale_l[4];    // and the rest scale - scale_f (double-float low part)
     double norms[4];     // N_j of the state written by the last completed step
     double obs[16];      // observables of the last sgpe_energy
     int step_idx;        // index into a per-step Omega table (real time)
@@ -62,16 +63,25 @@ template <bool IMAG, typename R> __device__ __forceinline__ cx<R> tfma(cx<R> t, 
     if (IMAG) return axpy(t.re, x, acc);
     return caxpy(t, x, acc);
 }
+__device__ __forceinline__ double shfl_up_r(double v, int off) { return __shfl_up_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ float shfl_up_r(float v, int off) { return __shfl_up_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ df shfl_up_r(df v, int off) {
+    return df(__shfl_up_sync(0xffffffffu, v.hi, off), __shfl_up_sync(0xffffffffu, v.lo, off));
+}
+__device__ __forceinline__ double shfl_dn_r(double v, int off) { return __shfl_down_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ float shfl_dn_r(float v, int off) { return __shfl_down_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ df shfl_dn_r(df v, int off) {
+    return df(__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off));
+}
 template <typename R> __device__ __forceinline__ cx<R> shup(cx<R> a, int off) {
-    return {__shfl_up_sync(0xffffffffu, a.re, off), __shfl_up_sync(0xffffffffu, a.im, off)};
+    return {shfl_up_r(a.re, off), shfl_up_r(a.im, off)};
 }
 template <typename R> __device__ __forceinline__ cx<R> shdn(cx<R> a, int off) {
-    return {__shfl_down_sync(0xffffffffu, a.re, off), __shfl_down_sync(0xffffffffu, a.im, off)};
+    return {shfl_dn_r(a.re, off), shfl_dn_r(a.im, off)};
 }
 
 template <typename R> __device__ __forceinline__ cx<R> tld(const typename V2<R>::T* t, int i) {
-    typename V2<R>::T v = __ldg(t + i);
-    return {v.x, v.y};
+    return unpack(__ldg(t + i));
 }
 
 // Solve T w = x for one line held in shared memory (buf, chunked layout) by the
@@ -214,6 +224,7 @@ __device__ __forceinline__ void finalize_norms(const double* partials, int nblk,
                 sc->norms[j] = N[j];
                 sc->scale[j] = d[j];
                 sc->scale_f[j] = (float)d[j];
+                sc->scale_l[j] = (float)(d[j] - (double)sc->scale_f[j]);
             }
             if (!finite) sc->err |= 1;
             if (advance_step) sc->step_idx += 1;
@@ -230,6 +241,14 @@ __device__ __forceinline__ void finalize_norms(const double* partials, int nblk,
 // The pointwise substeps at grid point (ix, iy) of the state A (one grid),
 // written to B; scale: the pending renormalisation scale per component; Ot the
 // Rabi coupling Omega/sqrt2 of this step.
+// Pending renormalisation scale of component j in the arithmetic type R.
+template <typename R> __device__ __forceinline__ R scale_of(const DevScalars* sc, int j);
+template <> __device__ __forceinline__ double scale_of<double>(const DevScalars* sc, int j) { return sc->scale[j]; }
+template <> __device__ __forceinline__ float scale_of<float>(const DevScalars* sc, int j) { return sc->scale_f[j]; }
+template <> __device__ __forceinline__ df scale_of<df>(const DevScalars* sc, int j) {
+    return df(sc->scale_f[j], sc->scale_l[j]);
+}
+
 // pointwise_point returns the three updated values in u; pointwise_at stores them.
 template <typename R, bool IMAG>
 __device__ __forceinline__ void pointwise_point(const typename V2<R>::T* __restrict__ A, const KParams& p,
@@ -239,10 +258,10 @@ __device__ __forceinline__ void pointwise_point(const typename V2<R>::T* __restr
     const size_t c = (size_t)iy * p.nx + ix;
     R d[3];
 #pragma unroll
-    for (int j = 0; j < 3; j++) d[j] = pick<R>(sc->scale[j], sc->scale_f[j]);
+    for (int j = 0; j < 3; j++) d[j] = scale_of<R>(sc, j);
 #pragma unroll
     for (int j = 0; j < 3; j++) u[j] = scl(d[j], ld<R>(A, j * plane + c));
-    const R dt = pick<R>(p.dt, p.f_dt);
+    const R dt = kc<R>(p, KC_DT);
     if ((mask & 1) && p.so_case) {
         cx<R> X[3], Y[3];
         const cx<R> zero = {R(0), R(0)};
@@ -262,7 +281,7 @@ __device__ __forceinline__ void pointwise_point(const typename V2<R>::T* __restr
         R gx[3], gy[3];
         if (p.renorm != 2) {
             // one scale for all components (DJ2, or none): the same products, formed once
-            const R g = pick<R>(p.hx, p.f_hx) * d[0], h = pick<R>(p.hy, p.f_hy) * d[0];
+            const R g = kc<R>(p, KC_HX) * d[0], h = kc<R>(p, KC_HY) * d[0];
 #pragma unroll
             for (int j = 0; j < 3; j++) {
                 gx[j] = g;
@@ -271,8 +290,8 @@ __device__ __forceinline__ void pointwise_point(const typename V2<R>::T* __restr
         } else {
 #pragma unroll
             for (int j = 0; j < 3; j++) {
-                gx[j] = pick<R>(p.hx, p.f_hx) * d[j];
-                gy[j] = pick<R>(p.hy, p.f_hy) * d[j];
+                gx[j] = kc<R>(p, KC_HX) * d[j];
+                gy[j] = kc<R>(p, KC_HY) * d[j];
             }
         }
         so_point<IMAG>(u, X, Y, gx, gy, p.so_case);
@@ -280,16 +299,16 @@ __device__ __forceinline__ void pointwise_point(const typename V2<R>::T* __restr
     if (mask & 2) {
         // V = wx^2 x^2/2 + wy^2 y^2/2 with x = kx dx: kx^2 is an exact integer
         const int kx = ix - p.nx / 2, ky = iy - p.ny / 2;
-        if (sizeof(R) == 8) {
-            // complex128: -dt folded into the coefficients (exponent -dt mu directly)
-            R Vn = (R)p.n_vx * (R)(kx * kx) + (p.dim == 2 ? (R)p.n_vy * (R)(ky * ky) : R(0));
+        if constexpr (!is_f32<R>()) {
+            // complex128 / double-float: -dt folded into the coefficients (exponent -dt mu directly)
+            R Vn = kc<R>(p, KC_NVX) * R(kx * kx) + (p.dim == 2 ? kc<R>(p, KC_NVY) * R(ky * ky) : R(0));
             calcnu_point_dt<IMAG>(u, Vn, p);
         } else {
-            R V = pick<R>(p.vx, p.f_vx) * (R)(kx * kx) + (p.dim == 2 ? pick<R>(p.vy, p.f_vy) * (R)(ky * ky) : R(0));
-            calcnu_point<IMAG>(u, V, pick<R>(p.c0, p.f_c0), pick<R>(p.c2, p.f_c2), dt);
+            R V = kc<R>(p, KC_VX) * R(kx * kx) + (p.dim == 2 ? kc<R>(p, KC_VY) * R(ky * ky) : R(0));
+            calcnu_point<IMAG>(u, V, kc<R>(p, KC_C0), kc<R>(p, KC_C2), dt);
         }
     }
-    if (mask & 4) herm_point<IMAG>(u, pick<R>(p.c2, p.f_c2), Ot, dt, &p);
+    if (mask & 4) herm_point<IMAG>(u, kc<R>(p, KC_C2), Ot, dt, &p);
 }
 
 template <typename R, bool IMAG>
@@ -313,8 +332,8 @@ __global__ void __launch_bounds__(128) k_pointwise(const typename V2<R>::T* __re
     const int iy = blockIdx.y * blockDim.y + threadIdx.y;
     pdl_wait();
     if (ix >= p.nx || iy >= p.ny) return;
-    const R Ot = omega_tab ? (R)(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440)
-                           : pick<R>(p.omega_t, p.f_omega_t);
+    const R Ot = omega_tab ? to_r<R>(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440)
+                           : kc<R>(p, KC_OMEGA);
     pointwise_at<R, IMAG>(A, B, p, sc, Ot, ix, iy, mask);
 }
 
@@ -345,7 +364,7 @@ __global__ void __launch_bounds__(256) k_cn_x(const typename V2<R>::T* in, typen
             cx<R> x = ldc<R>(in, base + i);
             cx<R> o = {fma(R(2), w.re, -x.re), fma(R(2), w.im, -x.im)};
             st<R>(out, base + i, o);
-            if (LAST) acc += (double)o.re * (double)o.re + (double)o.im * (double)o.im;
+            if (LAST) acc += dbl(o.re) * dbl(o.re) + dbl(o.im) * dbl(o.im);
         }
     }
     if (LAST && line < nlines) {
@@ -396,7 +415,7 @@ __global__ void __launch_bounds__(256) k_cn_y(const typename V2<R>::T* in, typen
             cx<R> x = ldc<R>(in, g);
             cx<R> o = {fma(R(2), wv.re, -x.re), fma(R(2), wv.im, -x.im)};
             st<R>(out, g, o);
-            acc += (double)o.re * (double)o.re + (double)o.im * (double)o.im;
+            acc += dbl(o.re) * dbl(o.re) + dbl(o.im) * dbl(o.im);
         }
     }
     if (finalize) {
@@ -444,6 +463,7 @@ static __global__ void __launch_bounds__(96) k_finalize(const double* partials, 
             sc->norms[q3] = N[q3];
             sc->scale[q3] = d[q3];
             sc->scale_f[q3] = (float)d[q3];
+            sc->scale_l[q3] = (float)(d[q3] - (double)sc->scale_f[q3]);
         }
         if (!finite) sc->err |= 1;
         if (advance_step) sc->step_idx += 1;
@@ -476,9 +496,10 @@ __global__ void k_coef(typename V2<R>::T* fa, typename V2<R>::T* fg, typename V2
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double dr = 1.0 + 2.0 * bre, di = 2.0 * bim;  // diagonal 1 + 2 bt
     const int len = 32 * C;
+    const cx<R> zero = {R(0), R(0)};
     for (int i = n; i < len; i++) {
-        fa[i].x = fa[i].y = (R)0;
-        fg[i].x = fg[i].y = (R)0;
+        st<R>(fa, i, zero);
+        st<R>(fg, i, zero);
     }
     double ur = dr, ui = di;
     for (int i = 0; i < n; i++) {
@@ -493,32 +514,30 @@ __global__ void k_coef(typename V2<R>::T* fa, typename V2<R>::T* fg, typename V2
         double ar, ai, gr, gi;
         cdiv(1.0, 0.0, ur, ui, &ar, &ai);
         cdiv(bre, bim, ur, ui, &gr, &gi);
-        fa[i].x = (R)ar;
-        fa[i].y = (R)ai;
-        fg[i].x = (R)gr;
-        fg[i].y = (R)gi;
+        st<R>(fa, i, cx<R>{to_r<R>(ar), to_r<R>(ai)});
+        st<R>(fg, i, cx<R>{to_r<R>(gr), to_r<R>(gi)});
     }
     // chunk products, computed from the rounded-to-FP64 fg values
     for (int k0 = 0; k0 < len; k0 += C) {
         int k1 = k0 + C;
         double Pr = 1.0, Pi = 0.0;
         for (int i = k0; i < k1; i++) {
-            double gr = (double)fg[i].x, gi = (double)fg[i].y;
+            const cx<R> g = unpack(fg[i]);
+            double gr = dbl(g.re), gi = dbl(g.im);
             double tr = Pr * gr - Pi * gi, ti = Pr * gi + Pi * gr;
             Pr = tr;
             Pi = ti;
-            fp[i].x = (R)Pr;
-            fp[i].y = (R)Pi;
+            st<R>(fp, i, cx<R>{to_r<R>(Pr), to_r<R>(Pi)});
         }
         Pr = 1.0;
         Pi = 0.0;
         for (int i = k1 - 1; i >= k0; i--) {
-            double gr = (double)fg[i].x, gi = (double)fg[i].y;
+            const cx<R> g = unpack(fg[i]);
+            double gr = dbl(g.re), gi = dbl(g.im);
             double tr = Pr * gr - Pi * gi, ti = Pr * gi + Pi * gr;
             Pr = tr;
             Pi = ti;
-            fq[i].x = (R)Pr;
-            fq[i].y = (R)Pi;
+            st<R>(fq, i, cx<R>{to_r<R>(Pr), to_r<R>(Pi)});
         }
     }
 }
@@ -532,7 +551,7 @@ __global__ void k_flush(typename V2<R>::T* A, size_t plane, const DevScalars* sc
     size_t total = 3 * plane;
     for (; i < total; i += (size_t)gridDim.x * blockDim.x) {
         int j = (int)(i / plane);
-        R d = (R)sc->scale[j];
+        R d = to_r<R>(sc->scale[j]);
         cx<R> v = ldc<R>(A, i);
         st<R>(A, i, scl(d, v));
     }
@@ -542,6 +561,7 @@ static __global__ void k_reset_scale(DevScalars* sc) {
     if (threadIdx.x < 4) {
         sc->scale[threadIdx.x] = 1.0;
         sc->scale_f[threadIdx.x] = 1.0f;
+        sc->scale_l[threadIdx.x] = 0.0f;
     }
 }
 
@@ -558,7 +578,7 @@ __global__ void __launch_bounds__(256) k_norms(const typename V2<R>::T* A, size_
          i += (size_t)gridDim.x * blockDim.x) {
         int j = (int)(i / plane);
         cx<R> a = ldc<R>(A, i);
-        double q = (double)a.re * (double)a.re + (double)a.im * (double)a.im;
+        double q = dbl(a.re) * dbl(a.re) + dbl(a.im) * dbl(a.im);
         if (j == 0) v[0] += q;
         else if (j == 1) v[1] += q;
         else v[2] += q;
@@ -588,7 +608,7 @@ __device__ __forceinline__ void obs_point(const typename V2<R>::T* __restrict__ 
         const cx<double> zero = {0.0, 0.0};
         for (int j = 0; j < 3; j++) {
             cx<R> a = ld<R>(A, j * plane + c);
-            u[j] = {(double)a.re, (double)a.im};
+            u[j] = {dbl(a.re), dbl(a.im)};
         }
         double x = (ix - p.nx / 2) * p.dx, y = (p.dim == 2) ? (iy - p.ny / 2) * p.dy : 0.0;
         double rr = x * x + y * y;
@@ -607,11 +627,11 @@ __device__ __forceinline__ void obs_point(const typename V2<R>::T* __restrict__ 
             cx<double> xm = zero, xp = zero, ym = zero, yp = zero;
             if (ix > 0) {
                 cx<R> a = ld<R>(A, j * plane + c - 1);
-                xm = {(double)a.re, (double)a.im};
+                xm = {dbl(a.re), dbl(a.im)};
             }
             if (ix + 1 < p.nx) {
                 cx<R> a = ld<R>(A, j * plane + c + 1);
-                xp = {(double)a.re, (double)a.im};
+                xp = {dbl(a.re), dbl(a.im)};
             }
             ek += 0.5 * nrm(sub(u[j], xm)) * idx2;
             if (ix == p.nx - 1) ek += 0.5 * nrm(u[j]) * idx2;
@@ -619,11 +639,11 @@ __device__ __forceinline__ void obs_point(const typename V2<R>::T* __restrict__ 
             if (p.dim == 2) {
                 if (iy > 0) {
                     cx<R> a = ld<R>(A, j * plane + c - p.nx);
-                    ym = {(double)a.re, (double)a.im};
+                    ym = {dbl(a.re), dbl(a.im)};
                 }
                 if (iy + 1 < p.ny) {
                     cx<R> a = ld<R>(A, j * plane + c + p.nx);
-                    yp = {(double)a.re, (double)a.im};
+                    yp = {dbl(a.re), dbl(a.im)};
                 }
                 ek += 0.5 * nrm(sub(u[j], ym)) * idy2;
                 if (iy == p.ny - 1) ek += 0.5 * nrm(u[j]) * idy2;

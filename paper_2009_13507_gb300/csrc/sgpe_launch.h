@@ -91,6 +91,9 @@ template <typename R> struct Launcher {
 
 cudaError_t reset_scale(cudaStream_t s, DevScalars* sc);
 
+// Device complex128 [n] -> double-float layout [n] (hi, lo per real part).
+cudaError_t cdf_from_c128(cudaStream_t s, const void* src, void* dst, size_t n);
+
 // End of a step: reduce the last sweep's nblk norm partials, publish N_j and the
 // next pending scale, advance the step counter (one block).
 cudaError_t finalize_step(cudaStream_t s, const double* partials, int nblk, double cell, int renorm, double mag,
@@ -103,5 +106,26 @@ KParams make_kparams(int dim, int nx, int ny, double dx, double dy, const sgpe_p
 
 // Store the message that sgpe_last_error(NULL) returns on this host thread.
 void set_thread_error(const char* msg);
+
+// Internal view of a single-grid context for the adjoint translation unit
+// (filled by ctx_view in sgpe_api.cu).
+struct CtxView {
+    int dim, nx, ny, esz;
+    bool dbl;
+    sgpe_precision prec;
+    cudaStream_t stream;
+    void* psi;
+    void* mid;
+    DevScalars* sc;
+    const void* const* tabs_real;  // [axis][4], bt = i dt/(4h^2)
+    const void* const* tabs_adj;   // [axis][4], bt = -i dt/(4h^2)
+    const Geometry* geo;
+    KParams kp;
+    double* partials;
+    bool ready;
+};
+bool ctx_view(sgpe_ctx* c, CtxView* v);
+sgpe_status ctx_fail(sgpe_ctx* c, sgpe_status st, const char* msg);
+cudaError_t ctx_flush(sgpe_ctx* c);
 
 }  // namespace sgpe

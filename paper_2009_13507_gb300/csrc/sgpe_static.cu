@@ -73,7 +73,7 @@ extern "C" sgpe_status sgpe_observables_noalloc(const void* psi_dev, int dim, in
         dy = dx;
     }
     if (nx < 3 || (dim == 2 && ny < 3) || !(dx > 0.0) || !(dy > 0.0) || !isfinite(dx) || !isfinite(dy) ||
-        (prec != SGPE_C128 && prec != SGPE_C64) || p->so_type < 0 || p->so_type > 3 || !isfinite(p->c0) ||
+        (prec != SGPE_C128 && prec != SGPE_C64 && prec != SGPE_CDF) || p->so_type < 0 || p->so_type > 3 || !isfinite(p->c0) ||
         !isfinite(p->c2) || !isfinite(p->gamma) || !isfinite(p->omega) || !isfinite(p->wx) || !isfinite(p->wy)) {
         set_thread_error("sgpe_observables_noalloc: invalid grid or parameters");
         return SGPE_EINVAL;
@@ -126,8 +126,9 @@ extern "C" sgpe_status sgpe_observables_noalloc(const void* psi_dev, int dim, in
     // flag must start at zero.
     if (e == cudaSuccess) e = cudaMemsetAsync(sc, 0, sizeof(DevScalars), s);
     if (e == cudaSuccess)
-        e = prec == SGPE_C128 ? Launcher<double>::observables(s, psi_dev, k, k.omega_t, partials, sc)
-                              : Launcher<float>::observables(s, psi_dev, k, k.omega_t, partials, sc);
+        e = prec == SGPE_C128  ? Launcher<double>::observables(s, psi_dev, k, k.omega_t, partials, sc)
+            : prec == SGPE_C64 ? Launcher<float>::observables(s, psi_dev, k, k.omega_t, partials, sc)
+                               : Launcher<df>::observables(s, psi_dev, k, k.omega_t, partials, sc);
     if (e == cudaSuccess) e = cudaMemcpyAsync(obs_dev, sc->obs, SGPE_NOBS * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) {
         char msg[200];

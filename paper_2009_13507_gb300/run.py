@@ -21,7 +21,7 @@ def main(argv=None):
     ap.add_argument("--dim", type=int, default=2, choices=(1, 2))
     ap.add_argument("--n", type=int, default=256, help="points per axis")
     ap.add_argument("--dx", type=float, default=0.05)
-    ap.add_argument("--precision", default="c128", choices=("c128", "c64"))
+    ap.add_argument("--precision", default="c128", choices=("c128", "c64", "cdf"))
     ap.add_argument("--steps", type=int, default=64)
     ap.add_argument("--real", action="store_true", help="real-time steps (default: imaginary time)")
     ap.add_argument("--c0", type=float, default=50.0)
@@ -46,7 +46,7 @@ def main(argv=None):
         psi0 = I.gaussian_phase_2d(n, n, args.dx, args.dx, seed=args.seed)
     else:
         psi0 = I.gaussian_jitter_1d(n, args.dx, seed=args.seed)
-    dtype = torch.complex128 if args.precision == "c128" else torch.complex64
+    dtype = torch.complex64 if args.precision == "c64" else torch.complex128
     s = sgpe.Solver(args.dim, n, ny, dx=args.dx, precision=args.precision, device=dev)
     s.set_params(sgpe.Physics(c0=args.c0, c2=args.c2, so_type=args.so_type, gamma=args.gamma, omega=args.omega,
                               dt=args.dt, renorm=0 if args.real else 1))

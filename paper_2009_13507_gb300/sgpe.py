@@ -19,7 +19,8 @@ _lib = None
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, EUNSUPPORTED = range(8)
 STATUS = {0: "SGPE_OK", 1: "SGPE_EINVAL", 2: "SGPE_ENOMEM", 3: "SGPE_ECUDA", 4: "SGPE_ENONFINITE",
           5: "SGPE_ETIMEOUT", 6: "SGPE_ESTATE", 7: "SGPE_EUNSUPPORTED"}
-C128, C64 = 0, 1
+C128, C64, CDF = 0, 1, 2
+PRECISIONS = {"c128": C128, "c64": C64, "cdf": CDF}
 NOBS = 16
 OBS_NAMES = ("N+", "N0", "N-", "N", "mag", "E", "mu", "rms+", "rms0", "rms-", "rms",
              "E_kin", "E_trap", "E_int", "E_rabi", "E_so")
@@ -132,13 +133,16 @@ class Solver:
         self.dy = float(dy if dy is not None else dx) if dim == 2 else float(dx)
         self.precision = precision
         self.device = torch.device(device)
-        self.cdtype = torch.complex128 if precision == "c128" else torch.complex64
-        self.npdtype = np.complex128 if precision == "c128" else np.complex64
+        if precision not in PRECISIONS:
+            raise ValueError("precision must be one of %s" % sorted(PRECISIONS))
+        # external (host / load_state) element type; "cdf" exchanges complex128
+        self.cdtype = torch.complex64 if precision == "c64" else torch.complex128
+        self.npdtype = np.complex64 if precision == "c64" else np.complex128
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
         self.ctx = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             rc = self.lib.sgpe_init_grid(ctypes.byref(self.ctx), self.dim, self.nx, self.ny, self.dx, self.dy,
-                                         C128 if precision == "c128" else C64,
+                                         PRECISIONS[precision],
                                          ctypes.c_void_p(self.stream.cuda_stream))
         if rc != OK:
             msg = self.lib.sgpe_last_error(None)
@@ -147,7 +151,11 @@ class Solver:
         nbytes = ctypes.c_size_t()
         self._check(self.lib.sgpe_workspace_bytes(self.ctx, ctypes.byref(nbytes)))
         self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
-        self.psi = torch.zeros((3, self.ny, self.nx), dtype=self.cdtype, device=self.device)
+        if precision == "cdf":
+            # bound state in the double-float pair layout (re_hi, re_lo, im_hi, im_lo)
+            self.psi = torch.zeros((3, self.ny, self.nx, 4), dtype=torch.float32, device=self.device)
+        else:
+            self.psi = torch.zeros((3, self.ny, self.nx), dtype=self.cdtype, device=self.device)
         self._check(self.lib.sgpe_bind(self.ctx, self.psi.data_ptr(), self.workspace.data_ptr()))
         self.physics = None
 
