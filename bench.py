@@ -10,8 +10,10 @@ advanced by one full time step).
 
 Also reported on the same line: the complex64 precision form on the same
 workload (FP64 reductions) with its energy error against the FP64 path, the
-dominant kernel's roofline, the oracle on the host cores (cpu_baseline) and the
-end-to-end throughput through the C ABI with host buffers.
+FP64-accurate double-float form (FP32 pairs) with its state and energy error
+against the FP64 path, the dominant kernel's roofline, the oracle on the host
+cores (cpu_baseline) and the end-to-end throughput through the C ABI with host
+buffers.
 
 --impl reference times the FP64 CPU oracle on the host cores instead (a bounded
 sample of the same workload per step).
@@ -383,6 +385,22 @@ def main():
     kms32, kcnt32 = s32.profile_steps(NSTEPS, True)
     kavg32 = {names[i]: kms32[i] / max(int(kcnt32[i]), 1) for i in range(4) if int(kcnt32[i]) > 0}
 
+    # FP64-accurate double-float form (FP32 pairs) on the same workload; its
+    # final state after one benchmark step against the complex128 one
+    sdf = sgpe.Solver(2, NX, NY, dx=DX, precision="cdf", device=dev)
+    sdf.set_params(sgpe.Physics(**PHYS))
+    msdf, endf, _ = timed_run(sdf, psi0_dev, args.steps, args.warmup)
+    tdf = statistics.mean(msdf)
+    edf = endf[-1][5]
+    for s_ in (solver, sdf):
+        reset(s_, psi0_dev)
+        s_.step_imag(NSTEPS)
+    st64, stdf = solver.get_state(), sdf.get_state()
+    state_err_df = float(np.linalg.norm((stdf - st64).ravel()) / np.linalg.norm(st64.ravel()))
+    reset(sdf, psi0_dev)
+    kmsdf, kcntdf = sdf.profile_steps(NSTEPS, True)
+    kavgdf = {names[i]: kmsdf[i] / max(int(kcntdf[i]), 1) for i in range(4) if int(kcntdf[i]) > 0}
+
     # end to end through the C ABI with host buffers: pinned host state in,
     # 2000 steps, observables and the final state out, copies inside the timed region
     host_in = torch.from_numpy(psi0.astype(np.complex128)).pin_memory()
@@ -429,7 +447,11 @@ def main():
         "chosen": {"form": "complex64 state, FP64 reductions", "value": ws * point_steps / (t32 * 1e-3),
                    "ms_per_step": t32, "energy_rel_err_vs_fp64": abs(e32 - e64) / abs(e64),
                    "speedup_vs_fp64": t_step / t32, "kernels_avg_ms": kavg32},
-        "energy": {"E_fp64": e64, "E_c64": e32, "E_profile_pass": e_prof[5]},
+        "fp64_accurate": {"form": "double-float (FP32 pairs), FP64 reductions", "value": ws * point_steps / (tdf * 1e-3),
+                          "ms_per_step": tdf, "energy_rel_err_vs_fp64": abs(edf - e64) / abs(e64),
+                          "state_rel_err_vs_fp64": state_err_df, "speedup_vs_fp64": t_step / tdf,
+                          "kernels_avg_ms": kavgdf},
+        "energy": {"E_fp64": e64, "E_c64": e32, "E_cdf": edf, "E_profile_pass": e_prof[5]},
         "forms": forms,
         "cpu_baseline": cpu,
         "e2e": {"value": ws * point_steps / (e2e_t * 1e-3), "unit": METRIC, "h2d_bytes_per_step": nbytes_state,
