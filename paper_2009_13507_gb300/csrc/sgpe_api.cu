@@ -302,17 +302,31 @@ sgpe_status sgpe_set_params(sgpe_ctx* c, const sgpe_params* p) {
 // ---------------------------------------------------------------------------
 // Step orchestration
 // ---------------------------------------------------------------------------
+// The fused 2D step with the register y sweep ends without a finalize launch:
+// each step's head kernel derives the pending scale from the previous y
+// sweep's norm partials, and end_steps publishes it after the last step.
+static bool head_scale(const sgpe_ctx* c) { return c->geo.fused && c->geo.reg_y; }
+
+static cudaError_t end_steps(sgpe_ctx* c, bool imag) {
+    if (!head_scale(c)) return cudaSuccess;
+    const int renorm = imag ? c->params.renorm : 0;
+    return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 0, c->sc);
+}
+
 template <typename R>
 static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab) {
     cudaError_t e;
     const int mode = imag ? 0 : 1;
     const int renorm = imag ? c->params.renorm : 0;
     if (c->geo.fused) {
-        if ((e = Launcher<R>::pwx(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, c->tabs[mode][0])))
+        if ((e = Launcher<R>::pwx(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, c->tabs[mode][0],
+                                  c->partials, c->geo.blocks_y / 3, renorm)))
             return e;
+        const bool head = head_scale(c);
         if ((e = Launcher<R>::cn_y(c->stream, imag, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials,
-                                   c->sc, renorm, 1, 1)))
+                                   c->sc, renorm, 1, 1, head)))
             return e;
+        if (head) return cudaSuccess;  // the next head kernel (or end_steps) takes the scale from the partials
         return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 1, c->sc);
     }
     if ((e = Launcher<R>::pointwise(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, 7))) return e;
@@ -378,6 +392,7 @@ static sgpe_status run_steps(sgpe_ctx* c, int nsteps, bool imag, const double* o
     } else {
         CK(enqueue_steps(c, nsteps, imag, omega_tab), "step kernels");
     }
+    if (nsteps > 0) CK(end_steps(c, imag), "end of steps");
     return SGPE_OK;
 }
 
@@ -573,6 +588,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
     int cnt[4] = {0, 0, 0, 0};
     const bool two = c->dim == 2;
     const bool fused = c->geo.fused;
+    const bool head = head_scale(c);
     sgpe_status out = SGPE_OK;
     for (int i0 = 0; i0 < nsteps && out == SGPE_OK; i0 += kBatch) {
       const int nb = nsteps - i0 < kBatch ? nsteps - i0 : kBatch;
@@ -581,7 +597,10 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
         cudaEvent_t* ev = evs[bi];
         e = cudaEventRecord(ev[0], c->stream);
         if (!e && fused)
-            e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::pwx(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, c->tabs[mode][0]); });
+            e = with_prec(c->prec, [&](auto r) {
+                return Launcher<decltype(r)>::pwx(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr,
+                                                  c->tabs[mode][0], c->partials, c->geo.blocks_y / 3, renorm);
+            });
         if (!e && !fused)
             e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::pointwise(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, 7); });
         if (!e) e = cudaEventRecord(ev[1], c->stream);
@@ -590,9 +609,12 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
             e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::cn_x(c->stream, im, !two, c->mid, xout, c->kp, c->tabs[mode][0], c->geo, c->partials, c->sc, renorm, 1); });
         if (!e) e = cudaEventRecord(ev[2], c->stream);
         if (!e && two)
-            e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials, c->sc, renorm, 1, 1); });
+            e = with_prec(c->prec, [&](auto r) {
+                return Launcher<decltype(r)>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo,
+                                                   c->partials, c->sc, renorm, 1, 1, head);
+            });
         if (!e) e = cudaEventRecord(ev[3], c->stream);
-        if (!e)
+        if (!e && !head)
             e = finalize_step(c->stream, c->partials, two ? c->geo.blocks_y : 3 * c->ny, c->kp.cell, renorm,
                               c->kp.mag, 1, c->sc);
         if (!e) e = cudaEventRecord(ev[4], c->stream);
@@ -604,7 +626,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
       }
       for (int bi = 0; bi < nb; bi++)
           for (int k = 0; k < 4; k++) {
-              if ((k == 2 && !two) || (k == 1 && fused)) continue;
+              if ((k == 2 && !two) || (k == 1 && fused) || (k == 3 && head)) continue;
               float ms = 0.f;
               cudaEventElapsedTime(&ms, evs[bi][k], evs[bi][k + 1]);
               acc[k] += ms;
@@ -613,6 +635,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
     }
     for (int b = 0; b < kBatch; b++)
         for (int k = 0; k < 5; k++) cudaEventDestroy(evs[b][k]);
+    if (out == SGPE_OK && nsteps > 0) CK(end_steps(c, im), "end of steps");
     for (int k = 0; k < 4; k++) {
         ms_out[k] = acc[k];
         launches_out[k] = cnt[k];
@@ -622,6 +645,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
 
 int sgpe_launches_per_step(const sgpe_ctx* c) {
     if (!c) return 0;
+    if (head_scale(c)) return 2;  // plus one end-of-steps launch per step call
     if (c->geo.fused) return 3;
     return c->dim == 2 ? 4 : 3;
 }

@@ -233,13 +233,16 @@ __global__ void __launch_bounds__(32) k_cnx_reg(const typename V2<R>::T* in, typ
 
 // ---------------------------------------------------------------------------
 // Fused head of a 2D step, one block per grid row iy (rows of at most 1024
-// points). All threads run the pointwise substeps (pending scale, SO, CALCNU,
-// HERM) of the row's points for the three components and stage the results in
-// shared memory in the lanes' chunk layout, each chunk padded to C + 1 entries
-// so that a lane's chunk reads are free of bank conflicts; then warp j solves
-// the Crank-Nicolson x line of component j from there and writes it to B.
-// Compared with separate pointwise and x-sweep kernels this saves one pass over
-// the state and one launch per step.
+// points). First the pending renormalisation scale: when the previous step's
+// y sweep left its norm partials (DevScalars::scale_src), warps 0..2 sum the m
+// partials of their component and thread 0 forms the scale (Eq. (DJ2) / (DJ));
+// every block does the same sums in the same order, so all blocks agree and no
+// separate end-of-step launch is needed. Then all threads run the pointwise
+// substeps (SO, CALCNU, HERM) of the row's points for the three components and
+// stage the results in shared memory in the lanes' chunk layout, each chunk
+// padded to C + 1 entries so that a lane's chunk reads are free of bank
+// conflicts; then warp j solves the Crank-Nicolson x line of component j from
+// there and writes it to B.
 // ---------------------------------------------------------------------------
 constexpr int kPwxThreads = 256;
 
@@ -250,33 +253,51 @@ template <typename R, int C> constexpr size_t pwx_smem_bytes() {
 template <typename R, bool IMAG, int C>
 __global__ void __launch_bounds__(kPwxThreads, C <= 8 ? 2 : 1)
     k_pwx(const typename V2<R>::T* __restrict__ A, typename V2<R>::T* __restrict__ B, KParams p,
-          const DevScalars* __restrict__ sc, const double* __restrict__ omega_tab, Tabs<R> t) {
+          const DevScalars* __restrict__ sc, const double* __restrict__ omega_tab, Tabs<R> t,
+          const double* __restrict__ partials, int m, int renorm) {
     using T = typename V2<R>::T;
     extern __shared__ __align__(16) unsigned char pwx_smem[];
     T* row = reinterpret_cast<T*>(pwx_smem);
+    __shared__ double red[3];
+    __shared__ R ds[3];
     constexpr int S = 32 * (C + 1);  // staged entries per component
     const int iy = blockIdx.x;
     const int nx = p.nx;
+    const int warp = threadIdx.x >> 5;
     pdl_wait();
+    if (*(volatile const int*)&sc->scale_src) {
+        if (warp < 3) {
+            const double s = sum_partials_warp(partials + (size_t)warp * m, m);
+            if ((threadIdx.x & 31) == 0) red[warp] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double N[3] = {red[0] * p.cell, red[1] * p.cell, red[2] * p.cell};
+            const bool finite = isfinite(N[0]) && isfinite(N[1]) && isfinite(N[2]);
+            double d[3];
+            renorm_factors(N, finite ? renorm : 0, p.mag, d);
+#pragma unroll
+            for (int j = 0; j < 3; j++) ds[j] = to_r<R>(d[j]);
+        }
+    } else if (threadIdx.x < 3) {
+        ds[threadIdx.x] = scale_of<R>(sc, threadIdx.x);
+    }
+    __syncthreads();
     const R Ot = omega_tab ? to_r<R>(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440)
                            : kc<R>(p, KC_OMEGA);
     for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
         cx<R> u[3];
-        pointwise_point<R, IMAG>(A, p, sc, Ot, ix, iy, 7, u);
+        pointwise_point<R, IMAG>(A, p, ds, Ot, ix, iy, 7, u);
         const int slot = (ix / C) * (C + 1) + (ix % C);
 #pragma unroll
         for (int j = 0; j < 3; j++) row[j * S + slot] = pack(u[j]);
     }
     __syncthreads();
-    const int warp = threadIdx.x >> 5;
     if (warp < 3) {
         const T* r = row + warp * S;
         const size_t base = ((size_t)warp * p.ny + iy) * nx;
-        cnx_solve_line<R, IMAG, C>(
-            [&](int i) {
-                return unpack(r[(i / C) * (C + 1) + (i % C)]);
-            },
-            B, base, nx, t, nullptr);
+        cnx_solve_line<R, IMAG, C>([&](int i) { return unpack(r[(i / C) * (C + 1) + (i % C)]); }, B, base, nx, t,
+                                   nullptr);
     }
 }
 
@@ -342,14 +363,21 @@ __device__ __forceinline__ void cny_cols(const typename V2<R>::T* in, typename V
     }
 }
 
+// sc (nullable): the fused 2D step, whose next head kernel derives the pending
+// scale from these partials: block 0 marks that (DevScalars::scale_src) and, if
+// advance, moves the step counter on (the head kernel of this step has finished).
 template <typename R, bool IMAG, int C>
 __global__ void __launch_bounds__(32) k_cny_reg(const typename V2<R>::T* in, typename V2<R>::T* out, KParams p,
-                                                Tabs<R> t, double* partials) {
+                                                Tabs<R> t, double* partials, DevScalars* sc, int advance) {
     constexpr int K = CnShape<R, C>::K;
     const int ncb = (p.nx + K - 1) / K;
     const int j = blockIdx.x / ncb;
     const int col = (blockIdx.x - j * ncb) * K;
     pdl_wait();
+    if (sc && blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->scale_src = 1;
+        if (advance) sc->step_idx += 1;
+    }
     cny_cols<R, IMAG, C>(in, out, p, t, j, col, partials ? partials + blockIdx.x : nullptr);
 }
 

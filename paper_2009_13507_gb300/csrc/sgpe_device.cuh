@@ -460,4 +460,53 @@ __device__ __forceinline__ void herm_point(cx<R> (&u)[3], R c2, R Ot, R dt, cons
     u[2] = axpy(k, Bm, axpy(-s, sAm, u[2]));
 }
 
+// HERM for the double-float state. The update psi - s_z A psi + k A^2 psi has
+// terms of sizes ~ dt C |psi| and ~ (dt C)^2 |psi| / 2. When w = (dt C)^2 <
+// 2^-25, the second term and the series corrections of s and k are formed in
+// FP32 from the leading parts (their FP32 rounding stays below 2^-50 |psi| and
+// the dropped series terms below 2^-57 |psi|); the A psi term and the updates
+// stay in double-float. Otherwise the general double-float evaluation.
+template <bool IMAG>
+__device__ __forceinline__ void herm_point_df(cx<df> (&u)[3], df c2, df Ot, const KParams& p) {
+    cx<df> a = cmul(u[2], u[1]);  // psi_-^* psi_0
+    a = {fma(c2, a.re, Ot), c2 * a.im};
+    cx<df> b = cmul(u[1], u[0]);  // psi_0^* psi_+
+    b = {fma(c2, b.re, Ot), c2 * b.im};
+    const float ar = a.re.hi, ai = a.im.hi, br = b.re.hi, bi = b.im.hi;
+    const float na = fmaf(ar, ar, ai * ai), nb = fmaf(br, br, bi * bi), C2 = na + nb;
+    const float w = p.kf[KC_DT2] * C2;
+    if (!(w < 2.98023223876953125e-08f)) {
+        // general case: every term in double-float
+        df na_d = nrm(a), nb_d = nrm(b), C2_d = na_d + nb_d, s, k;
+        herm_coeffs_dt<IMAG>(C2_d, p, &s, &k);
+        cx<df> ab = mul(a, b);
+        cx<df> Ap = mul(a, u[1]), A0 = add(cmul(a, u[0]), mul(b, u[2])), Am = cmul(b, u[1]);
+        cx<df> Bp = axpy(na_d, u[0], mul(ab, u[2])), B0 = scl(C2_d, u[1]), Bm = axpy(nb_d, u[2], cmul(ab, u[0]));
+        u[0] = axpy(k, Bp, axpy(-s, zunit<IMAG>(Ap), u[0]));
+        u[1] = axpy(k, B0, axpy(-s, zunit<IMAG>(A0), u[1]));
+        u[2] = axpy(k, Bm, axpy(-s, zunit<IMAG>(Am), u[2]));
+        return;
+    }
+    const float v = IMAG ? w : -w;
+    // s = dt (1 + v/6 + ...), k = +-dt^2 (1/2 + v/24 + ...)
+    const df s = add_f(kc<df>(p, KC_HS0), p.kf[KC_HS0 + 1] * v);
+    const float kk = fmaf(p.kf[KC_HK0 + 1], v, p.kf[KC_HK0]);
+    const float k = IMAG ? kk : -kk;
+    // A psi (double-float)
+    const cx<df> Ap = mul(a, u[1]);
+    const cx<df> A0 = add(cmul(a, u[0]), mul(b, u[2]));
+    const cx<df> Am = cmul(b, u[1]);
+    // k A^2 psi (FP32, leading parts)
+    const cx<float> a_f = {ar, ai}, b_f = {br, bi};
+    const cx<float> u0 = {u[0].re.hi, u[0].im.hi}, u1 = {u[1].re.hi, u[1].im.hi}, u2 = {u[2].re.hi, u[2].im.hi};
+    const cx<float> ab = mul(a_f, b_f);
+    const cx<float> Bp = scl(k, axpy(na, u0, mul(ab, u2)));
+    const cx<float> B0 = scl(k * C2, u1);
+    const cx<float> Bm = scl(k, axpy(nb, u2, cmul(ab, u0)));
+    const cx<df> sAp = zunit<IMAG>(Ap), sA0 = zunit<IMAG>(A0), sAm = zunit<IMAG>(Am);
+    u[0] = {add_f(u[0].re - s * sAp.re, Bp.re), add_f(u[0].im - s * sAp.im, Bp.im)};
+    u[1] = {add_f(u[1].re - s * sA0.re, B0.re), add_f(u[1].im - s * sA0.im, B0.im)};
+    u[2] = {add_f(u[2].re - s * sAm.re, Bm.re), add_f(u[2].im - s * sAm.im, Bm.im)};
+}
+
 }  // namespace sgpe

@@ -75,35 +75,46 @@ __device__ __forceinline__ df fma(df a, df b, df c) {
 
 __device__ __forceinline__ bool df_isfinite(df a) { return isfinite(a.hi); }
 
-// exp(x) for |x| < 2^-6 by its Taylor polynomial of degree 6 (first omitted
-// term x^7/7! < 2^-54, below the format's 2^-48), in double-float; other
+// a + b for an FP32 b (one error-free sum fewer than a full double-float add).
+__device__ __forceinline__ df add_f(df a, float b) {
+    df s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, s.lo + a.lo);
+}
+
+// exp(x) for |x| < 2^-6: 1 + x(1 + x(1/2 + x(1/6 + r))) with the tail
+// r = x/24 + x^2/120 + x^3/720 in FP32 (|r| < 2^-11; its FP32 rounding, scaled
+// by x^3 < 2^-18, stays below 2^-60) and the outer Horner steps in
+// double-float; truncation (x^7/7! < 2^-54) below the format's 2^-48. Other
 // arguments through FP64.
 __device__ __forceinline__ df exp_small(df x) {
     if (fabsf(x.hi) < 0.015625f) {
-        constexpr df c[7] = {df_from(1.0 / 720.0), df_from(1.0 / 120.0), df_from(1.0 / 24.0), df_from(1.0 / 6.0),
-                             df(0.5f, 0.0f),       df(1.0f, 0.0f),       df(1.0f, 0.0f)};
-        df p = c[0];
-#pragma unroll
-        for (int n = 1; n < 7; n++) p = fma(p, x, c[n]);
-        return p;
+        const float xf = x.hi;
+        const float r = xf * fmaf(xf, fmaf(xf, 1.0f / 720.0f, 1.0f / 120.0f), 1.0f / 24.0f);
+        constexpr df c6 = df_from(1.0 / 6.0);
+        df p = add_f(c6, r);
+        p = fma(p, x, df(0.5f, 0.0f));
+        p = fma(p, x, df(1.0f, 0.0f));
+        return fma(p, x, df(1.0f, 0.0f));
     }
     return df_from(exp(df_to(x)));
 }
 
-// (sin x, cos x) for |x| < 2^-6 by Taylor polynomials in t = x^2 (sin to x^7,
-// cos to x^6: omitted terms below 2^-62 relative); other arguments through FP64.
+// (sin x, cos x) for |x| < 2^-6, t = x^2 < 2^-12: sin(x)/x = 1 - t(1/6 - rs),
+// cos(x) = 1 - t(1/2 - t(1/24 - rc)), with the tails rs = t/120 - t^2/5040 and
+// rc = t/720 in FP32 (their rounding, scaled by t or t^2, below 2^-60); the
+// outer steps in double-float. Other arguments through FP64.
 __device__ __forceinline__ void sincos_small(df x, df* s, df* c) {
     if (fabsf(x.hi) < 0.015625f) {
         const df mt = -(x * x);
-        // sin(x)/x = sum (-t)^n/(2n+1)!, cos(x) = sum (-t)^n/(2n)!, n = 3..0
-        constexpr df sc[4] = {df_from(1.0 / 5040.0), df_from(1.0 / 120.0), df_from(1.0 / 6.0), df(1.0f, 0.0f)};
-        constexpr df cc[4] = {df_from(1.0 / 720.0), df_from(1.0 / 24.0), df(0.5f, 0.0f), df(1.0f, 0.0f)};
-        df ps = sc[0], pc = cc[0];
-#pragma unroll
-        for (int n = 1; n < 4; n++) {
-            ps = fma(ps, mt, sc[n]);
-            pc = fma(pc, mt, cc[n]);
-        }
+        const float tf = x.hi * x.hi;
+        const float rs = tf * fmaf(-tf, 1.0f / 5040.0f, 1.0f / 120.0f);
+        const float rc = tf * (1.0f / 720.0f);
+        constexpr df c6 = df_from(1.0 / 6.0), c24 = df_from(1.0 / 24.0);
+        df ps = add_f(c6, -rs);                  // 1/6 - t/120 + t^2/5040
+        ps = fma(ps, mt, df(1.0f, 0.0f));        // sin(x)/x
+        df pc = add_f(c24, -rc);                 // 1/24 - t/720
+        pc = fma(pc, mt, df(0.5f, 0.0f));        // 1/2 - t/24 + t^2/720
+        pc = fma(pc, mt, df(1.0f, 0.0f));        // cos(x)
         *s = ps * x;
         *c = pc;
         return;

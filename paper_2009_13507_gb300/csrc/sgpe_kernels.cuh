@@ -14,6 +14,8 @@
 // k_finalize.
 // Reductions are FP64 in both precisions and deterministic (fixed order).
 #pragma once
+#include <type_traits>
+
 #include "sgpe_device.cuh"
 
 namespace sgpe {
@@ -25,6 +27,8 @@ struct DevScalars {
     double scale[4];     // pending renormalisation scale per component (DJ2: all equal)
     float scale_f[4];    // the same rounded to FP32 (read by the complex64 form)
     float scale_l[4];    // and the rest scale - scale_f (double-float low part)
+    int scale_src;       // 1: the pending scale is still to be derived from the last y sweep's
+                         // norm partials (the fused 2D step); 0: scale[] holds it
     double norms[4];     // N_j of the state written by the last completed step
     double obs[16];      // observables of the last sgpe_energy
     int step_idx;        // index into a per-step Omega table (real time)
@@ -228,6 +232,7 @@ __device__ __forceinline__ void finalize_norms(const double* partials, int nblk,
             }
             if (!finite) sc->err |= 1;
             if (advance_step) sc->step_idx += 1;
+            sc->scale_src = 0;
             *ticket = 0u;
         }
     }
@@ -249,16 +254,16 @@ template <> __device__ __forceinline__ df scale_of<df>(const DevScalars* sc, int
     return df(sc->scale_f[j], sc->scale_l[j]);
 }
 
-// pointwise_point returns the three updated values in u; pointwise_at stores them.
+// pointwise_point returns the three updated values in u; pointwise_at stores
+// them. ds: the pending scale per component (3 values).
 template <typename R, bool IMAG>
 __device__ __forceinline__ void pointwise_point(const typename V2<R>::T* __restrict__ A, const KParams& p,
-                                                const DevScalars* sc, R Ot, int ix, int iy, int mask,
-                                                cx<R> (&u)[3]) {
+                                                const R* ds, R Ot, int ix, int iy, int mask, cx<R> (&u)[3]) {
     const size_t plane = (size_t)p.nx * p.ny;
     const size_t c = (size_t)iy * p.nx + ix;
     R d[3];
 #pragma unroll
-    for (int j = 0; j < 3; j++) d[j] = scale_of<R>(sc, j);
+    for (int j = 0; j < 3; j++) d[j] = ds[j];
 #pragma unroll
     for (int j = 0; j < 3; j++) u[j] = scl(d[j], ld<R>(A, j * plane + c));
     const R dt = kc<R>(p, KC_DT);
@@ -308,7 +313,12 @@ __device__ __forceinline__ void pointwise_point(const typename V2<R>::T* __restr
             calcnu_point<IMAG>(u, V, kc<R>(p, KC_C0), kc<R>(p, KC_C2), dt);
         }
     }
-    if (mask & 4) herm_point<IMAG>(u, kc<R>(p, KC_C2), Ot, dt, &p);
+    if (mask & 4) {
+        if constexpr (std::is_same<R, df>::value)
+            herm_point_df<IMAG>(u, kc<R>(p, KC_C2), Ot, p);
+        else
+            herm_point<IMAG>(u, kc<R>(p, KC_C2), Ot, dt, &p);
+    }
 }
 
 template <typename R, bool IMAG>
@@ -317,8 +327,9 @@ __device__ __forceinline__ void pointwise_at(const typename V2<R>::T* __restrict
                                              const DevScalars* sc, R Ot, int ix, int iy, int mask) {
     const size_t plane = (size_t)p.nx * p.ny;
     const size_t c = (size_t)iy * p.nx + ix;
+    const R ds[3] = {scale_of<R>(sc, 0), scale_of<R>(sc, 1), scale_of<R>(sc, 2)};
     cx<R> u[3];
-    pointwise_point<R, IMAG>(A, p, sc, Ot, ix, iy, mask, u);
+    pointwise_point<R, IMAG>(A, p, ds, Ot, ix, iy, mask, u);
 #pragma unroll
     for (int j = 0; j < 3; j++) st<R>(B, j * plane + c, u[j]);
 }
@@ -433,13 +444,11 @@ __global__ void __launch_bounds__(256) k_cn_y(const typename V2<R>::T* in, typen
 // advances the step counter. Few threads on purpose: the FP64 adds run on one
 // SM's FP64 pipe.
 // ---------------------------------------------------------------------------
-static __global__ void __launch_bounds__(96) k_finalize(const double* partials, int m, double cell, int renorm,
-                                                 double mag, int advance_step, DevScalars* sc) {
-    __shared__ double red[3];
-    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const double* q = partials + (size_t)j * m;
-    pdl_trigger();  // one small block: the next step's first kernel may launch now
-    pdl_wait();
+// Sum of the m partials q[0..m) by the calling warp in a fixed order (lane-
+// strided into four accumulators, then a shuffle tree): the same value in every
+// lane and in every block that calls it.
+__device__ __forceinline__ double sum_partials_warp(const double* q, int m) {
+    const int lane = threadIdx.x & 31;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     int b = lane;
     for (; b + 96 < m; b += 128) {
@@ -452,6 +461,17 @@ static __global__ void __launch_bounds__(96) k_finalize(const double* partials, 
     double s = (a0 + a1) + (a2 + a3);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    return s;
+}
+
+static __global__ void __launch_bounds__(96) k_finalize(const double* partials, int m, double cell, int renorm,
+                                                 double mag, int advance_step, DevScalars* sc) {
+    __shared__ double red[3];
+    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double* q = partials + (size_t)j * m;
+    pdl_trigger();  // one small block: the next step's first kernel may launch now
+    pdl_wait();
+    const double s = sum_partials_warp(q, m);
     if (lane == 0) red[j] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -467,6 +487,7 @@ static __global__ void __launch_bounds__(96) k_finalize(const double* partials, 
         }
         if (!finite) sc->err |= 1;
         if (advance_step) sc->step_idx += 1;
+        sc->scale_src = 0;
     }
 }
 
@@ -563,6 +584,7 @@ static __global__ void k_reset_scale(DevScalars* sc) {
         sc->scale_f[threadIdx.x] = 1.0f;
         sc->scale_l[threadIdx.x] = 0.0f;
     }
+    if (threadIdx.x == 0) sc->scale_src = 0;
 }
 
 // ---------------------------------------------------------------------------

@@ -71,16 +71,22 @@ template <typename R> struct Launcher {
     static cudaError_t pointwise(cudaStream_t s, bool imag, const void* A, void* B, const KParams& p,
                                  const DevScalars* sc, const double* omega_tab, int mask);
     // Fused pointwise substeps + CN along x of a 2D grid (Geometry::fused): A -> B.
+    // partials / m / renorm: the previous y sweep's norm partials (m per component)
+    // and the renormalisation mode, for the pending scale (DevScalars::scale_src).
     static cudaError_t pwx(cudaStream_t s, bool imag, const void* A, void* B, const KParams& p, const DevScalars* sc,
-                           const double* omega_tab, const void* const* tabs_x);
+                           const double* omega_tab, const void* const* tabs_x, const double* partials, int m,
+                           int renorm);
     // cn_x / cn_y write per-block FP64 norm partials when last / finalize is set
     // (the step's final sweep); finalize_step then reduces them.
     static cudaError_t cn_x(cudaStream_t s, bool imag, bool last, const void* in, void* out, const KParams& p,
                             const void* const* tabs, const Geometry& g, double* partials, DevScalars* sc, int renorm,
                             int advance);
+    // head_scale (register y sweep of the fused 2D step): the next step's head
+    // kernel derives the pending scale from this sweep's partials; the sweep
+    // marks that and advances the step counter by advance (no finalize_step).
     static cudaError_t cn_y(cudaStream_t s, bool imag, const void* in, void* out, const KParams& p,
                             const void* const* tabs, const Geometry& g, double* partials, DevScalars* sc, int renorm,
-                            int advance, int finalize);
+                            int advance, int finalize, bool head_scale = false);
     static cudaError_t coef(cudaStream_t s, void* fa, void* fg, void* fp, void* fq, int n, double bre, double bim);
     static cudaError_t flush(cudaStream_t s, void* A, size_t plane, const DevScalars* sc);
     static cudaError_t norms(cudaStream_t s, const void* A, size_t plane, double cell, int renorm, double mag,

@@ -36,23 +36,24 @@ static void launch_cnx_reg(int C, bool imag, dim3 grid, cudaStream_t s, const ty
 
 template <typename R, int C>
 static void cny_reg_c(bool imag, dim3 grid, cudaStream_t s, const typename V2<R>::T* in, typename V2<R>::T* out,
-                      const KParams& p, const Tabs<R>& t, double* partials) {
+                      const KParams& p, const Tabs<R>& t, double* partials, DevScalars* sc, int advance) {
     if (imag)
-        launch_pdl(k_cny_reg<R, true, C>, grid, dim3(32), 0, s, in, out, p, t, partials);
+        launch_pdl(k_cny_reg<R, true, C>, grid, dim3(32), 0, s, in, out, p, t, partials, sc, advance);
     else
-        launch_pdl(k_cny_reg<R, false, C>, grid, dim3(32), 0, s, in, out, p, t, partials);
+        launch_pdl(k_cny_reg<R, false, C>, grid, dim3(32), 0, s, in, out, p, t, partials, sc, advance);
 }
 
 template <typename R>
 static void launch_cny_reg(int C, bool imag, dim3 grid, cudaStream_t s, const typename V2<R>::T* in,
-                           typename V2<R>::T* out, const KParams& p, const Tabs<R>& t, double* partials) {
+                           typename V2<R>::T* out, const KParams& p, const Tabs<R>& t, double* partials,
+                           DevScalars* sc, int advance) {
     switch (C) {
-        case 1: cny_reg_c<R, 1>(imag, grid, s, in, out, p, t, partials); break;
-        case 2: cny_reg_c<R, 2>(imag, grid, s, in, out, p, t, partials); break;
-        case 4: cny_reg_c<R, 4>(imag, grid, s, in, out, p, t, partials); break;
-        case 8: cny_reg_c<R, 8>(imag, grid, s, in, out, p, t, partials); break;
-        case 16: cny_reg_c<R, 16>(imag, grid, s, in, out, p, t, partials); break;
-        default: cny_reg_c<R, 32>(imag, grid, s, in, out, p, t, partials); break;
+        case 1: cny_reg_c<R, 1>(imag, grid, s, in, out, p, t, partials, sc, advance); break;
+        case 2: cny_reg_c<R, 2>(imag, grid, s, in, out, p, t, partials, sc, advance); break;
+        case 4: cny_reg_c<R, 4>(imag, grid, s, in, out, p, t, partials, sc, advance); break;
+        case 8: cny_reg_c<R, 8>(imag, grid, s, in, out, p, t, partials, sc, advance); break;
+        case 16: cny_reg_c<R, 16>(imag, grid, s, in, out, p, t, partials, sc, advance); break;
+        default: cny_reg_c<R, 32>(imag, grid, s, in, out, p, t, partials, sc, advance); break;
     }
 }
 
@@ -84,12 +85,15 @@ template <typename R, bool IMAG> static cudaError_t pwx_allow_all() {
 
 template <typename R, int C>
 static void pwx_c(bool imag, int rows, cudaStream_t s, const typename V2<R>::T* A, typename V2<R>::T* B,
-                  const KParams& p, const DevScalars* sc, const double* omega_tab, const Tabs<R>& t) {
+                  const KParams& p, const DevScalars* sc, const double* omega_tab, const Tabs<R>& t,
+                  const double* partials, int m, int renorm) {
     const size_t smem = pwx_smem_bytes<R, C>();
     if (imag)
-        launch_pdl(k_pwx<R, true, C>, dim3(rows), dim3(kPwxThreads), smem, s, A, B, p, sc, omega_tab, t);
+        launch_pdl(k_pwx<R, true, C>, dim3(rows), dim3(kPwxThreads), smem, s, A, B, p, sc, omega_tab, t, partials, m,
+                   renorm);
     else
-        launch_pdl(k_pwx<R, false, C>, dim3(rows), dim3(kPwxThreads), smem, s, A, B, p, sc, omega_tab, t);
+        launch_pdl(k_pwx<R, false, C>, dim3(rows), dim3(kPwxThreads), smem, s, A, B, p, sc, omega_tab, t, partials,
+                   m, renorm);
 }
 
 template <typename R> cudaError_t Launcher<R>::setup() {
@@ -124,7 +128,8 @@ cudaError_t Launcher<R>::pointwise(cudaStream_t s, bool imag, const void* A, voi
 
 template <typename R>
 cudaError_t Launcher<R>::pwx(cudaStream_t s, bool imag, const void* A, void* B, const KParams& p,
-                             const DevScalars* sc, const double* omega_tab, const void* const* tabs_x) {
+                             const DevScalars* sc, const double* omega_tab, const void* const* tabs_x,
+                             const double* partials, int m, int renorm) {
     using T = typename V2<R>::T;
     if (p.dim != 2 || p.nx > kRegMaxN) return cudaErrorInvalidValue;
     Tabs<R> t = make_tabs<R>(tabs_x);
@@ -133,12 +138,12 @@ cudaError_t Launcher<R>::pwx(cudaStream_t s, bool imag, const void* A, void* B, 
     KParams q = p;
     fill_derived(q);
     switch (chunk_len(p.nx)) {
-        case 1: pwx_c<R, 1>(imag, p.ny, s, a, b, q, sc, omega_tab, t); break;
-        case 2: pwx_c<R, 2>(imag, p.ny, s, a, b, q, sc, omega_tab, t); break;
-        case 4: pwx_c<R, 4>(imag, p.ny, s, a, b, q, sc, omega_tab, t); break;
-        case 8: pwx_c<R, 8>(imag, p.ny, s, a, b, q, sc, omega_tab, t); break;
-        case 16: pwx_c<R, 16>(imag, p.ny, s, a, b, q, sc, omega_tab, t); break;
-        default: pwx_c<R, 32>(imag, p.ny, s, a, b, q, sc, omega_tab, t); break;
+        case 1: pwx_c<R, 1>(imag, p.ny, s, a, b, q, sc, omega_tab, t, partials, m, renorm); break;
+        case 2: pwx_c<R, 2>(imag, p.ny, s, a, b, q, sc, omega_tab, t, partials, m, renorm); break;
+        case 4: pwx_c<R, 4>(imag, p.ny, s, a, b, q, sc, omega_tab, t, partials, m, renorm); break;
+        case 8: pwx_c<R, 8>(imag, p.ny, s, a, b, q, sc, omega_tab, t, partials, m, renorm); break;
+        case 16: pwx_c<R, 16>(imag, p.ny, s, a, b, q, sc, omega_tab, t, partials, m, renorm); break;
+        default: pwx_c<R, 32>(imag, p.ny, s, a, b, q, sc, omega_tab, t, partials, m, renorm); break;
     }
     return cudaGetLastError();
 }
@@ -176,12 +181,13 @@ cudaError_t Launcher<R>::cn_x(cudaStream_t s, bool imag, bool last, const void* 
 template <typename R>
 cudaError_t Launcher<R>::cn_y(cudaStream_t s, bool imag, const void* in, void* out, const KParams& p,
                               const void* const* tabs, const Geometry& g, double* partials, DevScalars* sc,
-                              int renorm, int advance, int finalize) {
+                              int renorm, int advance, int finalize, bool head_scale) {
     using T = typename V2<R>::T;
     Tabs<R> t = make_tabs<R>(tabs);
     const int C = chunk_len(p.ny), S = chunk_stride(p.ny);
     if (g.reg_y) {
-        launch_cny_reg<R>(C, imag, dim3(g.blocks_y), s, (const T*)in, (T*)out, p, t, finalize ? partials : nullptr);
+        launch_cny_reg<R>(C, imag, dim3(g.blocks_y), s, (const T*)in, (T*)out, p, t, finalize ? partials : nullptr,
+                          head_scale ? sc : nullptr, advance);
         return cudaGetLastError();
     }
     dim3 block(32 * g.wy), grid(g.blocks_y);
