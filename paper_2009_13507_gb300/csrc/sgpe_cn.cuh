@@ -363,20 +363,29 @@ __device__ __forceinline__ void cny_cols(const typename V2<R>::T* in, typename V
     }
 }
 
-// sc (nullable): the fused 2D step, whose next head kernel derives the pending
-// scale from these partials: block 0 marks that (DevScalars::scale_src) and, if
-// advance, moves the step counter on (the head kernel of this step has finished).
+// sc (nullable): the fused 2D step. With renorm != 0 its next head kernel
+// derives the pending scale from these partials: block 0 marks that
+// (DevScalars::scale_src); with renorm == 0 the pending scale is 1 from here on
+// and block 0 stores it. If advance, block 0 also moves the step counter on (the
+// head kernel of this step has finished).
 template <typename R, bool IMAG, int C>
 __global__ void __launch_bounds__(32) k_cny_reg(const typename V2<R>::T* in, typename V2<R>::T* out, KParams p,
-                                                Tabs<R> t, double* partials, DevScalars* sc, int advance) {
+                                                Tabs<R> t, double* partials, DevScalars* sc, int renorm,
+                                                int advance) {
     constexpr int K = CnShape<R, C>::K;
     const int ncb = (p.nx + K - 1) / K;
     const int j = blockIdx.x / ncb;
     const int col = (blockIdx.x - j * ncb) * K;
     pdl_wait();
-    if (sc && blockIdx.x == 0 && threadIdx.x == 0) {
-        sc->scale_src = 1;
-        if (advance) sc->step_idx += 1;
+    if (sc && blockIdx.x == 0 && threadIdx.x < 3) {
+        if (renorm) {
+            if (threadIdx.x == 0) sc->scale_src = 1;
+        } else {
+            sc->scale[threadIdx.x] = 1.0;
+            sc->scale_f[threadIdx.x] = 1.0f;
+            sc->scale_l[threadIdx.x] = 0.0f;
+        }
+        if (advance && threadIdx.x == 0) sc->step_idx += 1;
     }
     cny_cols<R, IMAG, C>(in, out, p, t, j, col, partials ? partials + blockIdx.x : nullptr);
 }

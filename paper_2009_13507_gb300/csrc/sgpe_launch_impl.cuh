@@ -36,24 +36,25 @@ static void launch_cnx_reg(int C, bool imag, dim3 grid, cudaStream_t s, const ty
 
 template <typename R, int C>
 static void cny_reg_c(bool imag, dim3 grid, cudaStream_t s, const typename V2<R>::T* in, typename V2<R>::T* out,
-                      const KParams& p, const Tabs<R>& t, double* partials, DevScalars* sc, int advance) {
+                      const KParams& p, const Tabs<R>& t, double* partials, DevScalars* sc, int renorm,
+                      int advance) {
     if (imag)
-        launch_pdl(k_cny_reg<R, true, C>, grid, dim3(32), 0, s, in, out, p, t, partials, sc, advance);
+        launch_pdl(k_cny_reg<R, true, C>, grid, dim3(32), 0, s, in, out, p, t, partials, sc, renorm, advance);
     else
-        launch_pdl(k_cny_reg<R, false, C>, grid, dim3(32), 0, s, in, out, p, t, partials, sc, advance);
+        launch_pdl(k_cny_reg<R, false, C>, grid, dim3(32), 0, s, in, out, p, t, partials, sc, renorm, advance);
 }
 
 template <typename R>
 static void launch_cny_reg(int C, bool imag, dim3 grid, cudaStream_t s, const typename V2<R>::T* in,
                            typename V2<R>::T* out, const KParams& p, const Tabs<R>& t, double* partials,
-                           DevScalars* sc, int advance) {
+                           DevScalars* sc, int renorm, int advance) {
     switch (C) {
-        case 1: cny_reg_c<R, 1>(imag, grid, s, in, out, p, t, partials, sc, advance); break;
-        case 2: cny_reg_c<R, 2>(imag, grid, s, in, out, p, t, partials, sc, advance); break;
-        case 4: cny_reg_c<R, 4>(imag, grid, s, in, out, p, t, partials, sc, advance); break;
-        case 8: cny_reg_c<R, 8>(imag, grid, s, in, out, p, t, partials, sc, advance); break;
-        case 16: cny_reg_c<R, 16>(imag, grid, s, in, out, p, t, partials, sc, advance); break;
-        default: cny_reg_c<R, 32>(imag, grid, s, in, out, p, t, partials, sc, advance); break;
+        case 1: cny_reg_c<R, 1>(imag, grid, s, in, out, p, t, partials, sc, renorm, advance); break;
+        case 2: cny_reg_c<R, 2>(imag, grid, s, in, out, p, t, partials, sc, renorm, advance); break;
+        case 4: cny_reg_c<R, 4>(imag, grid, s, in, out, p, t, partials, sc, renorm, advance); break;
+        case 8: cny_reg_c<R, 8>(imag, grid, s, in, out, p, t, partials, sc, renorm, advance); break;
+        case 16: cny_reg_c<R, 16>(imag, grid, s, in, out, p, t, partials, sc, renorm, advance); break;
+        default: cny_reg_c<R, 32>(imag, grid, s, in, out, p, t, partials, sc, renorm, advance); break;
     }
 }
 
@@ -187,7 +188,7 @@ cudaError_t Launcher<R>::cn_y(cudaStream_t s, bool imag, const void* in, void* o
     const int C = chunk_len(p.ny), S = chunk_stride(p.ny);
     if (g.reg_y) {
         launch_cny_reg<R>(C, imag, dim3(g.blocks_y), s, (const T*)in, (T*)out, p, t, finalize ? partials : nullptr,
-                          head_scale ? sc : nullptr, advance);
+                          head_scale ? sc : nullptr, renorm, advance);
         return cudaGetLastError();
     }
     dim3 block(32 * g.wy), grid(g.blocks_y);
