@@ -116,6 +116,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(t: float, device=None) -> float:
+    """Max of t over the ranks of the default process group (t itself when
+    there is no group or a single rank): the replicas' benchmark time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_value(points_per_rank: int, world_size: int, t_ms: float) -> float:
+    """Whole-job point-steps/s of world_size independent replicas that each
+    advance points_per_rank point-steps, timed by the slowest rank (t_ms)."""
+    return world_size * points_per_rank / (t_ms * 1e-3)
+
+
 def cpu_oracle_rate(steps: int = CPU_SAMPLE_STEPS):
     """FP64 CPU oracle (single thread, as it stands) on the same workload: steps time steps of 256x256."""
     from oracle import oracle as O
@@ -350,14 +368,9 @@ def main():
     clocks.start()
     ms64, en64, _ = timed_run(solver, psi0_dev, args.steps, args.warmup)
     clk = clocks.stop()
-    t_step = statistics.mean(ms64)  # ms per benchmark step on this rank
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(statistics.mean(ms64), dev)  # ms per benchmark step, slowest rank
     point_steps = NX * NY * NSTEPS
-    value = ws * point_steps / (t_step * 1e-3)
+    value = replica_value(point_steps, ws, t_step)
 
     # per-kernel device times (CUDA events on the solver's stream, eager launches, same workload)
     reset(solver, psi0_dev)
@@ -379,7 +392,7 @@ def main():
     s32.set_params(sgpe.Physics(**PHYS))
     psi0_dev32 = psi0_dev.to(torch.complex64)
     ms32, en32, _ = timed_run(s32, psi0_dev32, args.steps, args.warmup)
-    t32 = statistics.mean(ms32)
+    t32 = max_over_ranks(statistics.mean(ms32), dev)
     e64, e32 = en64[-1][5], en32[-1][5]
     reset(s32, psi0_dev32)
     kms32, kcnt32 = s32.profile_steps(NSTEPS, True)
@@ -390,7 +403,7 @@ def main():
     sdf = sgpe.Solver(2, NX, NY, dx=DX, precision="cdf", device=dev)
     sdf.set_params(sgpe.Physics(**PHYS))
     msdf, endf, _ = timed_run(sdf, psi0_dev, args.steps, args.warmup)
-    tdf = statistics.mean(msdf)
+    tdf = max_over_ranks(statistics.mean(msdf), dev)
     edf = endf[-1][5]
     for s_ in (solver, sdf):
         reset(s_, psi0_dev)
@@ -416,7 +429,7 @@ def main():
         t1 = time.perf_counter()
         if k >= args.warmup:
             e2e_ms.append((t1 - t0) * 1e3)
-    e2e_t = statistics.mean(e2e_ms)
+    e2e_t = max_over_ranks(statistics.mean(e2e_ms), dev)
     nbytes_state = 3 * NX * NY * 16
 
     forms = extra_workloads(dev) if (rank == 0 and not args.no_extra) else None
@@ -446,17 +459,17 @@ def main():
         "kernels": {"avg_ms": kavg, "share": share, "dominant": dom},
         "hbm_view": {"algorithmic_bytes_per_point_step": 192,
                      "effective_GBps": value / ws * 192 / 1e9},
-        "chosen": {"form": "complex64 state, FP64 reductions", "value": ws * point_steps / (t32 * 1e-3),
+        "chosen": {"form": "complex64 state, FP64 reductions", "value": replica_value(point_steps, ws, t32),
                    "ms_per_step": t32, "energy_rel_err_vs_fp64": abs(e32 - e64) / abs(e64),
                    "speedup_vs_fp64": t_step / t32, "kernels_avg_ms": kavg32},
-        "fp64_accurate": {"form": "double-float (FP32 pairs), FP64 reductions", "value": ws * point_steps / (tdf * 1e-3),
+        "fp64_accurate": {"form": "double-float (FP32 pairs), FP64 reductions", "value": replica_value(point_steps, ws, tdf),
                           "ms_per_step": tdf, "energy_rel_err_vs_fp64": abs(edf - e64) / abs(e64),
                           "state_rel_err_vs_fp64": state_err_df, "speedup_vs_fp64": t_step / tdf,
                           "kernels_avg_ms": kavgdf},
         "energy": {"E_fp64": e64, "E_c64": e32, "E_cdf": edf, "E_profile_pass": e_prof[5]},
         "forms": forms,
         "cpu_baseline": cpu,
-        "e2e": {"value": ws * point_steps / (e2e_t * 1e-3), "unit": METRIC, "h2d_bytes_per_step": nbytes_state,
+        "e2e": {"value": replica_value(point_steps, ws, e2e_t), "unit": METRIC, "h2d_bytes_per_step": nbytes_state,
                 "d2h_bytes_per_step": nbytes_state + 16 * 8, "ms_per_step": e2e_t},
         "gpu_launches": args.steps * launches,
         "clocks": clk,
