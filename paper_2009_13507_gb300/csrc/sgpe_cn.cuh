@@ -265,6 +265,14 @@ __global__ void __launch_bounds__(kPwxThreads, C <= 8 ? 2 : 1)
     const int nx = p.nx;
     const int warp = threadIdx.x >> 5;
     pdl_wait();
+    // the row's loads first (they need no scale), then the scale, then the substeps
+    constexpr int PPT = (32 * C + kPwxThreads - 1) / kPwxThreads;  // points per thread
+    PointIn<R> in[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        const int ix = threadIdx.x + k * kPwxThreads;
+        if (ix < nx) pointwise_load<R>(A, p, ix, iy, p.so_case != 0, in[k]);
+    }
     if (*(volatile const int*)&sc->scale_src) {
         if (warp < 3) {
             const double s = sum_partials_warp(partials + (size_t)warp * m, m);
@@ -285,12 +293,16 @@ __global__ void __launch_bounds__(kPwxThreads, C <= 8 ? 2 : 1)
     __syncthreads();
     const R Ot = omega_tab ? to_r<R>(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440)
                            : kc<R>(p, KC_OMEGA);
-    for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
-        cx<R> u[3];
-        pointwise_point<R, IMAG>(A, p, ds, Ot, ix, iy, 7, u);
-        const int slot = (ix / C) * (C + 1) + (ix % C);
 #pragma unroll
-        for (int j = 0; j < 3; j++) row[j * S + slot] = pack(u[j]);
+    for (int k = 0; k < PPT; k++) {
+        const int ix = threadIdx.x + k * kPwxThreads;
+        if (ix < nx) {
+            cx<R> u[3];
+            pointwise_apply<R, IMAG>(in[k], p, ds, Ot, ix, iy, 7, u);
+            const int slot = (ix / C) * (C + 1) + (ix % C);
+#pragma unroll
+            for (int j = 0; j < 3; j++) row[j * S + slot] = pack(u[j]);
+        }
     }
     __syncthreads();
     if (warp < 3) {

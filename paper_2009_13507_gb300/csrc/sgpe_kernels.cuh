@@ -254,35 +254,53 @@ template <> __device__ __forceinline__ df scale_of<df>(const DevScalars* sc, int
     return df(sc->scale_f[j], sc->scale_l[j]);
 }
 
-// pointwise_point returns the three updated values in u; pointwise_at stores
-// them. ds: the pending scale per component (3 values).
-template <typename R, bool IMAG>
-__device__ __forceinline__ void pointwise_point(const typename V2<R>::T* __restrict__ A, const KParams& p,
-                                                const R* ds, R Ot, int ix, int iy, int mask, cx<R> (&u)[3]) {
+// The state at one grid point as loaded: the three values and their raw
+// differences psi(x+1) - psi(x-1), psi(y+1) - psi(y-1) (zero ghosts), before
+// the pending scale is applied. Loading needs no scale, so a kernel can issue
+// these loads while it still works out the scale.
+template <typename R> struct PointIn {
+    cx<R> u[3], X[3], Y[3];
+};
+
+template <typename R>
+__device__ __forceinline__ void pointwise_load(const typename V2<R>::T* __restrict__ A, const KParams& p, int ix,
+                                               int iy, bool so, PointIn<R>& in) {
     const size_t plane = (size_t)p.nx * p.ny;
     const size_t c = (size_t)iy * p.nx + ix;
-    R d[3];
+    const cx<R> zero = {R(0), R(0)};
 #pragma unroll
-    for (int j = 0; j < 3; j++) d[j] = ds[j];
-#pragma unroll
-    for (int j = 0; j < 3; j++) u[j] = scl(d[j], ld<R>(A, j * plane + c));
-    const R dt = kc<R>(p, KC_DT);
-    if ((mask & 1) && p.so_case) {
-        cx<R> X[3], Y[3];
-        const cx<R> zero = {R(0), R(0)};
+    for (int j = 0; j < 3; j++) {
+        in.u[j] = ld<R>(A, j * plane + c);
+        in.X[j] = zero;
+        in.Y[j] = zero;
+    }
+    if (so) {
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             cx<R> xp = (ix + 1 < p.nx) ? ld<R>(A, j * plane + c + 1) : zero;
             cx<R> xm = (ix > 0) ? ld<R>(A, j * plane + c - 1) : zero;
-            X[j] = sub(xp, xm);
+            in.X[j] = sub(xp, xm);
             if (p.dim == 2) {
                 cx<R> yp = (iy + 1 < p.ny) ? ld<R>(A, j * plane + c + p.nx) : zero;
                 cx<R> ym = (iy > 0) ? ld<R>(A, j * plane + c - p.nx) : zero;
-                Y[j] = sub(yp, ym);
-            } else {
-                Y[j] = zero;
+                in.Y[j] = sub(yp, ym);
             }
         }
+    }
+}
+
+// The pointwise substeps at one loaded grid point; u: the three updated values.
+// ds: the pending scale per component (3 values); mask as for pointwise_point.
+template <typename R, bool IMAG>
+__device__ __forceinline__ void pointwise_apply(const PointIn<R>& in, const KParams& p, const R* ds, R Ot, int ix,
+                                                int iy, int mask, cx<R> (&u)[3]) {
+    R d[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) d[j] = ds[j];
+#pragma unroll
+    for (int j = 0; j < 3; j++) u[j] = scl(d[j], in.u[j]);
+    const R dt = kc<R>(p, KC_DT);
+    if ((mask & 1) && p.so_case) {
         R gx[3], gy[3];
         if (p.renorm != 2) {
             // one scale for all components (DJ2, or none): the same products, formed once
@@ -299,7 +317,7 @@ __device__ __forceinline__ void pointwise_point(const typename V2<R>::T* __restr
                 gy[j] = kc<R>(p, KC_HY) * d[j];
             }
         }
-        so_point<IMAG>(u, X, Y, gx, gy, p.so_case);
+        so_point<IMAG>(u, in.X, in.Y, gx, gy, p.so_case);
     }
     if (mask & 2) {
         // V = wx^2 x^2/2 + wy^2 y^2/2 with x = kx dx: kx^2 is an exact integer
@@ -319,6 +337,16 @@ __device__ __forceinline__ void pointwise_point(const typename V2<R>::T* __restr
         else
             herm_point<IMAG>(u, kc<R>(p, KC_C2), Ot, dt, &p);
     }
+}
+
+// pointwise_point: load and apply at one grid point; pointwise_at stores the
+// result. ds: the pending scale per component (3 values).
+template <typename R, bool IMAG>
+__device__ __forceinline__ void pointwise_point(const typename V2<R>::T* __restrict__ A, const KParams& p,
+                                                const R* ds, R Ot, int ix, int iy, int mask, cx<R> (&u)[3]) {
+    PointIn<R> in;
+    pointwise_load<R>(A, p, ix, iy, (mask & 1) && p.so_case, in);
+    pointwise_apply<R, IMAG>(in, p, ds, Ot, ix, iy, mask, u);
 }
 
 template <typename R, bool IMAG>
