@@ -282,10 +282,20 @@ __global__ void __launch_bounds__(kPwxThreads, C <= 8 ? 2 : 1)
         if (threadIdx.x == 0) {
             double N[3] = {red[0] * p.cell, red[1] * p.cell, red[2] * p.cell};
             const bool finite = isfinite(N[0]) && isfinite(N[1]) && isfinite(N[2]);
-            double d[3];
-            renorm_factors(N, finite ? renorm : 0, p.mag, d);
+            if (std::is_same<R, df>::value && renorm == 1) {
+                // double-float: Eq. (DJ2) directly in pairs (no FP64 square root
+                // and no FP64 -> pair split of the factor on this path)
+                const double Nt = N[0] + N[1] + N[2];
+                df f = df(1.0f, 0.0f);
+                if (finite && Nt > 0.0) f = df_rsqrt(df_from(Nt));
 #pragma unroll
-            for (int j = 0; j < 3; j++) ds[j] = to_r<R>(d[j]);
+                for (int j = 0; j < 3; j++) ds[j] = to_r_df<R>(f);
+            } else {
+                double d[3];
+                renorm_factors(N, finite ? renorm : 0, p.mag, d);
+#pragma unroll
+                for (int j = 0; j < 3; j++) ds[j] = to_r<R>(d[j]);
+            }
         }
     } else if (threadIdx.x < 3) {
         ds[threadIdx.x] = scale_of<R>(sc, threadIdx.x);

@@ -37,6 +37,9 @@ __device__ __forceinline__ double dbl(df x) { return df_to(x); }
 template <typename R> __device__ __forceinline__ R to_r(double x) { return (R)x; }
 template <> __device__ __forceinline__ df to_r<df>(double x) { return df_from(x); }
 template <typename R> constexpr bool is_f32() { return sizeof(R) == 4; }
+// A double-float value as R (only meaningful for R = df; the others take its sum).
+template <typename R> __device__ __forceinline__ R to_r_df(df x) { return (R)df_to(x); }
+template <> __device__ __forceinline__ df to_r_df<df>(df x) { return x; }
 
 template <typename R> __device__ __forceinline__ cx<R> mk(R a, R b) { return cx<R>{a, b}; }
 template <typename R> __device__ __forceinline__ cx<R> add(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }

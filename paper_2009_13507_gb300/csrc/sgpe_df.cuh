@@ -75,6 +75,19 @@ __device__ __forceinline__ df fma(df a, df b, df c) {
 
 __device__ __forceinline__ bool df_isfinite(df a) { return isfinite(a.hi); }
 
+// 1/sqrt(a) for a > 0: FP32 estimate, then two Newton steps y <- y (3 - a y^2)/2
+// in double-float (error ~2^-23, then ~2^-45, then the format's ~2^-48).
+__device__ __forceinline__ df df_rsqrt(df a) {
+    df y = df(rsqrtf(a.hi), 0.0f);
+#pragma unroll
+    for (int it = 0; it < 2; it++) {
+        const df ay2 = (a * y) * y;
+        const df h = df(1.5f, 0.0f) - df(0.5f * ay2.hi, 0.5f * ay2.lo);
+        y = y * h;
+    }
+    return y;
+}
+
 // a + b for an FP32 b (one error-free sum fewer than a full double-float add).
 __device__ __forceinline__ df add_f(df a, float b) {
     df s = two_sum(a.hi, b);

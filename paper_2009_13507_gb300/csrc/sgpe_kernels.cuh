@@ -189,7 +189,7 @@ __device__ __forceinline__ void renorm_factors(const double (&N)[3], int renorm,
     d[0] = d[1] = d[2] = 1.0;
     if (!(N[0] + N[1] + N[2] > 0.0)) return;  // a zero state has no normalisation: left as it is
     if (renorm == 1) {
-        double f = 1.0 / sqrt(N[0] + N[1] + N[2]);
+        double f = rsqrt(N[0] + N[1] + N[2]);  // one reciprocal square root: a short FP64 chain
         d[0] = d[1] = d[2] = f;
     } else if (renorm == 2) {
         double m = mag;
@@ -477,16 +477,12 @@ __global__ void __launch_bounds__(256) k_cn_y(const typename V2<R>::T* in, typen
 // lane and in every block that calls it.
 __device__ __forceinline__ double sum_partials_warp(const double* q, int m) {
     const int lane = threadIdx.x & 31;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int b = lane;
-    for (; b + 96 < m; b += 128) {
-        a0 += __ldcg(q + b);
-        a1 += __ldcg(q + b + 32);
-        a2 += __ldcg(q + b + 64);
-        a3 += __ldcg(q + b + 96);
-    }
-    for (; b < m; b += 32) a0 += __ldcg(q + b);
-    double s = (a0 + a1) + (a2 + a3);
+    // up to 256 partials: all eight loads of a lane in flight at once, then a tree
+    double v[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = (lane + 32 * k < m) ? __ldcg(q + lane + 32 * k) : 0.0;
+    double s = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+    for (int b = lane + 256; b < m; b += 32) s += __ldcg(q + b);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     return s;

@@ -31,6 +31,8 @@ def main(argv=None):
     ap.add_argument("--omega", type=float, default=0.5)
     ap.add_argument("--dt", type=float, default=2e-4)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--renorm", type=int, default=None, choices=(0, 1, 2),
+                    help="renormalisation mode (default: 1 in imaginary time, 0 in real time)")
     args = ap.parse_args(argv)
 
     import numpy as np
@@ -49,7 +51,7 @@ def main(argv=None):
     dtype = torch.complex64 if args.precision == "c64" else torch.complex128
     s = sgpe.Solver(args.dim, n, ny, dx=args.dx, precision=args.precision, device=dev)
     s.set_params(sgpe.Physics(c0=args.c0, c2=args.c2, so_type=args.so_type, gamma=args.gamma, omega=args.omega,
-                              dt=args.dt, renorm=0 if args.real else 1))
+                              dt=args.dt, renorm=(0 if args.real else 1) if args.renorm is None else args.renorm))
     s.load_state(torch.from_numpy(psi0.astype(np.complex128)).to(dev).to(dtype))
     s.synchronize()
     t0 = time.perf_counter()
