@@ -208,7 +208,11 @@ sgpe_status sgpe_substep(sgpe_ctx* ctx, int which, int imag, double omega);
  * context's stream around every kernel; writes the summed device time in ms of
  * each kernel kind to ms_out[0..3] (0 pointwise SO/CALCNU/HERM, 1 Crank-Nicolson
  * along x, 2 along y, 3 end-of-step norm reduction and renormalisation scale;
- * unused kinds 0) and the launch counts to launches_out[0..3].
+ * unused kinds 0) and the launch counts to launches_out[0..3]. On 2D grids
+ * with lines of at most 1024 points kind 0 is the fused kernel (pending scale,
+ * pointwise substeps and the x sweep), kind 1 has no launches, and the end of
+ * step runs inside kinds 0 and 2 (kind 3 has no launches; one untimed
+ * end-of-steps launch follows the last step).
  * Advances the state exactly like the step functions. Synchronises the stream.
  */
 sgpe_status sgpe_profile_steps(sgpe_ctx* ctx, int nsteps, int imag, double* ms_out, int* launches_out);
@@ -335,7 +339,11 @@ int sgpe_batch_launches_per_step(const sgpe_batch* b);
 const char* sgpe_batch_last_error(const sgpe_batch* b);
 sgpe_status sgpe_batch_destroy(sgpe_batch* b);
 
-/* Number of kernel launches one step enqueues (for launch accounting). */
+/*
+ * Number of kernel launches one step enqueues (for launch accounting): 2 on 2D
+ * grids with lines of at most 1024 points (plus one end-of-steps launch per
+ * sgpe_step_imag / sgpe_step_real call), 3 in 1D, 3 or 4 for longer lines.
+ */
 int sgpe_launches_per_step(const sgpe_ctx* ctx);
 
 /* Last error message of this context (never NULL; "" when there is none). With

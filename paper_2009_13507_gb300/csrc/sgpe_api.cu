@@ -290,7 +290,9 @@ sgpe_status sgpe_set_params(sgpe_ctx* c, const sgpe_params* p) {
             double b = p->dt / (4.0 * h * h);
             double bre = m == 0 ? b : 0.0, bim = m == 0 ? 0.0 : (m == 1 ? b : -b);
             void** t = c->tabs[m][a];
-            cudaError_t e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::coef(c->stream, t[0], t[1], t[2], t[3], n, bre, bim); });
+            cudaError_t e = with_prec(c->prec, [&](auto r) {
+                return Launcher<decltype(r)>::coef(c->stream, t[0], t[1], t[2], t[3], n, bre, bim);
+            });
             CK(e, "COEF kernel");
         }
     c->have_params = true;
@@ -447,7 +449,9 @@ sgpe_status sgpe_normalize(sgpe_ctx* c, double* norms_out) {
     if (st) return st;
     CK(flush_any(c), "flush");
     size_t plane = (size_t)c->nx * c->ny;
-    cudaError_t e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::norms(c->stream, c->psi, plane, c->kp.cell, 0, 0.0, c->partials, c->sc); });
+    cudaError_t e = with_prec(c->prec, [&](auto r) {
+        return Launcher<decltype(r)>::norms(c->stream, c->psi, plane, c->kp.cell, 0, 0.0, c->partials, c->sc);
+    });
     CK(e, "norms kernel");
     double n[4];
     CK(cudaMemcpyAsync(n, c->sc->norms, sizeof(n), cudaMemcpyDeviceToHost, c->stream), "copy norms");
@@ -547,21 +551,32 @@ sgpe_status sgpe_substep(sgpe_ctx* c, int which, int imag, double omega) {
     if (which <= 2) {
         KParams k = c->kp;
         k.omega_t = omega / sqrt(2.0);
-        e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::pointwise(c->stream, im, c->psi, c->mid, k, c->sc, nullptr, 1 << which); });
+        e = with_prec(c->prec, [&](auto r) {
+            return Launcher<decltype(r)>::pointwise(c->stream, im, c->psi, c->mid, k, c->sc, nullptr, 1 << which);
+        });
         CK(e, "pointwise kernel");
         CK(cudaMemcpyAsync(c->psi, c->mid, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy back");
     } else if (which == 3) {
         CK(cudaMemcpyAsync(c->mid, c->psi, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy");
-        e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::cn_x(c->stream, im, false, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo, c->partials, c->sc, 0, 0); });
+        e = with_prec(c->prec, [&](auto r) {
+            return Launcher<decltype(r)>::cn_x(c->stream, im, false, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo,
+                                               c->partials, c->sc, 0, 0);
+        });
         CK(e, "cn_x kernel");
     } else if (which == 4) {
         CK(cudaMemcpyAsync(c->mid, c->psi, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy");
-        e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials, c->sc, 0, 0, 0); });
+        e = with_prec(c->prec, [&](auto r) {
+            return Launcher<decltype(r)>::cn_y(c->stream, im, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo,
+                                               c->partials, c->sc, 0, 0, 0);
+        });
         CK(e, "cn_y kernel");
     } else {
         size_t plane = (size_t)c->nx * c->ny;
         int rn = c->params.renorm ? c->params.renorm : 1;
-        e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::norms(c->stream, c->psi, plane, c->kp.cell, rn, c->kp.mag, c->partials, c->sc); });
+        e = with_prec(c->prec, [&](auto r) {
+            return Launcher<decltype(r)>::norms(c->stream, c->psi, plane, c->kp.cell, rn, c->kp.mag, c->partials,
+                                                c->sc);
+        });
         CK(e, "norms kernel");
         CK(flush_any(c), "flush");
     }
@@ -602,11 +617,16 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
                                                   c->tabs[mode][0], c->partials, c->geo.blocks_y / 3, renorm);
             });
         if (!e && !fused)
-            e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::pointwise(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, 7); });
+            e = with_prec(c->prec, [&](auto r) {
+                return Launcher<decltype(r)>::pointwise(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, 7);
+            });
         if (!e) e = cudaEventRecord(ev[1], c->stream);
         void* xout = two ? c->mid : c->psi;
         if (!e && !fused)
-            e = with_prec(c->prec, [&](auto r) { return Launcher<decltype(r)>::cn_x(c->stream, im, !two, c->mid, xout, c->kp, c->tabs[mode][0], c->geo, c->partials, c->sc, renorm, 1); });
+            e = with_prec(c->prec, [&](auto r) {
+                return Launcher<decltype(r)>::cn_x(c->stream, im, !two, c->mid, xout, c->kp, c->tabs[mode][0], c->geo,
+                                                   c->partials, c->sc, renorm, 1);
+            });
         if (!e) e = cudaEventRecord(ev[2], c->stream);
         if (!e && two)
             e = with_prec(c->prec, [&](auto r) {

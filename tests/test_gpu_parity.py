@@ -136,6 +136,21 @@ def test_fixed_magnetisation_renorm(mag):
     assert abs(o["N"] - 1) < 1e-12 and abs(o["mag"] - mag) < 1e-12
 
 
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("cdf", 1e-10)])
+def test_fixed_magnetisation_renorm_2d(precision, tol):
+    """Eq. (DJ) on the two-launch 2D step, where the head kernel derives the
+    per-component scale from the previous sweep's norm partials."""
+    phys = dict(c0=30.0, c2=2.0, so_type=1, gamma=0.5, omega=0.0, dt=5e-4, renorm=2, mag=0.3)
+    prob, s = make_pair(2, 64, 48, dx=0.15, precision=precision, **phys)
+    psi = I.gaussian_phase_2d(64, 48, 0.15, 0.15, seed=3)
+    s.set_state(psi)
+    s.step_imag(60)
+    ref = O.step(prob, psi, 60, True)
+    assert relerr(s.get_state(), ref) < tol
+    o = s.energy()
+    assert abs(o["N"] - 1) < 1e-12 and abs(o["mag"] - 0.3) < 1e-12
+
+
 @pytest.mark.parametrize("dim,nx,ny", [(2, 3, 3), (2, 5, 7), (2, 17, 3), (2, 33, 65), (1, 3, 1), (1, 33, 1),
                                        (1, 1000, 1), (2, 4096, 3), (2, 3, 4096)])
 def test_edge_sizes(dim, nx, ny):
