@@ -137,15 +137,23 @@ template <typename R, int C> struct CnShape {
 // part): about 2^-44 relative, i.e. FP64-grade for the few dozen terms of a
 // lane, on the FP32 pipe instead of GB300's much slower FP64 pipe.
 template <typename R> struct NormAcc;
+// complex128 and double-float: real and imaginary squares in two accumulators,
+// which halves the dependent chain of a lane's sum.
 template <> struct NormAcc<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(cx<double> o) { s += o.re * o.re + o.im * o.im; }
-    __device__ __forceinline__ double value() const { return s; }
+    double sr = 0.0, si = 0.0;
+    __device__ __forceinline__ void add(cx<double> o) {
+        sr = fma(o.re, o.re, sr);
+        si = fma(o.im, o.im, si);
+    }
+    __device__ __forceinline__ double value() const { return sr + si; }
 };
 template <> struct NormAcc<df> {
-    df s = df(0);
-    __device__ __forceinline__ void add(cx<df> o) { s = fma(o.re, o.re, fma(o.im, o.im, s)); }
-    __device__ __forceinline__ double value() const { return df_to(s); }
+    df sr = df(0), si = df(0);
+    __device__ __forceinline__ void add(cx<df> o) {
+        sr = fma(o.re, o.re, sr);
+        si = fma(o.im, o.im, si);
+    }
+    __device__ __forceinline__ double value() const { return df_to(sr + si); }
 };
 template <> struct NormAcc<float> {
     float hi = 0.0f, lo = 0.0f;
