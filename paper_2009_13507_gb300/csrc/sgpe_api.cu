@@ -358,8 +358,26 @@ static cudaError_t enqueue_steps(sgpe_ctx* c, int n, bool imag, const double* om
 
 static const int kGraphSteps = 32;
 
+// 1D grids with lines of at most 1024 points in the complex64 and double-float
+// forms run the whole step loop in one block (the FP32-pipe forms fit one SM;
+// the complex128 form spreads its FP64 pointwise work over several SMs instead).
+static bool one_block_1d(const sgpe_ctx* c) {
+    return c->dim == 1 && c->nx <= kRegMaxN && c->prec != SGPE_C128;
+}
+
 static sgpe_status run_steps(sgpe_ctx* c, int nsteps, bool imag, const double* omega_tab) {
     if (omega_tab) CK(cudaMemsetAsync(&c->sc->step_idx, 0, sizeof(int), c->stream), "step_idx reset");
+    if (one_block_1d(c)) {
+        if (nsteps == 0) return SGPE_OK;
+        const int mode = imag ? 0 : 1;
+        const int renorm = imag ? c->params.renorm : 0;
+        cudaError_t e = with_prec(c->prec, [&](auto r) {
+            return Launcher<decltype(r)>::step1d(c->stream, imag, c->psi, c->kp, c->sc, omega_tab, c->tabs[mode][0],
+                                                 nsteps, renorm);
+        });
+        CK(e, "1D step loop");
+        return SGPE_OK;
+    }
     int G = nsteps < kGraphSteps ? nsteps : kGraphSteps;
     int reps = G > 0 ? nsteps / G : 0;
     int rem = G > 0 ? nsteps - reps * G : 0;
@@ -665,6 +683,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
 
 int sgpe_launches_per_step(const sgpe_ctx* c) {
     if (!c) return 0;
+    if (one_block_1d(c)) return 0;  // one launch per step call
     if (head_scale(c)) return 2;  // plus one end-of-steps launch per step call
     if (c->geo.fused) return 3;
     return c->dim == 2 ? 4 : 3;

@@ -332,6 +332,106 @@ __global__ void __launch_bounds__(kPwxThreads, C <= 8 ? 2 : 1)
 }
 
 // ---------------------------------------------------------------------------
+// The whole 1D step loop in one block (lines of at most 1024 points): the
+// three component lines live in shared memory for all nsteps steps, so a step
+// costs no launch and no global traffic. Per step: the pointwise substeps of
+// every point (pending scale, SO, CALCNU, HERM) into the padded chunk staging
+// area, the x sweep of component j by warp j back into the state, each warp's
+// FP64 norm partial, then thread 0 forms the next pending scale (Eq. (DJ2) /
+// (DJ)). At the end the state goes back to A and the last norms and the
+// pending scale are published, as after the multi-launch path. One SM carries
+// the whole grid, which suits the complex64 and double-float forms (FP32
+// pipe); the complex128 form keeps the multi-launch path, whose pointwise
+// kernel spreads its FP64 work over several SMs.
+// ---------------------------------------------------------------------------
+constexpr int kStep1dThreads = 256;
+
+template <typename R, int C> constexpr size_t step1d_smem_bytes(int nx) {
+    return ((size_t)3 * nx + (size_t)3 * 32 * (C + 1)) * sizeof(typename V2<R>::T);
+}
+
+template <typename R, bool IMAG, int C>
+__global__ void __launch_bounds__(kStep1dThreads, 1)
+    k_step1d(typename V2<R>::T* __restrict__ A, KParams p, DevScalars* sc, const double* __restrict__ omega_tab,
+             Tabs<R> t, int nsteps, int renorm) {
+    using T = typename V2<R>::T;
+    extern __shared__ __align__(16) unsigned char step1d_smem[];
+    const int nx = p.nx;
+    T* st_ = reinterpret_cast<T*>(step1d_smem);  // state [3][nx]
+    T* stage = st_ + 3 * nx;                     // [3][32 (C + 1)]
+    constexpr int S = 32 * (C + 1);
+    constexpr int PPT = (32 * C + kStep1dThreads - 1) / kStep1dThreads;
+    __shared__ R ds[3];
+    __shared__ double red[3], dlast[3];
+    const int warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 3 * nx; i += kStep1dThreads) st_[i] = __ldcg(A + i);
+    if (threadIdx.x < 3) {
+        ds[threadIdx.x] = scale_of<R>(sc, threadIdx.x);
+        dlast[threadIdx.x] = sc->scale[threadIdx.x];
+    }
+    const int step0 = sc->step_idx;
+    const cx<R> zero = {R(0), R(0)};
+    bool finite = true;
+    __syncthreads();
+    for (int s = 0; s < nsteps; s++) {
+        const R Ot = omega_tab ? to_r<R>(__ldg(omega_tab + step0 + s) * 0.70710678118654752440) : kc<R>(p, KC_OMEGA);
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            const int ix = threadIdx.x + k * kStep1dThreads;
+            if (ix < nx) {
+                PointIn<R> in;
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    in.u[j] = unpack(st_[j * nx + ix]);
+                    const cx<R> xp = ix + 1 < nx ? unpack(st_[j * nx + ix + 1]) : zero;
+                    const cx<R> xm = ix > 0 ? unpack(st_[j * nx + ix - 1]) : zero;
+                    in.X[j] = sub(xp, xm);
+                    in.Y[j] = zero;
+                }
+                cx<R> u[3];
+                pointwise_apply<R, IMAG>(in, p, ds, Ot, ix, 0, 7, u);
+                const int slot = (ix / C) * (C + 1) + (ix % C);
+#pragma unroll
+                for (int j = 0; j < 3; j++) stage[j * S + slot] = pack(u[j]);
+            }
+        }
+        __syncthreads();
+        if (warp < 3) {
+            const T* r = stage + warp * S;
+            cnx_solve_line<R, IMAG, C>([&](int i) { return unpack(r[(i / C) * (C + 1) + (i % C)]); }, st_,
+                                       (size_t)warp * nx, nx, t, red + warp);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double N[3] = {red[0] * p.cell, red[1] * p.cell, red[2] * p.cell};
+            const bool fin = isfinite(N[0]) && isfinite(N[1]) && isfinite(N[2]);
+            finite = finite && fin;
+            double d[3];
+            renorm_factors(N, fin ? renorm : 0, p.mag, d);
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                ds[j] = to_r<R>(d[j]);
+                dlast[j] = d[j];
+                sc->norms[j] = N[j];
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < 3 * nx; i += kStep1dThreads) A[i] = st_[i];
+    if (threadIdx.x == 0 && nsteps > 0) {
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            sc->scale[j] = dlast[j];
+            sc->scale_f[j] = (float)dlast[j];
+            sc->scale_l[j] = (float)(dlast[j] - (double)sc->scale_f[j]);
+        }
+        sc->scale_src = 0;
+        if (!finite) sc->err |= 1;
+        sc->step_idx = step0 + nsteps;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // CN along y: block = one warp solving K adjacent columns of one component
 // (K = 2 for small chunks: a lane's chunk rows then load 32 contiguous bytes
 // per row in FP64). Norm partials as for the x sweep, one slot per block.

@@ -70,6 +70,11 @@ template <typename R> struct Launcher {
     static cudaError_t setup();
     static cudaError_t pointwise(cudaStream_t s, bool imag, const void* A, void* B, const KParams& p,
                                  const DevScalars* sc, const double* omega_tab, int mask);
+    // The whole loop of nsteps 1D steps in one block (lines of at most 1024
+    // points), the state in shared memory; A is read at the start and written
+    // at the end.
+    static cudaError_t step1d(cudaStream_t s, bool imag, void* A, const KParams& p, DevScalars* sc,
+                              const double* omega_tab, const void* const* tabs_x, int nsteps, int renorm);
     // Fused pointwise substeps + CN along x of a 2D grid (Geometry::fused): A -> B.
     // partials / m / renorm: the previous y sweep's norm partials (m per component)
     // and the renormalisation mode, for the pending scale (DevScalars::scale_src).

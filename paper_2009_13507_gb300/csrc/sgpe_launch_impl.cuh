@@ -97,8 +97,55 @@ static void pwx_c(bool imag, int rows, cudaStream_t s, const typename V2<R>::T* 
                    m, renorm);
 }
 
+template <typename R, bool IMAG, int C> static cudaError_t step1d_allow() {
+    return cudaFuncSetAttribute(k_step1d<R, IMAG, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)step1d_smem_bytes<R, C>(32 * C));
+}
+
+template <typename R, bool IMAG> static cudaError_t step1d_allow_all() {
+    cudaError_t e;
+    if ((e = step1d_allow<R, IMAG, 1>())) return e;
+    if ((e = step1d_allow<R, IMAG, 2>())) return e;
+    if ((e = step1d_allow<R, IMAG, 4>())) return e;
+    if ((e = step1d_allow<R, IMAG, 8>())) return e;
+    if ((e = step1d_allow<R, IMAG, 16>())) return e;
+    return step1d_allow<R, IMAG, 32>();
+}
+
+template <typename R, int C>
+static void step1d_c(bool imag, cudaStream_t s, typename V2<R>::T* A, const KParams& p, DevScalars* sc,
+                     const double* omega_tab, const Tabs<R>& t, int nsteps, int renorm) {
+    const size_t smem = step1d_smem_bytes<R, C>(p.nx);
+    if (imag)
+        k_step1d<R, true, C><<<1, kStep1dThreads, smem, s>>>(A, p, sc, omega_tab, t, nsteps, renorm);
+    else
+        k_step1d<R, false, C><<<1, kStep1dThreads, smem, s>>>(A, p, sc, omega_tab, t, nsteps, renorm);
+}
+
+template <typename R>
+cudaError_t Launcher<R>::step1d(cudaStream_t s, bool imag, void* A, const KParams& p, DevScalars* sc,
+                                const double* omega_tab, const void* const* tabs_x, int nsteps, int renorm) {
+    using T = typename V2<R>::T;
+    if (p.dim != 1 || p.nx > kRegMaxN) return cudaErrorInvalidValue;
+    Tabs<R> t = make_tabs<R>(tabs_x);
+    KParams q = p;
+    fill_derived(q);
+    T* a = (T*)A;
+    switch (chunk_len(p.nx)) {
+        case 1: step1d_c<R, 1>(imag, s, a, q, sc, omega_tab, t, nsteps, renorm); break;
+        case 2: step1d_c<R, 2>(imag, s, a, q, sc, omega_tab, t, nsteps, renorm); break;
+        case 4: step1d_c<R, 4>(imag, s, a, q, sc, omega_tab, t, nsteps, renorm); break;
+        case 8: step1d_c<R, 8>(imag, s, a, q, sc, omega_tab, t, nsteps, renorm); break;
+        case 16: step1d_c<R, 16>(imag, s, a, q, sc, omega_tab, t, nsteps, renorm); break;
+        default: step1d_c<R, 32>(imag, s, a, q, sc, omega_tab, t, nsteps, renorm); break;
+    }
+    return cudaGetLastError();
+}
+
 template <typename R> cudaError_t Launcher<R>::setup() {
     cudaError_t e;
+    if ((e = step1d_allow_all<R, true>())) return e;
+    if ((e = step1d_allow_all<R, false>())) return e;
     if ((e = pwx_allow_all<R, true>())) return e;
     if ((e = pwx_allow_all<R, false>())) return e;
     if ((e = allow_smem(k_cn_x<R, true, false>))) return e;

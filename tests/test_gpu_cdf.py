@@ -1,6 +1,7 @@
 """The double-float form (SGPE_CDF: every real part a pair of FP32 numbers,
 ~48 significant bits, all step arithmetic on the FP32 pipe) against the FP64
-CPU oracle, through the C ABI.
+CPU oracle, through the C ABI; and the one-block 1D step loop that the
+double-float and complex64 forms use on 1D grids.
 
 It is held to the same bar as the complex128 form: 1e-10 normwise relative for
 whole steps and observables; single substeps to 1e-12 (one substep's
@@ -164,3 +165,44 @@ def test_unsupported_entry_points_say_so():
     assert lib.sgpe_adjoint_workspace_bytes(s.ctx, 4, 2, ctypes.byref(size)) == sgpe.OK
     rc = lib.sgpe_adjoint_loss_grad(s.ctx, 4, None, None, 2, None, None, None, None)
     assert rc == sgpe.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", ["cdf", "c64"])
+def test_1d_one_block_loop_split_calls(precision):
+    """1D grids in the FP32-pipe forms run the whole loop in one block; two calls
+    of 7 steps continue exactly where one call of 14 goes (the pending scale
+    and the step counter are handed over between calls)."""
+    prob, s = make_pair(1, 200, 1, dx=0.06, precision=precision, **PHYS_1D)
+    psi = I.gaussian_jitter_1d(200, 0.06, seed=4)
+    s.set_state(psi)
+    s.step_imag(14)
+    a = s.get_state()
+    s.set_state(psi)
+    s.step_imag(7)
+    s.step_imag(7)
+    assert np.array_equal(a, s.get_state())
+
+
+def test_1d_one_block_loop_omega_table_cdf():
+    import torch
+    phys = dict(PHYS_1D, renorm=0)
+    prob, s = make_pair(1, 256, 1, dx=0.05, precision="cdf", **phys)
+    psi = I.gaussian_jitter_1d(256, 0.05, seed=6)
+    om = 0.3 * np.sin(np.linspace(0, 4, 80)) + 0.1 * I.uniform(11, 80)
+    s.set_state(psi)
+    s.step_real(80, torch.tensor(om, dtype=torch.float64, device="cuda:0"))
+    assert relerr(s.get_state(), O.step(prob, psi, 80, False, omega_t=om)) < 1e-10
+
+
+@pytest.mark.parametrize("imag", [True, False])
+def test_1d_config_complex64(imag):
+    """The 1D workload in the complex64 form (one-block loop): its error against
+    the FP64 oracle after 2000 steps."""
+    prob, s = make_pair(1, 256, 1, dx=0.05, precision="c64", **PHYS_1D)
+    psi = I.gaussian_jitter_1d(256, 0.05, seed=0)
+    s.set_state(psi)
+    (s.step_imag(2000) if imag else s.step_real(2000))
+    ref = O.step(prob, psi, 2000, imag)
+    assert relerr(s.get_state(), ref) < 2e-5
+    oe = O.observables(prob, ref)
+    assert abs(s.energy()["E"] - oe["E"]) < 1e-5 * abs(oe["E"])
