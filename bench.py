@@ -176,7 +176,8 @@ def extra_workloads(dev, reps=2):
     """The other workloads of the method, each measured with CUDA events on its
     solver's stream after one warm-up run (rank 0 only):
       1d_imag       1D, Nx = 256, dx = 0.05, c0 = 10, c2 = -0.5, gamma p_x Sigma_x (0.5),
-                    Omega = 0.2, dt = 1e-4, 10,000 imaginary-time steps, complex128
+                    Omega = 0.2, dt = 1e-4, 10,000 imaginary-time steps, complex128 (and the
+                    double-float and complex64 forms with their energy error)
       quench        2D 512 x 512, dx = 0.04, the 2D physics above; ground state prepared
                     in FP64 (3000 imaginary-time steps, untimed), then Omega 0.5 -> 0 and
                     10,000 real-time steps at dt = 1e-4 in complex64 and complex128
@@ -201,19 +202,26 @@ def extra_workloads(dev, reps=2):
         return a.elapsed_time(b)
 
     out = {}
-    # 1D imaginary time
-    s1 = sgpe.Solver(1, 256, dx=0.05, device=dev)
-    s1.set_params(sgpe.Physics(c0=10.0, c2=-0.5, so_type=1, gamma=0.5, omega=0.2, dt=1e-4, renorm=1))
-    p1 = torch.from_numpy(I.gaussian_jitter_1d(256, 0.05, seed=0)).to(dev)
-    ms = []
-    for r in range(reps + 1):
-        s1.load_state(p1)
-        t = ev_time(s1.stream, lambda: s1.step_imag(10000))
-        if r:
-            ms.append(t)
-    e1 = s1.energy()
-    out["1d_imag"] = {"value": 256 * 10000 / (statistics.mean(ms) * 1e-3), "unit": METRIC,
-                      "ms": statistics.mean(ms), "E": e1["E"], "precision": "complex128"}
+    # 1D imaginary time in the three precisions
+    d1 = {}
+    for prec in ("c128", "cdf", "c64"):
+        s1 = sgpe.Solver(1, 256, dx=0.05, precision=prec, device=dev)
+        s1.set_params(sgpe.Physics(c0=10.0, c2=-0.5, so_type=1, gamma=0.5, omega=0.2, dt=1e-4, renorm=1))
+        p1 = torch.from_numpy(I.gaussian_jitter_1d(256, 0.05, seed=0)).to(dev).to(s1.cdtype)
+        ms = []
+        for r in range(reps + 1):
+            s1.load_state(p1)
+            t = ev_time(s1.stream, lambda: s1.step_imag(10000))
+            if r:
+                ms.append(t)
+        d1[prec] = {"value": 256 * 10000 / (statistics.mean(ms) * 1e-3), "ms": statistics.mean(ms),
+                    "E": s1.energy()["E"]}
+    out["1d_imag"] = {"value": d1["c128"]["value"], "unit": METRIC, "ms": d1["c128"]["ms"], "E": d1["c128"]["E"],
+                      "precision": "complex128",
+                      "cdf_value": d1["cdf"]["value"],
+                      "cdf_energy_rel_err_vs_fp64": abs(d1["cdf"]["E"] - d1["c128"]["E"]) / abs(d1["c128"]["E"]),
+                      "c64_value": d1["c64"]["value"],
+                      "c64_energy_rel_err_vs_fp64": abs(d1["c64"]["E"] - d1["c128"]["E"]) / abs(d1["c128"]["E"])}
     # 512 x 512 real-time quench
     n3, dx3 = 512, 0.04
     phys = dict(PHYS)
