@@ -309,10 +309,15 @@ sgpe_status sgpe_set_params(sgpe_ctx* c, const sgpe_params* p) {
 // sweep's norm partials, and end_steps publishes it after the last step.
 static bool head_scale(const sgpe_ctx* c) { return c->geo.fused && c->geo.reg_y; }
 
+// The register y sweep of the complex64 and double-float forms leaves its norm
+// partials as double-float pairs (summed on the FP32 pipe).
+static int y_parts_df(const sgpe_ctx* c) { return c->dim == 2 && c->geo.reg_y && c->prec != SGPE_C128; }
+
 static cudaError_t end_steps(sgpe_ctx* c, bool imag) {
     if (!head_scale(c)) return cudaSuccess;
     const int renorm = imag ? c->params.renorm : 0;
-    return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 0, c->sc);
+    return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 0, c->sc,
+                         y_parts_df(c));
 }
 
 template <typename R>
@@ -329,7 +334,8 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
                                    c->sc, renorm, 1, 1, head)))
             return e;
         if (head) return cudaSuccess;  // the next head kernel (or end_steps) takes the scale from the partials
-        return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 1, c->sc);
+        return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 1, c->sc,
+                             y_parts_df(c));
     }
     if ((e = Launcher<R>::pointwise(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, 7))) return e;
     if (c->dim == 2) {
@@ -339,13 +345,14 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
         if ((e = Launcher<R>::cn_y(c->stream, imag, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials,
                                    c->sc, renorm, 1, 1)))
             return e;
-        return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 1, c->sc);
+        return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 1, c->sc,
+                             y_parts_df(c));
     }
     if ((e = Launcher<R>::cn_x(c->stream, imag, true, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo, c->partials,
                                c->sc, renorm, 1)))
         return e;
     // 1D: one partial per line (3 lines)
-    return finalize_step(c->stream, c->partials, 3 * c->ny, c->kp.cell, renorm, c->kp.mag, 1, c->sc);
+    return finalize_step(c->stream, c->partials, 3 * c->ny, c->kp.cell, renorm, c->kp.mag, 1, c->sc, 0);
 }
 
 static cudaError_t enqueue_steps(sgpe_ctx* c, int n, bool imag, const double* omega_tab) {
@@ -654,7 +661,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
         if (!e) e = cudaEventRecord(ev[3], c->stream);
         if (!e && !head)
             e = finalize_step(c->stream, c->partials, two ? c->geo.blocks_y : 3 * c->ny, c->kp.cell, renorm,
-                              c->kp.mag, 1, c->sc);
+                              c->kp.mag, 1, c->sc, two ? y_parts_df(c) : 0);
         if (!e) e = cudaEventRecord(ev[4], c->stream);
       }
       if (!e) e = cudaEventSynchronize(evs[nb - 1][4]);

@@ -172,6 +172,33 @@ template <> struct NormAcc<float> {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// Norm partial type of the sweeps' step-ending sums: FP64 for the complex128
+// state, a double-float pair (FP32 pipe) for the complex64 and double-float forms.
+template <typename R> struct PartT { using T = df; };
+template <> struct PartT<double> { using T = double; };
+
+template <typename P, typename Acc> __device__ __forceinline__ P acc_value(const Acc& a);
+template <> __device__ __forceinline__ double acc_value<double, NormAcc<double>>(const NormAcc<double>& a) {
+    return a.value();
+}
+template <> __device__ __forceinline__ double acc_value<double, NormAcc<float>>(const NormAcc<float>& a) {
+    return a.value();
+}
+template <> __device__ __forceinline__ double acc_value<double, NormAcc<df>>(const NormAcc<df>& a) {
+    return a.value();
+}
+template <> __device__ __forceinline__ df acc_value<df, NormAcc<float>>(const NormAcc<float>& a) {
+    return fast_two_sum(a.hi, a.lo);
+}
+template <> __device__ __forceinline__ df acc_value<df, NormAcc<df>>(const NormAcc<df>& a) { return a.sr + a.si; }
+
+__device__ __forceinline__ df warp_sum(df v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        v = v + df(__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off));
+    return v;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -281,7 +308,24 @@ __global__ void __launch_bounds__(kPwxThreads, C <= 8 ? 2 : 1)
         const int ix = threadIdx.x + k * kPwxThreads;
         if (ix < nx) pointwise_load<R>(A, p, ix, iy, p.so_case != 0, in[k]);
     }
-    if (*(volatile const int*)&sc->scale_src) {
+    if (*(volatile const int*)&sc->scale_src && !std::is_same<R, double>::value) {
+        // complex64 / double-float: the y sweep left double-float partials
+        __shared__ df red_df[3];
+        if (warp < 3) {
+            const df s = sum_partials_warp(reinterpret_cast<const df*>(partials) + (size_t)warp * m, m);
+            if ((threadIdx.x & 31) == 0) red_df[warp] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const df S[3] = {red_df[0], red_df[1], red_df[2]};
+            df f[3];
+            double d[3], N[3];
+            bool finite;
+            scale_from_df_sums(S, p.cell, renorm, p.mag, f, d, N, finite);
+#pragma unroll
+            for (int j = 0; j < 3; j++) ds[j] = to_r_df<R>(f[j]);
+        }
+    } else if (*(volatile const int*)&sc->scale_src) {
         if (warp < 3) {
             const double s = sum_partials_warp(partials + (size_t)warp * m, m);
             if ((threadIdx.x & 31) == 0) red[warp] = s;
@@ -290,20 +334,10 @@ __global__ void __launch_bounds__(kPwxThreads, C <= 8 ? 2 : 1)
         if (threadIdx.x == 0) {
             double N[3] = {red[0] * p.cell, red[1] * p.cell, red[2] * p.cell};
             const bool finite = isfinite(N[0]) && isfinite(N[1]) && isfinite(N[2]);
-            if (std::is_same<R, df>::value && renorm == 1) {
-                // double-float: Eq. (DJ2) directly in pairs (no FP64 square root
-                // and no FP64 -> pair split of the factor on this path)
-                const double Nt = N[0] + N[1] + N[2];
-                df f = df(1.0f, 0.0f);
-                if (finite && Nt > 0.0) f = df_rsqrt(df_from(Nt));
+            double d[3];
+            renorm_factors(N, finite ? renorm : 0, p.mag, d);
 #pragma unroll
-                for (int j = 0; j < 3; j++) ds[j] = to_r_df<R>(f);
-            } else {
-                double d[3];
-                renorm_factors(N, finite ? renorm : 0, p.mag, d);
-#pragma unroll
-                for (int j = 0; j < 3; j++) ds[j] = to_r<R>(d[j]);
-            }
+            for (int j = 0; j < 3; j++) ds[j] = to_r<R>(d[j]);
         }
     } else if (threadIdx.x < 3) {
         ds[threadIdx.x] = scale_of<R>(sc, threadIdx.x);
@@ -438,9 +472,9 @@ __global__ void __launch_bounds__(kStep1dThreads, 1)
 // ---------------------------------------------------------------------------
 // Columns [col, col + K) of component j of one grid by the calling warp; part
 // (nullable) as for cnx_line.
-template <typename R, bool IMAG, int C>
+template <typename R, bool IMAG, int C, typename P = double>
 __device__ __forceinline__ void cny_cols(const typename V2<R>::T* in, typename V2<R>::T* out, const KParams& p,
-                                         const Tabs<R>& t, int j, int col, double* part) {
+                                         const Tabs<R>& t, int j, int col, P* part) {
     constexpr int K = CnShape<R, C>::K;
     constexpr bool KEEP = CnShape<R, C>::KEEP;
     constexpr bool INC = sizeof(R) == 4;
@@ -488,7 +522,7 @@ __device__ __forceinline__ void cny_cols(const typename V2<R>::T* in, typename V
         }
     }
     if (part) {
-        const double t = warp_sum(acc.value());
+        const P t = warp_sum(acc_value<P>(acc));
         if (lane == 0) *part = t;
     }
 }
@@ -517,7 +551,9 @@ __global__ void __launch_bounds__(32) k_cny_reg(const typename V2<R>::T* in, typ
         }
         if (advance && threadIdx.x == 0) sc->step_idx += 1;
     }
-    cny_cols<R, IMAG, C>(in, out, p, t, j, col, partials ? partials + blockIdx.x : nullptr);
+    using P = typename PartT<R>::T;
+    P* parts = reinterpret_cast<P*>(partials);
+    cny_cols<R, IMAG, C, P>(in, out, p, t, j, col, parts ? parts + blockIdx.x : nullptr);
 }
 
 }  // namespace sgpe

@@ -5,8 +5,9 @@ namespace sgpe {
 template struct Launcher<double>;
 
 cudaError_t finalize_step(cudaStream_t s, const double* partials, int nblk, double cell, int renorm, double mag,
-                          int advance, DevScalars* sc) {
-    return launch_pdl(k_finalize, dim3(1), dim3(96), 0, s, partials, nblk / 3, cell, renorm, mag, advance, sc);
+                          int advance, DevScalars* sc, int part_df) {
+    return launch_pdl(k_finalize, dim3(1), dim3(96), 0, s, partials, nblk / 3, cell, renorm, mag, advance, sc,
+                      part_df);
 }
 
 cudaError_t reset_scale(cudaStream_t s, DevScalars* sc) {

@@ -488,21 +488,90 @@ __device__ __forceinline__ double sum_partials_warp(const double* q, int m) {
     return s;
 }
 
+// The same for partials held as double-float pairs (the complex64 and
+// double-float forms: their sweeps sum the norms on the FP32 pipe); the tree is
+// pairwise, so the sum keeps about 2^-48 * log2(m) relative accuracy.
+__device__ __forceinline__ df df_shfl_xor(df v, int off) {
+    return df(__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off));
+}
+__device__ __forceinline__ df sum_partials_warp(const df* q, int m) {
+    const int lane = threadIdx.x & 31;
+    const float2* q2 = reinterpret_cast<const float2*>(q);
+    df v[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const float2 e = (lane + 32 * k < m) ? __ldcg(q2 + lane + 32 * k) : make_float2(0.0f, 0.0f);
+        v[k] = df(e.x, e.y);
+    }
+    df s = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+    for (int b = lane + 256; b < m; b += 32) {
+        const float2 e = __ldcg(q2 + b);
+        s = s + df(e.x, e.y);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s = s + df_shfl_xor(s, off);
+    return s;
+}
+
+// The pending scale from double-float norm sums S_j (before the cell factor):
+// Eq. (DJ2) in pairs (FP32 estimate of 1/sqrt, Newton steps; no FP64 on this
+// path); Eq. (DJ) and a missing renormalisation through renorm_factors in FP64.
+// f: the factor of every component as a pair (DJ2); d: the FP64 factors; N: the norms.
+__device__ __forceinline__ void scale_from_df_sums(const df (&S)[3], double cell, int renorm, double mag, df (&f)[3],
+                                                   double (&d)[3], double (&N)[3], bool& finite) {
+    const df c = df_from(cell);
+    df Nd[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        Nd[j] = S[j] * c;
+        N[j] = df_to(Nd[j]);
+    }
+    finite = isfinite(Nd[0].hi) && isfinite(Nd[1].hi) && isfinite(Nd[2].hi);
+    if (finite && renorm == 1) {
+        const df Nt = (Nd[0] + Nd[1]) + Nd[2];
+        const df g = Nt.hi > 0.0f ? df_rsqrt(Nt) : df(1.0f, 0.0f);
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            f[j] = g;
+            d[j] = df_to(g);
+        }
+        return;
+    }
+    renorm_factors(N, finite ? renorm : 0, mag, d);
+#pragma unroll
+    for (int j = 0; j < 3; j++) f[j] = df_from(d[j]);
+}
+
+// part_df: the partials are double-float pairs (see sum_partials_warp above).
 static __global__ void __launch_bounds__(96) k_finalize(const double* partials, int m, double cell, int renorm,
-                                                 double mag, int advance_step, DevScalars* sc) {
+                                                 double mag, int advance_step, DevScalars* sc, int part_df) {
     __shared__ double red[3];
+    __shared__ df red_df[3];
     const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const double* q = partials + (size_t)j * m;
     pdl_trigger();  // one small block: the next step's first kernel may launch now
     pdl_wait();
-    const double s = sum_partials_warp(q, m);
-    if (lane == 0) red[j] = s;
+    if (part_df) {
+        const df s = sum_partials_warp(reinterpret_cast<const df*>(partials) + (size_t)j * m, m);
+        if (lane == 0) red_df[j] = s;
+    } else {
+        const double s = sum_partials_warp(partials + (size_t)j * m, m);
+        if (lane == 0) red[j] = s;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double N[3] = {red[0] * cell, red[1] * cell, red[2] * cell};
-        bool finite = isfinite(N[0]) && isfinite(N[1]) && isfinite(N[2]);
-        double d[3];
-        renorm_factors(N, finite ? renorm : 0, mag, d);
+        double N[3], d[3];
+        bool finite;
+        if (part_df) {
+            const df S[3] = {red_df[0], red_df[1], red_df[2]};
+            df f[3];
+            scale_from_df_sums(S, cell, renorm, mag, f, d, N, finite);
+        } else {
+            N[0] = red[0] * cell;
+            N[1] = red[1] * cell;
+            N[2] = red[2] * cell;
+            finite = isfinite(N[0]) && isfinite(N[1]) && isfinite(N[2]);
+            renorm_factors(N, finite ? renorm : 0, mag, d);
+        }
         for (int q3 = 0; q3 < 3; q3++) {
             sc->norms[q3] = N[q3];
             sc->scale[q3] = d[q3];

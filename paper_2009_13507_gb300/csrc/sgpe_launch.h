@@ -108,7 +108,7 @@ cudaError_t cdf_from_c128(cudaStream_t s, const void* src, void* dst, size_t n);
 // End of a step: reduce the last sweep's nblk norm partials, publish N_j and the
 // next pending scale, advance the step counter (one block).
 cudaError_t finalize_step(cudaStream_t s, const double* partials, int nblk, double cell, int renorm, double mag,
-                          int advance, DevScalars* sc);
+                          int advance, DevScalars* sc, int part_df);
 
 // Validation of sgpe_params (nullptr when valid, else the reason) and the kernel
 // constants of one grid.
