@@ -206,3 +206,19 @@ def test_1d_config_complex64(imag):
     assert relerr(s.get_state(), ref) < 2e-5
     oe = O.observables(prob, ref)
     assert abs(s.energy()["E"] - oe["E"]) < 1e-5 * abs(oe["E"])
+
+
+@pytest.mark.parametrize("precision", ["cdf", "c64", "c128"])
+def test_2d_split_calls_continue_exactly(precision):
+    """Two calls of 7 steps give bit for bit the state of one call of 14 on the
+    two-launch 2D step: the end-of-steps kernel publishes the scale that the
+    next head kernel would have derived from the same norm partials."""
+    prob, s = make_pair(2, 96, 80, dx=0.1, precision=precision, **PHYS_2D)
+    psi = I.gaussian_phase_2d(96, 80, 0.1, 0.1, seed=9)
+    s.set_state(psi)
+    s.step_imag(14)
+    a = s.get_state()
+    s.set_state(psi)
+    s.step_imag(7)
+    s.step_imag(7)
+    assert np.array_equal(a, s.get_state())
