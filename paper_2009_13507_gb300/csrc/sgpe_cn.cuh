@@ -65,6 +65,7 @@ __device__ __forceinline__ void solve_chunk(cx<R> (&v)[C], const LaneTabs<R, IMA
             B = tfma<IMAG>(A, Bp, B);
             A = tmul<IMAG>(A, Ap);
         }
+        if (scan_done(lane < 2 * off, A)) break;  // see tiny_carry
     }
     cx<R> cin = shup(B, 1);
     if (lane == 0) cin = {R(0), R(0)};
@@ -84,6 +85,7 @@ __device__ __forceinline__ void solve_chunk(cx<R> (&v)[C], const LaneTabs<R, IMA
             B = tfma<IMAG>(A, Bn, B);
             A = tmul<IMAG>(A, An);
         }
+        if (scan_done(lane + 2 * off >= 32, A)) break;
     }
     cx<R> cb = shdn(B, 1);
     if (lane == 31) cb = {R(0), R(0)};

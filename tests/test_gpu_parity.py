@@ -41,6 +41,23 @@ def test_substep_parity_fp64(dim, nx, ny, which, imag):
     assert relerr(s.get_state(), ref) < 1e-13
 
 
+@pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("which", ["cn_x", "cn_y"])
+@pytest.mark.parametrize("bt", [0.02, 1.0, 50.0])
+def test_cn_sweeps_across_bt(bt, which, imag):
+    """CN sweeps for bt = dt/(4 dx^2) from small to large. The lanes' carry scan
+    of the complex128 sweeps stops once the composed chunk factors are below
+    2^-64: with 8-point chunks bt = 0.02 stops after one level, bt = 1 after
+    three, bt = 50 runs all five (|fg| ~ 0.87). All must match the oracle's LU."""
+    dx = 0.1
+    phys = dict(PHYS_2D, dt=4.0 * dx * dx * bt)
+    prob, s = make_pair(2, 200, 150, dx=dx, **phys)
+    psi = _rand(prob, 17, env=3.0)
+    s.set_state(psi)
+    s.substep(which, imag)
+    assert relerr(s.get_state(), O.substep(prob, psi, which, imag)) < 1e-13
+
+
 @pytest.mark.parametrize("so", [0, 1, 2, 3])
 @pytest.mark.parametrize("dim", [1, 2])
 def test_so_variants_parity(dim, so):
