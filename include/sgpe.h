@@ -342,7 +342,9 @@ sgpe_status sgpe_batch_destroy(sgpe_batch* b);
 /*
  * Number of kernel launches one step enqueues (for launch accounting): 2 on 2D
  * grids with lines of at most 1024 points (plus one end-of-steps launch per
- * sgpe_step_imag / sgpe_step_real call), 3 in 1D, 3 or 4 for longer lines.
+ * sgpe_step_imag / sgpe_step_real call), 3 or 4 for longer lines; 0 on 1D grids
+ * whose whole step loop is one launch per call (lines of at most 1024 points in
+ * SGPE_C64 and SGPE_CDF, at most 256 in SGPE_C128), 3 on other 1D grids.
  */
 int sgpe_launches_per_step(const sgpe_ctx* ctx);
 

@@ -365,11 +365,12 @@ static cudaError_t enqueue_steps(sgpe_ctx* c, int n, bool imag, const double* om
 
 static const int kGraphSteps = 32;
 
-// 1D grids with lines of at most 1024 points in the complex64 and double-float
-// forms run the whole step loop in one block (the FP32-pipe forms fit one SM;
-// the complex128 form spreads its FP64 pointwise work over several SMs instead).
+// 1D grids run the whole step loop in one launch: lines of at most 1024 points
+// in the complex64 and double-float forms in one block (the FP32-pipe forms fit
+// one SM); complex128 lines of at most 256 points in one cluster of up to 8
+// CTAs with the FP64 work of a point split over three threads.
 static bool one_block_1d(const sgpe_ctx* c) {
-    return c->dim == 1 && c->nx <= kRegMaxN && c->prec != SGPE_C128;
+    return c->dim == 1 && c->nx <= kRegMaxN && (c->prec != SGPE_C128 || c->nx <= kCl1dMaxN);
 }
 
 static sgpe_status run_steps(sgpe_ctx* c, int nsteps, bool imag, const double* omega_tab) {

@@ -33,12 +33,33 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// One launch of a single thread-block cluster of `cluster` CTAs (grid.x == cluster).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_cluster(void (*kernel)(KArgs...), unsigned cluster, dim3 block, size_t smem,
+                                  cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster);
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Launch geometry shared by the API layer (buffer sizing) and the launchers.
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 // Chunk length of a line of n points split over the 32 lanes of a warp: the
 // next power of two of ceil(n/32) for n <= 1024 (register kernels, compile-time
 // chunk), ceil(n/32) above (shared-memory kernels).
 constexpr int kRegMaxN = 1024;
+// Longest 1D line of the complex128 cluster step loop (8 CTAs of 32 points).
+constexpr int kCl1dMaxN = 256;
 inline int chunk_len(int n) {
     int c = ceil_div(n, 32);
     if (n > kRegMaxN) return c;

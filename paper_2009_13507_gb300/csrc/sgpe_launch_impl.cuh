@@ -4,6 +4,7 @@
 #include "sgpe_cn.cuh"
 #include "sgpe_kernels.cuh"
 #include "sgpe_launch.h"
+#include "sgpe_step1d_cl.cuh"
 
 namespace sgpe {
 
@@ -131,6 +132,16 @@ cudaError_t Launcher<R>::step1d(cudaStream_t s, bool imag, void* A, const KParam
     KParams q = p;
     fill_derived(q);
     T* a = (T*)A;
+    if constexpr (std::is_same<R, double>::value) {
+        // complex128: one cluster of ceil(nx/32) CTAs (the FP64 work of a point split over three threads)
+        if (p.nx > kCl1dMaxN) return cudaErrorInvalidValue;
+        const unsigned Q = (unsigned)ceil_div(p.nx, 32);
+        const cudaError_t e = imag ? launch_cluster(k_step1d_cl<true>, Q, dim3(kCl1dThreads), 0, s, a, q, sc,
+                                                    omega_tab, t, nsteps, renorm)
+                                   : launch_cluster(k_step1d_cl<false>, Q, dim3(kCl1dThreads), 0, s, a, q, sc,
+                                                    omega_tab, t, nsteps, renorm);
+        return e ? e : cudaGetLastError();
+    }
     switch (chunk_len(p.nx)) {
         case 1: step1d_c<R, 1>(imag, s, a, q, sc, omega_tab, t, nsteps, renorm); break;
         case 2: step1d_c<R, 2>(imag, s, a, q, sc, omega_tab, t, nsteps, renorm); break;
