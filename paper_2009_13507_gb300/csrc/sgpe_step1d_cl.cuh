@@ -49,6 +49,16 @@ __device__ __forceinline__ void cl_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+// The two halves of a barrier that only says "this CTA runs" (no ordering):
+// a CTA may store into a peer's shared memory once it has passed this wait.
+__device__ __forceinline__ void cl_arrive_relaxed() {
+    __syncwarp();
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cl_wait() {
+    __syncwarp();
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+}
 // Generic address of the same shared-memory object in CTA `rank` of the cluster.
 template <typename T> __device__ __forceinline__ T* cl_map(T* p, unsigned rank) {
     uint64_t r;
@@ -88,11 +98,11 @@ __device__ __forceinline__ cx<double> so_comp(int j, cx<double> u, const cx<doub
     return sub(u, zunit<IMAG>(h));
 }
 
-// CALCNU factor of component j (the exponent of calcnu_point_dt) applied to u.
+// CALCNU factor of component j (the exponent of calcnu_point_dt) applied to u;
+// rp, r0, rm: the densities |psi_j|^2 of the three components at the point.
 template <bool IMAG>
-__device__ __forceinline__ cx<double> calcnu_comp(int j, cx<double> u, const cx<double> (&w)[3], double Vn,
+__device__ __forceinline__ cx<double> calcnu_comp(int j, cx<double> u, double rp, double r0, double rm, double Vn,
                                                   const KParams& p) {
-    const double rp = nrm(w[0]), r0 = nrm(w[1]), rm = nrm(w[2]);
     const double base = fma(p.kd[KC_NC0], rp + r0 + rm, Vn);
     const double nc2 = p.kd[KC_NC2];
     const double x = j == 0 ? fma(nc2, rp - rm + r0, base) : j == 1 ? fma(nc2, rp + rm, base)
@@ -103,14 +113,22 @@ __device__ __forceinline__ cx<double> calcnu_comp(int j, cx<double> u, const cx<
     return mul(cx<double>{c, s}, u);
 }
 
-// HERM update of component j (the formulas of herm_point for that component).
+// The off-diagonal entries of the HERM matrix at a point (herm_point):
+// a = c2 psi_-^* psi_0 + Ot, b = c2 psi_0^* psi_+ + Ot.
+__device__ __forceinline__ cx<double> herm_a(const cx<double> (&u)[3], double c2, double Ot) {
+    const cx<double> a = cmul(u[2], u[1]);
+    return {fma(c2, a.re, Ot), c2 * a.im};
+}
+__device__ __forceinline__ cx<double> herm_b(const cx<double> (&u)[3], double c2, double Ot) {
+    const cx<double> b = cmul(u[1], u[0]);
+    return {fma(c2, b.re, Ot), c2 * b.im};
+}
+
+// HERM update of component j (the formulas of herm_point for that component)
+// from the point's values u and its matrix entries a, b.
 template <bool IMAG>
-__device__ __forceinline__ cx<double> herm_comp(int j, const cx<double> (&u)[3], double c2, double Ot,
+__device__ __forceinline__ cx<double> herm_comp(int j, const cx<double> (&u)[3], cx<double> a, cx<double> b,
                                                 const KParams& p) {
-    cx<double> a = cmul(u[2], u[1]);  // psi_-^* psi_0
-    a = {fma(c2, a.re, Ot), c2 * a.im};
-    cx<double> b = cmul(u[1], u[0]);  // psi_0^* psi_+
-    b = {fma(c2, b.re, Ot), c2 * b.im};
     const double na = nrm(a), nb = nrm(b);
     const double C2 = na + nb;
     double s, k;
@@ -131,14 +149,25 @@ __device__ __forceinline__ cx<double> herm_comp(int j, const cx<double> (&u)[3],
 }
 
 struct Cl1dShared {
-    double2 st[3][32];            // the CTA's slice of the three lines (raw state)
-    double2 xX[3][32];            // SO: raw differences of each component
-    double2 xa[3][32], xb[3][32];  // values after SO (for CALCNU) and after CALCNU (for HERM)
-    double2 fA[3][kCl1dMaxQ], fB[3][kCl1dMaxQ];  // forward segment maps of the cluster's CTAs
-    double2 bA[3][kCl1dMaxQ], bB[3][kCl1dMaxQ];  // backward segment maps
-    double part[3][kCl1dMaxQ];                   // norm partials of the cluster's CTAs
+    double2 st[3][32];   // the CTA's slice of the three lines (raw state)
+    double2 xX[3][32];   // SO: raw differences of each component
+    double xr[3][32];    // densities after SO (for CALCNU)
+    double2 xb[3][32];   // values after CALCNU (for HERM)
+    double2 xab[2][32];  // the HERM entries a (from warp 0) and b (from warp 2)
+    // x sweep: the CTAs' segment maps y_end = A y_in + B (forward) and
+    // w_start = A w_next + B (backward); the factors A depend on the tables only
+    double2 fAs[kCl1dMaxQ], bAs[kCl1dMaxQ];
+    double2 fB[3][kCl1dMaxQ], bB[3][kCl1dMaxQ];
+    // weights of the earlier (forward) / later (backward) segments' B in this
+    // CTA's incoming carry, nearest first, cut where they fall below 2^-64
+    double2 wf[kCl1dMaxQ], wb[kCl1dMaxQ];
+    int nwf, nwb;
+    double part[3][kCl1dMaxQ];  // norm partials of the cluster's CTAs
+    double Nc[3];               // the summed norms
     double ds[3];
 };
+
+constexpr int kScanLv = 5;  // levels of a full 32-lane scan
 
 // Launched as one cluster of Q = ceil(nx/32) CTAs of kCl1dThreads threads
 // (grid Q, cluster Q), nx <= kCl1dMaxN. A: the state [3][nx]; t: the x tables
@@ -155,6 +184,7 @@ __global__ void __launch_bounds__(kCl1dThreads, 1)
     const int i = (int)q * 32 + lane;
     const bool valid = i < nx;
     const cx<double> zero = {0.0, 0.0};
+    cl_arrive_relaxed();  // matched by the cl_wait before the first store into a peer
     S.st[j][lane] = valid ? __ldcg(A + (size_t)j * nx + i) : make_double2(0.0, 0.0);
     if (threadIdx.x < 3) S.ds[threadIdx.x] = sc->scale[threadIdx.x];
     const int step0 = sc->step_idx;
@@ -165,8 +195,75 @@ __global__ void __launch_bounds__(kCl1dThreads, 1)
     const double c2 = p.kd[KC_C2];
     double dlast[3] = {S.ds[0], S.ds[1], S.ds[2]};
     bool finite = true;
+    // The x sweep's scan factors depend on the tables only: the factor each lane
+    // applies at each level (fw, bw), the number of levels (see tiny_carry) and
+    // the lane's composed factor, once for all steps.
+    cx<double> fw[kScanLv], bw[kScanLv], fAc, bAc;
+    int nlf = kScanLv, nlb = kScanLv;
+    {
+        cx<double> a = fg;
+#pragma unroll
+        for (int l = 0; l < kScanLv; l++) {
+            const int off = 1 << l;
+            fw[l] = a;
+            const cx<double> ap = shup(a, off);
+            if (lane >= off) a = tmul<IMAG>(a, ap);
+            if (scan_done(lane < 2 * off, a)) {
+                nlf = l + 1;
+                break;
+            }
+        }
+        fAc = a;
+        a = fg;
+#pragma unroll
+        for (int l = 0; l < kScanLv; l++) {
+            const int off = 1 << l;
+            bw[l] = a;
+            const cx<double> an = shdn(a, off);
+            if (lane + off < 32) a = tmul<IMAG>(a, an);
+            if (scan_done(lane + 2 * off >= 32, a)) {
+                nlb = l + 1;
+                break;
+            }
+        }
+        bAc = a;
+    }
+    const cx<double> fAu = shup(fAc, 1), bAd = shdn(bAc, 1);  // the neighbouring lanes' composed factors
+    cl_wait();  // every CTA of the cluster runs
+    if (j == 0 && lane == 31)
+        for (unsigned r = 0; r < Q; r++) *cl_map(&S.fAs[q], r) = pack(fAc);
+    if (j == 0 && lane == 0)
+        for (unsigned r = 0; r < Q; r++) *cl_map(&S.bAs[q], r) = pack(bAc);
     __syncthreads();
-    cl_sync();  // every CTA has loaded its slice: neighbours may be read
+    cl_sync();  // every CTA has loaded its slice (neighbours may be read) and published its factors
+    if (threadIdx.x == 0) {
+        // forward carry into CTA q: sum over r of wf[r] B(q - 1 - r), wf[r] = prod_{k<r} A(q - 1 - k)
+        cx<double> w = {1.0, 0.0};
+        int n = 0;
+        for (int r = 0; r < (int)q; r++) {
+            if (r > 0) {
+                w = tmul<IMAG>(w, unpack(S.fAs[q - r]));
+                if (tiny_carry(w.re) && tiny_carry(w.im)) break;
+            }
+            S.wf[r] = pack(w);
+            n = r + 1;
+        }
+        S.nwf = n;
+        // backward carry into CTA q: sum over r of wb[r] B(q + 1 + r), wb[r] = prod_{k<r} A(q + 1 + k)
+        w = {1.0, 0.0};
+        n = 0;
+        for (int r = 0; r + (int)q + 1 < (int)Q; r++) {
+            if (r > 0) {
+                w = tmul<IMAG>(w, unpack(S.bAs[q + r]));
+                if (tiny_carry(w.re) && tiny_carry(w.im)) break;
+            }
+            S.wb[r] = pack(w);
+            n = r + 1;
+        }
+        S.nwb = n;
+    }
+    __syncthreads();
+    const int nwf = S.nwf, nwb = S.nwb;
     for (int s = 0; s < nsteps; s++) {
         const double Ot = omega_tab ? __ldg(omega_tab + step0 + s) * 0.70710678118654752440 : p.kd[KC_OMEGA];
         // --- pointwise substeps of (point i, component j)
@@ -190,97 +287,76 @@ __global__ void __launch_bounds__(kCl1dThreads, 1)
             }
             u = so_comp<IMAG>(j, u, X, gx, p.so_case);
         }
-        S.xa[j][lane] = pack(u);
+        S.xr[j][lane] = nrm(u);
         __syncthreads();
-        {
-            const cx<double> w[3] = {unpack(S.xa[0][lane]), unpack(S.xa[1][lane]), unpack(S.xa[2][lane])};
-            u = calcnu_comp<IMAG>(j, u, w, Vn, p);
-        }
+        u = calcnu_comp<IMAG>(j, u, S.xr[0][lane], S.xr[1][lane], S.xr[2][lane], Vn, p);
         S.xb[j][lane] = pack(u);
         __syncthreads();
-        {
-            const cx<double> w[3] = {unpack(S.xb[0][lane]), unpack(S.xb[1][lane]), unpack(S.xb[2][lane])};
-            u = herm_comp<IMAG>(j, w, c2, Ot, p);
-        }
+        const cx<double> w[3] = {unpack(S.xb[0][lane]), unpack(S.xb[1][lane]), unpack(S.xb[2][lane])};
+        if (j == 0) S.xab[0][lane] = pack(herm_a(w, c2, Ot));
+        if (j == 2) S.xab[1][lane] = pack(herm_b(w, c2, Ot));
+        __syncthreads();
+        u = herm_comp<IMAG>(j, w, unpack(S.xab[0][lane]), unpack(S.xab[1][lane]), p);
         const cx<double> x = valid ? u : zero;  // the CN right-hand side
         // --- CN along x, forward: y_i = fa_i x_i + fg_i y_{i-1}
         const cx<double> yl = tmul<IMAG>(fa, x);
-        cx<double> sA = fg, sB = yl;
+        cx<double> sB = yl;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const cx<double> Ap = shup(sA, off), Bp = shup(sB, off);
-            if (lane >= off) {
-                sB = tfma<IMAG>(sA, Bp, sB);
-                sA = tmul<IMAG>(sA, Ap);
-            }
-            if (scan_done(lane < 2 * off, sA)) break;
+        for (int l = 0; l < kScanLv; l++) {
+            if (l >= nlf) break;
+            const int off = 1 << l;
+            const cx<double> Bp = shup(sB, off);
+            if (lane >= off) sB = tfma<IMAG>(fw[l], Bp, sB);
         }
         if (lane == 31)
-            for (unsigned r = 0; r < Q; r++) {
-                *cl_map(&S.fA[j][q], r) = pack(sA);
-                *cl_map(&S.fB[j][q], r) = pack(sB);
-            }
+            for (unsigned r = 0; r < Q; r++) *cl_map(&S.fB[j][q], r) = pack(sB);
         cl_sync();
         // y at the last point of the previous CTAs' segments
         cx<double> cinC = zero;
         if (q > 0) {
             cinC = unpack(S.fB[j][q - 1]);
-            cx<double> w = unpack(S.fA[j][q - 1]);
-            for (int r = (int)q - 2; r >= 0; r--) {
-                if (tiny_carry(w.re) && tiny_carry(w.im)) break;
-                cinC = tfma<IMAG>(w, unpack(S.fB[j][r]), cinC);
-                w = tmul<IMAG>(w, unpack(S.fA[j][r]));
-            }
+            for (int r = 1; r < nwf; r++) cinC = tfma<IMAG>(unpack(S.wf[r]), unpack(S.fB[j][q - 1 - r]), cinC);
         }
-        const cx<double> Au = shup(sA, 1), Bu = shup(sB, 1);
-        const cx<double> yprev = lane == 0 ? cinC : tfma<IMAG>(Au, cinC, Bu);
+        const cx<double> Bu = shup(sB, 1);
+        const cx<double> yprev = lane == 0 ? cinC : tfma<IMAG>(fAu, cinC, Bu);
         const cx<double> y = tfma<IMAG>(fg, yprev, yl);
         // --- backward: w_i = y_i + fg_i w_{i+1}
-        sA = fg;
         sB = y;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const cx<double> An = shdn(sA, off), Bn = shdn(sB, off);
-            if (lane + off < 32) {
-                sB = tfma<IMAG>(sA, Bn, sB);
-                sA = tmul<IMAG>(sA, An);
-            }
-            if (scan_done(lane + 2 * off >= 32, sA)) break;
+        for (int l = 0; l < kScanLv; l++) {
+            if (l >= nlb) break;
+            const int off = 1 << l;
+            const cx<double> Bn = shdn(sB, off);
+            if (lane + off < 32) sB = tfma<IMAG>(bw[l], Bn, sB);
         }
         if (lane == 0)
-            for (unsigned r = 0; r < Q; r++) {
-                *cl_map(&S.bA[j][q], r) = pack(sA);
-                *cl_map(&S.bB[j][q], r) = pack(sB);
-            }
+            for (unsigned r = 0; r < Q; r++) *cl_map(&S.bB[j][q], r) = pack(sB);
         cl_sync();
         cx<double> cbC = zero;
         if (q + 1 < Q) {
             cbC = unpack(S.bB[j][q + 1]);
-            cx<double> w = unpack(S.bA[j][q + 1]);
-            for (unsigned r = q + 2; r < Q; r++) {
-                if (tiny_carry(w.re) && tiny_carry(w.im)) break;
-                cbC = tfma<IMAG>(w, unpack(S.bB[j][r]), cbC);
-                w = tmul<IMAG>(w, unpack(S.bA[j][r]));
-            }
+            for (int r = 1; r < nwb; r++) cbC = tfma<IMAG>(unpack(S.wb[r]), unpack(S.bB[j][q + 1 + r]), cbC);
         }
-        const cx<double> An = shdn(sA, 1), Bn = shdn(sB, 1);
-        const cx<double> wnext = lane == 31 ? cbC : tfma<IMAG>(An, cbC, Bn);
+        const cx<double> Bn = shdn(sB, 1);
+        const cx<double> wnext = lane == 31 ? cbC : tfma<IMAG>(bAd, cbC, Bn);
         const cx<double> wv = tfma<IMAG>(fg, wnext, y);
         const cx<double> o = valid ? cx<double>{fma(2.0, wv.re, -x.re), fma(2.0, wv.im, -x.im)} : zero;
         S.st[j][lane] = pack(o);
-        // --- norm partials to every CTA, then the same scale everywhere
+        // --- norm partials to every CTA; every CTA sums them in the same order
         const double pn = warp_sum(nrm(o));
         if (lane == 0)
             for (unsigned r = 0; r < Q; r++) *cl_map(&S.part[j][q], r) = pn;
         cl_sync();
+        {
+            double v = lane < (int)Q ? S.part[j][lane] : 0.0;  // Q <= 8: lanes 0..7
+            v += __shfl_xor_sync(0xffffffffu, v, 4);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            if (lane == 0) S.Nc[j] = v * p.cell;
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
-            double N[3];
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                double acc = 0.0;
-                for (unsigned r = 0; r < Q; r++) acc += S.part[k][r];
-                N[k] = acc * p.cell;
-            }
+            double N[3] = {S.Nc[0], S.Nc[1], S.Nc[2]};
             const bool fin = isfinite(N[0]) && isfinite(N[1]) && isfinite(N[2]);
             finite = finite && fin;
             double dn[3];
