@@ -287,8 +287,16 @@ template <typename R, int C> constexpr size_t pwx_smem_bytes() {
     return (size_t)3 * 32 * (C + 1) * sizeof(typename V2<R>::T);
 }
 
+// Two blocks per SM (at most 128 registers a thread) for rows of up to 512
+// points, except the complex64 real-time form at 512 points, which measured
+// faster with one block and its unconstrained registers (512^2 real time:
+// complex128 199 -> 179, double-float 154 -> 94, complex64 63 -> 67 us/step).
+template <typename R, int C, bool IMAG> constexpr int pwx_min_blocks() {
+    return (C <= 8 || (C <= 16 && !(sizeof(R) == 4 && !IMAG))) ? 2 : 1;
+}
+
 template <typename R, bool IMAG, int C>
-__global__ void __launch_bounds__(kPwxThreads, C <= 8 ? 2 : 1)
+__global__ void __launch_bounds__(kPwxThreads, pwx_min_blocks<R, C, IMAG>())
     k_pwx(const typename V2<R>::T* __restrict__ A, typename V2<R>::T* __restrict__ B, KParams p,
           const DevScalars* __restrict__ sc, const double* __restrict__ omega_tab, Tabs<R> t,
           const double* __restrict__ partials, int m, int renorm) {
