@@ -327,12 +327,20 @@ sgpe_status sgpe_batch_step_real(sgpe_batch* b, int nsteps);
 sgpe_status sgpe_batch_energy(sgpe_batch* b, double* out);
 
 /*
- * Choose the warps per block of the two sweeps (1, 2 or 4 each) by timing
- * nsteps imaginary-time steps per candidate with CUDA events; writes the
- * choice to choice[0..1] (nullable). Advances the bound state by 9 * (nsteps + 1)
- * steps: tune before loading the state to be advanced. Synchronises.
+ * Choose the launch shape by timing nsteps imaginary-time steps per candidate
+ * with CUDA events: the x part (0: pointwise substeps and x sweep fused, one
+ * 256-thread block per row, the default; 1, 2 or 4: warps per block of a
+ * separate x sweep after a pointwise kernel) and the warps per block of the y
+ * sweep (1, 2 or 4). Writes the choice to choice[0..1] (nullable). Advances the
+ * bound state by 12 * (nsteps + 1) steps: tune before loading the state to be
+ * advanced. Synchronises.
  */
 sgpe_status sgpe_batch_autotune(sgpe_batch* b, int nsteps, int* choice);
+
+/* Set the launch shape directly (x in {0, 1, 2, 4}, y in {1, 2, 4}, as chosen by
+ * sgpe_batch_autotune); SGPE_EINVAL otherwise. Results do not depend on it
+ * beyond rounding. */
+sgpe_status sgpe_batch_set_tiles(sgpe_batch* b, int x, int y);
 
 /* Kernel launches per batched step; last error of a batch; release (not the buffers). */
 int sgpe_batch_launches_per_step(const sgpe_batch* b);

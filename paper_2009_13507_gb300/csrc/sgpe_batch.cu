@@ -69,6 +69,60 @@ __global__ void __launch_bounds__(128) kb_pointwise(const typename V2<R>::T* __r
     pointwise_at<R, IMAG>(A + I.off, B + I.off, I.p, scs + tl.x, kc<R>(I.p, KC_OMEGA), ix, iy, 7);
 }
 
+// Fused row kernel (the batched form of k_pwx): one block per row of one
+// instance, work entry (instance, row iy, first partial slot or -1). The
+// pointwise substeps (pending scale of the instance, SO, CALCNU, HERM) of the
+// row's points are staged in shared memory in the lanes' chunk layout, then
+// warp j solves the x line of component j. 2D rows go to B for the y sweep; a 1D
+// instance is one row, written back to A in place (every read of the row is done
+// before the staging barrier) with its three norm partials.
+template <typename R, bool IMAG, int C>
+__global__ void __launch_bounds__(kPwxThreads, pwx_min_blocks<R, C, IMAG>())
+    kb_pwx(typename V2<R>::T* A, typename V2<R>::T* B, const BInst* __restrict__ insts,
+           const typename V2<R>::T* __restrict__ pool, const int4* __restrict__ rows,
+           const DevScalars* __restrict__ scs, double* partials) {
+    using T = typename V2<R>::T;
+    extern __shared__ __align__(16) unsigned char kbpwx_smem[];
+    T* row = reinterpret_cast<T*>(kbpwx_smem);
+    __shared__ R ds[3];
+    constexpr int S = 32 * (C + 1);
+    constexpr int PPT = (32 * C + kPwxThreads - 1) / kPwxThreads;
+    const int4 e = rows[blockIdx.x];
+    const BInst& I = insts[e.x];
+    const KParams& p = I.p;
+    const int iy = e.y, nx = p.nx;
+    const int warp = threadIdx.x >> 5;
+    PointIn<R> in[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        const int ix = threadIdx.x + k * kPwxThreads;
+        if (ix < nx) pointwise_load<R>(A + I.off, p, ix, iy, p.so_case != 0, in[k]);
+    }
+    if (threadIdx.x < 3) ds[threadIdx.x] = scale_of<R>(scs + e.x, threadIdx.x);
+    __syncthreads();
+    const R Ot = kc<R>(p, KC_OMEGA);
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        const int ix = threadIdx.x + k * kPwxThreads;
+        if (ix < nx) {
+            cx<R> u[3];
+            pointwise_apply<R, IMAG>(in[k], p, ds, Ot, ix, iy, 7, u);
+            const int slot = (ix / C) * (C + 1) + (ix % C);
+#pragma unroll
+            for (int j = 0; j < 3; j++) row[j * S + slot] = pack(u[j]);
+        }
+    }
+    __syncthreads();
+    if (warp < 3) {
+        const T* r = row + warp * S;
+        const Tabs<R> t = inst_tabs<R>(pool, I, IMAG ? 0 : 1, 0);
+        T* out = (p.dim == 2 ? B : A) + I.off;
+        const size_t base = ((size_t)warp * p.ny + iy) * nx;
+        cnx_solve_line<R, IMAG, C>([&](int i) { return unpack(r[(i / C) * (C + 1) + (i % C)]); }, out, base, nx, t,
+                                   e.z >= 0 ? partials + e.z + warp : nullptr);
+    }
+}
+
 // Work entry of the x sweep: (instance, line, partial slot or -1).
 template <typename R, bool IMAG, int C>
 __global__ void kb_cnx(typename V2<R>::T* A, typename V2<R>::T* B, const BInst* __restrict__ insts,
@@ -205,17 +259,18 @@ struct sgpe_batch {
     std::vector<sgpe_instance> inst;
     std::vector<BInst> hinst;
     std::vector<int2> tiles;
-    std::map<int, std::vector<int4>> cnx, cny;  // work lists by chunk length
+    std::map<int, std::vector<int4>> cnx, cny, rows;  // work lists by chunk length (rows: the fused x part)
     size_t state_elems;
     long long tab_elems;
     int nslots;
     // workspace layout (byte offsets)
     size_t o_inst, o_sc, o_tiles, o_part, o_tab, o_mid, total;
-    std::map<int, size_t> o_cnx, o_cny;
+    std::map<int, size_t> o_cnx, o_cny, o_rows;
     // bound buffers
     void* psi;
     unsigned char* work;
-    // launch shape (warps per block of the x / y sweeps)
+    // launch shape: x part (0: the fused row kernel; 1, 2 or 4: warps per block of
+    // the separate x sweep after the pointwise kernel), warps per block of the y sweep
     int wx, wy;
     std::map<BGraphKey, cudaGraphExec_t> graphs;
     bool graphs_ok;
@@ -245,6 +300,23 @@ static void binvalidate(sgpe_batch* b) {
     b->graphs.clear();
 }
 
+template <typename R, bool IMAG, int C>
+static void kb_pwx_c(dim3 grid, dim3 block, cudaStream_t s, typename V2<R>::T* A, typename V2<R>::T* B,
+                     const BInst* I, const typename V2<R>::T* pool, const int4* w, const DevScalars* sc,
+                     double* part) {
+    kb_pwx<R, IMAG, C><<<grid, block, pwx_smem_bytes<R, C>(), s>>>(A, B, I, pool, w, sc, part);
+}
+
+// Shared-memory allowance of the fused row kernels (rows of 1024 points stage 51 KB).
+template <typename R, bool IMAG> static cudaError_t kb_pwx_allow() {
+    cudaError_t e = cudaSuccess;
+    if (!e) e = cudaFuncSetAttribute(kb_pwx<R, IMAG, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)pwx_smem_bytes<R, 16>());
+    if (!e) e = cudaFuncSetAttribute(kb_pwx<R, IMAG, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)pwx_smem_bytes<R, 32>());
+    return e;
+}
+
 // Enqueue one step for all instances.
 template <typename R, bool IMAG>
 static cudaError_t benqueue_step(sgpe_batch* b) {
@@ -256,8 +328,24 @@ static cudaError_t benqueue_step(sgpe_batch* b) {
     const int2* tiles = (const int2*)(b->work + b->o_tiles);
     double* part = (double*)(b->work + b->o_part);
     const T* pool = (const T*)(b->work + b->o_tab);
-    kb_pointwise<R, IMAG><<<(unsigned)b->tiles.size(), 128, 0, b->stream>>>(A, B, I, tiles, sc);
+    if (b->wx == 0) {
+        for (auto& kv : b->rows) {
+            const int4* w = (const int4*)(b->work + b->o_rows[kv.first]);
+            const dim3 grid((unsigned)kv.second.size()), block(kPwxThreads);
+            switch (kv.first) {
+                case 1: kb_pwx_c<R, IMAG, 1>(grid, block, b->stream, A, B, I, pool, w, sc, part); break;
+                case 2: kb_pwx_c<R, IMAG, 2>(grid, block, b->stream, A, B, I, pool, w, sc, part); break;
+                case 4: kb_pwx_c<R, IMAG, 4>(grid, block, b->stream, A, B, I, pool, w, sc, part); break;
+                case 8: kb_pwx_c<R, IMAG, 8>(grid, block, b->stream, A, B, I, pool, w, sc, part); break;
+                case 16: kb_pwx_c<R, IMAG, 16>(grid, block, b->stream, A, B, I, pool, w, sc, part); break;
+                default: kb_pwx_c<R, IMAG, 32>(grid, block, b->stream, A, B, I, pool, w, sc, part); break;
+            }
+        }
+    } else {
+        kb_pointwise<R, IMAG><<<(unsigned)b->tiles.size(), 128, 0, b->stream>>>(A, B, I, tiles, sc);
+    }
     for (auto& kv : b->cnx) {
+        if (b->wx == 0) break;  // fused into kb_pwx
         const int4* w = (const int4*)(b->work + b->o_cnx[kv.first]);
         int nw = (int)kv.second.size();
         dim3 grid((nw + b->wx - 1) / b->wx), block(32 * b->wx);
@@ -391,7 +479,7 @@ sgpe_status sgpe_batch_create(sgpe_batch** out, int n, const sgpe_instance* inst
     b->inst.assign(inst, inst + n);
     b->psi = nullptr;
     b->work = nullptr;
-    b->wx = 1;
+    b->wx = 0;
     b->wy = 1;
     b->graphs_ok = true;
     b->err[0] = 0;
@@ -421,9 +509,11 @@ sgpe_status sgpe_batch_create(sgpe_batch** out, int n, const sgpe_instance* inst
         if (q.dim == 1) {
             I.nslot = 3;
             for (int l = 0; l < 3; l++) b->cnx[Cx].push_back(make_int4(i, l, slot + l, 0));
+            b->rows[Cx].push_back(make_int4(i, 0, slot, 0));
             slot += 3;
         } else {
             for (int l = 0; l < 3 * q.ny; l++) b->cnx[Cx].push_back(make_int4(i, l, -1, 0));
+            for (int r = 0; r < q.ny; r++) b->rows[Cx].push_back(make_int4(i, r, -1, 0));
             const int Cy = chunk_len(q.ny);
             const int K = cny_cols_per_warp(Cy, b->esz);
             int cnt = 0;
@@ -450,6 +540,10 @@ sgpe_status sgpe_batch_create(sgpe_batch** out, int n, const sgpe_instance* inst
     }
     for (auto& kv : b->cny) {
         b->o_cny[kv.first] = o;
+        o = al256(o + sizeof(int4) * kv.second.size());
+    }
+    for (auto& kv : b->rows) {
+        b->o_rows[kv.first] = o;
         o = al256(o + sizeof(int4) * kv.second.size());
     }
     b->o_part = o;
@@ -496,6 +590,16 @@ sgpe_status sgpe_batch_bind(sgpe_batch* b, void* psi_dev, void* workspace_dev) {
     for (auto& kv : b->cny)
         BCK(cudaMemcpyAsync(b->work + b->o_cny[kv.first], kv.second.data(), sizeof(int4) * kv.second.size(),
                             cudaMemcpyHostToDevice, s), "copy");
+    for (auto& kv : b->rows)
+        BCK(cudaMemcpyAsync(b->work + b->o_rows[kv.first], kv.second.data(), sizeof(int4) * kv.second.size(),
+                            cudaMemcpyHostToDevice, s), "copy");
+    if (b->prec == SGPE_C128) {
+        BCK((kb_pwx_allow<double, true>()), "kernel attributes");
+        BCK((kb_pwx_allow<double, false>()), "kernel attributes");
+    } else {
+        BCK((kb_pwx_allow<float, true>()), "kernel attributes");
+        BCK((kb_pwx_allow<float, false>()), "kernel attributes");
+    }
     DevScalars* sc = (DevScalars*)(b->work + b->o_sc);
     kb_reset<<<(b->n + 127) / 128, 128, 0, s>>>(sc, b->n, 1);
     BCK(cudaGetLastError(), "reset");
@@ -579,15 +683,15 @@ sgpe_status sgpe_batch_autotune(sgpe_batch* b, int nsteps, int* choice) {
     if (!b) return SGPE_EINVAL;
     if (!b->psi) return bfail(b, SGPE_ESTATE, "no buffers bound");
     if (nsteps < 1) return bfail(b, SGPE_EINVAL, "nsteps < 1");
-    const int cand[3] = {1, 2, 4};
+    const int candx[4] = {0, 1, 2, 4}, cand[3] = {1, 2, 4};
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0), "event");
     BCK(cudaEventCreate(&e1), "event");
     float best = 1e30f;
-    int bx = 1, by = 1;
-    for (int ix = 0; ix < 3; ix++)
+    int bx = 0, by = 1;
+    for (int ix = 0; ix < 4; ix++)
         for (int iy = 0; iy < 3; iy++) {
-            b->wx = cand[ix];
+            b->wx = candx[ix];
             b->wy = cand[iy];
             binvalidate(b);
             BCK(benqueue_steps(b, 1, true), "warm-up");
@@ -599,7 +703,7 @@ sgpe_status sgpe_batch_autotune(sgpe_batch* b, int nsteps, int* choice) {
             cudaEventElapsedTime(&ms, e0, e1);
             if (ms < best) {
                 best = ms;
-                bx = cand[ix];
+                bx = candx[ix];
                 by = cand[iy];
             }
         }
@@ -617,8 +721,19 @@ sgpe_status sgpe_batch_autotune(sgpe_batch* b, int nsteps, int* choice) {
     return SGPE_OK;
 }
 
+sgpe_status sgpe_batch_set_tiles(sgpe_batch* b, int x, int y) {
+    if (!b) return SGPE_EINVAL;
+    if ((x != 0 && x != 1 && x != 2 && x != 4) || (y != 1 && y != 2 && y != 4))
+        return bfail(b, SGPE_EINVAL, "sgpe_batch_set_tiles: x in {0, 1, 2, 4}, y in {1, 2, 4}");
+    b->wx = x;
+    b->wy = y;
+    binvalidate(b);
+    return SGPE_OK;
+}
+
 int sgpe_batch_launches_per_step(const sgpe_batch* b) {
     if (!b) return 0;
+    if (b->wx == 0) return 1 + (int)b->rows.size() + (int)b->cny.size();
     return 2 + (int)b->cnx.size() + (int)b->cny.size();
 }
 

@@ -33,7 +33,8 @@ EXPORTS = ("sgpe_init_grid", "sgpe_workspace_bytes", "sgpe_bind", "sgpe_set_para
            "sgpe_last_error", "sgpe_destroy", "sgpe_adjoint_workspace_bytes", "sgpe_adjoint_loss_grad",
            "sgpe_batch_create", "sgpe_batch_sizes", "sgpe_batch_offsets", "sgpe_batch_bind",
            "sgpe_batch_load_state", "sgpe_batch_step_imag", "sgpe_batch_step_real", "sgpe_batch_energy",
-           "sgpe_batch_autotune", "sgpe_batch_launches_per_step", "sgpe_batch_last_error", "sgpe_batch_destroy")
+           "sgpe_batch_autotune", "sgpe_batch_set_tiles", "sgpe_batch_launches_per_step", "sgpe_batch_last_error",
+           "sgpe_batch_destroy")
 
 
 class SgpeError(RuntimeError):
@@ -89,6 +90,7 @@ def load():
         "sgpe_batch_step_real": (I, [P, I]),
         "sgpe_batch_energy": (I, [P, P]),
         "sgpe_batch_autotune": (I, [P, I, P]),
+        "sgpe_batch_set_tiles": (I, [P, I, I]),
         "sgpe_batch_launches_per_step": (I, [P]),
         "sgpe_batch_last_error": (ctypes.c_char_p, [P]),
         "sgpe_batch_destroy": (I, [P]),
@@ -408,6 +410,11 @@ class BatchSolver:
         ch = np.zeros(2, dtype=np.int32)
         self._check(self.lib.sgpe_batch_autotune(self.b, int(nsteps), ch.ctypes.data))
         return int(ch[0]), int(ch[1])
+
+    def set_tiles(self, x, y):
+        """Launch shape: x part 0 (fused row kernel) or 1/2/4 warps per block of a separate x sweep;
+        y sweep 1/2/4 warps per block."""
+        self._check(self.lib.sgpe_batch_set_tiles(self.b, int(x), int(y)))
 
     def launches_per_step(self):
         return int(self.lib.sgpe_batch_launches_per_step(self.b))

@@ -35,10 +35,13 @@ SMALL = [
 ]
 
 
+@pytest.mark.parametrize("tiles", [(0, 1), (2, 2)])
 @pytest.mark.parametrize("precision", ["c128", "c64"])
-def test_small_uneven_batch_matches_oracle(precision):
+def test_small_uneven_batch_matches_oracle(precision, tiles):
+    """Both x parts: the fused row kernel (0) and pointwise kernel + separate x sweep (2 warps per block)."""
     import torch
     bs = sgpe.BatchSolver(SMALL, precision=precision)
+    bs.set_tiles(*tiles)
     states = [_initial(s, 10 + i) for i, s in enumerate(bs.specs)]
     bs.load_state(bs.pack(states))
     bs.step_imag(30)
@@ -69,7 +72,7 @@ def test_batch_workload_sampled_against_oracle():
         inst.append(d)
     bs = sgpe.BatchSolver(inst, precision="c128")
     choice = bs.autotune(2)
-    assert all(c in (1, 2, 4) for c in choice)
+    assert choice[0] in (0, 1, 2, 4) and choice[1] in (1, 2, 4)
     states = [_initial(s, 100 + i) for i, s in enumerate(bs.specs)]
     bs.load_state(bs.pack(states))
     bs.step_imag(12)
@@ -85,6 +88,18 @@ def test_batch_workload_sampled_against_oracle():
         assert relerr(got[i], ref) < 1e-10, i
         assert abs(obs[i, 5] - O.observables(prob, ref)["E"]) < 1e-10 * abs(obs[i, 5])
     assert np.all(np.abs(obs[:, 3] - 1.0) < 1e-12)  # every instance renormalised
+
+
+def test_batch_set_tiles_rejects_bad_shapes():
+    bs = sgpe.BatchSolver(SMALL[:2], precision="c128")
+    for x, y in ((3, 1), (0, 0), (8, 2), (-1, 1)):
+        with pytest.raises(sgpe.SgpeError) as e:
+            bs.set_tiles(x, y)
+        assert e.value.status == sgpe.EINVAL
+    bs.set_tiles(4, 4)
+    n_sep = bs.launches_per_step()
+    bs.set_tiles(0, 4)
+    assert bs.launches_per_step() < n_sep  # the fused row kernel replaces the pointwise kernel
 
 
 def test_batch_rejects_bad_instances():

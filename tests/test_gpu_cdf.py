@@ -167,11 +167,12 @@ def test_unsupported_entry_points_say_so():
     assert rc == sgpe.EUNSUPPORTED
 
 
-@pytest.mark.parametrize("precision", ["cdf", "c64"])
+@pytest.mark.parametrize("precision", ["cdf", "c64", "c128"])
 def test_1d_one_block_loop_split_calls(precision):
-    """1D grids in the FP32-pipe forms run the whole loop in one block; two calls
-    of 7 steps continue exactly where one call of 14 goes (the pending scale
-    and the step counter are handed over between calls)."""
+    """1D grids run the whole loop in one launch (one block in the FP32-pipe
+    forms, one cluster in complex128); two calls of 7 steps continue exactly
+    where one call of 14 goes (the pending scale and the step counter are
+    handed over between calls)."""
     prob, s = make_pair(1, 200, 1, dx=0.06, precision=precision, **PHYS_1D)
     psi = I.gaussian_jitter_1d(200, 0.06, seed=4)
     s.set_state(psi)
@@ -183,10 +184,11 @@ def test_1d_one_block_loop_split_calls(precision):
     assert np.array_equal(a, s.get_state())
 
 
-def test_1d_one_block_loop_omega_table_cdf():
+@pytest.mark.parametrize("precision", ["cdf", "c128"])
+def test_1d_one_block_loop_omega_table(precision):
     import torch
     phys = dict(PHYS_1D, renorm=0)
-    prob, s = make_pair(1, 256, 1, dx=0.05, precision="cdf", **phys)
+    prob, s = make_pair(1, 256, 1, dx=0.05, precision=precision, **phys)
     psi = I.gaussian_jitter_1d(256, 0.05, seed=6)
     om = 0.3 * np.sin(np.linspace(0, 4, 80)) + 0.1 * I.uniform(11, 80)
     s.set_state(psi)

@@ -168,9 +168,12 @@ def test_fixed_magnetisation_renorm_2d(precision, tol):
     assert abs(o["N"] - 1) < 1e-12 and abs(o["mag"] - 0.3) < 1e-12
 
 
-@pytest.mark.parametrize("dim,nx,ny", [(2, 3, 3), (2, 5, 7), (2, 17, 3), (2, 33, 65), (1, 3, 1), (1, 33, 1),
-                                       (1, 1000, 1), (2, 4096, 3), (2, 3, 4096)])
+@pytest.mark.parametrize("dim,nx,ny", [(2, 3, 3), (2, 5, 7), (2, 17, 3), (2, 33, 65), (1, 3, 1), (1, 32, 1),
+                                       (1, 33, 1), (1, 224, 1), (1, 256, 1), (1, 257, 1), (1, 1000, 1),
+                                       (2, 4096, 3), (2, 3, 4096)])
 def test_edge_sizes(dim, nx, ny):
+    """Ragged and extreme grids. 1D complex128 lines of 32 (one CTA), 224, 256 (the largest) points run
+    the one-cluster step loop; 257 and 1000 the three-launch path."""
     prob, s = make_pair(dim, nx, ny, dx=0.1, **(PHYS_2D if dim == 2 else PHYS_1D))
     psi = _rand(prob, nx * 7 + ny, env=2.0)
     s.set_state(psi)
