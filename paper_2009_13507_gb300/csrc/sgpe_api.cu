@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <map>
+#include <algorithm>
 #include <vector>
 #include <tuple>
 
@@ -24,20 +25,21 @@ Geometry make_geometry(int dim, int nx, int ny, int esz) {
     g.nx = nx;
     g.ny = ny;
     g.esz = esz;
-    // x sweep: register kernel (4 lines per block) up to kRegMaxN points, else shared-memory kernel
+    // x sweep: register kernel (one warp per line) up to kRegMaxN points; longer
+    // lines: one block of long_warps(nx) warps per line, the line staged in
+    // shared memory (32 * nw chunks of kLongC + 1 entries)
     g.reg_x = nx <= kRegMaxN;
     g.fused = dim == 2 && g.reg_x;
-    size_t per_warp_x = (size_t)(32 * chunk_stride(nx) + 32) * esz;
-    g.wx = 4;
-    while (!g.reg_x && g.wx > 1 && g.wx * per_warp_x > 96 * 1024) g.wx >>= 1;
-    g.smem_x = g.reg_x ? 0 : g.wx * per_warp_x;
-    g.blocks_x = g.reg_x ? 3 * ny : ceil_div(3 * ny, g.wx);
-    // y sweep: register kernel (4 columns per block, 2 per warp), else shared-memory kernel
+    g.wx = g.reg_x ? 1 : long_warps(nx);
+    g.smem_x = g.reg_x ? 0 : (size_t)32 * g.wx * (kLongC + 1) * esz;
+    g.blocks_x = 3 * ny;
+    // y sweep: register kernel up to kRegMaxN points; longer columns: tiles of wy
+    // adjacent columns (a 32-byte row segment where the block stays within
+    // kLongMaxWarps warps), long_warps(ny) warps per column
     g.reg_y = ny <= kRegMaxN;
-    size_t per_warp_y = (size_t)(32 * chunk_stride(ny) + 32) * esz;
-    g.wy = 2;
-    while (!g.reg_y && g.wy > 1 && g.wy * per_warp_y > 160 * 1024) g.wy >>= 1;
-    g.smem_y = g.reg_y ? 0 : g.wy * per_warp_y;
+    const int nwy = long_warps(ny);
+    g.wy = g.reg_y ? 1 : std::max(1, std::min(32 / esz, kLongMaxWarps / nwy));
+    g.smem_y = g.reg_y ? 0 : (size_t)g.wy * 32 * nwy * (kLongC + 1) * esz;
     g.blocks_y = dim == 2 ? 3 * ceil_div(nx, g.reg_y ? cny_cols_per_warp(chunk_len(ny), esz) : g.wy) : 0;
     g.blocks_obs = ceil_div(nx, 32) * ceil_div(ny, 4);
     g.blocks_norm = kNormBlocks;

@@ -593,4 +593,231 @@ __global__ void __launch_bounds__(32) k_cny_reg(const typename V2<R>::T* in, typ
     cny_cols<R, IMAG, C, P>(in, out, p, t, j, col, parts ? parts + blockIdx.x : nullptr);
 }
 
+// ---------------------------------------------------------------------------
+// Crank-Nicolson sweeps for lines longer than 1024 points (Sec. 3 LU / LUX /
+// LUY). A line of n points is held by a group of nw = ceil(n / 512) warps, 16
+// points per lane (lane g = part * 32 + lane of the group owns points
+// [16 g, 16 g + 16)), staged in shared memory in a padded chunk layout (stride
+// 17: conflict-free chunk reads). Each lane runs the forward and backward
+// recurrences of its chunk with the precomputed LU factors (chunk products fp,
+// fq over 16-point chunks); the chunk maps are composed by shuffles inside each
+// warp and then across the group's warps through shared memory, both
+// compositions stopping once the composed factor is negligible (tiny_carry).
+// ---------------------------------------------------------------------------
+constexpr int kLongS = kLongC + 1;  // padded chunk stride (shared memory)
+__device__ __forceinline__ int long_slot(int i) { return (i >> 4) * kLongS + (i & (kLongC - 1)); }
+
+// Solve T w = x for the lane's chunk v (in: x, out: w) at points [i0, i0 + 16)
+// of a line held by the nw warps of a group; part: this warp's index in the
+// group; seg: the group's shared scratch of 4 nw entries. Every thread of the
+// block must call this (block barriers inside).
+template <typename R, bool IMAG>
+__device__ __forceinline__ void group_solve(cx<R> (&v)[kLongC], const Tabs<R>& t, int i0, int part, int nw,
+                                            cx<R>* seg) {
+    const int lane = threadIdx.x & 31;
+    const cx<R> zero = {R(0), R(0)};
+    cx<R> y = zero;
+#pragma unroll
+    for (int m = 0; m < kLongC; m++) {
+        y = tfma<IMAG>(tld<R>(t.fg, i0 + m), y, tmul<IMAG>(tld<R>(t.fa, i0 + m), v[m]));
+        v[m] = y;
+    }
+    cx<R> A = tld<R>(t.fp, i0 + kLongC - 1), B = y;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const cx<R> Ap = shup(A, off), Bp = shup(B, off);
+        if (lane >= off) {
+            B = tfma<IMAG>(A, Bp, B);
+            A = tmul<IMAG>(A, Ap);
+        }
+        if (scan_done(lane < 2 * off, A)) break;
+    }
+    if (lane == 31) {
+        seg[part] = A;
+        seg[nw + part] = B;
+    }
+    __syncthreads();
+    // y at the last point of the group's earlier warps
+    cx<R> cw = zero;
+    if (part > 0) {
+        cw = seg[nw + part - 1];
+        cx<R> wgt = seg[part - 1];
+        for (int r = part - 2; r >= 0; r--) {
+            if (tiny_carry(wgt.re) && tiny_carry(wgt.im)) break;
+            cw = tfma<IMAG>(wgt, seg[nw + r], cw);
+            wgt = tmul<IMAG>(wgt, seg[r]);
+        }
+    }
+    const cx<R> Au = shup(A, 1), Bu = shup(B, 1);
+    const cx<R> cin = lane == 0 ? cw : tfma<IMAG>(Au, cw, Bu);
+    cx<R> w = zero;
+#pragma unroll
+    for (int m = kLongC - 1; m >= 0; m--) {
+        const cx<R> yi = tfma<IMAG>(tld<R>(t.fp, i0 + m), cin, v[m]);
+        w = tfma<IMAG>(tld<R>(t.fg, i0 + m), w, yi);
+        v[m] = w;
+    }
+    A = tld<R>(t.fq, i0);
+    B = w;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const cx<R> An = shdn(A, off), Bn = shdn(B, off);
+        if (lane + off < 32) {
+            B = tfma<IMAG>(A, Bn, B);
+            A = tmul<IMAG>(A, An);
+        }
+        if (scan_done(lane + 2 * off >= 32, A)) break;
+    }
+    if (lane == 0) {
+        seg[2 * nw + part] = A;
+        seg[3 * nw + part] = B;
+    }
+    __syncthreads();
+    // w at the first point of the group's later warps
+    cx<R> cbw = zero;
+    if (part + 1 < nw) {
+        cbw = seg[3 * nw + part + 1];
+        cx<R> wgt = seg[2 * nw + part + 1];
+        for (int r = part + 2; r < nw; r++) {
+            if (tiny_carry(wgt.re) && tiny_carry(wgt.im)) break;
+            cbw = tfma<IMAG>(wgt, seg[3 * nw + r], cbw);
+            wgt = tmul<IMAG>(wgt, seg[2 * nw + r]);
+        }
+    }
+    const cx<R> An = shdn(A, 1), Bn = shdn(B, 1);
+    const cx<R> cb = lane == 31 ? cbw : tfma<IMAG>(An, cbw, Bn);
+#pragma unroll
+    for (int m = 0; m < kLongC; m++) v[m] = tfma<IMAG>(tld<R>(t.fq, i0 + m), cb, v[m]);
+}
+
+// The sweep of one staged line: lane chunk in from shared memory (line, padded
+// layout), solve, and the result o written back to the lane's own slots.
+// complex64: increment form o = x + 2 e, T e = bt L x (the differences of
+// neighbouring values exact); otherwise o = 2 w - x. Returns |o|^2 summed over
+// the lane's points (for the norm partials).
+template <typename R, bool IMAG>
+__device__ __forceinline__ double long_line(cx<R>* line, int n, const Tabs<R>& t, int part, int nw, cx<R>* seg) {
+    const int i0 = (part * 32 + (threadIdx.x & 31)) * kLongC;
+    constexpr bool INC = sizeof(R) == 4;
+    const cx<R> zero = {R(0), R(0)};
+    cx<R> v[kLongC];
+#pragma unroll
+    for (int m = 0; m < kLongC; m++) v[m] = line[long_slot(i0 + m)];
+    if constexpr (INC) {
+        const cx<R> a0 = tld<R>(t.fa, 0), g0 = tld<R>(t.fg, 0);
+        cx<R> bt;
+        if (IMAG) {
+            bt = {g0.re / a0.re, R(0)};
+        } else {
+            const R den = nrm(a0);
+            const cx<R> q = cmul(a0, g0);  // conj(a0) g0
+            bt = {q.re / den, q.im / den};
+        }
+        cx<R> prev = i0 > 0 ? line[long_slot(i0 - 1)] : zero;
+        const cx<R> last = i0 + kLongC < n ? line[long_slot(i0 + kLongC)] : zero;
+#pragma unroll
+        for (int m = 0; m < kLongC; m++) {
+            const cx<R> cur = v[m];
+            const cx<R> nxt = m + 1 < kLongC ? v[m + 1] : last;
+            v[m] = i0 + m < n ? tmul<IMAG>(bt, add(sub(prev, cur), sub(nxt, cur))) : zero;
+            prev = cur;
+        }
+    }
+    group_solve<R, IMAG>(v, t, i0, part, nw, seg);
+    NormAcc<R> acc;
+#pragma unroll
+    for (int m = 0; m < kLongC; m++) {
+        if (i0 + m < n) {
+            const cx<R> x = line[long_slot(i0 + m)];
+            const cx<R> o = INC ? cx<R>{fma(R(2), v[m].re, x.re), fma(R(2), v[m].im, x.im)}
+                                : cx<R>{fma(R(2), v[m].re, -x.re), fma(R(2), v[m].im, -x.im)};
+            line[long_slot(i0 + m)] = o;
+            acc.add(o);
+        }
+    }
+    return acc.value();
+}
+
+// CN along x for lines of 1025..8192 points: one block of nw warps per line
+// (line l = j*ny + iy, row iy of component j). in may equal out. With part
+// non-null (1D: the step's last pass) the block writes the FP64 norm of its
+// line to part[line].
+template <typename R, bool IMAG>
+__global__ void __launch_bounds__(32 * kLongMaxWarps) k_cn_x(const typename V2<R>::T* in, typename V2<R>::T* out,
+                                                             KParams p, Tabs<R> t, double* part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<R>* line = reinterpret_cast<cx<R>*>(smem_raw);
+    __shared__ cx<R> seg[4 * kLongMaxWarps];
+    __shared__ double red[kLongMaxWarps];
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = p.nx, span = 32 * kLongC * nw;
+    const size_t base = (size_t)blockIdx.x * n;
+    for (int i = threadIdx.x; i < span; i += blockDim.x) line[long_slot(i)] = i < n ? ldc<R>(in, base + i) : cx<R>{R(0), R(0)};
+    __syncthreads();
+    double acc = long_line<R, IMAG>(line, n, t, warp, nw, seg);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) st<R>(out, base + i, line[long_slot(i)]);
+    if (part) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) red[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < nw; w++) s += red[w];
+            part[blockIdx.x] = s;
+        }
+    }
+}
+
+// CN along y for columns of 1025..8192 points: one block per tile of kc (1, 2
+// or 4) adjacent columns [col0, col0 + kc) of component j, staged in shared memory (row
+// segments of kc elements), nw warps per column. With part non-null the block
+// writes the FP64 norm of its tile to part[blockIdx.x] (the blocks of
+// component j are contiguous).
+template <typename R, bool IMAG>
+__global__ void __launch_bounds__(32 * kLongMaxWarps) k_cn_y(const typename V2<R>::T* in, typename V2<R>::T* out,
+                                                             KParams p, Tabs<R> t, int kc, double* part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ cx<R> seg[4 * kLongMaxWarps];
+    __shared__ double red[kLongMaxWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = (blockDim.x >> 5) / kc;
+    const int n = p.ny, span = 32 * kLongC * nw;
+    const int ncb = (p.nx + kc - 1) / kc;
+    const int j = blockIdx.x / ncb;
+    const int col0 = (blockIdx.x - j * ncb) * kc;
+    const size_t base = (size_t)j * p.nx * p.ny;
+    cx<R>* lines = reinterpret_cast<cx<R>*>(smem_raw);  // [kc][span padded]
+    const size_t lstride = (size_t)(span / kLongC) * kLongS;
+    const int lkc = kc == 4 ? 2 : kc == 2 ? 1 : 0;  // kc is 1, 2 or 4
+    for (int q = threadIdx.x; q < span * kc; q += blockDim.x) {
+        const int i = q >> lkc, c = q & (kc - 1);
+        const int col = col0 + c;
+        lines[c * lstride + long_slot(i)] =
+            (i < n && col < p.nx) ? ldc<R>(in, base + (size_t)i * p.nx + col) : cx<R>{R(0), R(0)};
+    }
+    __syncthreads();
+    const int c = warp / nw;
+    double acc = long_line<R, IMAG>(lines + c * lstride, n, t, warp - c * nw, nw, seg + 4 * nw * c);
+    __syncthreads();
+    for (int q = threadIdx.x; q < n * kc; q += blockDim.x) {
+        const int i = q >> lkc, cc = q & (kc - 1);
+        const int col = col0 + cc;
+        if (col < p.nx) st<R>(out, base + (size_t)i * p.nx + col, lines[cc * lstride + long_slot(i)]);
+    }
+    if (part) {
+        if (col0 + c >= p.nx) acc = 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) red[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+            part[blockIdx.x] = s;
+        }
+    }
+}
+
 }  // namespace sgpe

@@ -265,6 +265,10 @@ inline void fill_derived(KParams& k) {
 }
 
 // Constant i of the pointwise substeps in the arithmetic type R.
+// Lines longer than 1024 points: 16 points a lane, at most 16 warps a block.
+constexpr int kLongC = 16;
+constexpr int kLongMaxWarps = 16;
+
 template <typename R> __device__ __forceinline__ R kc(const KParams& p, int i);
 template <> __device__ __forceinline__ double kc<double>(const KParams& p, int i) { return p.kd[i]; }
 template <> __device__ __forceinline__ float kc<float>(const KParams& p, int i) { return p.kf[i]; }

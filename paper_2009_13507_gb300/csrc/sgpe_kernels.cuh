@@ -51,12 +51,6 @@ template <typename R> struct Tabs {
     const typename V2<R>::T* fq;
 };
 
-// Shared-memory slot of line element i: chunk k = i / C at k*S, S = C | 1 (odd,
-// so that the 32 lanes walking their chunks hit distinct banks).
-__device__ __forceinline__ int slot(int i, int C, int S) {
-    int k = i / C;
-    return k * S + (i - k * C);
-}
 
 template <bool IMAG, typename R> __device__ __forceinline__ cx<R> tmul(cx<R> t, cx<R> x) {
     if (IMAG) return scl(t.re, x);
@@ -101,6 +95,10 @@ template <typename R> __device__ __forceinline__ cx<R> shdn(cx<R> a, int off) {
 __device__ __forceinline__ bool tiny_carry(double x) {
     return ((unsigned)__double2hiint(x) & 0x7fffffffu) < 0x3BF00000u;  // |x| < 2^-64
 }
+// (also used, in every precision, to cut the composition of the warps' segment
+// maps of lines longer than 1024 points)
+__device__ __forceinline__ bool tiny_carry(float x) { return fabsf(x) < 5.42101086242752217e-20f; }
+__device__ __forceinline__ bool tiny_carry(df x) { return fabsf(x.hi) < 5.42101086242752217e-20f; }
 // Whether every lane of the warp is done after a level: edge (its window
 // reaches the line's end) or a negligible composed factor A.
 template <typename R> __device__ __forceinline__ bool scan_done(bool edge, const cx<R>& A) {
@@ -112,62 +110,6 @@ template <typename R> __device__ __forceinline__ bool scan_done(bool edge, const
 
 template <typename R> __device__ __forceinline__ cx<R> tld(const typename V2<R>::T* t, int i) {
     return unpack(__ldg(t + i));
-}
-
-// Solve T w = x for one line held in shared memory (buf, chunked layout) by the
-// calling warp; on return buf holds w up to the backward carry, which is left
-// per chunk in carry[0..31]: w_i = buf[slot(i)] + fq_i * carry[i / C].
-// All 32 lanes must call this.
-template <typename R, bool IMAG>
-__device__ __forceinline__ void warp_solve(cx<R>* buf, cx<R>* carry, int n, int C, int S, const Tabs<R>& t) {
-    const int lane = threadIdx.x & 31;
-    const int i0 = lane * C;
-    const int i1 = min(n, i0 + C);
-    // forward sweep inside the chunk, zero carry
-    cx<R> y = {R(0), R(0)};
-    for (int i = i0; i < i1; i++) {
-        int s = slot(i, C, S);
-        y = tfma<IMAG>(tld<R>(t.fg, i), y, tmul<IMAG>(tld<R>(t.fa, i), buf[s]));
-        buf[s] = y;
-    }
-    // inclusive scan of the chunk maps y_end = A y_in + B over the lanes
-    cx<R> A = (i1 > i0) ? tld<R>(t.fp, i1 - 1) : cx<R>{R(1), R(0)};
-    cx<R> B = y;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        cx<R> Ap = shup(A, off), Bp = shup(B, off);
-        if (lane >= off) {
-            B = tfma<IMAG>(A, Bp, B);
-            A = tmul<IMAG>(A, Ap);
-        }
-        if (scan_done(lane < 2 * off, A)) break;
-    }
-    cx<R> cin = shup(B, 1);
-    if (lane == 0) cin = {R(0), R(0)};
-    // backward sweep inside the chunk with the forward carry folded in
-    cx<R> w = {R(0), R(0)};
-    for (int i = i1 - 1; i >= i0; i--) {
-        int s = slot(i, C, S);
-        cx<R> yi = tfma<IMAG>(tld<R>(t.fp, i), cin, buf[s]);
-        w = tfma<IMAG>(tld<R>(t.fg, i), w, yi);
-        buf[s] = w;
-    }
-    // scan of the backward chunk maps w_start = A w_next + B from the right
-    A = (i1 > i0) ? tld<R>(t.fq, i0) : cx<R>{R(1), R(0)};
-    B = w;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        cx<R> An = shdn(A, off), Bn = shdn(B, off);
-        if (lane + off < 32) {
-            B = tfma<IMAG>(A, Bn, B);
-            A = tmul<IMAG>(A, An);
-        }
-        if (scan_done(lane + 2 * off >= 32, A)) break;
-    }
-    cx<R> cb = shdn(B, 1);
-    if (lane == 31) cb = {R(0), R(0)};
-    carry[lane] = cb;
-    __syncwarp();
 }
 
 // Deterministic block reduction of NV doubles per thread; result valid in
@@ -405,95 +347,6 @@ __global__ void __launch_bounds__(128) k_pointwise(const typename V2<R>::T* __re
 }
 
 // ---------------------------------------------------------------------------
-// Crank-Nicolson along x: line l = j*ny + iy is row iy of component j; one warp
-// per line, WX = blockDim.x/32 lines per block. in may equal out (in place).
-// LAST: this is the step's final pass (1D) -> FP64 norms and the next scale.
-// ---------------------------------------------------------------------------
-template <typename R, bool IMAG, bool LAST>
-__global__ void __launch_bounds__(256) k_cn_x(const typename V2<R>::T* in, typename V2<R>::T* out, KParams p,
-                                              Tabs<R> t, int C, int S, double* partials, DevScalars* sc,
-                                              int renorm, int advance_step) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw) + (size_t)warp * 32 * S;
-    cx<R>* carry = reinterpret_cast<cx<R>*>(smem_raw) + (size_t)nw * 32 * S + warp * 32;
-    const int nlines = 3 * p.ny;
-    const int line = blockIdx.x * nw + warp;
-    const int n = p.nx;
-    double acc = 0.0;
-    if (line < nlines) {
-        const size_t base = (size_t)line * n;
-        for (int i = lane; i < n; i += 32) buf[slot(i, C, S)] = ldc<R>(in, base + i);
-        __syncwarp();
-        warp_solve<R, IMAG>(buf, carry, n, C, S, t);
-        for (int i = lane; i < n; i += 32) {
-            cx<R> w = tfma<IMAG>(tld<R>(t.fq, i), carry[i / C], buf[slot(i, C, S)]);
-            cx<R> x = ldc<R>(in, base + i);
-            cx<R> o = {fma(R(2), w.re, -x.re), fma(R(2), w.im, -x.im)};
-            st<R>(out, base + i, o);
-            if (LAST) acc += dbl(o.re) * dbl(o.re) + dbl(o.im) * dbl(o.im);
-        }
-    }
-    if (LAST && line < nlines) {
-        // one partial per line; lines of component j are contiguous
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (lane == 0) partials[line] = acc;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Crank-Nicolson along y (2D): block = W warps, column tile [col0, col0+W) of
-// component j; the tile is staged in shared memory, each warp solves one column.
-// Writes out (the state A), FP64 norm partials, and the last block publishes
-// the norms and the next pending scale.
-// ---------------------------------------------------------------------------
-template <typename R, bool IMAG>
-__global__ void __launch_bounds__(256) k_cn_y(const typename V2<R>::T* in, typename V2<R>::T* out, KParams p,
-                                              Tabs<R> t, int C, int S, double* partials, DevScalars* sc,
-                                              int renorm, int advance_step, int finalize) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int W = blockDim.x >> 5;
-    const int warp = threadIdx.x >> 5;
-    const int ncb = (p.nx + W - 1) / W;
-    const int j = blockIdx.x / ncb;
-    const int col0 = (blockIdx.x - j * ncb) * W;
-    const int n = p.ny;
-    const size_t plane = (size_t)p.nx * p.ny;
-    const size_t base = (size_t)j * plane;
-    cx<R>* bufs = reinterpret_cast<cx<R>*>(smem_raw);
-    cx<R>* carry = bufs + (size_t)W * 32 * S;
-    // stage the tile: element (row i, column col0 + w) -> bufs[w][slot(i)]
-    for (int q = threadIdx.x; q < n * W; q += blockDim.x) {
-        int i = q / W, w = q - i * W;
-        int col = col0 + w;
-        if (col < p.nx) bufs[(size_t)w * 32 * S + slot(i, C, S)] = ldc<R>(in, base + (size_t)i * p.nx + col);
-    }
-    __syncthreads();
-    if (col0 + warp < p.nx) warp_solve<R, IMAG>(bufs + (size_t)warp * 32 * S, carry + warp * 32, n, C, S, t);
-    __syncthreads();
-    double acc = 0.0;
-    for (int q = threadIdx.x; q < n * W; q += blockDim.x) {
-        int i = q / W, w = q - i * W;
-        int col = col0 + w;
-        if (col < p.nx) {
-            cx<R> wv = tfma<IMAG>(tld<R>(t.fq, i), carry[w * 32 + i / C], bufs[(size_t)w * 32 * S + slot(i, C, S)]);
-            size_t g = base + (size_t)i * p.nx + col;
-            cx<R> x = ldc<R>(in, g);
-            cx<R> o = {fma(R(2), wv.re, -x.re), fma(R(2), wv.im, -x.im)};
-            st<R>(out, g, o);
-            acc += dbl(o.re) * dbl(o.re) + dbl(o.im) * dbl(o.im);
-        }
-    }
-    if (finalize) {
-        __shared__ double red[8];
-        double v[1] = {acc};
-        block_reduce<1>(v, red);
-        if (threadIdx.x == 0) partials[blockIdx.x] = v[0];  // blocks of component j are contiguous
-    }
-}
-
-// ---------------------------------------------------------------------------
 // End of a step: one block of 3 warps; warp j sums the m partial norms of
 // component j (partials[j*m .. j*m + m), fixed order), then thread 0 publishes
 // N_j, the next pending scale (Eq. (DJ2) / (DJ) for renorm != 0, else 1) and
@@ -630,14 +483,13 @@ __device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi,
     }
 }
 
-// Tables have 32*C entries; entries past n are zero (fa = fg = 0, hence the
-// chunk products vanish there too).
+// Tables have len entries (a multiple of the chunk length C); entries past n
+// are zero (fa = fg = 0, hence the chunk products vanish there too).
 template <typename R>
 __global__ void k_coef(typename V2<R>::T* fa, typename V2<R>::T* fg, typename V2<R>::T* fp,
-                       typename V2<R>::T* fq, int n, int C, double bre, double bim) {
+                       typename V2<R>::T* fq, int n, int C, int len, double bre, double bim) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double dr = 1.0 + 2.0 * bre, di = 2.0 * bim;  // diagonal 1 + 2 bt
-    const int len = 32 * C;
     const cx<R> zero = {R(0), R(0)};
     for (int i = n; i < len; i++) {
         st<R>(fa, i, zero);

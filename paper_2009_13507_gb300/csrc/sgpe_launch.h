@@ -61,15 +61,16 @@ constexpr int kRegMaxN = 1024;
 // Longest 1D line of the complex128 cluster step loop (8 CTAs of 32 points).
 constexpr int kCl1dMaxN = 256;
 inline int chunk_len(int n) {
+    if (n > kRegMaxN) return kLongC;
     int c = ceil_div(n, 32);
-    if (n > kRegMaxN) return c;
     int p = 1;
     while (p < c) p <<= 1;
     return p;
 }
-inline int chunk_stride(int n) { return chunk_len(n) | 1; }
+// Warps of the group that holds a line longer than kRegMaxN points (kLongC points a lane).
+inline int long_warps(int n) { return ceil_div(n, 32 * kLongC); }
 // Entries of each coefficient table of an n-point axis (padded with zeros past n).
-inline int table_len(int n) { return 32 * chunk_len(n); }
+inline int table_len(int n) { return n > kRegMaxN ? 32 * kLongC * long_warps(n) : 32 * chunk_len(n); }
 // Columns per warp of the register y sweep (must match CnShape<C>::K).
 inline int cny_cols_per_warp(int C, int esz) { return (esz == 8 && C <= 8) ? 2 : 1; }
 constexpr int kObsAcc = 11;
@@ -77,8 +78,8 @@ constexpr int kNormBlocks = 304;
 
 struct Geometry {
     int dim, nx, ny, esz;
-    int wx;  // warps (lines) per block of the x sweep
-    int wy;  // warps (columns) per block of the y sweep (shared-memory kernel)
+    int wx;  // lines longer than kRegMaxN: warps per block (one line) of the x sweep
+    int wy;  // lines longer than kRegMaxN: columns per block (1, 2 or 4) of the y sweep
     bool reg_x, reg_y;  // register-chunk kernels (lines of at most kRegMaxN points)
     bool fused;         // 2D with register x lines: pointwise + CN-x in one kernel
     size_t smem_x, smem_y;

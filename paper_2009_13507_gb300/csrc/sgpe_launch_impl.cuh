@@ -159,10 +159,8 @@ template <typename R> cudaError_t Launcher<R>::setup() {
     if ((e = step1d_allow_all<R, false>())) return e;
     if ((e = pwx_allow_all<R, true>())) return e;
     if ((e = pwx_allow_all<R, false>())) return e;
-    if ((e = allow_smem(k_cn_x<R, true, false>))) return e;
-    if ((e = allow_smem(k_cn_x<R, true, true>))) return e;
-    if ((e = allow_smem(k_cn_x<R, false, false>))) return e;
-    if ((e = allow_smem(k_cn_x<R, false, true>))) return e;
+    if ((e = allow_smem(k_cn_x<R, true>))) return e;
+    if ((e = allow_smem(k_cn_x<R, false>))) return e;
     if ((e = allow_smem(k_cn_y<R, true>))) return e;
     if ((e = allow_smem(k_cn_y<R, false>))) return e;
     return cudaSuccess;
@@ -213,27 +211,17 @@ cudaError_t Launcher<R>::cn_x(cudaStream_t s, bool imag, bool last, const void* 
                               int renorm, int advance) {
     using T = typename V2<R>::T;
     Tabs<R> t = make_tabs<R>(tabs);
-    const int C = chunk_len(p.nx), S = chunk_stride(p.nx);
     if (g.reg_x) {
-        launch_cnx_reg<R>(C, imag, dim3(g.blocks_x), s, (const T*)in, (T*)out, p, t, last ? partials : nullptr);
+        launch_cnx_reg<R>(chunk_len(p.nx), imag, dim3(g.blocks_x), s, (const T*)in, (T*)out, p, t,
+                          last ? partials : nullptr);
         return cudaGetLastError();
     }
-    dim3 block(32 * g.wx), grid(g.blocks_x);
-    if (imag) {
-        if (last)
-            k_cn_x<R, true, true><<<grid, block, g.smem_x, s>>>((const T*)in, (T*)out, p, t, C, S, partials, sc,
-                                                                renorm, advance);
-        else
-            k_cn_x<R, true, false><<<grid, block, g.smem_x, s>>>((const T*)in, (T*)out, p, t, C, S, partials, sc,
-                                                                 renorm, advance);
-    } else {
-        if (last)
-            k_cn_x<R, false, true><<<grid, block, g.smem_x, s>>>((const T*)in, (T*)out, p, t, C, S, partials, sc,
-                                                                 renorm, advance);
-        else
-            k_cn_x<R, false, false><<<grid, block, g.smem_x, s>>>((const T*)in, (T*)out, p, t, C, S, partials, sc,
-                                                                  renorm, advance);
-    }
+    const dim3 block(32 * g.wx), grid(g.blocks_x);
+    double* part = last ? partials : nullptr;
+    if (imag)
+        k_cn_x<R, true><<<grid, block, g.smem_x, s>>>((const T*)in, (T*)out, p, t, part);
+    else
+        k_cn_x<R, false><<<grid, block, g.smem_x, s>>>((const T*)in, (T*)out, p, t, part);
     return cudaGetLastError();
 }
 
@@ -243,26 +231,24 @@ cudaError_t Launcher<R>::cn_y(cudaStream_t s, bool imag, const void* in, void* o
                               int renorm, int advance, int finalize, bool head_scale) {
     using T = typename V2<R>::T;
     Tabs<R> t = make_tabs<R>(tabs);
-    const int C = chunk_len(p.ny), S = chunk_stride(p.ny);
     if (g.reg_y) {
-        launch_cny_reg<R>(C, imag, dim3(g.blocks_y), s, (const T*)in, (T*)out, p, t, finalize ? partials : nullptr,
-                          head_scale ? sc : nullptr, renorm, advance);
+        launch_cny_reg<R>(chunk_len(p.ny), imag, dim3(g.blocks_y), s, (const T*)in, (T*)out, p, t,
+                          finalize ? partials : nullptr, head_scale ? sc : nullptr, renorm, advance);
         return cudaGetLastError();
     }
-    dim3 block(32 * g.wy), grid(g.blocks_y);
+    const dim3 block(32 * g.wy * long_warps(p.ny)), grid(g.blocks_y);
+    double* part = finalize ? partials : nullptr;
     if (imag)
-        k_cn_y<R, true><<<grid, block, g.smem_y, s>>>((const T*)in, (T*)out, p, t, C, S, partials, sc, renorm, advance,
-                                                      finalize);
+        k_cn_y<R, true><<<grid, block, g.smem_y, s>>>((const T*)in, (T*)out, p, t, g.wy, part);
     else
-        k_cn_y<R, false><<<grid, block, g.smem_y, s>>>((const T*)in, (T*)out, p, t, C, S, partials, sc, renorm,
-                                                       advance, finalize);
+        k_cn_y<R, false><<<grid, block, g.smem_y, s>>>((const T*)in, (T*)out, p, t, g.wy, part);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t Launcher<R>::coef(cudaStream_t s, void* fa, void* fg, void* fp, void* fq, int n, double bre, double bim) {
     using T = typename V2<R>::T;
-    k_coef<R><<<1, 32, 0, s>>>((T*)fa, (T*)fg, (T*)fp, (T*)fq, n, chunk_len(n), bre, bim);
+    k_coef<R><<<1, 32, 0, s>>>((T*)fa, (T*)fg, (T*)fp, (T*)fq, n, chunk_len(n), table_len(n), bre, bim);
     return cudaGetLastError();
 }
 

@@ -58,6 +58,24 @@ def test_cn_sweeps_across_bt(bt, which, imag):
     assert relerr(s.get_state(), O.substep(prob, psi, which, imag)) < 1e-13
 
 
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-13), ("cdf", 1e-12)])
+@pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("which,nx,ny", [("cn_x", 1500, 7), ("cn_y", 7, 1500), ("cn_x", 4096, 3),
+                                         ("cn_y", 3, 2100)])
+@pytest.mark.parametrize("bt", [0.02, 50.0])
+def test_cn_long_lines(bt, which, nx, ny, imag, precision, tol):
+    """Lines longer than 1024 points: a group of ceil(n/512) warps per line, 16
+    points a lane, the warps' chunk maps composed through shared memory (cut
+    once negligible at small bt, all of them at bt = 50); ragged last warp."""
+    dx = 0.1
+    phys = dict(PHYS_2D, dt=4.0 * dx * dx * bt)
+    prob, s = make_pair(2, nx, ny, dx=dx, precision=precision, **phys)
+    psi = _rand(prob, 29, env=3.0)
+    s.set_state(psi)
+    s.substep(which, imag)
+    assert relerr(s.get_state(), O.substep(prob, psi, which, imag)) < tol
+
+
 @pytest.mark.parametrize("so", [0, 1, 2, 3])
 @pytest.mark.parametrize("dim", [1, 2])
 def test_so_variants_parity(dim, so):
