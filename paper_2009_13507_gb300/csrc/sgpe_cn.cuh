@@ -607,22 +607,23 @@ __global__ void __launch_bounds__(32) k_cny_reg(const typename V2<R>::T* in, typ
 constexpr int kLongS = kLongC + 1;  // padded chunk stride (shared memory)
 __device__ __forceinline__ int long_slot(int i) { return (i >> 4) * kLongS + (i & (kLongC - 1)); }
 
-// Solve T w = x for the lane's chunk v (in: x, out: w) at points [i0, i0 + 16)
-// of a line held by the nw warps of a group; part: this warp's index in the
-// group; seg: the group's shared scratch of 4 nw entries. Every thread of the
-// block must call this (block barriers inside).
+// Solve T w = x for the lane's chunk v (in: x, out: w) at points [16 g, 16 g + 16),
+// g = part * 32 + lane, of a line held by the nw warps of a group; part: this
+// warp's index in the group; seg: the group's shared scratch of 4 nw entries.
+// The tables are lane-interleaved (k_coef): chunk entry m of lane g at m G + g,
+// G = 32 nw. Every thread of the block must call this (block barriers inside).
 template <typename R, bool IMAG>
-__device__ __forceinline__ void group_solve(cx<R> (&v)[kLongC], const Tabs<R>& t, int i0, int part, int nw,
-                                            cx<R>* seg) {
+__device__ __forceinline__ void group_solve(cx<R> (&v)[kLongC], const Tabs<R>& t, int part, int nw, cx<R>* seg) {
     const int lane = threadIdx.x & 31;
+    const int G = 32 * nw, g = part * 32 + lane;
     const cx<R> zero = {R(0), R(0)};
     cx<R> y = zero;
 #pragma unroll
     for (int m = 0; m < kLongC; m++) {
-        y = tfma<IMAG>(tld<R>(t.fg, i0 + m), y, tmul<IMAG>(tld<R>(t.fa, i0 + m), v[m]));
+        y = tfma<IMAG>(tld<R>(t.fg, m * G + g), y, tmul<IMAG>(tld<R>(t.fa, m * G + g), v[m]));
         v[m] = y;
     }
-    cx<R> A = tld<R>(t.fp, i0 + kLongC - 1), B = y;
+    cx<R> A = tld<R>(t.fp, (kLongC - 1) * G + g), B = y;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const cx<R> Ap = shup(A, off), Bp = shup(B, off);
@@ -653,11 +654,11 @@ __device__ __forceinline__ void group_solve(cx<R> (&v)[kLongC], const Tabs<R>& t
     cx<R> w = zero;
 #pragma unroll
     for (int m = kLongC - 1; m >= 0; m--) {
-        const cx<R> yi = tfma<IMAG>(tld<R>(t.fp, i0 + m), cin, v[m]);
-        w = tfma<IMAG>(tld<R>(t.fg, i0 + m), w, yi);
+        const cx<R> yi = tfma<IMAG>(tld<R>(t.fp, m * G + g), cin, v[m]);
+        w = tfma<IMAG>(tld<R>(t.fg, m * G + g), w, yi);
         v[m] = w;
     }
-    A = tld<R>(t.fq, i0);
+    A = tld<R>(t.fq, g);
     B = w;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -687,7 +688,7 @@ __device__ __forceinline__ void group_solve(cx<R> (&v)[kLongC], const Tabs<R>& t
     const cx<R> An = shdn(A, 1), Bn = shdn(B, 1);
     const cx<R> cb = lane == 31 ? cbw : tfma<IMAG>(An, cbw, Bn);
 #pragma unroll
-    for (int m = 0; m < kLongC; m++) v[m] = tfma<IMAG>(tld<R>(t.fq, i0 + m), cb, v[m]);
+    for (int m = 0; m < kLongC; m++) v[m] = tfma<IMAG>(tld<R>(t.fq, m * G + g), cb, v[m]);
 }
 
 // The sweep of one staged line: lane chunk in from shared memory (line, padded
@@ -723,7 +724,7 @@ __device__ __forceinline__ double long_line(cx<R>* line, int n, const Tabs<R>& t
             prev = cur;
         }
     }
-    group_solve<R, IMAG>(v, t, i0, part, nw, seg);
+    group_solve<R, IMAG>(v, t, part, nw, seg);
     NormAcc<R> acc;
 #pragma unroll
     for (int m = 0; m < kLongC; m++) {

@@ -484,16 +484,21 @@ __device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi,
 }
 
 // Tables have len entries (a multiple of the chunk length C); entries past n
-// are zero (fa = fg = 0, hence the chunk products vanish there too).
+// are zero (fa = fg = 0, hence the chunk products vanish there too). With
+// interleave (lines longer than 1024 points) entry i of every table is stored at
+// (i % C) * (len / C) + i / C: lane g of a line's warp group reads its chunk
+// entry m at m * G + g, G = len / C lanes, so a warp's table reads are coalesced.
 template <typename R>
 __global__ void k_coef(typename V2<R>::T* fa, typename V2<R>::T* fg, typename V2<R>::T* fp,
-                       typename V2<R>::T* fq, int n, int C, int len, double bre, double bim) {
+                       typename V2<R>::T* fq, int n, int C, int len, int interleave, double bre, double bim) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double dr = 1.0 + 2.0 * bre, di = 2.0 * bim;  // diagonal 1 + 2 bt
     const cx<R> zero = {R(0), R(0)};
+    const int G = len / C;
+    auto at = [&](int i) { return interleave ? (i % C) * G + i / C : i; };
     for (int i = n; i < len; i++) {
-        st<R>(fa, i, zero);
-        st<R>(fg, i, zero);
+        st<R>(fa, at(i), zero);
+        st<R>(fg, at(i), zero);
     }
     double ur = dr, ui = di;
     for (int i = 0; i < n; i++) {
@@ -508,30 +513,30 @@ __global__ void k_coef(typename V2<R>::T* fa, typename V2<R>::T* fg, typename V2
         double ar, ai, gr, gi;
         cdiv(1.0, 0.0, ur, ui, &ar, &ai);
         cdiv(bre, bim, ur, ui, &gr, &gi);
-        st<R>(fa, i, cx<R>{to_r<R>(ar), to_r<R>(ai)});
-        st<R>(fg, i, cx<R>{to_r<R>(gr), to_r<R>(gi)});
+        st<R>(fa, at(i), cx<R>{to_r<R>(ar), to_r<R>(ai)});
+        st<R>(fg, at(i), cx<R>{to_r<R>(gr), to_r<R>(gi)});
     }
     // chunk products, computed from the rounded-to-FP64 fg values
     for (int k0 = 0; k0 < len; k0 += C) {
         int k1 = k0 + C;
         double Pr = 1.0, Pi = 0.0;
         for (int i = k0; i < k1; i++) {
-            const cx<R> g = unpack(fg[i]);
+            const cx<R> g = unpack(fg[at(i)]);
             double gr = dbl(g.re), gi = dbl(g.im);
             double tr = Pr * gr - Pi * gi, ti = Pr * gi + Pi * gr;
             Pr = tr;
             Pi = ti;
-            st<R>(fp, i, cx<R>{to_r<R>(Pr), to_r<R>(Pi)});
+            st<R>(fp, at(i), cx<R>{to_r<R>(Pr), to_r<R>(Pi)});
         }
         Pr = 1.0;
         Pi = 0.0;
         for (int i = k1 - 1; i >= k0; i--) {
-            const cx<R> g = unpack(fg[i]);
+            const cx<R> g = unpack(fg[at(i)]);
             double gr = dbl(g.re), gi = dbl(g.im);
             double tr = Pr * gr - Pi * gi, ti = Pr * gi + Pi * gr;
             Pr = tr;
             Pi = ti;
-            st<R>(fq, i, cx<R>{to_r<R>(Pr), to_r<R>(Pi)});
+            st<R>(fq, at(i), cx<R>{to_r<R>(Pr), to_r<R>(Pi)});
         }
     }
 }

@@ -248,7 +248,8 @@ cudaError_t Launcher<R>::cn_y(cudaStream_t s, bool imag, const void* in, void* o
 template <typename R>
 cudaError_t Launcher<R>::coef(cudaStream_t s, void* fa, void* fg, void* fp, void* fq, int n, double bre, double bim) {
     using T = typename V2<R>::T;
-    k_coef<R><<<1, 32, 0, s>>>((T*)fa, (T*)fg, (T*)fp, (T*)fq, n, chunk_len(n), table_len(n), bre, bim);
+    k_coef<R><<<1, 32, 0, s>>>((T*)fa, (T*)fg, (T*)fp, (T*)fq, n, chunk_len(n), table_len(n), n > kRegMaxN ? 1 : 0,
+                               bre, bim);
     return cudaGetLastError();
 }
 
