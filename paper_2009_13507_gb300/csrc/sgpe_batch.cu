@@ -2,12 +2,15 @@
 // sizes, uneven physical parameters) advanced together by the same split step
 // (arXiv:2009.13507, Sec. 3 and Appendix A) in grouped launches replayed from
 // CUDA graphs. Every launch covers all instances through device work lists:
-//   pointwise   one block per 128-point tile of any instance
-//   CN along x  one warp per line; one launch per chunk length C (the
-//               register kernels are compiled per C)
-//   CN along y  one warp per column pair (2D instances), one launch per C
+//   x part      either the fused row kernel (pointwise substeps + CN along x,
+//               one block per row, one launch per chunk length C) or a
+//               pointwise kernel (one block per 128-point tile of any
+//               instance) and CN along x (one warp per line, one launch per C;
+//               the register kernels are compiled per C)
+//   CN along y  one warp per column or column pair (2D instances), one launch per C
 //   finalize    one block per instance (norms, renormalisation scale)
-// Warps per block of the two sweeps are chosen by sgpe_batch_autotune.
+// The x part and the warps per block of the sweeps are chosen by
+// sgpe_batch_autotune (or set by sgpe_batch_set_tiles).
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>

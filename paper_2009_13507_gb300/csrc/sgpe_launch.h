@@ -54,9 +54,10 @@ inline cudaError_t launch_cluster(void (*kernel)(KArgs...), unsigned cluster, di
 
 // Launch geometry shared by the API layer (buffer sizing) and the launchers.
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
-// Chunk length of a line of n points split over the 32 lanes of a warp: the
-// next power of two of ceil(n/32) for n <= 1024 (register kernels, compile-time
-// chunk), ceil(n/32) above (shared-memory kernels).
+// Chunk length (points per lane) of a line of n points: for n <= 1024 the line
+// is split over the 32 lanes of one warp, chunk = the next power of two of
+// ceil(n/32) (register kernels, compile-time chunk); longer lines are held by a
+// group of long_warps(n) warps with kLongC points a lane.
 constexpr int kRegMaxN = 1024;
 // Longest 1D line of the complex128 cluster step loop (8 CTAs of 32 points).
 constexpr int kCl1dMaxN = 256;
