@@ -188,10 +188,11 @@ def test_fixed_magnetisation_renorm_2d(precision, tol):
 
 @pytest.mark.parametrize("dim,nx,ny", [(2, 3, 3), (2, 5, 7), (2, 17, 3), (2, 33, 65), (1, 3, 1), (1, 32, 1),
                                        (1, 33, 1), (1, 224, 1), (1, 256, 1), (1, 257, 1), (1, 1000, 1),
-                                       (2, 4096, 3), (2, 3, 4096)])
+                                       (2, 1500, 4), (2, 2560, 3), (2, 4096, 3), (2, 3, 4096)])
 def test_edge_sizes(dim, nx, ny):
     """Ragged and extreme grids. 1D complex128 lines of 32 (one CTA), 224, 256 (the largest) points run
-    the one-cluster step loop; 257 and 1000 the three-launch path."""
+    the one-cluster step loop; 257 and 1000 the three-launch path. 2D rows of 1500, 2560 and 4096 points
+    take the long-line x sweep (warp groups) after the pointwise kernel."""
     prob, s = make_pair(dim, nx, ny, dx=0.1, **(PHYS_2D if dim == 2 else PHYS_1D))
     psi = _rand(prob, nx * 7 + ny, env=2.0)
     s.set_state(psi)
@@ -213,8 +214,10 @@ def test_precision_form_error_is_small():
     assert abs(s.energy()["E"] - oe["E"]) / abs(oe["E"]) < 1e-5
 
 
-def test_precision_form_max_line():
-    prob, s = make_pair(2, 8192, 3, dx=0.01, precision="c64", **PHYS_2D)
+@pytest.mark.parametrize("nx,ny", [(8192, 3), (2048, 5)])
+def test_precision_form_max_line(nx, ny):
+    """complex64 long rows: 8192 points (16-warp groups, one column per y tile) and 2048 (4-warp groups)."""
+    prob, s = make_pair(2, nx, ny, dx=0.01, precision="c64", **PHYS_2D)
     psi = _rand(prob, 3, env=2.0)
     s.set_state(psi)
     s.step_real(2)
