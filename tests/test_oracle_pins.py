@@ -358,3 +358,116 @@ def test_table4_energies(oracle, row):
         assert abs(o["mag"] - m) < 1e-12
     # 4 printed decimals; the second-order SO stencil adds ~6e-5 at DX = 0.05
     assert abs(o["E"] - E_paper) < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# rms sizes (LENGTH / RADIUS) and the chemical potential: closed forms and the
+# GP Hamiltonian built independently from the spin matrices
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim", [1, 2])
+def test_rms_of_displaced_gaussians_closed_form(oracle, dim):
+    """Component j is a_j exp(-|r - r_j|^2 / (2 s_j^2)): its density is a Gaussian
+    of variance s_j^2/2 per axis centred at r_j, so <r^2>_j = |r_j|^2 + d s_j^2/2
+    whatever a_j. Different amplitudes, centres and widths per component catch a
+    missing 1/N_j, a shifted origin and mixed-up components; the total rms is the
+    N_j-weighted mean with N_j = a_j^2 (pi s_j^2)^(d/2). The grid sum of a Gaussian
+    well inside the grid equals the integral to rounding."""
+    amp = np.array([1.7, 0.6, 1.1])
+    cen = np.array([[0.9, -0.4], [-0.3, 0.7], [0.2, 0.5]])
+    wid = np.array([0.8, 1.3, 1.0])
+    if dim == 1:
+        prob = oracle.Problem(dim=1, nx=400, dx=0.05)
+        x = I.grid_x(400, 0.05)
+        psi = np.stack([amp[j] * np.exp(-(x - cen[j, 0]) ** 2 / (2 * wid[j] ** 2)) for j in range(3)])[:, None, :]
+        r2 = cen[:, 0] ** 2 + wid ** 2 / 2
+    else:
+        prob = oracle.Problem(dim=2, nx=160, ny=150, dx=0.1, dy=0.11)
+        x = I.grid_x(160, 0.1)[None, :]
+        y = I.grid_x(150, 0.11)[:, None]
+        psi = np.stack([amp[j] * np.exp(-((x - cen[j, 0]) ** 2 + (y - cen[j, 1]) ** 2) / (2 * wid[j] ** 2))
+                        for j in range(3)])
+        r2 = cen[:, 0] ** 2 + cen[:, 1] ** 2 + wid ** 2
+    o = oracle.observables(prob, psi.astype(complex))
+    for j, k in enumerate(("rms+", "rms0", "rms-")):
+        assert abs(o[k] - np.sqrt(r2[j])) < 1e-12 * np.sqrt(r2[j])
+    Nj = amp ** 2 * (np.pi * wid ** 2) ** (dim / 2)
+    tot = np.sqrt(np.sum(Nj * r2) / np.sum(Nj))
+    assert abs(o["rms"] - tot) < 1e-12 * tot
+    for j, k in enumerate(("N+", "N0", "N-")):
+        assert abs(o[k] - Nj[j]) < 1e-12 * Nj[j]
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_mu_times_norm_is_expectation_of_gp_hamiltonian(oracle, dim):
+    """mu N = Re <psi, H_GP psi> for any state, H_GP the right-hand side of
+    Eqs. (1)-(2) assembled from dense operators (gp_rhs): the quartic terms
+    enter twice, the quadratic ones once. Unnormalised random states with every
+    term switched on catch a missing 1/N or E_int in place of 2 E_int."""
+    if dim == 1:
+        prob = oracle.Problem(dim=1, nx=30, dx=0.25, c0=6.0, c2=-1.4, so_type=1, gamma=0.7, omega=0.45)
+    else:
+        prob = oracle.Problem(dim=2, nx=9, ny=7, dx=0.35, dy=0.3, c0=6.0, c2=2.1, so_type=2, gamma=0.7, omega=0.45,
+                              wx=1.1, wy=0.8)
+    cell = prob.dx * (prob.dy if dim == 2 else 1.0)
+    psi = rand_state(prob, 41, envelope=0.0) * 1.9
+    o = oracle.observables(prob, psi)
+    Nt = np.sum(abs(psi) ** 2) * cell
+    h = np.real(np.vdot(psi.ravel(), gp_rhs(prob, psi).ravel())) * cell
+    assert abs(o["N"] - Nt) < 1e-13 * Nt
+    assert abs(o["mu"] * Nt - h) < 1e-12 * abs(h)
+    # and E itself differs from mu N by the interaction energy alone
+    assert abs((o["mu"] * Nt - o["E"]) - o["E_int"]) < 1e-12 * abs(h)
+
+
+def test_mu_is_the_eigenvalue_of_the_interacting_ground_state(oracle):
+    """At the imaginary-time fixed point H_GP psi = mu psi (mu the Lagrange
+    multiplier of the norm): the oracle's mu leaves a residual of the size of
+    the splitting error, while the energy per particle E (different from mu
+    when c0, c2 != 0) does not."""
+    prob = oracle.Problem(dim=1, nx=96, dx=0.15, dt=1e-3, c0=10.0, c2=-0.5, so_type=1, gamma=0.5, omega=0.2)
+    psi = I.gaussian_jitter_1d(96, 0.15, seed=3, amp=1e-2)
+    # tau = 20: converged; the fixed point of the Lie splitting is O(dt) from the
+    # eigenstate (residual 7.6e-4 at dt = 1e-3, 3.1e-4 at dt = 5e-4)
+    out = oracle.step(prob, psi, 20000, imag=True)
+    o = oracle.observables(prob, out)
+    Hpsi = gp_rhs(prob, out)
+    nrm = np.linalg.norm(out.ravel())
+    res_mu = np.linalg.norm((Hpsi - o["mu"] * out).ravel()) / nrm
+    res_E = np.linalg.norm((Hpsi - o["E"] * out).ravel()) / nrm
+    assert o["mu"] - o["E"] > 0.5          # repulsive: mu = E + E_int/N well above E
+    assert res_mu < 2e-3 * abs(o["mu"])
+    assert res_E > 100 * res_mu
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_rms_of_linear_ground_state(oracle, dim):
+    """Noninteracting harmonic ground state: <x^2> = 1/2 per axis, so rms = 1/sqrt2
+    in 1D and 1 in 2D in the continuum (closed form, O(dx^2) grid error), and on
+    the grid the dense eigenvector's sum r^2 |v|^2 / sum |v|^2 of the lowest
+    eigenvalue of the discrete Hamiltonian (same value in every component)."""
+    # rms is first order in the state's O(dt) distance from the eigenvector
+    # (7e-4 relative at dt = 4e-3 in 1D): a small dt for a 1e-4 comparison
+    if dim == 1:
+        prob = oracle.Problem(dim=1, nx=128, dx=0.1, dt=2.5e-4)
+        closed, nsteps = np.sqrt(0.5), 40000
+    else:
+        prob = oracle.Problem(dim=2, nx=24, ny=24, dx=0.4, dy=0.4, dt=2.5e-4)
+        closed, nsteps = 1.0, 40000
+    if dim == 1:
+        psi = I.gaussian_phase_2d(prob.nx, 1, prob.dx, prob.dx, 1)[:, :1, :]
+        psi = psi / np.sqrt(np.sum(abs(psi) ** 2) * prob.dx)
+    else:
+        psi = I.gaussian_phase_2d(prob.nx, prob.ny, prob.dx, prob.dy, 1)
+    out = oracle.step(prob, psi, nsteps, imag=True)
+    o = oracle.observables(prob, out)
+    g = grid_ops(prob)
+    w, v = np.linalg.eigh(-0.5 * g["Lap"] + g["V"])
+    x = I.grid_x(prob.nx, prob.dx)
+    if dim == 1:
+        r2 = x ** 2
+    else:
+        r2 = (x[None, :] ** 2 + I.grid_x(prob.ny, prob.dy)[:, None] ** 2).ravel()
+    dense = np.sqrt(np.sum(r2 * abs(v[:, 0]) ** 2) / np.sum(abs(v[:, 0]) ** 2))
+    for k in ("rms+", "rms0", "rms-", "rms"):
+        assert abs(o[k] - dense) < 1e-4 * dense
+        assert abs(o[k] - closed) < (2e-3 if dim == 1 else 3e-2) * closed
