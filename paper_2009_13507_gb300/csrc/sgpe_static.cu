@@ -95,31 +95,8 @@ extern "C" sgpe_status sgpe_observables_noalloc(const void* psi_dev, int dim, in
     unsigned char* base = nullptr;
     cudaError_t e = scratch_on_current_device(&base);
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    KParams k;
-    memset(&k, 0, sizeof(k));
-    k.dim = dim;
-    k.nx = nx;
-    k.ny = ny;
-    k.dx = dx;
-    k.dy = dy;
-    const double gt = p->gamma / sqrt(2.0);
-    if (p->so_type != 0 && p->gamma != 0.0) {
-        if (dim == 1) {
-            k.so_case = p->so_type;
-            k.sx = (p->so_type == 3 ? p->gamma : gt) / (2.0 * dx);
-        } else {
-            double eta = p->so_type == 1 ? 1.0 : (p->so_type == 2 ? -1.0 : 0.0);
-            k.so_case = 4;
-            k.sx = gt / (2.0 * dx);
-            k.sy = gt * eta / (2.0 * dy);
-        }
-    }
-    k.c0 = p->c0;
-    k.c2 = p->c2;
-    k.wx2h = 0.5 * p->wx * p->wx;
-    k.wy2h = dim == 2 ? 0.5 * p->wy * p->wy : 0.0;
-    k.omega_t = p->omega / sqrt(2.0);
-    k.cell = dim == 2 ? dx * dy : dx;
+    // the same kernel constants as a context's sgpe_energy (dt plays no part in the observables)
+    const KParams k = make_kparams(dim, nx, ny, dx, dy, p);
     DevScalars* sc = (DevScalars*)base;
     double* partials = (double*)(base + kScalarsBytes);
     // The scratch keeps the previous call's contents: the ticket and the error

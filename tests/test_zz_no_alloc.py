@@ -16,9 +16,9 @@ from paper_2009_13507_gb300 import sgpe
 pytestmark = pytest.mark.gpu
 
 
-def _case(dim, nx, ny, precision, seed):
+def _case(dim, nx, ny, precision, seed, so_type=1):
     import torch
-    phys = sgpe.Physics(c0=50.0, c2=1.0, so_type=1, gamma=0.8, omega=0.5, dt=2e-4, renorm=1)
+    phys = sgpe.Physics(c0=50.0, c2=1.0, so_type=so_type, gamma=0.8, omega=0.5, dt=2e-4, renorm=1)
     s = sgpe.Solver(dim, nx, ny, dx=0.1, precision=precision)
     s.set_params(phys)
     if dim == 2:
@@ -32,12 +32,16 @@ def _case(dim, nx, ny, precision, seed):
     return s, phys, ref, out
 
 
-@pytest.mark.parametrize("dim,nx,ny,precision", [(2, 64, 48, "c128"), (2, 200, 150, "c64"), (1, 300, 1, "c128")])
-def test_noalloc_matches_energy_twice(dim, nx, ny, precision):
-    s, phys, ref, out = _case(dim, nx, ny, precision, seed=nx)
+@pytest.mark.parametrize("dim,nx,ny,precision,so_type", [
+    (2, 64, 48, "c128", 1), (2, 200, 150, "c64", 1), (2, 90, 70, "cdf", 2), (1, 300, 1, "c128", 1),
+    (1, 257, 1, "cdf", 2), (1, 129, 1, "c64", 3)])
+def test_noalloc_matches_energy_twice(dim, nx, ny, precision, so_type):
+    """Every precision (the double-float state in its pair layout) and the 1D SO
+    options gamma p_x Sigma_y and gamma p_x Sigma_z besides Sigma_x and 2D Rashba."""
+    s, phys, ref, out = _case(dim, nx, ny, precision, seed=nx, so_type=so_type)
     lib = s.lib
     p = phys.c()
-    prec = sgpe.C128 if precision == "c128" else sgpe.C64
+    prec = sgpe.PRECISIONS[precision]
     for call in range(2):
         out.fill_(float("nan"))
         rc = lib.sgpe_observables_noalloc(s.psi.data_ptr(), dim, nx, ny, s.dx, s.dy, prec, ctypes.byref(p),
