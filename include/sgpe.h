@@ -239,8 +239,13 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* ctx, int nsteps, int imag, double* ms_o
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture. All calls share the one array, so calls whose work overlaps on the
  * GPU (other streams, other host threads) race: order them on one stream.
+ * The address is kept for the life of the process: after cudaDeviceReset the
+ * library's module and its array are gone, so do not call this entry point on
+ * that device again in the same process.
  * Returns SGPE_EINVAL for null or misaligned pointers or bad parameters,
- * SGPE_ECUDA if a CUDA call fails. Asynchronous.
+ * SGPE_ECUDA if a CUDA call fails. Asynchronous: a state holding NaN or Inf is
+ * not reported through the return code (that would need a synchronisation); it
+ * shows up as a non-finite obs_dev[SGPE_OBS_N].
  */
 sgpe_status sgpe_observables_noalloc(const void* psi_dev, int dim, int nx, int ny, double dx, double dy,
                                      sgpe_precision prec, const sgpe_params* p, double* obs_dev, void* cuda_stream);
@@ -268,13 +273,49 @@ sgpe_status sgpe_adjoint_workspace_bytes(const sgpe_ctx* ctx, int nsteps, int ch
  *  loss_out        host, 1 double (nullable); dw_out host, 2 doubles dL/dwx,
  *                  dL/dwy (nullable; dL/dwy = 0 in 1D).
  *  domega_dev      device, nsteps doubles: dL/dOmega_n.
- * Reductions are FP64 in both precisions. Synchronises the stream.
+ * Reductions are FP64 in both precisions. Synchronises the stream. This is
+ * sgpe_adjoint_forward, the loss and its cotangent at psi_N, and
+ * sgpe_adjoint_step, in one call.
  * SGPE_ESTATE without bound buffers or parameters; SGPE_EINVAL for bad sizes,
  * null or misaligned pointers.
  */
 sgpe_status sgpe_adjoint_loss_grad(sgpe_ctx* ctx, int nsteps, const double* omega_dev, const double* rho_target_dev,
                                    int checkpoint_every, void* adj_workspace, double* loss_out, double* domega_dev,
                                    double* dw_out);
+
+/*
+ * The adjoint of nsteps real-time steps for any final-state cotangent, in two
+ * calls. With the convention g = dL/dRe(psi) + i dL/dIm(psi) (PyTorch's), a
+ * loss L(psi_N, Omega, wx, wy) defined by the caller is differentiated through
+ * the discrete propagator psi_N = S_{N-1} ... S_0 psi_0, S_n the real-time split
+ * step of Sec. 3 (SO -> CALCNU -> HERM with Omega_n -> CN along x -> along y),
+ * by reversing every substep (Appendix A's substeps, transposed).
+ *
+ * sgpe_adjoint_forward: run nsteps real-time steps from the bound state psi_0
+ * (which ends as psi_N; a pending renormalisation scale is applied first), with
+ * Omega_n from omega_dev (device, nsteps doubles) and the other parameters from
+ * sgpe_set_params, storing psi_n every checkpoint_every steps in adj_workspace
+ * (device, sgpe_adjoint_workspace_bytes(nsteps, checkpoint_every) bytes, 256-byte
+ * aligned). Synchronises the stream (it reads the Omega table).
+ *
+ * sgpe_adjoint_step: reverse the nsteps steps whose checkpoints adj_workspace
+ * holds (same nsteps, checkpoint_every and Omega table as the forward call; the
+ * parameters must not change in between). lambda_dev (device, [3][ny][nx]
+ * complex of the context's precision, aligned to its element size) holds
+ * dL/dpsi_N on entry and dL/dpsi_0 on exit. domega_dev (device, nsteps doubles)
+ * receives the part of dL/dOmega_n that flows through the propagator, dw_out
+ * (host, 2 doubles, nullable) that of (dL/dwx, dL/dwy) (dL/dwy = 0 in 1D). The
+ * bound state is not touched; the reverse recomputes the steps between
+ * checkpoints in the workspace. Reductions are FP64 in both precisions.
+ * Synchronises the stream. SGPE_ESTATE when the workspace holds no forward pass
+ * of these nsteps and checkpoint_every, or without bound buffers / parameters;
+ * SGPE_EINVAL for bad sizes, null or misaligned pointers; SGPE_EUNSUPPORTED
+ * for SGPE_CDF.
+ */
+sgpe_status sgpe_adjoint_forward(sgpe_ctx* ctx, int nsteps, const double* omega_dev, int checkpoint_every,
+                                 void* adj_workspace);
+sgpe_status sgpe_adjoint_step(sgpe_ctx* ctx, int nsteps, const double* omega_dev, int checkpoint_every,
+                              void* adj_workspace, void* lambda_dev, double* domega_dev, double* dw_out);
 
 /* ------------------------------------------------------------------------
  * Batched form: many independent grids advanced together by the split step of

@@ -150,3 +150,23 @@ def final_psi(prob, psi0, omega_t):
         for n in range(len(omega_t)):
             psi = prop.step(psi, float(omega_t[n]), float(prob.wx), float(prob.wy))
     return psi.numpy()
+
+
+def vjp(prob, psi0, omega_t, lam):
+    """The propagator's vector-Jacobian product for a final-state cotangent lam:
+    with L = Re sum conj(lam) psi_N (so that dL/dpsi_N = lam in the convention
+    g = dL/dRe + i dL/dIm), returns psi_N, dL/dpsi_0 (same convention),
+    dL/dOmega_n, dL/dwx, dL/dwy."""
+    prop = RealTimePropagator(prob)
+    p0 = torch.tensor(np.asarray(psi0), dtype=torch.complex128, requires_grad=True)
+    om = torch.tensor(np.asarray(omega_t, dtype=np.float64), requires_grad=True)
+    wx = torch.tensor(float(prob.wx), dtype=torch.float64, requires_grad=True)
+    wy = torch.tensor(float(prob.wy), dtype=torch.float64, requires_grad=True)
+    lt = torch.as_tensor(np.asarray(lam), dtype=torch.complex128)
+    psi = p0
+    for n in range(om.shape[0]):
+        psi = prop.step(psi, om[n], wx, wy)
+    L = (torch.conj(lt) * psi).real.sum()
+    g0, gom, gwx, gwy = torch.autograd.grad(L, (p0, om, wx, wy), allow_unused=True)
+    gwy = torch.zeros(()) if gwy is None else gwy
+    return psi.detach().numpy(), g0.numpy(), gom.numpy(), float(gwx), float(gwy)

@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
         cmd = ["gcc", "-std=gnu99", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
-               "-fcx-fortran-rules", "-o", tmp, _SRC, "-lm"]
+               "-fcx-fortran-rules", "-fopenmp", "-o", tmp, _SRC, "-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
     return _LIB
@@ -68,8 +68,24 @@ def _load():
         lib.orc_observables.argtypes = [P, C, ctypes.c_double, C]
         lib.orc_apply_hso.argtypes = [P, C, C]
         lib.orc_norms.argtypes = [P, C, C]
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_get_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads for the oracle's point and line loops (n <= 0: all cores the
+    process may use); results do not depend on it. Returns the count in use."""
+    lib = _load()
+    if n <= 0 and hasattr(os, "sched_getaffinity"):
+        n = len(os.sched_getaffinity(0))
+    lib.orc_set_threads(int(n))
+    return int(lib.orc_get_threads())
+
+
+def get_threads() -> int:
+    return int(_load().orc_get_threads())
 
 
 @dataclass

@@ -21,6 +21,12 @@
  * (an approximation of) exp(-z H_k), which is the real-time update of Sec. 2
  * and Appendix A with dt -> -i dt in imaginary time.
  *
+ * Threads: the loops over independent grid points and independent lines may
+ * run on several OpenMP threads (orc_set_threads; one thread by default). Each
+ * point or line is computed by the same code whichever thread runs it, and
+ * every sum over the grid (norms, observables) stays one sequential loop, so
+ * the results are bitwise the same for any thread count.
+ *
  * Parity: the substeps are pinned by the CPU tests (dense solves, scipy expm,
  * finite-difference derivatives against Eqs. (1)-(2), Hermiticity and norm
  * identities, closed-form ground-state energies, the paper's Table 4 energies).
@@ -29,6 +35,22 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int g_threads = 1;
+
+/* Number of threads for the point and line loops (n <= 0: all available). */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    g_threads = n > 0 ? n : omp_get_num_procs();
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+}
+int orc_get_threads(void) { return g_threads; }
 
 typedef double complex cplx;
 
@@ -123,6 +145,7 @@ void orc_so(const orc_params* p, cplx* psi, cplx z) {
     size_t n = (size_t)3 * p->nx * p->ny;
     cplx* old = malloc(n * sizeof(cplx));
     memcpy(old, psi, n * sizeof(cplx));
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int iy = 0; iy < p->ny; iy++)
         for (int ix = 0; ix < p->nx; ix++) {
             cplx h[3];
@@ -140,6 +163,7 @@ void orc_so(const orc_params* p, cplx* psi, cplx z) {
  *   psi_j <- exp(-z mu_j) psi_j.
  */
 void orc_calcnu(const orc_params* p, cplx* psi, cplx z) {
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int iy = 0; iy < p->ny; iy++)
         for (int ix = 0; ix < p->nx; ix++) {
             cplx* pp = &psi[IDX(p, 0, iy, ix)];
@@ -167,6 +191,7 @@ void orc_calcnu(const orc_params* p, cplx* psi, cplx z) {
  */
 void orc_herm(const orc_params* p, cplx* psi, cplx z, double omega) {
     const double Ot = omega / sqrt(2.0);
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int iy = 0; iy < p->ny; iy++)
         for (int ix = 0; ix < p->nx; ix++) {
             cplx* pp = &psi[IDX(p, 0, iy, ix)];
@@ -229,6 +254,7 @@ static void cn_line(cplx* f, size_t stride, int n, cplx bt) {
 
 void orc_cn_x(const orc_params* p, cplx* psi, cplx z) {
     cplx bt = z / (4.0 * p->dx * p->dx);
+#pragma omp parallel for collapse(2) num_threads(g_threads) schedule(static)
     for (int j = 0; j < 3; j++)
         for (int iy = 0; iy < p->ny; iy++) cn_line(&psi[IDX(p, j, iy, 0)], 1, p->nx, bt);
 }
@@ -236,6 +262,7 @@ void orc_cn_x(const orc_params* p, cplx* psi, cplx z) {
 void orc_cn_y(const orc_params* p, cplx* psi, cplx z) {
     if (p->dim != 2) return;
     cplx bt = z / (4.0 * p->dy * p->dy);
+#pragma omp parallel for collapse(2) num_threads(g_threads) schedule(static)
     for (int j = 0; j < 3; j++)
         for (int ix = 0; ix < p->nx; ix++) cn_line(&psi[IDX(p, j, 0, ix)], (size_t)p->nx, p->ny, bt);
 }
@@ -280,6 +307,7 @@ void orc_renorm(const orc_params* p, cplx* psi) {
     } else {
         return;
     }
+#pragma omp parallel for collapse(2) num_threads(g_threads) schedule(static)
     for (int j = 0; j < 3; j++)
         for (int iy = 0; iy < p->ny; iy++)
             for (int ix = 0; ix < p->nx; ix++) psi[IDX(p, j, iy, ix)] *= d[j];

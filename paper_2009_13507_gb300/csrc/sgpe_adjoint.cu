@@ -12,6 +12,7 @@
 //   are non-holomorphic (they depend on |psi|^2 and conj(psi)) and get explicit
 //   reverse passes below, recomputing their inputs from the stored psi_n.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <vector>
@@ -334,9 +335,43 @@ static cudaError_t adj_forward_step(const CtxView& v, const void* in, void* out,
     return Launcher<R>::cn_x(v.stream, false, false, v.mid, out, k, v.tabs_real, *v.geo, v.partials, v.sc, 0, 0);
 }
 
+// Marks the workspace as holding the checkpoints of a forward pass of nsteps
+// steps with checkpoint_every = K (checked by the reverse entry point).
+constexpr double kAdjTag = 7.0e7 + 13.0;
+__global__ void ka_tag(double* scal, int nsteps, int K) {
+    scal[4] = kAdjTag;
+    scal[5] = (double)nsteps;
+    scal[6] = (double)K;
+}
+
+// Forward pass with checkpoints: the bound state psi holds psi_0 and ends as
+// psi_N; psi_n is stored every K steps (n = 0, K, 2K, ...).
 template <typename R>
-static sgpe_status adj_run(sgpe_ctx* c, const CtxView& v, int nsteps, const double* omega_host, const double* tgt,
-                           int K, unsigned char* ws, double* loss_out, double* domega_dev, double* dw_out) {
+static cudaError_t adj_forward(const CtxView& v, int nsteps, const double* omega_host, int K, unsigned char* ws) {
+    const AdjLayout L = adj_layout(v.nx, v.ny, v.esz, nsteps, K);
+    const size_t st = (size_t)3 * v.nx * v.ny * v.esz;
+    const size_t sst = (st + 255) & ~(size_t)255;
+    cudaStream_t s = v.stream;
+    double* scal = (double*)(ws + L.scal);
+    cudaError_t e = cudaSuccess;
+    for (int n = 0; n < nsteps && !e; n++) {
+        if (n % K == 0) e = cudaMemcpyAsync(ws + L.ckpt + sst * (n / K), v.psi, st, cudaMemcpyDeviceToDevice, s);
+        if (!e) e = adj_forward_step<R>(v, v.psi, v.psi, omega_host[n]);
+    }
+    if (!e) {
+        ka_tag<<<1, 1, 0, s>>>(scal, nsteps, K);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+// Reverse pass over the nsteps steps whose checkpoints the forward pass left in
+// ws: G (device, [3][ny][nx], inside ws) holds dL/dpsi_N on entry; on exit the
+// returned buffer (G or the workspace's second gradient buffer) holds dL/dpsi_0.
+// dL/dOmega_n goes to domega_dev[n]; dL/dwx, dL/dwy are added to scal[1], scal[2].
+template <typename R>
+static cudaError_t adj_reverse(const CtxView& v, int nsteps, const double* omega_host, int K, unsigned char* ws,
+                               double* domega_dev, typename V2<R>::T** result) {
     using T = typename V2<R>::T;
     const AdjLayout L = adj_layout(v.nx, v.ny, v.esz, nsteps, K);
     const size_t st = (size_t)3 * v.nx * v.ny * v.esz;
@@ -350,21 +385,10 @@ static sgpe_status adj_run(sgpe_ctx* c, const CtxView& v, int nsteps, const doub
     double* scal = (double*)(ws + L.scal);  // [0] loss, [1..2] dw
     dim3 blk(32, 4), grd(ceil_div(v.nx, 32), ceil_div(v.ny, 4));
     const int nblk = grd.x * grd.y;
-    cudaError_t e = cudaMemsetAsync(scal, 0, sizeof(double) * 8, s);
-    // forward with checkpoints: the bound state psi holds psi_0 and ends as psi_N
-    for (int n = 0; n < nsteps && !e; n++) {
-        if (n % K == 0) e = cudaMemcpyAsync(ckpt(n / K), v.psi, st, cudaMemcpyDeviceToDevice, s);
-        if (!e) e = adj_forward_step<R>(v, v.psi, v.psi, omega_host[n]);
-    }
-    // loss and its gradient at psi_N
-    if (!e) {
-        ka_loss<R><<<grd, blk, 0, s>>>((const T*)v.psi, tgt, G, v.kp, part);
-        ka_reduce<<<1, 256, 0, s>>>(part, nblk, 1, scal, nullptr);
-        e = cudaGetLastError();
-    }
     KParams kneg = v.kp;  // SO with dt -> -dt
     kneg.hx = -kneg.hx;
     kneg.hy = -kneg.hy;
+    cudaError_t e = cudaSuccess;
     for (int sg = L.nck - 1; sg >= 0 && !e; sg--) {
         const int s0 = sg * K, s1 = (s0 + K < nsteps) ? s0 + K : nsteps;
         e = cudaMemcpyAsync(seg(0), ckpt(sg), st, cudaMemcpyDeviceToDevice, s);
@@ -385,6 +409,31 @@ static sgpe_status adj_run(sgpe_ctx* c, const CtxView& v, int nsteps, const doub
             G2 = t;
         }
     }
+    *result = G;
+    return e;
+}
+
+template <typename R>
+static sgpe_status adj_run(sgpe_ctx* c, const CtxView& v, int nsteps, const double* omega_host, const double* tgt,
+                           int K, unsigned char* ws, double* loss_out, double* domega_dev, double* dw_out) {
+    using T = typename V2<R>::T;
+    const AdjLayout L = adj_layout(v.nx, v.ny, v.esz, nsteps, K);
+    cudaStream_t s = v.stream;
+    T* G = (T*)(ws + L.g);
+    double* part = (double*)(ws + L.part);
+    double* scal = (double*)(ws + L.scal);
+    dim3 blk(32, 4), grd(ceil_div(v.nx, 32), ceil_div(v.ny, 4));
+    const int nblk = grd.x * grd.y;
+    cudaError_t e = cudaMemsetAsync(scal, 0, sizeof(double) * 8, s);
+    if (!e) e = adj_forward<R>(v, nsteps, omega_host, K, ws);
+    // loss and its gradient at psi_N
+    if (!e) {
+        ka_loss<R><<<grd, blk, 0, s>>>((const T*)v.psi, tgt, G, v.kp, part);
+        ka_reduce<<<1, 256, 0, s>>>(part, nblk, 1, scal, nullptr);
+        e = cudaGetLastError();
+    }
+    T* g0 = nullptr;
+    if (!e) e = adj_reverse<R>(v, nsteps, omega_host, K, ws, domega_dev, &g0);
     double h[3] = {0, 0, 0};
     if (!e) e = cudaMemcpyAsync(h, scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
@@ -394,6 +443,34 @@ static sgpe_status adj_run(sgpe_ctx* c, const CtxView& v, int nsteps, const doub
         dw_out[0] = h[1];
         dw_out[1] = h[2];
     }
+    return SGPE_OK;
+}
+
+// Common argument checks and the Omega(t) table on the host (the reverse
+// kernels take Omega_n as a launch argument). Synchronises the stream.
+static sgpe_status adj_prepare(sgpe_ctx* c, CtxView* v, int nsteps, const double* omega_dev, int K,
+                               const void* ws, std::vector<double>* om, const char* who) {
+    char msg[160];
+    if (!ctx_view(c, v) || !v->ready) {
+        snprintf(msg, sizeof(msg), "%s: no buffers bound or no parameters", who);
+        return ctx_fail(c, SGPE_ESTATE, msg);
+    }
+    if (v->prec == SGPE_CDF) {
+        snprintf(msg, sizeof(msg), "%s: not available for SGPE_CDF", who);
+        return ctx_fail(c, SGPE_EUNSUPPORTED, msg);
+    }
+    if (nsteps < 1 || K < 1 || !omega_dev || !ws) {
+        snprintf(msg, sizeof(msg), "%s: bad arguments", who);
+        return ctx_fail(c, SGPE_EINVAL, msg);
+    }
+    if (((uintptr_t)ws & 255) || ((uintptr_t)omega_dev & 7)) {
+        snprintf(msg, sizeof(msg), "%s: misaligned buffer", who);
+        return ctx_fail(c, SGPE_EINVAL, msg);
+    }
+    om->resize(nsteps);
+    cudaError_t e = cudaMemcpyAsync(om->data(), omega_dev, sizeof(double) * nsteps, cudaMemcpyDeviceToHost, v->stream);
+    if (!e) e = cudaStreamSynchronize(v->stream);
+    if (e) return ctx_fail(c, SGPE_ECUDA, cudaGetErrorString(e));
     return SGPE_OK;
 }
 
@@ -412,22 +489,80 @@ sgpe_status sgpe_adjoint_loss_grad(sgpe_ctx* c, int nsteps, const double* omega_
                                    double* dw_out) {
     if (!c) return SGPE_EINVAL;
     CtxView v;
-    if (!ctx_view(c, &v) || !v.ready) return ctx_fail(c, SGPE_ESTATE, "adjoint: no buffers bound or no parameters");
-    if (v.prec == SGPE_CDF) return ctx_fail(c, SGPE_EUNSUPPORTED, "adjoint: not available for SGPE_CDF");
-    if (nsteps < 1 || checkpoint_every < 1 || !omega_dev || !rho_target_dev || !adj_workspace || !domega_dev)
-        return ctx_fail(c, SGPE_EINVAL, "adjoint: bad arguments");
-    if (((uintptr_t)adj_workspace & 255) || ((uintptr_t)omega_dev & 7) || ((uintptr_t)rho_target_dev & 7) ||
-        ((uintptr_t)domega_dev & 7))
-        return ctx_fail(c, SGPE_EINVAL, "adjoint: misaligned buffer");
+    std::vector<double> om;
+    if (!rho_target_dev || !domega_dev || ((uintptr_t)rho_target_dev & 7) || ((uintptr_t)domega_dev & 7))
+        return ctx_fail(c, SGPE_EINVAL, "adjoint: null or misaligned target / gradient buffer");
+    sgpe_status st = adj_prepare(c, &v, nsteps, omega_dev, checkpoint_every, adj_workspace, &om, "adjoint");
+    if (st) return st;
     cudaError_t e = ctx_flush(c);  // apply any pending renormalisation: the forward starts at scale 1
-    std::vector<double> om(nsteps);
-    if (!e) e = cudaMemcpyAsync(om.data(), omega_dev, sizeof(double) * nsteps, cudaMemcpyDeviceToHost, v.stream);
-    if (!e) e = cudaStreamSynchronize(v.stream);
     if (e) return ctx_fail(c, SGPE_ECUDA, cudaGetErrorString(e));
     return v.dbl ? adj_run<double>(c, v, nsteps, om.data(), rho_target_dev, checkpoint_every,
                                    (unsigned char*)adj_workspace, loss_out, domega_dev, dw_out)
                  : adj_run<float>(c, v, nsteps, om.data(), rho_target_dev, checkpoint_every,
                                   (unsigned char*)adj_workspace, loss_out, domega_dev, dw_out);
+}
+
+sgpe_status sgpe_adjoint_forward(sgpe_ctx* c, int nsteps, const double* omega_dev, int checkpoint_every,
+                                 void* adj_workspace) {
+    if (!c) return SGPE_EINVAL;
+    CtxView v;
+    std::vector<double> om;
+    sgpe_status st = adj_prepare(c, &v, nsteps, omega_dev, checkpoint_every, adj_workspace, &om, "adjoint_forward");
+    if (st) return st;
+    cudaError_t e = ctx_flush(c);  // apply any pending renormalisation: the forward starts at scale 1
+    if (e) return ctx_fail(c, SGPE_ECUDA, cudaGetErrorString(e));
+    unsigned char* ws = (unsigned char*)adj_workspace;
+    e = v.dbl ? adj_forward<double>(v, nsteps, om.data(), checkpoint_every, ws)
+              : adj_forward<float>(v, nsteps, om.data(), checkpoint_every, ws);
+    if (e) return ctx_fail(c, SGPE_ECUDA, cudaGetErrorString(e));
+    return SGPE_OK;
+}
+
+sgpe_status sgpe_adjoint_step(sgpe_ctx* c, int nsteps, const double* omega_dev, int checkpoint_every,
+                              void* adj_workspace, void* lambda_dev, double* domega_dev, double* dw_out) {
+    if (!c) return SGPE_EINVAL;
+    CtxView v;
+    std::vector<double> om;
+    sgpe_status st = adj_prepare(c, &v, nsteps, omega_dev, checkpoint_every, adj_workspace, &om, "adjoint_step");
+    if (st) return st;
+    if (!lambda_dev || !domega_dev || ((uintptr_t)lambda_dev & (v.esz - 1)) || ((uintptr_t)domega_dev & 7))
+        return ctx_fail(c, SGPE_EINVAL, "adjoint_step: null or misaligned cotangent / gradient buffer");
+    unsigned char* ws = (unsigned char*)adj_workspace;
+    const AdjLayout L = adj_layout(v.nx, v.ny, v.esz, nsteps, checkpoint_every);
+    double* scal = (double*)(ws + L.scal);
+    double tag[3] = {0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(tag, scal + 4, sizeof(tag), cudaMemcpyDeviceToHost, v.stream);
+    if (!e) e = cudaStreamSynchronize(v.stream);
+    if (e) return ctx_fail(c, SGPE_ECUDA, cudaGetErrorString(e));
+    if (tag[0] != kAdjTag || tag[1] != (double)nsteps || tag[2] != (double)checkpoint_every)
+        return ctx_fail(c, SGPE_ESTATE,
+                        "adjoint_step: the workspace holds no forward pass of these nsteps and checkpoint_every "
+                        "(call sgpe_adjoint_forward first)");
+    const size_t st_bytes = (size_t)3 * v.nx * v.ny * v.esz;
+    e = cudaMemsetAsync(scal + 1, 0, sizeof(double) * 2, v.stream);
+    if (!e) e = cudaMemcpyAsync(ws + L.g, lambda_dev, st_bytes, cudaMemcpyDeviceToDevice, v.stream);
+    void* g0 = nullptr;
+    if (!e) {
+        if (v.dbl) {
+            double2* r = nullptr;
+            e = adj_reverse<double>(v, nsteps, om.data(), checkpoint_every, ws, domega_dev, &r);
+            g0 = r;
+        } else {
+            float2* r = nullptr;
+            e = adj_reverse<float>(v, nsteps, om.data(), checkpoint_every, ws, domega_dev, &r);
+            g0 = r;
+        }
+    }
+    if (!e) e = cudaMemcpyAsync(lambda_dev, g0, st_bytes, cudaMemcpyDeviceToDevice, v.stream);
+    double h[2] = {0, 0};
+    if (!e) e = cudaMemcpyAsync(h, scal + 1, sizeof(h), cudaMemcpyDeviceToHost, v.stream);
+    if (!e) e = cudaStreamSynchronize(v.stream);
+    if (e) return ctx_fail(c, SGPE_ECUDA, cudaGetErrorString(e));
+    if (dw_out) {
+        dw_out[0] = h[0];
+        dw_out[1] = h[1];
+    }
+    return SGPE_OK;
 }
 
 }  // extern "C"

@@ -31,6 +31,7 @@ EXPORTS = ("sgpe_init_grid", "sgpe_workspace_bytes", "sgpe_bind", "sgpe_set_para
            "sgpe_step_real", "sgpe_normalize", "sgpe_energy", "sgpe_set_state", "sgpe_get_state", "sgpe_load_state",
            "sgpe_substep", "sgpe_profile_steps", "sgpe_observables_noalloc", "sgpe_launches_per_step",
            "sgpe_last_error", "sgpe_destroy", "sgpe_adjoint_workspace_bytes", "sgpe_adjoint_loss_grad",
+           "sgpe_adjoint_forward", "sgpe_adjoint_step",
            "sgpe_batch_create", "sgpe_batch_sizes", "sgpe_batch_offsets", "sgpe_batch_bind",
            "sgpe_batch_load_state", "sgpe_batch_step_imag", "sgpe_batch_step_real", "sgpe_batch_energy",
            "sgpe_batch_autotune", "sgpe_batch_set_tiles", "sgpe_batch_launches_per_step", "sgpe_batch_last_error",
@@ -81,6 +82,8 @@ def load():
         "sgpe_destroy": (I, [P]),
         "sgpe_adjoint_workspace_bytes": (I, [P, I, I, ctypes.POINTER(S)]),
         "sgpe_adjoint_loss_grad": (I, [P, I, P, P, I, P, P, P, P]),
+        "sgpe_adjoint_forward": (I, [P, I, P, I, P]),
+        "sgpe_adjoint_step": (I, [P, I, P, I, P, P, P, P]),
         "sgpe_batch_create": (I, [ctypes.POINTER(P), I, P, I, P]),
         "sgpe_batch_sizes": (I, [P, ctypes.POINTER(S), ctypes.POINTER(S)]),
         "sgpe_batch_offsets": (I, [P, P]),
@@ -274,6 +277,36 @@ class Solver:
                                                     ws.data_ptr(), L.ctypes.data, dom.data_ptr(), dw.ctypes.data))
         return float(L[0]), dom, (float(dw[0]), float(dw[1]))
 
+    def adjoint_forward(self, omega_t, checkpoint_every=50):
+        """Run len(omega_t) real-time steps from the current state (which ends as
+        psi_N), keeping checkpoints for adjoint_step (sgpe_adjoint_forward).
+        Returns the tape: the workspace tensor and the Omega table it belongs to."""
+        torch = self.torch
+        om = torch.as_tensor(omega_t, dtype=torch.float64, device=self.device).contiguous()
+        n = int(om.numel())
+        nb = ctypes.c_size_t()
+        self._check(self.lib.sgpe_adjoint_workspace_bytes(self.ctx, n, int(checkpoint_every), ctypes.byref(nb)))
+        ws = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        self._check(self.lib.sgpe_adjoint_forward(self.ctx, n, om.data_ptr(), int(checkpoint_every), ws.data_ptr()))
+        return {"ws": ws, "omega": om, "K": int(checkpoint_every)}
+
+    def adjoint_step(self, tape, lam):
+        """Reverse the steps of a tape from adjoint_forward for the cotangent
+        lam = dL/dpsi_N (device tensor [3][ny][nx] of the state's complex dtype,
+        g = dL/dRe + i dL/dIm); returns (dL/dpsi_0, dL/dOmega (float64 tensor),
+        (dL/dwx, dL/dwy)) (sgpe_adjoint_step)."""
+        torch = self.torch
+        om = tape["omega"]
+        n = int(om.numel())
+        g = lam.detach().to(device=self.device, dtype=self.cdtype).reshape(3, self.ny, self.nx).contiguous().clone()
+        dom = torch.zeros(n, dtype=torch.float64, device=self.device)
+        dw = np.zeros(2)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        self._check(self.lib.sgpe_adjoint_step(self.ctx, n, om.data_ptr(), tape["K"], tape["ws"].data_ptr(),
+                                               g.data_ptr(), dom.data_ptr(), dw.ctypes.data))
+        return g, dom, (float(dw[0]), float(dw[1]))
+
 
 def _rabi_trap_loss_function():
     import torch
@@ -299,6 +332,46 @@ def _rabi_trap_loss_function():
             return grad * dom, grad * dw, None, None, None, None
 
     return RabiTrapLoss
+
+
+def _propagate_function():
+    import torch
+
+    class RealTimePropagation(torch.autograd.Function):
+        """psi_N = S_{N-1} ... S_0 psi_0, the real-time split steps of `solver` with
+        Rabi strengths Omega_n and trap frequencies w = (wx, wy): a differentiable
+        map of (psi_0, Omega(t), w) whose backward runs the library's adjoint
+        (sgpe_adjoint_forward in forward, sgpe_adjoint_step in backward), so any
+        loss the caller computes from psi_N can be differentiated."""
+
+        @staticmethod
+        def forward(ctx, psi0, omega_t, w, solver, checkpoint_every=50):
+            ph = solver.physics
+            phys = Physics(c0=ph.c0, c2=ph.c2, so_type=ph.so_type, gamma=ph.gamma, omega=ph.omega,
+                           wx=float(w[0]), wy=float(w[1]), dt=ph.dt, renorm=0, mag=ph.mag)
+            solver.set_params(phys)
+            solver.load_state(psi0.detach().contiguous())
+            tape = solver.adjoint_forward(omega_t.detach(), checkpoint_every)
+            solver.synchronize()
+            ctx.solver, ctx.tape, ctx.phys = solver, tape, phys
+            ctx.wdev = w.device
+            return solver.psi.clone()
+
+        @staticmethod
+        def backward(ctx, grad):
+            solver = ctx.solver
+            if solver.physics != ctx.phys:
+                solver.set_params(ctx.phys)
+            g0, dom, dw = solver.adjoint_step(ctx.tape, grad)
+            solver.synchronize()
+            return g0, dom, torch.tensor(dw, dtype=torch.float64, device=ctx.wdev), None, None
+
+    return RealTimePropagation
+
+
+def propagate_real(psi0, omega_t, w, solver, checkpoint_every=50):
+    """Differentiable real-time propagation through the GPU solver (see RealTimePropagation)."""
+    return _propagate_function().apply(psi0, omega_t, w, solver, checkpoint_every)
 
 
 def rabi_trap_loss(omega_t, w, solver, psi0, rho_tgt, checkpoint_every=50):

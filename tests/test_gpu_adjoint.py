@@ -105,3 +105,123 @@ def test_differentiation_workload_against_central_differences():
     fdy = (loss(om, wy=1.0 + h) - loss(om, wy=1.0 - h)) / (2 * h)
     assert abs(fdx - dw[0]) < 1e-4 * abs(fdx) + floor
     assert abs(fdy - dw[1]) < 1e-4 * abs(fdy) + floor
+
+
+def test_adjoint_precision_form_moderate_size():
+    """The complex64 adjoint (FP32 state, FP64 gradient sums) against the oracle
+    adjoint at 64 x 64, 50 real-time steps with the workload's physics (c0 = 50,
+    c2 = 1, Rashba gamma = 0.8) and a varying Omega(t), checkpoint every 10 steps:
+    its error against the exact FP64 derivative is the stated error of the form
+    (measured on GB300: loss 1.6e-6, dL/dOmega 7.0e-4 of its largest entry,
+    dL/dw 1.0e-5)."""
+    phys = dict(c0=50.0, c2=1.0, so_type=1, gamma=0.8, omega=0.5, wx=1.0, wy=1.0, dt=1e-3, renorm=0)
+    n, dx, nsteps = 64, 0.2, 50
+    prob, s = make_pair(2, n, n, dx=dx, precision="c64", **phys)
+    psi0 = I.gaussian_phase_2d(n, n, dx, dx, seed=6)
+    tgt = I.gaussian_target(n, n, dx, dx, seed=8)
+    om = 0.5 + 0.2 * np.cos(np.arange(nsteps) * 0.3)
+    L_ref, g_om, g_wx, g_wy, _ = A.loss_and_grad(prob, psi0, om, tgt)
+    s.set_state(psi0)
+    L, dom, dw = s.loss_grad(om, tgt, checkpoint_every=10)
+    e_L = abs(L - L_ref) / abs(L_ref)
+    e_om = np.max(np.abs(dom.cpu().numpy() - g_om)) / np.max(np.abs(g_om))
+    e_w = max(abs(dw[0] - g_wx) / abs(g_wx), abs(dw[1] - g_wy) / abs(g_wy))
+    print("complex64 adjoint vs oracle: loss %.2e, dL/dOmega %.2e, dL/dw %.2e" % (e_L, e_om, e_w))
+    assert e_L < 1e-5
+    assert e_om < 1e-3
+    assert e_w < 1e-3
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("K", [1, 5, 24])
+def test_adjoint_step_random_cotangent(dim, K):
+    """sgpe_adjoint_forward + sgpe_adjoint_step for a random final-state cotangent
+    lam: dL/dpsi_0, dL/dOmega_n and dL/d(wx, wy) of L = Re sum conj(lam) psi_N
+    against the oracle's vector-Jacobian product (exact derivative of the
+    discrete propagator), complex128 at 1e-9."""
+    import torch
+    prob, s, psi0, _, om = _small(dim)
+    cell = prob.dx * (prob.dy if dim == 2 else 1.0)
+    lam = I.random_state(psi0.shape, 91 + K, cell)
+    psiN, g0, gom, gwx, gwy = A.vjp(prob, psi0, om, lam)
+    s.set_state(psi0)
+    tape = s.adjoint_forward(om, checkpoint_every=K)
+    assert np.linalg.norm(s.get_state() - psiN) < 1e-11 * np.linalg.norm(psiN)
+    g, dom, dw = s.adjoint_step(tape, torch.from_numpy(lam).cuda())
+    s.synchronize()
+    assert np.linalg.norm(g.cpu().numpy() - g0) < 1e-9 * np.linalg.norm(g0)
+    assert np.max(np.abs(dom.cpu().numpy() - gom)) < 1e-9 * np.max(np.abs(gom))
+    assert abs(dw[0] - gwx) < 1e-9 * abs(gwx)
+    if dim == 2:
+        assert abs(dw[1] - gwy) < 1e-9 * abs(gwy)
+    # the reverse leaves the bound state (psi_N) alone and can run again on the same tape
+    g2, dom2, dw2 = s.adjoint_step(tape, torch.from_numpy(lam).cuda())
+    s.synchronize()
+    assert torch.equal(g2, g) and torch.equal(dom2, dom) and dw2 == dw
+    assert np.linalg.norm(s.get_state() - psiN) < 1e-11 * np.linalg.norm(psiN)
+
+
+def test_adjoint_step_precision_form():
+    """complex64: the same products against the FP64 oracle, stated bound."""
+    import torch
+    prob, s, psi0, _, om = _small(2, precision="c64")
+    lam = I.random_state(psi0.shape, 93, prob.dx * prob.dy)
+    psiN, g0, gom, gwx, gwy = A.vjp(prob, psi0, om, lam)
+    s.set_state(psi0)
+    tape = s.adjoint_forward(om, checkpoint_every=6)
+    g, dom, dw = s.adjoint_step(tape, torch.from_numpy(lam).cuda())
+    s.synchronize()
+    e_g = np.linalg.norm(g.cpu().numpy() - g0) / np.linalg.norm(g0)
+    e_om = np.max(np.abs(dom.cpu().numpy() - gom)) / np.max(np.abs(gom))
+    print("complex64 adjoint_step vs oracle: dpsi0 %.2e, dOmega %.2e" % (e_g, e_om))
+    assert e_g < 1e-4 and e_om < 1e-3
+    assert abs(dw[0] - gwx) < 1e-3 * abs(gwx)
+
+
+def test_adjoint_step_needs_its_forward_pass():
+    import torch
+    prob, s, psi0, _, om = _small(2)
+    s.set_state(psi0)
+    tape = s.adjoint_forward(om, checkpoint_every=5)
+    lam = torch.zeros((3, prob.ny, prob.nx), dtype=torch.complex128, device="cuda:0")
+    fresh = dict(tape, ws=torch.zeros_like(tape["ws"]))
+    with pytest.raises(sgpe.SgpeError) as e:
+        s.adjoint_step(fresh, lam)
+    assert e.value.status == sgpe.ESTATE
+    with pytest.raises(sgpe.SgpeError) as e:
+        s.adjoint_step(dict(tape, K=6), lam)
+    assert e.value.status == sgpe.ESTATE
+
+
+def test_propagate_real_any_loss():
+    """propagate_real (a torch.autograd.Function on sgpe_adjoint_forward /
+    sgpe_adjoint_step) under a loss written in torch by the caller, against
+    torch.autograd through the oracle's differentiable propagator with the same
+    loss: gradients w.r.t. psi_0, Omega(t) and (wx, wy)."""
+    import torch
+    prob, s, psi0, _, om = _small(2)
+    cell = prob.dx * prob.dy
+
+    def user_loss(psi):
+        rho = psi.real ** 2 + psi.imag ** 2
+        spin = (torch.conj(psi[0]) * psi[2]).real.sum() * cell
+        return cell * (rho[1] ** 2).sum() + 0.3 * spin + cell * (rho[0] - rho[2]).sum() ** 2
+
+    p0 = torch.from_numpy(psi0).cuda().requires_grad_(True)
+    omt = torch.tensor(om, dtype=torch.float64, device="cuda:0", requires_grad=True)
+    w = torch.tensor([prob.wx, prob.wy], dtype=torch.float64, device="cuda:0", requires_grad=True)
+    L = user_loss(sgpe.propagate_real(p0, omt, w, s, 5))
+    L.backward()
+    prop = A.RealTimePropagator(prob)
+    q0 = torch.from_numpy(psi0).requires_grad_(True)
+    oq = torch.tensor(om, dtype=torch.float64, requires_grad=True)
+    wq = torch.tensor([prob.wx, prob.wy], dtype=torch.float64, requires_grad=True)
+    psi = q0
+    for n in range(len(om)):
+        psi = prop.step(psi, oq[n], wq[0], wq[1])
+    Lr = user_loss(psi)
+    Lr.backward()
+    assert abs(L.item() - Lr.item()) < 1e-12 * abs(Lr.item())
+    assert torch.linalg.norm(p0.grad.cpu() - q0.grad) < 1e-9 * torch.linalg.norm(q0.grad)
+    assert torch.max(torch.abs(omt.grad.cpu() - oq.grad)) < 1e-9 * torch.max(torch.abs(oq.grad))
+    assert torch.allclose(w.grad.cpu(), wq.grad, rtol=1e-9, atol=0)

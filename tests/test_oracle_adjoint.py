@@ -59,3 +59,39 @@ def test_gradient_matches_central_differences(oracle, dim):
         setattr(pm, name, getattr(prob, name) - h)
         fd = (_c_loss(oracle, pp, psi0, om, tgt) - _c_loss(oracle, pm, psi0, om, tgt)) / (2 * h)
         assert abs(fd - g) <= 1e-5 * abs(fd), (name, fd, g)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_vjp_matches_central_differences(oracle, dim):
+    """The vector-Jacobian product for a random cotangent lam (L = Re sum conj(lam)
+    psi_N): directional derivatives of the C oracle's L along a random complex
+    direction of psi_0 (dL = Re sum conj(g_0) d), along single Omega_n and along wx
+    / wy, by central differences."""
+    from oracle import adjoint as A
+    prob, psi0, om, _ = _case(oracle, dim)
+    cell = prob.dx * (prob.dy if dim == 2 else 1.0)
+    lam = I.random_state(psi0.shape, 77, cell)
+    d = I.random_state(psi0.shape, 78, cell)
+
+    def c_L(p, psi, omv):
+        out = oracle.step(p, psi, len(omv), imag=False, omega_t=omv)
+        return float(np.real(np.sum(np.conj(lam) * out)))
+
+    psiN, g0, gom, gwx, gwy = A.vjp(prob, psi0, om, lam)
+    assert np.linalg.norm(psiN - oracle.step(prob, psi0, len(om), imag=False, omega_t=om)) < 1e-13 * np.linalg.norm(psiN)
+    h = 1e-5
+    fd = (c_L(prob, psi0 + h * d, om) - c_L(prob, psi0 - h * d, om)) / (2 * h)
+    an = float(np.real(np.sum(np.conj(g0) * d)))
+    assert abs(fd - an) < 1e-6 * max(abs(fd), 1e-3 * np.linalg.norm(g0) * np.linalg.norm(d)), (fd, an)
+    for n in (0, len(om) // 2, len(om) - 1):
+        op, omn = om.copy(), om.copy()
+        op[n] += h
+        omn[n] -= h
+        fd = (c_L(prob, psi0, op) - c_L(prob, psi0, omn)) / (2 * h)
+        assert abs(fd - gom[n]) <= 1e-6 * max(abs(fd), 1e-2 * abs(gom).max()), (n, fd, gom[n])
+    for name, g in (("wx", gwx),) + ((("wy", gwy),) if dim == 2 else ()):
+        pp, pm = oracle.Problem(**prob.__dict__), oracle.Problem(**prob.__dict__)
+        setattr(pp, name, getattr(prob, name) + h)
+        setattr(pm, name, getattr(prob, name) - h)
+        fd = (c_L(pp, psi0, om) - c_L(pm, psi0, om)) / (2 * h)
+        assert abs(fd - g) <= 1e-6 * max(abs(fd), 1e-3), (name, fd, g)

@@ -471,3 +471,23 @@ def test_rms_of_linear_ground_state(oracle, dim):
     for k in ("rms+", "rms0", "rms-", "rms"):
         assert abs(o[k] - dense) < 1e-4 * dense
         assert abs(o[k] - closed) < (2e-3 if dim == 1 else 3e-2) * closed
+
+
+@pytest.mark.parametrize("imag", [True, False])
+def test_oracle_threads_do_not_change_results(oracle, imag):
+    """The oracle's point and line loops on several OpenMP threads give bitwise the
+    same state and observables as on one (every grid sum stays sequential)."""
+    prob = oracle.Problem(dim=2, nx=70, ny=45, dx=0.15, dy=0.2, c0=30.0, c2=-1.0, so_type=1, gamma=0.6,
+                          omega=0.4, dt=1e-3, renorm=1)
+    psi = I.gaussian_phase_2d(70, 45, 0.15, 0.2, seed=12)
+    try:
+        oracle.set_threads(1)
+        a = oracle.step(prob, psi, 15, imag)
+        oa = oracle.observables(prob, a)
+        for n in (2, 5):
+            assert oracle.set_threads(n) == n
+            b = oracle.step(prob, psi, 15, imag)
+            assert np.array_equal(a, b)
+            assert oracle.observables(prob, b) == oa
+    finally:
+        oracle.set_threads(1)
