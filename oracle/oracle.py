@@ -29,7 +29,7 @@ OBS_NAMES = (
     "E_kin", "E_trap", "E_int", "E_rabi", "E_so",
 )
 
-SUBSTEP = {"so": 0, "calcnu": 1, "herm": 2, "cn_x": 3, "cn_y": 4, "renorm": 5}
+SUBSTEP = {"so": 0, "calcnu": 1, "herm": 2, "cn_x": 3, "cn_y": 4, "renorm": 5, "so_cn": 6, "so_cn_rev": 7}
 
 
 def build(force: bool = False) -> str:
@@ -53,6 +53,7 @@ class _Params(ctypes.Structure):
         ("wx", ctypes.c_double), ("wy", ctypes.c_double),
         ("dt", ctypes.c_double),
         ("renorm", ctypes.c_int), ("mag", ctypes.c_double),
+        ("split", ctypes.c_int), ("so_mode", ctypes.c_int),
     ]
 
 
@@ -106,11 +107,13 @@ class Problem:
     dt: float = 1e-4
     renorm: int = 1
     mag: float = 0.0
+    split: int = 0      # 0 Lie, 1 Strang
+    so_mode: int = 0    # 0 explicit Euler SO, 1 Crank-Nicolson SO
 
     def _c(self) -> _Params:
         return _Params(self.dim, self.nx, self.ny if self.dim == 2 else 1, self.dx, self.dy,
                        self.c0, self.c2, self.so_type, self.gamma, self.omega, self.wx, self.wy,
-                       self.dt, self.renorm, self.mag)
+                       self.dt, self.renorm, self.mag, self.split, self.so_mode)
 
     @property
     def shape(self):
@@ -137,7 +140,7 @@ def step(prob: Problem, psi, nsteps: int, imag: bool, omega_t=None) -> np.ndarra
 
 
 def substep(prob: Problem, psi, which: str, imag: bool, omega=None) -> np.ndarray:
-    """Apply one substep ('so', 'calcnu', 'herm', 'cn_x', 'cn_y', 'renorm')."""
+    """Apply one substep ('so', 'calcnu', 'herm', 'cn_x', 'cn_y', 'renorm', 'so_cn', 'so_cn_rev')."""
     lib = _load()
     a = _state(prob, psi)
     p = prob._c()

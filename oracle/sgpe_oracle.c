@@ -66,6 +66,9 @@ typedef struct {
     double dt;           /* time step Delta */
     int renorm;          /* 0 none, 1 Eq. (DJ2), 2 Eq. (DJ) with magnetisation mag */
     double mag;
+    int split;           /* 0: Lie splitting, one full dt per substep (the paper's successive
+                            treatment); 1: Strang splitting (half steps around the kinetic step) */
+    int so_mode;         /* 0: SO by explicit Euler, Eqs. (p1)-(p2); 1: SO by Crank-Nicolson */
 } orc_params;
 
 #define IDX(p, j, iy, ix) ((((size_t)(j)) * (p)->ny + (size_t)(iy)) * (p)->nx + (size_t)(ix))
@@ -153,6 +156,118 @@ void orc_so(const orc_params* p, cplx* psi, cplx z) {
             for (int j = 0; j < 3; j++) psi[IDX(p, j, iy, ix)] = old[IDX(p, j, iy, ix)] - z * h[j];
         }
     free(old);
+}
+
+/* 3x3 complex matrices (row major) for the block elimination below. */
+static void m3_mul(const cplx* a, const cplx* b, cplx* c) {
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            cplx t = 0.0;
+            for (int k = 0; k < 3; k++) t += a[3 * i + k] * b[3 * k + j];
+            c[3 * i + j] = t;
+        }
+}
+static void m3_vec(const cplx* a, const cplx* x, cplx* y) {
+    for (int i = 0; i < 3; i++) y[i] = a[3 * i] * x[0] + a[3 * i + 1] * x[1] + a[3 * i + 2] * x[2];
+}
+/* inverse by the adjugate (the matrices here are I + small terms) */
+static void m3_inv(const cplx* a, cplx* r) {
+    cplx c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+    cplx c10 = a[2] * a[7] - a[1] * a[8], c11 = a[0] * a[8] - a[2] * a[6], c12 = a[1] * a[6] - a[0] * a[7];
+    cplx c20 = a[1] * a[5] - a[2] * a[4], c21 = a[2] * a[3] - a[0] * a[5], c22 = a[0] * a[4] - a[1] * a[3];
+    cplx det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    r[0] = c00 / det; r[1] = c10 / det; r[2] = c20 / det;
+    r[3] = c01 / det; r[4] = c11 / det; r[5] = c21 / det;
+    r[6] = c02 / det; r[7] = c12 / det; r[8] = c22 / det;
+}
+
+/*
+ * Crank-Nicolson for the SO operator of one line: H = g S p with p = -i d/ds
+ * (the central difference of the SO substep, zero ghosts), S a 3x3 spin
+ * matrix of Eq. (smat) and g a real strength:
+ *   (I + z/2 H) psi' = (I - z/2 H) psi,
+ * a block-tridiagonal system in the three components: with B = -i z g S / (4 h),
+ *   row i:  -B psi'_{i-1} + psi'_i + B psi'_{i+1} = psi_i - B (psi_{i+1} - psi_{i-1}),
+ * solved by block Gaussian elimination (3x3 blocks, no pivoting).
+ * f: the line's components at f[j*cstride + i*stride], n points.
+ */
+static void so_cn_line(cplx* f, size_t cstride, size_t stride, int n, const cplx S[9], double g, double h, cplx z) {
+    cplx B[9];
+    for (int k = 0; k < 9; k++) B[k] = -I * z * g * S[k] / (4.0 * h);
+    cplx* r = malloc((size_t)n * 3 * sizeof(cplx));
+    cplx* Ch = malloc((size_t)n * 9 * sizeof(cplx));
+    for (int i = 0; i < n; i++) {
+        cplx d[3];
+        for (int j = 0; j < 3; j++) {
+            cplx up = i + 1 < n ? f[j * cstride + (i + 1) * stride] : 0.0;
+            cplx dn = i > 0 ? f[j * cstride + (i - 1) * stride] : 0.0;
+            d[j] = up - dn;
+        }
+        cplx Bd[3];
+        m3_vec(B, d, Bd);
+        for (int j = 0; j < 3; j++) r[3 * i + j] = f[j * cstride + i * stride] - Bd[j];
+    }
+    /* forward elimination: M_i = I + B Ch_{i-1}, Ch_i = M_i^{-1} B, r_i <- M_i^{-1} (r_i + B r_{i-1}) */
+    for (int i = 0; i < n; i++) {
+        cplx M[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, Mi[9], t[3];
+        if (i > 0) {
+            cplx BC[9];
+            m3_mul(B, &Ch[9 * (i - 1)], BC);
+            for (int k = 0; k < 9; k++) M[k] += BC[k];
+            m3_vec(B, &r[3 * (i - 1)], t);
+            for (int j = 0; j < 3; j++) r[3 * i + j] += t[j];
+        }
+        m3_inv(M, Mi);
+        m3_mul(Mi, B, &Ch[9 * i]);
+        m3_vec(Mi, &r[3 * i], t);
+        for (int j = 0; j < 3; j++) r[3 * i + j] = t[j];
+    }
+    /* back substitution: x_i = r_i - Ch_i x_{i+1} */
+    for (int i = n - 2; i >= 0; i--) {
+        cplx t[3];
+        m3_vec(&Ch[9 * i], &r[3 * (i + 1)], t);
+        for (int j = 0; j < 3; j++) r[3 * i + j] -= t[j];
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < 3; j++) f[j * cstride + i * stride] = r[3 * i + j];
+    free(r);
+    free(Ch);
+}
+
+/*
+ * SO substep by Crank-Nicolson instead of explicit Euler: the SO operator of
+ * Sec. 2 treated like the kinetic term. 1D: H_SO = gamma S p_x with S = Sigma_x,
+ * Sigma_y or Sigma_z (OPT_SO 1..3), one block line per grid. 2D: H_SO =
+ * gamma (eta p_y Sigma_x - p_x Sigma_y) = H_x + H_y, H_x = -gamma Sigma_y p_x
+ * along x lines and H_y = gamma eta Sigma_x p_y along y lines, each by
+ * Crank-Nicolson in turn (x then y; y then x when reverse), as the kinetic term
+ * is treated along x and then y. Each factor is a Cayley transform of a
+ * Hermitian operator, so in real time the substep conserves the norm.
+ */
+void orc_so_cn(const orc_params* p, cplx* psi, cplx z, int reverse) {
+    if (p->so_type == 0 || p->gamma == 0.0) return;
+    const double r2 = 1.0 / sqrt(2.0);
+    const cplx SX[9] = {0, r2, 0, r2, 0, r2, 0, r2, 0};
+    const cplx SY[9] = {0, -I * r2, 0, I * r2, 0, -I * r2, 0, I * r2, 0};
+    const cplx SZ[9] = {1, 0, 0, 0, 0, 0, 0, 0, -1};
+    const size_t plane = (size_t)p->nx * p->ny;
+    if (p->dim == 1) {
+        const cplx* S = p->so_type == 1 ? SX : (p->so_type == 2 ? SY : SZ);
+        so_cn_line(psi, plane, 1, p->nx, S, p->gamma, p->dx, z);
+        return;
+    }
+    const double eta = p->so_type == 1 ? 1.0 : (p->so_type == 2 ? -1.0 : 0.0);
+    for (int pass = 0; pass < 2; pass++) {
+        const int along_x = (pass == 0) != (reverse != 0);
+        if (along_x) {
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+            for (int iy = 0; iy < p->ny; iy++) so_cn_line(&psi[IDX(p, 0, iy, 0)], plane, 1, p->nx, SY, -p->gamma, p->dx, z);
+        } else if (eta != 0.0) {
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+            for (int ix = 0; ix < p->nx; ix++)
+                so_cn_line(&psi[IDX(p, 0, 0, ix)], plane, (size_t)p->nx, p->ny, SX, eta * p->gamma, p->dy, z);
+        }
+    }
 }
 
 /*
@@ -322,16 +437,34 @@ void orc_step(const orc_params* p, cplx* psi, int nsteps, int imag, const double
     cplx z = imag ? (cplx)p->dt : I * p->dt;
     for (int n = 0; n < nsteps; n++) {
         double om = omega_t ? omega_t[n] : p->omega;
-        orc_so(p, psi, z);
-        orc_calcnu(p, psi, z);
-        orc_herm(p, psi, z, om);
-        orc_cn_x(p, psi, z);
-        orc_cn_y(p, psi, z);
+        if (!p->split) {
+            if (p->so_mode) orc_so_cn(p, psi, z, 0);
+            else orc_so(p, psi, z);
+            orc_calcnu(p, psi, z);
+            orc_herm(p, psi, z, om);
+            orc_cn_x(p, psi, z);
+            orc_cn_y(p, psi, z);
+        } else {
+            /* Strang: the same substeps with z/2 around the kinetic step (CN along
+               x and y, which commute), then again in the reverse order */
+            cplx h = 0.5 * z;
+            if (p->so_mode) orc_so_cn(p, psi, h, 0);
+            else orc_so(p, psi, h);
+            orc_calcnu(p, psi, h);
+            orc_herm(p, psi, h, om);
+            orc_cn_x(p, psi, z);
+            orc_cn_y(p, psi, z);
+            orc_herm(p, psi, h, om);
+            orc_calcnu(p, psi, h);
+            if (p->so_mode) orc_so_cn(p, psi, h, 1);
+            else orc_so(p, psi, h);
+        }
         if (imag && p->renorm) orc_renorm(p, psi);
     }
 }
 
-/* One named substep, for per-substep tests: 0 SO, 1 CALCNU, 2 HERM, 3 CN-x, 4 CN-y, 5 RENORM. */
+/* One named substep, for per-substep tests: 0 SO, 1 CALCNU, 2 HERM, 3 CN-x, 4 CN-y, 5 RENORM,
+   6 SO by Crank-Nicolson (x lines, then y lines), 7 the same in the reverse order. */
 int orc_substep(const orc_params* p, cplx* psi, int which, int imag, double omega) {
     cplx z = imag ? (cplx)p->dt : I * p->dt;
     switch (which) {
@@ -341,6 +474,8 @@ int orc_substep(const orc_params* p, cplx* psi, int which, int imag, double omeg
         case 3: orc_cn_x(p, psi, z); return 0;
         case 4: orc_cn_y(p, psi, z); return 0;
         case 5: orc_renorm(p, psi); return 0;
+        case 6: orc_so_cn(p, psi, z, 0); return 0;
+        case 7: orc_so_cn(p, psi, z, 1); return 0;
         default: return -1;
     }
 }
