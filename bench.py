@@ -232,14 +232,18 @@ def extra_workloads(dev, reps=2):
       quench        2D 512 x 512, dx = 0.04, the 2D physics above; ground state prepared
                     in FP64 (3000 imaginary-time steps, untimed), then Omega 0.5 -> 0 and
                     10,000 real-time steps at dt = 1e-4 in complex64 and complex128
-                    (energy / norm drift of complex64 against complex128)
+                    (energy / norm of complex64 against complex128 after 10,000 steps, and
+                    of both against the FP64 oracle on every host core after 1,000)
       batched       64 instances (32 1D nx ~ U{128..1024}, 32 2D n ~ U{128..384}), per-instance
                     (gamma, Omega, c0, c2) drawn, 1,000 imaginary-time steps, autotuned tiles
       adjoint       2D 256 x 256 real time, 500 steps at dt = 2e-4, gradient of the
                     final-density loss w.r.t. Omega(t) and (wx, wy), checkpoint every 50
+                    (the loss also against the FP64 oracle)
+      step_options  the headline workload with Strang splitting, with the SO substep by
+                    Crank-Nicolson, and with both (complex128)
       large         the 2D physics above at 2048 x 2048 and 4096 x 4096 (dx = 0.05), 10
-                    imaginary-time steps in complex64 and complex128: the state (100 MB to
-                    805 MB) does not fit in L2, so the two streaming passes go to HBM;
+                    imaginary-time steps in complex64, double-float and complex128: the state
+                    (100 MB to 805 MB) does not fit in L2, so the two streaming passes go to HBM;
                     effective GB/s (96 / 192 algorithmic bytes per point-step) against the
                     measured HBM copy peak
     """
@@ -300,10 +304,32 @@ def extra_workloads(dev, reps=2):
         t = ev_time(s3.stream, lambda: s3.step_real(10000))
         e = s3.energy()
         q[prec] = {"value": n3 * n3 * 10000 / (t * 1e-3), "ms": t, "E0": e0["E"], "E": e["E"], "N": e["N"]}
+    # against the FP64 oracle (every host core): the first 1000 quench steps from the same ground state
+    from oracle import oracle as O
+    O.build()
+    n_orc = 1000
+    ground_h = ground.cpu().numpy()
+    prob3 = O.Problem(dim=2, nx=n3, ny=n3, dx=dx3, dy=dx3, **dict(phys, omega=0.0, dt=1e-4, renorm=0))
+    cores = O.set_threads(0)
+    t0 = time.perf_counter()
+    ref3 = O.observables(prob3, O.step(prob3, ground_h, n_orc, False))
+    t_orc = time.perf_counter() - t0
+    O.set_threads(1)
+    vs_oracle = {}
+    for prec in ("c128", "c64"):
+        s3 = sgpe.Solver(2, n3, n3, dx=dx3, precision=prec, device=dev)
+        s3.set_params(sgpe.Physics(**dict(phys, omega=0.0, dt=1e-4, renorm=0)))
+        s3.load_state(ground.to(s3.cdtype))
+        s3.step_real(n_orc)
+        e = s3.energy()
+        vs_oracle[prec] = {"energy_rel_err": abs(e["E"] - ref3["E"]) / abs(ref3["E"]),
+                           "norm_err": abs(e["N"] - ref3["N"])}
     out["quench"] = {"value": q["c64"]["value"], "unit": METRIC, "precision": "complex64 (FP64 reductions)",
                      "fp64_value": q["c128"]["value"],
-                     "energy_rel_err_vs_fp64": abs(q["c64"]["E"] - q["c128"]["E"]) / abs(q["c128"]["E"]),
-                     "norm_err_vs_fp64": abs(q["c64"]["N"] - q["c128"]["N"]),
+                     "vs_oracle_after_1000_steps": vs_oracle,
+                     "oracle": {"steps": n_orc, "seconds": t_orc, "cores": cores},
+                     "energy_rel_err_vs_fp64_gpu_10000_steps": abs(q["c64"]["E"] - q["c128"]["E"]) / abs(q["c128"]["E"]),
+                     "norm_err_vs_fp64_gpu_10000_steps": abs(q["c64"]["N"] - q["c128"]["N"]),
                      "energy_drift_fp64": q["c128"]["E"] - q["c128"]["E0"], "detail": q}
     # batched
     inst = []
@@ -339,10 +365,11 @@ def extra_workloads(dev, reps=2):
     peak = measured_hbm_gbs()
     big = {}
     for n4 in (2048, 4096):
-        for prec in ("c64", "c128"):
+        for prec in ("c64", "cdf", "c128"):
             sl = sgpe.Solver(2, n4, n4, dx=DX, precision=prec, device=dev)
             sl.set_params(sgpe.Physics(**PHYS))
             pl = torch.from_numpy(I.gaussian_phase_2d(n4, n4, DX, DX, seed=0)).to(sl.cdtype).to(dev)
+            # (the double-float state is 16 bytes a complex number, like complex128)
             ms = []
             for r in range(reps + 1):
                 sl.load_state(pl)
@@ -375,8 +402,31 @@ def extra_workloads(dev, reps=2):
             if r:
                 times.append((time.perf_counter() - t0) * 1e3)
         ares[prec] = {"ms_per_gradient": statistics.mean(times), "loss": L, "dL_dwx": dw[0], "dL_dwy": dw[1]}
+    # the loss of the same 500 real-time steps by the FP64 oracle (every host core)
+    proba = O.Problem(dim=2, nx=NX, ny=NY, dx=DX, dy=DX, **dict(PHYS, renorm=0))
+    O.set_threads(0)
+    psiN = O.step(proba, psi0, 500, False, omega_t=np.full(500, 0.5))
+    O.set_threads(1)
+    L_orc = DX * DX * float(np.sum((np.sum(np.abs(psiN) ** 2, axis=0) - tgt) ** 2))
+    # the step options on the headline workload (complex128, 2000 imaginary-time steps)
+    var = {}
+    for name, kw in (("strang", dict(split=1)), ("so_crank_nicolson", dict(so_mode=1)),
+                     ("strang_so_crank_nicolson", dict(split=1, so_mode=1))):
+        sv = sgpe.Solver(2, NX, NY, dx=DX, precision="c128", device=dev)
+        sv.set_params(sgpe.Physics(**dict(PHYS, **kw)))
+        pv = torch.from_numpy(psi0.astype(np.complex128)).to(dev)
+        ms = []
+        for r in range(reps + 1):
+            sv.load_state(pv)
+            t = ev_time(sv.stream, lambda: sv.step_imag(NSTEPS))
+            if r:
+                ms.append(t)
+        var[name] = {"value": NX * NY * NSTEPS / (statistics.mean(ms) * 1e-3), "ms": statistics.mean(ms),
+                     "E": sv.energy()["E"], "launches_per_step": sv.launches_per_step()}
+    out["step_options"] = var
     out["adjoint"] = {"value": ares["c64"]["ms_per_gradient"], "unit": "ms per gradient", "precision": "complex64",
                       "fp64_ms_per_gradient": ares["c128"]["ms_per_gradient"],
+                      "loss_rel_err_vs_oracle": {p_: abs(ares[p_]["loss"] - L_orc) / L_orc for p_ in ("c64", "c128")},
                       "loss_rel_err_vs_fp64": abs(ares["c64"]["loss"] - ares["c128"]["loss"]) / ares["c128"]["loss"],
                       "dL_dwx_rel_err_vs_fp64": abs(ares["c64"]["dL_dwx"] - ares["c128"]["dL_dwx"])
                       / abs(ares["c128"]["dL_dwx"])}
@@ -472,6 +522,13 @@ def main():
     dom_name = ("k_pwx<double, imag, 8> (SO+CALCNU+HERM, CN-x)" if fused
                 else "k_pointwise<double> (SO+CALCNU+HERM)")
     achieved_tflops = dom_flops * NX * NY / (dom_ms * 1e-3) / 1e12
+    # the FP64 roof measured on this GPU in this run (FMA-chain kernel, CUDA events)
+    try:
+        fp64_peak = sgpe.measure_fp64_rate(solver.stream)
+        peak_source = "measured in this run: FP64 FMA-chain kernel (sgpe_measure_fp64_rate), CUDA events"
+    except Exception as exc:  # keep the line; say why the nominal figure is used
+        fp64_peak = FP64_PEAK_TFLOPS
+        peak_source = "nominal FP64 (152 SMs x 2 DFMA/clk x 2 x 2.07 GHz); measurement failed: %s" % exc
 
     # precision form (complex64 state, FP64 reductions) on the same workload
     s32 = sgpe.Solver(2, NX, NY, dx=DX, precision="c64", device=dev)
@@ -540,9 +597,9 @@ def main():
         "time_steps_per_bench_step": NSTEPS,
         "config": bench_config(ws),
         "roofline": {"bound": "alu", "kernel": dom_name,
-                     "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": HEAD_TRAFFIC_BYTES,
-                     "peak_source": "nominal FP64: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (measured 1.20 at 1995 MHz)",
+                     "achieved": achieved_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / fp64_peak, "traffic": HEAD_TRAFFIC_BYTES,
+                     "peak_source": peak_source, "nominal_peak": FP64_PEAK_TFLOPS,
                      "flops_per_point": dom_flops, "avg_launch_ms": dom_ms},
         "kernels": {"avg_ms": kavg, "share": share, "dominant": dom},
         "hbm_view": hbm_view(value / ws * 192 / 1e9),

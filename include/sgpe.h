@@ -77,6 +77,19 @@ typedef enum { SGPE_C128 = 0, SGPE_C64 = 1, SGPE_CDF = 2 } sgpe_precision;
  *  dt       time step Delta (> 0).
  *  renorm   imaginary time only: 0 none, 1 Eq. (DJ2) (unit norm), 2 Eq. (DJ) (unit
  *           norm and magnetisation mag, |mag| < 1). Real time never renormalises.
+ *  split    0: Lie splitting, the substeps treated successively with one full dt
+ *           each (Sec. 3). 1: Strang splitting: SO, CALCNU and HERM with dt/2,
+ *           Crank-Nicolson along x and y with dt, then HERM, CALCNU and SO with
+ *           dt/2 (second order in dt where every substep is symmetric).
+ *  so_mode  0: the SO substep by explicit Euler, Appendix A Eqs. (p1)-(p2) (in real
+ *           time the norm grows by dt^2 |H_SO psi|^2 per step). 1: the SO operator
+ *           treated by Crank-Nicolson like the kinetic term, (I + z/2 H_SO) psi' =
+ *           (I - z/2 H_SO) psi along lines (2D: the part -gamma Sigma_y p_x along x
+ *           lines, then gamma eta Sigma_x p_y along y lines; the reverse order in the
+ *           second half of a Strang step): unitary in real time. Needs lines of at
+ *           most 1024 points (SGPE_EUNSUPPORTED from sgpe_set_params otherwise).
+ *           split or so_mode other than 0: unfused kernels (more launches per step);
+ *           not available for the batched and adjoint entry points.
  */
 typedef struct {
     double c0, c2;
@@ -86,6 +99,8 @@ typedef struct {
     double dt;
     int renorm;
     double mag;
+    int split;
+    int so_mode;
 } sgpe_params;
 
 /* Indices of the observables written by sgpe_energy (SGPE_NOBS doubles). */
@@ -196,7 +211,9 @@ sgpe_status sgpe_load_state(sgpe_ctx* ctx, const void* psi_dev);
 /*
  * Apply ONE substep to the bound state, for per-substep checks: which = 0 SO,
  * 1 CALCNU, 2 HERM, 3 Crank-Nicolson along x, 4 along y (2D only), 5
- * renormalisation by params.renorm; imag selects z = dt (1) or z = i dt (0);
+ * renormalisation by params.renorm, 6 the SO substep by Crank-Nicolson (x lines
+ * then y lines; with the step's SO time step: dt, or dt/2 when params.split =
+ * 1), 7 the same in the reverse order; imag selects z = dt (1) or z = i dt (0);
  * omega is the Rabi strength used by HERM. The pending scale is applied first.
  * Asynchronous.
  */
@@ -216,6 +233,17 @@ sgpe_status sgpe_substep(sgpe_ctx* ctx, int which, int imag, double omega);
  * Advances the state exactly like the step functions. Synchronises the stream.
  */
 sgpe_status sgpe_profile_steps(sgpe_ctx* ctx, int nsteps, int imag, double* ms_out, int* launches_out);
+
+/*
+ * Measurement aid (no counterpart in the paper): the FP64 fused multiply-add
+ * rate of the current device in TFLOP/s (FMA = 2 flops), from a kernel of
+ * independent FMA chains, 8 blocks of 256 threads per SM, timed with CUDA events
+ * on cuda_stream (best of three timed launches after one warm-up, ~0.1 s).
+ * It is the measured roof of the FP64 step kernels. Synchronises the stream.
+ * Returns SGPE_EINVAL for a null output, SGPE_ECUDA if a CUDA call fails
+ * (sgpe_last_error(NULL) then says which).
+ */
+sgpe_status sgpe_measure_fp64_rate(void* cuda_stream, double* tflops_out);
 
 /*
  * sgpe_observables_noalloc -- the SGPE_NOBS observables of sgpe_energy for a

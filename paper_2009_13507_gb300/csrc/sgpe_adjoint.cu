@@ -459,6 +459,10 @@ static sgpe_status adj_prepare(sgpe_ctx* c, CtxView* v, int nsteps, const double
         snprintf(msg, sizeof(msg), "%s: not available for SGPE_CDF", who);
         return ctx_fail(c, SGPE_EUNSUPPORTED, msg);
     }
+    if (v->kp.split || v->kp.so_mode) {
+        snprintf(msg, sizeof(msg), "%s: the reverse of Lie splitting with the Euler SO only", who);
+        return ctx_fail(c, SGPE_EUNSUPPORTED, msg);
+    }
     if (nsteps < 1 || K < 1 || !omega_dev || !ws) {
         snprintf(msg, sizeof(msg), "%s: bad arguments", who);
         return ctx_fail(c, SGPE_EINVAL, msg);
@@ -490,10 +494,10 @@ sgpe_status sgpe_adjoint_loss_grad(sgpe_ctx* c, int nsteps, const double* omega_
     if (!c) return SGPE_EINVAL;
     CtxView v;
     std::vector<double> om;
-    if (!rho_target_dev || !domega_dev || ((uintptr_t)rho_target_dev & 7) || ((uintptr_t)domega_dev & 7))
-        return ctx_fail(c, SGPE_EINVAL, "adjoint: null or misaligned target / gradient buffer");
     sgpe_status st = adj_prepare(c, &v, nsteps, omega_dev, checkpoint_every, adj_workspace, &om, "adjoint");
     if (st) return st;
+    if (!rho_target_dev || !domega_dev || ((uintptr_t)rho_target_dev & 7) || ((uintptr_t)domega_dev & 7))
+        return ctx_fail(c, SGPE_EINVAL, "adjoint: null or misaligned target / gradient buffer");
     cudaError_t e = ctx_flush(c);  // apply any pending renormalisation: the forward starts at scale 1
     if (e) return ctx_fail(c, SGPE_ECUDA, cudaGetErrorString(e));
     return v.dbl ? adj_run<double>(c, v, nsteps, om.data(), rho_target_dev, checkpoint_every,

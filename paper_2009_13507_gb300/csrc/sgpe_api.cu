@@ -15,6 +15,7 @@
 #include "sgpe_device.cuh"
 #include "sgpe_kernels.cuh"
 #include "sgpe_launch.h"
+#include "sgpe_socn.cuh"
 
 using namespace sgpe;
 
@@ -39,7 +40,7 @@ Geometry make_geometry(int dim, int nx, int ny, int esz) {
     g.reg_y = ny <= kRegMaxN;
     const int nwy = long_warps(ny);
     g.wy = g.reg_y ? 1 : std::max(1, std::min(32 / esz, kLongMaxWarps / nwy));
-    g.smem_y = g.reg_y ? 0 : (size_t)g.wy * 32 * nwy * (kLongC + 1) * esz;
+    g.smem_y = g.reg_y ? 0 : (size_t)g.wy * (32 * nwy * (kLongC + 1) + long_col_pad(esz, g.wy)) * esz;
     g.blocks_y = dim == 2 ? 3 * ceil_div(nx, g.reg_y ? cny_cols_per_warp(chunk_len(ny), esz) : g.wy) : 0;
     g.blocks_obs = ceil_div(nx, 32) * ceil_div(ny, 4);
     g.blocks_norm = kNormBlocks;
@@ -79,10 +80,16 @@ struct sgpe_ctx {
     void* mid;
     void* tabs[3][2][4];  // [mode: 0 imag, 1 real, 2 real with -dt (adjoint)][axis: 0 x, 1 y][fa, fg, fp, fq]
     double* partials;
+    // SO by Crank-Nicolson (params.so_mode = 1): skew tables [mode: 0 imag, 1 real][axis][m: +1, -1][4]
+    // and the line families [mode][axis]
+    void* tabs_so[2][2][2][4];
+    SoCnLines socn[2][2];
+    bool socn_y;  // 2D with eta != 0: a y part
     // parameters
     bool have_params;
     sgpe_params params;
     KParams kp;
+    KParams kp_half;  // the same with dt/2 (Strang splitting)
     // graph cache
     std::map<GraphKey, cudaGraphExec_t> graphs;
     bool graphs_ok;
@@ -119,7 +126,7 @@ static sgpe_status cuda_fail(sgpe_ctx* c, cudaError_t e, const char* where) {
     } while (0)
 
 struct Layout {
-    size_t sc, mid, tabs[3][2][4], partials, total;
+    size_t sc, mid, tabs[3][2][4], tabs_so[2][2][2][4], partials, total;
 };
 
 static Layout layout_of(const sgpe_ctx* c) {
@@ -136,6 +143,15 @@ static Layout layout_of(const sgpe_ctx* c) {
                 L.tabs[m][a][k] = off;
                 off = align256(off + (size_t)table_len(n) * c->esz);
             }
+        }
+    for (int m = 0; m < 2; m++)
+        for (int a = 0; a < 2; a++) {
+            const int n = a == 0 ? c->nx : c->ny;
+            for (int q = 0; q < 2; q++)
+                for (int k = 0; k < 4; k++) {
+                    L.tabs_so[m][a][q][k] = off;
+                    off = align256(off + (size_t)table_len(n) * c->esz);
+                }
         }
     L.partials = off;
     size_t np = 0;
@@ -160,6 +176,8 @@ const char* check_params(const sgpe_params* p) {
     if (p->so_type < 0 || p->so_type > 3) return "so_type must be 0..3";
     if (p->renorm < 0 || p->renorm > 2) return "renorm must be 0, 1 or 2";
     if (p->renorm == 2 && !(fabs(p->mag) < 1.0)) return "renorm 2 needs |mag| < 1";
+    if (p->split != 0 && p->split != 1) return "split must be 0 (Lie) or 1 (Strang)";
+    if (p->so_mode != 0 && p->so_mode != 1) return "so_mode must be 0 (Euler) or 1 (Crank-Nicolson)";
     const double vals[] = {p->c0, p->c2, p->gamma, p->omega, p->wx, p->wy, p->mag};
     for (double v : vals)
         if (!isfinite(v)) return "non-finite parameter";
@@ -203,9 +221,84 @@ KParams make_kparams(int dim, int nx, int ny, double dx, double dy, const sgpe_p
     k.cell = dim == 2 ? dx * dy : dx;
     k.renorm = p->renorm;
     k.mag = p->mag;
+    k.split = p->split;
+    k.so_mode = p->so_mode;
     return k;
 }
 }  // namespace sgpe
+
+// The SO-CN line families and their skew tables for the current parameters:
+// the SO time step is dt (dt/2 with Strang splitting); along each family the
+// operator is g S p (1D: gamma Sigma_(x|y|z); 2D: -gamma Sigma_y along x,
+// eta gamma Sigma_x along y) and a_(+1) = -i z g / (4 h).
+static void spin_eigvecs(int which, double* ur, double* ui) {
+    // columns: eigenvectors of m = +1, 0, -1 (U[j][k] at 3j + k)
+    const double r = 0.70710678118654752440;
+    for (int q = 0; q < 9; q++) ur[q] = ui[q] = 0.0;
+    if (which == 0) {  // Sigma_x
+        const double u[9] = {0.5, r, 0.5, r, 0.0, -r, 0.5, -r, 0.5};
+        for (int q = 0; q < 9; q++) ur[q] = u[q];
+    } else if (which == 1) {  // Sigma_y
+        const double u[9] = {0.5, r, 0.5, 0.0, 0.0, 0.0, -0.5, r, -0.5};
+        for (int q = 0; q < 9; q++) ur[q] = u[q];
+        ui[3] = r;   // U[1][0] = i/sqrt2
+        ui[5] = -r;  // U[1][2] = -i/sqrt2
+    } else {  // Sigma_z
+        ur[0] = ur[4] = ur[8] = 1.0;
+    }
+}
+
+static sgpe_status build_socn(sgpe_ctx* c) {
+    const sgpe_params& p = c->params;
+    c->socn_y = false;
+    if (c->kp.so_case == 0 || c->nx > kRegMaxN || (c->dim == 2 && c->ny > kRegMaxN)) return SGPE_OK;
+    const double dts = p.split ? 0.5 * p.dt : p.dt;
+    const double eta = p.so_type == 1 ? 1.0 : (p.so_type == 2 ? -1.0 : 0.0);
+    c->socn_y = c->dim == 2 && eta != 0.0;
+    for (int a = 0; a < c->dim; a++) {
+        int which;
+        double g, h = a == 0 ? c->dx : c->dy;
+        if (c->dim == 1) {
+            which = p.so_type - 1;
+            g = p.gamma;
+        } else if (a == 0) {
+            which = 1;
+            g = -p.gamma;
+        } else {
+            which = 0;
+            g = eta * p.gamma;
+        }
+        for (int m = 0; m < 2; m++) {
+            SoCnLines& L = c->socn[m][a];
+            spin_eigvecs(which, L.ur, L.ui);
+            const double q = dts * g / (4.0 * h);
+            L.are = m == 0 ? 0.0 : q;   // imaginary time: a = -i dt g/(4h)
+            L.aim = m == 0 ? -q : 0.0;  // real time: a = dt g/(4h)
+            L.plane = (long long)c->nx * c->ny;
+            if (a == 0) {
+                L.n = c->nx;
+                L.nlines = c->ny;
+                L.stride = 1;
+                L.lstride = c->nx;
+            } else {
+                L.n = c->ny;
+                L.nlines = c->nx;
+                L.stride = c->nx;
+                L.lstride = 1;
+            }
+            if (a == 1 && !c->socn_y) continue;
+            void** tp = c->tabs_so[m][a][0];
+            void** tm = c->tabs_so[m][a][1];
+            cudaError_t e = with_prec(c->prec, [&](auto r) {
+                cudaError_t e1 = Launcher<decltype(r)>::coef_skew(c->stream, tp[0], tp[1], tp[2], tp[3], L.n, L.are, L.aim);
+                if (e1) return e1;
+                return Launcher<decltype(r)>::coef_skew(c->stream, tm[0], tm[1], tm[2], tm[3], L.n, -L.are, -L.aim);
+            });
+            CK(e, "SO Crank-Nicolson tables");
+        }
+    }
+    return SGPE_OK;
+}
 
 extern "C" {
 
@@ -270,6 +363,10 @@ sgpe_status sgpe_bind(sgpe_ctx* c, void* psi_dev, void* workspace_dev) {
     for (int m = 0; m < 3; m++)
         for (int a = 0; a < 2; a++)
             for (int k = 0; k < 4; k++) c->tabs[m][a][k] = c->work + L.tabs[m][a][k];
+    for (int m = 0; m < 2; m++)
+        for (int a = 0; a < 2; a++)
+            for (int q = 0; q < 2; q++)
+                for (int k = 0; k < 4; k++) c->tabs_so[m][a][q][k] = c->work + L.tabs_so[m][a][q][k];
     c->partials = (double*)(c->work + L.partials);
     c->have_params = false;
     CK(cudaMemsetAsync(c->sc, 0, sizeof(DevScalars), c->stream), "sgpe_bind memset");
@@ -281,9 +378,15 @@ sgpe_status sgpe_set_params(sgpe_ctx* c, const sgpe_params* p) {
     if (!c || !p) return SGPE_EINVAL;
     if (!c->psi) return fail(c, SGPE_ESTATE, "sgpe_set_params: no buffers bound");
     if (const char* why = check_params(p)) return fail(c, SGPE_EINVAL, "%s", why);
+    if (p->so_mode && p->so_type != 0 && (c->nx > kRegMaxN || (c->dim == 2 && c->ny > kRegMaxN)))
+        return fail(c, SGPE_EUNSUPPORTED, "so_mode 1 needs lines of at most %d points", kRegMaxN);
     invalidate_graphs(c);
     c->params = *p;
     c->kp = make_kparams(c->dim, c->nx, c->ny, c->dx, c->dy, p);
+    sgpe_params ph = *p;
+    ph.dt = 0.5 * p->dt;
+    c->kp_half = make_kparams(c->dim, c->nx, c->ny, c->dx, c->dy, &ph);
+    if (sgpe_status st = build_socn(c)) return st;
     // COEF: Crank-Nicolson tables, bt = z/(4 h^2), z = dt (imaginary), i dt (real), -i dt (adjoint)
     for (int m = 0; m < 3; m++)
         for (int a = 0; a < (c->dim == 2 ? 2 : 1); a++) {
@@ -309,7 +412,11 @@ sgpe_status sgpe_set_params(sgpe_ctx* c, const sgpe_params* p) {
 // The fused 2D step with the register y sweep ends without a finalize launch:
 // each step's head kernel derives the pending scale from the previous y
 // sweep's norm partials, and end_steps publishes it after the last step.
-static bool head_scale(const sgpe_ctx* c) { return c->geo.fused && c->geo.reg_y; }
+// Strang splitting or the SO substep by Crank-Nicolson: the unfused step of
+// enqueue_step_general.
+static bool general_path(const sgpe_ctx* c) { return c->params.split != 0 || c->params.so_mode != 0; }
+
+static bool head_scale(const sgpe_ctx* c) { return c->geo.fused && c->geo.reg_y && !general_path(c); }
 
 // The register y sweep of the complex64 and double-float forms leaves its norm
 // partials as double-float pairs (summed on the FP32 pipe).
@@ -322,11 +429,73 @@ static cudaError_t end_steps(sgpe_ctx* c, bool imag) {
                          y_parts_df(c));
 }
 
+// The SO substep by Crank-Nicolson on the line families of the grid, in -> out:
+// x lines then y lines (reverse: y then x); scale: apply the pending scale.
+template <typename R>
+static cudaError_t so_cn_pass(sgpe_ctx* c, int mode, const void* in, void* out, bool reverse, bool scale) {
+    const SoCnLines* L = c->socn[mode];
+    if (!c->socn_y)
+        return Launcher<R>::socn(c->stream, in, out, L[0], c->tabs_so[mode][0][0], c->tabs_so[mode][0][1], c->sc,
+                                 scale ? 1 : 0);
+    const int a0 = reverse ? 1 : 0, a1 = 1 - a0;
+    cudaError_t e = Launcher<R>::socn(c->stream, in, out, L[a0], c->tabs_so[mode][a0][0], c->tabs_so[mode][a0][1],
+                                      c->sc, scale ? 1 : 0);
+    if (e) return e;
+    return Launcher<R>::socn(c->stream, out, out, L[a1], c->tabs_so[mode][a1][0], c->tabs_so[mode][a1][1], c->sc, 0);
+}
+
+// One step with Strang splitting (params.split = 1: the pointwise and SO
+// substeps with dt/2 before the Crank-Nicolson sweeps, then again in the
+// reverse order) and / or the SO substep by Crank-Nicolson (params.so_mode = 1):
+// unfused kernels, A -> B -> A, the norms and the next pending scale at the end.
+template <typename R>
+static cudaError_t enqueue_step_general(sgpe_ctx* c, bool imag, const double* omega_tab) {
+    cudaError_t e;
+    const int mode = imag ? 0 : 1;
+    const int renorm = imag ? c->params.renorm : 0;
+    const bool strang = c->params.split != 0;
+    const bool socn = c->params.so_mode != 0 && c->kp.so_case != 0;
+    const KParams& kh = strang ? c->kp_half : c->kp;
+    void* A = c->psi;
+    void* B = c->mid;
+    int mask = 7;
+    if (socn) {
+        if ((e = so_cn_pass<R>(c, mode, A, A, false, true))) return e;
+        mask = 2 | 4 | kMaskNoScale;
+    }
+    if ((e = Launcher<R>::pointwise(c->stream, imag, A, B, kh, c->sc, omega_tab, mask))) return e;
+    if (c->dim == 2) {
+        if ((e = Launcher<R>::cn_x(c->stream, imag, false, B, B, c->kp, c->tabs[mode][0], c->geo, c->partials, c->sc,
+                                   renorm, 0)))
+            return e;
+        if ((e = Launcher<R>::cn_y(c->stream, imag, B, A, c->kp, c->tabs[mode][1], c->geo, c->partials, c->sc, renorm,
+                                   0, 0)))
+            return e;
+    } else {
+        if ((e = Launcher<R>::cn_x(c->stream, imag, false, B, A, c->kp, c->tabs[mode][0], c->geo, c->partials, c->sc,
+                                   renorm, 0)))
+            return e;
+    }
+    if (strang) {
+        if ((e = Launcher<R>::pointwise(c->stream, imag, A, B, kh, c->sc, omega_tab,
+                                        2 | 4 | kMaskReverse | kMaskNoScale)))
+            return e;
+        if (socn)
+            e = so_cn_pass<R>(c, mode, B, A, true, false);
+        else
+            e = Launcher<R>::pointwise(c->stream, imag, B, A, kh, c->sc, omega_tab, 1 | kMaskNoScale);
+        if (e) return e;
+    }
+    return Launcher<R>::norms(c->stream, A, (size_t)c->nx * c->ny, c->kp.cell, renorm, c->kp.mag, c->partials, c->sc,
+                              1);
+}
+
 template <typename R>
 static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab) {
     cudaError_t e;
     const int mode = imag ? 0 : 1;
     const int renorm = imag ? c->params.renorm : 0;
+    if (general_path(c)) return enqueue_step_general<R>(c, imag, omega_tab);
     if (c->geo.fused) {
         if ((e = Launcher<R>::pwx(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, c->tabs[mode][0],
                                   c->partials, c->geo.blocks_y / 3, renorm)))
@@ -372,7 +541,7 @@ static const int kGraphSteps = 32;
 // one SM); complex128 lines of at most 256 points in one cluster of up to 8
 // CTAs with the FP64 work of a point split over three threads.
 static bool one_block_1d(const sgpe_ctx* c) {
-    return c->dim == 1 && c->nx <= kRegMaxN && (c->prec != SGPE_C128 || c->nx <= kCl1dMaxN);
+    return c->dim == 1 && c->nx <= kRegMaxN && (c->prec != SGPE_C128 || c->nx <= kCl1dMaxN) && !general_path(c);
 }
 
 static sgpe_status run_steps(sgpe_ctx* c, int nsteps, bool imag, const double* omega_tab) {
@@ -568,7 +737,9 @@ sgpe_status sgpe_get_state(sgpe_ctx* c, void* host_psi) {
 sgpe_status sgpe_substep(sgpe_ctx* c, int which, int imag, double omega) {
     sgpe_status st = check_ready(c);
     if (st) return st;
-    if (which < 0 || which > 5) return fail(c, SGPE_EINVAL, "which must be 0..5");
+    if (which < 0 || which > 7) return fail(c, SGPE_EINVAL, "which must be 0..7");
+    if (which >= 6 && c->kp.so_case != 0 && (c->nx > kRegMaxN || (c->dim == 2 && c->ny > kRegMaxN)))
+        return fail(c, SGPE_EUNSUPPORTED, "SO by Crank-Nicolson needs lines of at most %d points", kRegMaxN);
     if (which == 4 && c->dim != 2) return fail(c, SGPE_EINVAL, "no y sweep in 1D");
     if (!isfinite(omega)) return fail(c, SGPE_EINVAL, "non-finite omega");
     CK(flush_any(c), "flush");
@@ -598,6 +769,13 @@ sgpe_status sgpe_substep(sgpe_ctx* c, int which, int imag, double omega) {
                                                c->partials, c->sc, 0, 0, 0);
         });
         CK(e, "cn_y kernel");
+    } else if (which >= 6) {
+        if (c->kp.so_case != 0) {
+            e = with_prec(c->prec, [&](auto r) {
+                return so_cn_pass<decltype(r)>(c, mode, c->psi, c->psi, which == 7, false);
+            });
+            CK(e, "SO Crank-Nicolson kernel");
+        }
     } else {
         size_t plane = (size_t)c->nx * c->ny;
         int rn = c->params.renorm ? c->params.renorm : 1;
@@ -615,6 +793,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
     sgpe_status st = check_ready(c);
     if (st) return st;
     if (nsteps < 0 || !ms_out || !launches_out) return fail(c, SGPE_EINVAL, "bad profile arguments");
+    if (general_path(c)) return fail(c, SGPE_EUNSUPPORTED, "profile_steps: Lie splitting with the Euler SO only");
     const bool im = imag != 0;
     const int mode = im ? 0 : 1;
     const int renorm = im ? c->params.renorm : 0;
@@ -693,6 +872,11 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
 
 int sgpe_launches_per_step(const sgpe_ctx* c) {
     if (!c) return 0;
+    if (general_path(c)) {
+        const int so = (c->params.so_mode && c->kp.so_case) ? (c->socn_y ? 2 : 1) : 0;
+        const int sweeps = c->dim == 2 ? 2 : 1;
+        return so + 1 + sweeps + (c->params.split ? 1 + (so ? so : 1) : 0) + 1;
+    }
     if (one_block_1d(c)) return 0;  // one launch per step call
     if (head_scale(c)) return 2;  // plus one end-of-steps launch per step call
     if (c->geo.fused) return 3;
@@ -737,3 +921,68 @@ sgpe_status ctx_fail(sgpe_ctx* c, sgpe_status st, const char* msg) { return fail
 
 cudaError_t ctx_flush(sgpe_ctx* c) { return flush_any(c); }
 }  // namespace sgpe
+
+// ---------------------------------------------------------------------------
+// Measurement aid: the FP64 FMA rate of the current device.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kPeakChains = 16;
+constexpr int kPeakIters = 1024;
+__device__ double g_peak_sink[1];
+
+// Every thread runs kPeakChains independent FMA chains of kPeakIters steps
+// (x <- x * a + b with |a| < 1, so the values stay finite); the result is
+// folded into one word so that the work is not optimised away.
+__global__ void __launch_bounds__(256) k_fp64_fma(double a, double b, int rounds) {
+    double x[kPeakChains];
+#pragma unroll
+    for (int c = 0; c < kPeakChains; c++) x[c] = (double)(threadIdx.x + c);
+    for (int r = 0; r < rounds; r++) {
+#pragma unroll 16
+        for (int i = 0; i < kPeakIters; i++) {
+#pragma unroll
+            for (int c = 0; c < kPeakChains; c++) x[c] = fma(x[c], a, b);
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kPeakChains; c++) s += x[c];
+    if (s == 1.2345678e-300) g_peak_sink[0] = s;
+}
+
+}  // namespace
+
+extern "C" sgpe_status sgpe_measure_fp64_rate(void* cuda_stream, double* tflops_out) {
+    if (!tflops_out) return SGPE_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (!e) e = cudaEventCreate(&t0);
+    if (!e) e = cudaEventCreate(&t1);
+    const int blocks = 8 * sms, threads = 256, rounds = 4;
+    double best = 0.0;
+    for (int rep = 0; rep < 4 && !e; rep++) {
+        e = cudaEventRecord(t0, s);
+        if (!e) {
+            k_fp64_fma<<<blocks, threads, 0, s>>>(0.999999, 1e-7, rounds);
+            e = cudaGetLastError();
+        }
+        if (!e) e = cudaEventRecord(t1, s);
+        if (!e) e = cudaEventSynchronize(t1);
+        float ms = 0.f;
+        if (!e) e = cudaEventElapsedTime(&ms, t0, t1);
+        const double flops = 2.0 * (double)blocks * threads * kPeakChains * kPeakIters * rounds;
+        if (!e && rep > 0 && ms > 0.f) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (e) {
+        set_thread_error(cudaGetErrorString(e));
+        return SGPE_ECUDA;
+    }
+    *tflops_out = best;
+    return SGPE_OK;
+}

@@ -472,6 +472,13 @@ sgpe_status sgpe_batch_create(sgpe_batch** out, int n, const sgpe_instance* inst
             set_thread_error(m);
             return SGPE_EINVAL;
         }
+        if (q.params.split || q.params.so_mode) {
+            char m[160];
+            snprintf(m, sizeof(m), "sgpe_batch_create: instance %d: Strang splitting and the SO by Crank-Nicolson "
+                     "are single-grid options", i);
+            set_thread_error(m);
+            return SGPE_EUNSUPPORTED;
+        }
     }
     sgpe_batch* b = new (std::nothrow) sgpe_batch();
     if (!b) return SGPE_ENOMEM;

@@ -48,7 +48,10 @@ template <typename R, bool IMAG, int C> struct LaneTabs {
 };
 
 // Solve T w = x for the lane's chunk v (in: x, out: w), all 32 lanes together.
-template <typename R, bool IMAG, int C>
+// SKEW: T has opposite off-diagonals (lower -a, upper +a; the Crank-Nicolson
+// matrix of a first-derivative operator): the backward recurrence then runs with
+// -fg and fq holds the chunk products of -fg (k_coef_skew).
+template <typename R, bool IMAG, int C, bool SKEW = false>
 __device__ __forceinline__ void solve_chunk(cx<R> (&v)[C], const LaneTabs<R, IMAG, C>& t) {
     const int lane = threadIdx.x & 31;
     cx<R> y = {R(0), R(0)};
@@ -73,7 +76,12 @@ __device__ __forceinline__ void solve_chunk(cx<R> (&v)[C], const LaneTabs<R, IMA
 #pragma unroll
     for (int m = C - 1; m >= 0; m--) {
         cx<R> yi = tfma<IMAG>(t.fp[m], cin, v[m]);
-        w = tfma<IMAG>(t.fg[m], w, yi);
+        if (SKEW) {
+            const cx<R> g = t.fg[m];
+            w = tfma<IMAG>(cx<R>{-g.re, -g.im}, w, yi);
+        } else {
+            w = tfma<IMAG>(t.fg[m], w, yi);
+        }
         v[m] = w;
     }
     A = t.fq[0];
@@ -751,9 +759,20 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps) k_cn_x(const typename V2<R
     __shared__ cx<R> seg[4 * kLongMaxWarps];
     __shared__ double red[kLongMaxWarps];
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = p.nx, span = 32 * kLongC * nw;
+    const int n = p.nx;
     const size_t base = (size_t)blockIdx.x * n;
-    for (int i = threadIdx.x; i < span; i += blockDim.x) line[long_slot(i)] = i < n ? ldc<R>(in, base + i) : cx<R>{R(0), R(0)};
+    // the block's 32 nw threads stage the span = 16 * 32 nw points: all 16 loads of a
+    // thread in flight before the shared-memory stores
+    {
+        cx<R> tmp[kLongC];
+#pragma unroll
+        for (int k = 0; k < kLongC; k++) {
+            const int i = threadIdx.x + k * (int)blockDim.x;
+            tmp[k] = i < n ? ldc<R>(in, base + i) : cx<R>{R(0), R(0)};
+        }
+#pragma unroll
+        for (int k = 0; k < kLongC; k++) line[long_slot(threadIdx.x + k * (int)blockDim.x)] = tmp[k];
+    }
     __syncthreads();
     double acc = long_line<R, IMAG>(line, n, t, warp, nw, seg);
     __syncthreads();
@@ -790,13 +809,25 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps) k_cn_y(const typename V2<R
     const int col0 = (blockIdx.x - j * ncb) * kc;
     const size_t base = (size_t)j * p.nx * p.ny;
     cx<R>* lines = reinterpret_cast<cx<R>*>(smem_raw);  // [kc][span padded]
-    const size_t lstride = (size_t)(span / kLongC) * kLongS;
+    // complex64 tiles of 4 columns: the columns start 8 elements (8 banks pairs) apart
+    // modulo 16, so the 4 threads that stage one row segment use different banks
+    const size_t lstride = (size_t)(span / kLongC) * kLongS + long_col_pad(sizeof(cx<R>), kc);
     const int lkc = kc == 4 ? 2 : kc == 2 ? 1 : 0;  // kc is 1, 2 or 4
-    for (int q = threadIdx.x; q < span * kc; q += blockDim.x) {
-        const int i = q >> lkc, c = q & (kc - 1);
-        const int col = col0 + c;
-        lines[c * lstride + long_slot(i)] =
-            (i < n && col < p.nx) ? ldc<R>(in, base + (size_t)i * p.nx + col) : cx<R>{R(0), R(0)};
+    // the block's 32 nw kc threads stage span * kc = 16 * blockDim values: all 16 loads
+    // of a thread in flight before the shared-memory stores
+    {
+        cx<R> tmp[kLongC];
+#pragma unroll
+        for (int k = 0; k < kLongC; k++) {
+            const int q = threadIdx.x + k * (int)blockDim.x;
+            const int i = q >> lkc, col = col0 + (q & (kc - 1));
+            tmp[k] = (i < n && col < p.nx) ? ldc<R>(in, base + (size_t)i * p.nx + col) : cx<R>{R(0), R(0)};
+        }
+#pragma unroll
+        for (int k = 0; k < kLongC; k++) {
+            const int q = threadIdx.x + k * (int)blockDim.x;
+            lines[(q & (kc - 1)) * lstride + long_slot(q >> lkc)] = tmp[k];
+        }
     }
     __syncthreads();
     const int c = warp / nw;

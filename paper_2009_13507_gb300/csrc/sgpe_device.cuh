@@ -220,6 +220,7 @@ struct KParams {
     double cell;      // dx (1D) or dx*dy
     int renorm;       // 0, 1 (DJ2), 2 (DJ)
     double mag;
+    int split, so_mode;  // Strang splitting, SO by Crank-Nicolson (sgpe_params)
     // Constants of the pointwise substeps in each arithmetic type (kc<R>):
     // kd the FP64 value, kf its FP32 rounding, kl the FP32 rest kd - kf (the
     // double-float low part); filled by fill_derived on the host before a
@@ -268,6 +269,9 @@ inline void fill_derived(KParams& k) {
 // Lines longer than 1024 points: 16 points a lane, at most 16 warps a block.
 constexpr int kLongC = 16;
 constexpr int kLongMaxWarps = 16;
+// Extra elements between the staged columns of a y tile of lines longer than
+// 1024 points (complex64 tiles of 4 columns; see k_cn_y).
+__host__ __device__ constexpr int long_col_pad(int elem_bytes, int kc) { return (elem_bytes == 8 && kc == 4) ? 8 : 0; }
 
 template <typename R> __device__ __forceinline__ R kc(const KParams& p, int i);
 template <> __device__ __forceinline__ double kc<double>(const KParams& p, int i) { return p.kd[i]; }

@@ -210,8 +210,10 @@ __device__ __forceinline__ void finalize_norms(const double* partials, int nblk,
 
 // ---------------------------------------------------------------------------
 // Pointwise substeps (SO, CALCNU, HERM) of one step; mask selects substeps
-// (bit 0 SO, bit 1 CALCNU, bit 2 HERM). Applies the pending scale on load.
-// Block (32, BY); one thread per grid point.
+// (bit 0 SO, bit 1 CALCNU, bit 2 HERM) and how: bit 3 (kMaskReverse) HERM
+// before CALCNU (the second half of a Strang step), bit 4 (kMaskNoScale) the
+// pending scale is not applied (a later kernel of the same step). Applies the
+// pending scale on load otherwise. Block (32, BY); one thread per grid point.
 // ---------------------------------------------------------------------------
 // The pointwise substeps at grid point (ix, iy) of the state A (one grid),
 // written to B; scale: the pending renormalisation scale per component; Ot the
@@ -223,6 +225,9 @@ template <> __device__ __forceinline__ float scale_of<float>(const DevScalars* s
 template <> __device__ __forceinline__ df scale_of<df>(const DevScalars* sc, int j) {
     return df(sc->scale_f[j], sc->scale_l[j]);
 }
+
+constexpr int kMaskReverse = 8;
+constexpr int kMaskNoScale = 16;
 
 // The state at one grid point as loaded: the three values and their raw
 // differences psi(x+1) - psi(x-1), psi(y+1) - psi(y-1) (zero ghosts), before
@@ -289,7 +294,7 @@ __device__ __forceinline__ void pointwise_apply(const PointIn<R>& in, const KPar
         }
         so_point<IMAG>(u, in.X, in.Y, gx, gy, p.so_case);
     }
-    if (mask & 2) {
+    auto calcnu = [&]() {
         // V = wx^2 x^2/2 + wy^2 y^2/2 with x = kx dx: kx^2 is an exact integer
         const int kx = ix - p.nx / 2, ky = iy - p.ny / 2;
         if constexpr (!is_f32<R>()) {
@@ -300,12 +305,19 @@ __device__ __forceinline__ void pointwise_apply(const PointIn<R>& in, const KPar
             R V = kc<R>(p, KC_VX) * R(kx * kx) + (p.dim == 2 ? kc<R>(p, KC_VY) * R(ky * ky) : R(0));
             calcnu_point<IMAG>(u, V, kc<R>(p, KC_C0), kc<R>(p, KC_C2), dt);
         }
-    }
-    if (mask & 4) {
+    };
+    auto herm = [&]() {
         if constexpr (std::is_same<R, df>::value)
             herm_point_df<IMAG>(u, kc<R>(p, KC_C2), Ot, p);
         else
             herm_point<IMAG>(u, kc<R>(p, KC_C2), Ot, dt, &p);
+    };
+    if (mask & kMaskReverse) {
+        if (mask & 4) herm();
+        if (mask & 2) calcnu();
+    } else {
+        if (mask & 2) calcnu();
+        if (mask & 4) herm();
     }
 }
 
@@ -325,7 +337,8 @@ __device__ __forceinline__ void pointwise_at(const typename V2<R>::T* __restrict
                                              const DevScalars* sc, R Ot, int ix, int iy, int mask) {
     const size_t plane = (size_t)p.nx * p.ny;
     const size_t c = (size_t)iy * p.nx + ix;
-    const R ds[3] = {scale_of<R>(sc, 0), scale_of<R>(sc, 1), scale_of<R>(sc, 2)};
+    const bool ns = (mask & kMaskNoScale) != 0;
+    const R ds[3] = {ns ? R(1) : scale_of<R>(sc, 0), ns ? R(1) : scale_of<R>(sc, 1), ns ? R(1) : scale_of<R>(sc, 2)};
     cx<R> u[3];
     pointwise_point<R, IMAG>(A, p, ds, Ot, ix, iy, mask, u);
 #pragma unroll
@@ -571,7 +584,7 @@ static __global__ void k_reset_scale(DevScalars* sc) {
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(256) k_norms(const typename V2<R>::T* A, size_t plane, double cell, int renorm,
-                                               double mag, double* partials, DevScalars* sc) {
+                                               double mag, double* partials, DevScalars* sc, int advance) {
     __shared__ double red[8 * 3];
     double v[3] = {0.0, 0.0, 0.0};
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * plane;
@@ -586,7 +599,8 @@ __global__ void __launch_bounds__(256) k_norms(const typename V2<R>::T* A, size_
     block_reduce<3>(v, red);
     if (threadIdx.x == 0)
         for (int j = 0; j < 3; j++) partials[3 * blockIdx.x + j] = v[j];
-    if (last_block(&sc->ticket[2])) finalize_norms(partials, gridDim.x, cell, renorm, mag, false, sc, &sc->ticket[2]);
+    if (last_block(&sc->ticket[2]))
+        finalize_norms(partials, gridDim.x, cell, renorm, mag, advance != 0, sc, &sc->ticket[2]);
 }
 
 // ---------------------------------------------------------------------------

@@ -13,6 +13,7 @@ namespace sgpe {
 
 struct KParams;
 struct DevScalars;
+struct SoCnLines;
 
 // Launch a step kernel with programmatic stream serialization: its blocks may
 // be scheduled before the previous kernel on the stream completes; the kernel
@@ -117,8 +118,15 @@ template <typename R> struct Launcher {
                             int advance, int finalize, bool head_scale = false);
     static cudaError_t coef(cudaStream_t s, void* fa, void* fg, void* fp, void* fq, int n, double bre, double bim);
     static cudaError_t flush(cudaStream_t s, void* A, size_t plane, const DevScalars* sc);
+    // advance: also move the step counter on (the last kernel of a step).
     static cudaError_t norms(cudaStream_t s, const void* A, size_t plane, double cell, int renorm, double mag,
-                             double* partials, DevScalars* sc);
+                             double* partials, DevScalars* sc, int advance = 0);
+    // SO substep by Crank-Nicolson on one family of lines (lines of at most
+    // kRegMaxN points); tabs_p / tabs_m: the skew tables of m = +1 / -1.
+    static cudaError_t socn(cudaStream_t s, const void* in, void* out, const SoCnLines& L, const void* const* tabs_p,
+                            const void* const* tabs_m, const DevScalars* sc, int scale);
+    static cudaError_t coef_skew(cudaStream_t s, void* fa, void* fg, void* fp, void* fq, int n, double are,
+                                 double aim);
     static cudaError_t observables(cudaStream_t s, const void* A, const KParams& p, double omega_t,
                                    double* partials, DevScalars* sc);
 };

@@ -4,6 +4,7 @@
 #include "sgpe_cn.cuh"
 #include "sgpe_kernels.cuh"
 #include "sgpe_launch.h"
+#include "sgpe_socn.cuh"
 #include "sgpe_step1d_cl.cuh"
 
 namespace sgpe {
@@ -153,8 +154,48 @@ cudaError_t Launcher<R>::step1d(cudaStream_t s, bool imag, void* A, const KParam
     return cudaGetLastError();
 }
 
+template <typename R, int C> static cudaError_t socn_allow() {
+    return cudaFuncSetAttribute(k_socn<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)socn_smem_bytes<R, C>());
+}
+
+template <typename R, int C>
+static void socn_c(cudaStream_t s, const typename V2<R>::T* in, typename V2<R>::T* out, const SoCnLines& L,
+                   const Tabs<R>& tp, const Tabs<R>& tm, const DevScalars* sc, int scale) {
+    k_socn<R, C><<<L.nlines, kSoCnThreads, socn_smem_bytes<R, C>(), s>>>(in, out, L, tp, tm, sc, scale);
+}
+
+template <typename R>
+cudaError_t Launcher<R>::socn(cudaStream_t s, const void* in, void* out, const SoCnLines& L, const void* const* tabs_p,
+                              const void* const* tabs_m, const DevScalars* sc, int scale) {
+    using T = typename V2<R>::T;
+    if (L.n > kRegMaxN) return cudaErrorInvalidValue;
+    const Tabs<R> tp = make_tabs<R>(tabs_p), tm = make_tabs<R>(tabs_m);
+    const T* a = (const T*)in;
+    T* b = (T*)out;
+    switch (chunk_len(L.n)) {
+        case 1: socn_c<R, 1>(s, a, b, L, tp, tm, sc, scale); break;
+        case 2: socn_c<R, 2>(s, a, b, L, tp, tm, sc, scale); break;
+        case 4: socn_c<R, 4>(s, a, b, L, tp, tm, sc, scale); break;
+        case 8: socn_c<R, 8>(s, a, b, L, tp, tm, sc, scale); break;
+        case 16: socn_c<R, 16>(s, a, b, L, tp, tm, sc, scale); break;
+        default: socn_c<R, 32>(s, a, b, L, tp, tm, sc, scale); break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launcher<R>::coef_skew(cudaStream_t s, void* fa, void* fg, void* fp, void* fq, int n, double are,
+                                   double aim) {
+    using T = typename V2<R>::T;
+    const int C = chunk_len(n);
+    k_coef_skew<R><<<1, 32, 0, s>>>((T*)fa, (T*)fg, (T*)fp, (T*)fq, n, C, 32 * C, are, aim);
+    return cudaGetLastError();
+}
+
 template <typename R> cudaError_t Launcher<R>::setup() {
     cudaError_t e;
+    if ((e = socn_allow<R, 16>())) return e;
+    if ((e = socn_allow<R, 32>())) return e;
     if ((e = step1d_allow_all<R, true>())) return e;
     if ((e = step1d_allow_all<R, false>())) return e;
     if ((e = pwx_allow_all<R, true>())) return e;
@@ -264,9 +305,9 @@ template <typename R> cudaError_t Launcher<R>::flush(cudaStream_t s, void* A, si
 
 template <typename R>
 cudaError_t Launcher<R>::norms(cudaStream_t s, const void* A, size_t plane, double cell, int renorm, double mag,
-                               double* partials, DevScalars* sc) {
+                               double* partials, DevScalars* sc, int advance) {
     using T = typename V2<R>::T;
-    k_norms<R><<<kNormBlocks, 256, 0, s>>>((const T*)A, plane, cell, renorm, mag, partials, sc);
+    k_norms<R><<<kNormBlocks, 256, 0, s>>>((const T*)A, plane, cell, renorm, mag, partials, sc, advance);
     return cudaGetLastError();
 }
 

@@ -111,3 +111,32 @@ def batch_table(seed: int, n1d: int = 32, n2d: int = 32):
                         omega=float(u[i, 2]), c0=1.0 + 99.0 * float(u[i, 3]),
                         c2=-2.0 + 4.0 * float(u[i, 4])))
     return out
+
+
+def vortex_state_2d(nx: int, ny: int, dx: float, dy: float, charges, width: float = 2.0,
+                    amplitudes=(1.0, 1.0, 1.0)) -> np.ndarray:
+    """[3][ny][nx] complex128 initial state with a vortex of angular momentum L_j
+    imprinted in component j (Sec. 4's initial states): a Gaussian of the given
+    width times (x + i y)^L for L > 0 and (x - i y)^|L| for L < 0, times
+    amplitudes[j]; unit norm. E.g. charges (-1, 0, 1) for the polar and (0, 1, 2)
+    for the ferromagnetic Rashba-coupled states."""
+    x = grid_x(nx, dx)[None, :]
+    y = grid_x(ny, dy)[:, None]
+    g = np.exp(-(x**2 + y**2) / (2.0 * width**2))
+    comps = []
+    for L, a in zip(charges, amplitudes):
+        z = x + 1j * y if L >= 0 else x - 1j * y
+        comps.append(a * g * z ** abs(int(L)))
+    psi = np.stack([np.broadcast_to(c, (ny, nx)) for c in comps]).astype(np.complex128)
+    return _unit(psi, dx * dy)
+
+
+def stripe_state_2d(nx: int, ny: int, dx: float, dy: float, gamma: float, width: float = 2.0) -> np.ndarray:
+    """[3][ny][nx] complex128 stripe initial state (Sec. 4): a Gaussian times
+    sin(gamma x) in the components +1 and -1 and cos(gamma x) in component 0; unit norm."""
+    x = grid_x(nx, dx)[None, :]
+    y = grid_x(ny, dy)[:, None]
+    g = np.exp(-(x**2 + y**2) / (2.0 * width**2))
+    s, c = g * np.sin(gamma * x), g * np.cos(gamma * x)
+    psi = np.stack([s, c, s]).astype(np.complex128)
+    return _unit(psi, dx * dy)

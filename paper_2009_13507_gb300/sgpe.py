@@ -24,12 +24,12 @@ PRECISIONS = {"c128": C128, "c64": C64, "cdf": CDF}
 NOBS = 16
 OBS_NAMES = ("N+", "N0", "N-", "N", "mag", "E", "mu", "rms+", "rms0", "rms-", "rms",
              "E_kin", "E_trap", "E_int", "E_rabi", "E_so")
-SUBSTEP = {"so": 0, "calcnu": 1, "herm": 2, "cn_x": 3, "cn_y": 4, "renorm": 5}
+SUBSTEP = {"so": 0, "calcnu": 1, "herm": 2, "cn_x": 3, "cn_y": 4, "renorm": 5, "so_cn": 6, "so_cn_rev": 7}
 
 # Every symbol include/sgpe.h declares (checked by the CPU test suite).
 EXPORTS = ("sgpe_init_grid", "sgpe_workspace_bytes", "sgpe_bind", "sgpe_set_params", "sgpe_step_imag",
            "sgpe_step_real", "sgpe_normalize", "sgpe_energy", "sgpe_set_state", "sgpe_get_state", "sgpe_load_state",
-           "sgpe_substep", "sgpe_profile_steps", "sgpe_observables_noalloc", "sgpe_launches_per_step",
+           "sgpe_substep", "sgpe_profile_steps", "sgpe_measure_fp64_rate", "sgpe_observables_noalloc", "sgpe_launches_per_step",
            "sgpe_last_error", "sgpe_destroy", "sgpe_adjoint_workspace_bytes", "sgpe_adjoint_loss_grad",
            "sgpe_adjoint_forward", "sgpe_adjoint_step",
            "sgpe_batch_create", "sgpe_batch_sizes", "sgpe_batch_offsets", "sgpe_batch_bind",
@@ -49,7 +49,7 @@ class Params(ctypes.Structure):
     _fields_ = [("c0", ctypes.c_double), ("c2", ctypes.c_double), ("so_type", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("omega", ctypes.c_double), ("wx", ctypes.c_double),
                 ("wy", ctypes.c_double), ("dt", ctypes.c_double), ("renorm", ctypes.c_int),
-                ("mag", ctypes.c_double)]
+                ("mag", ctypes.c_double), ("split", ctypes.c_int), ("so_mode", ctypes.c_int)]
 
 
 def load():
@@ -76,6 +76,7 @@ def load():
         "sgpe_load_state": (I, [P, P]),
         "sgpe_substep": (I, [P, I, I, D]),
         "sgpe_profile_steps": (I, [P, I, I, P, P]),
+        "sgpe_measure_fp64_rate": (I, [P, P]),
         "sgpe_observables_noalloc": (I, [P, I, I, I, D, D, I, ctypes.POINTER(Params), P, P]),
         "sgpe_launches_per_step": (I, [P]),
         "sgpe_last_error": (ctypes.c_char_p, [P]),
@@ -119,10 +120,12 @@ class Physics:
     dt: float = 1e-4
     renorm: int = 1
     mag: float = 0.0
+    split: int = 0      # 0 Lie, 1 Strang splitting
+    so_mode: int = 0    # 0 explicit-Euler SO, 1 SO by Crank-Nicolson (unitary)
 
     def c(self) -> Params:
         return Params(self.c0, self.c2, self.so_type, self.gamma, self.omega, self.wx, self.wy, self.dt,
-                      self.renorm, self.mag)
+                      self.renorm, self.mag, self.split, self.so_mode)
 
 
 class Solver:
@@ -308,6 +311,18 @@ class Solver:
         return g, dom, (float(dw[0]), float(dw[1]))
 
 
+def measure_fp64_rate(stream=None) -> float:
+    """The device's FP64 FMA rate in TFLOP/s (sgpe_measure_fp64_rate)."""
+    lib = load()
+    out = ctypes.c_double()
+    rc = lib.sgpe_measure_fp64_rate(ctypes.c_void_p(stream.cuda_stream if stream is not None else 0),
+                                    ctypes.byref(out))
+    if rc != OK:
+        msg = lib.sgpe_last_error(None)
+        raise SgpeError(rc, msg.decode() if msg else "sgpe_measure_fp64_rate")
+    return float(out.value)
+
+
 def _rabi_trap_loss_function():
     import torch
 
@@ -348,7 +363,8 @@ def _propagate_function():
         def forward(ctx, psi0, omega_t, w, solver, checkpoint_every=50):
             ph = solver.physics
             phys = Physics(c0=ph.c0, c2=ph.c2, so_type=ph.so_type, gamma=ph.gamma, omega=ph.omega,
-                           wx=float(w[0]), wy=float(w[1]), dt=ph.dt, renorm=0, mag=ph.mag)
+                           wx=float(w[0]), wy=float(w[1]), dt=ph.dt, renorm=0, mag=ph.mag, split=ph.split,
+                           so_mode=ph.so_mode)
             solver.set_params(phys)
             solver.load_state(psi0.detach().contiguous())
             tape = solver.adjoint_forward(omega_t.detach(), checkpoint_every)

@@ -33,3 +33,23 @@ def test_batch_table_ranges():
         else:
             assert r["dim"] == 2 and 128 <= r["nx"] <= 384 and r["nx"] == r["ny"]
         assert 0 <= r["gamma"] <= 1 and 0 <= r["omega"] <= 1 and 1 <= r["c0"] <= 100 and -2 <= r["c2"] <= 2
+
+
+def test_vortex_and_stripe_states():
+    """The vortex initial states carry the imprinted angular momentum: the phase of
+    component j winds L_j times around the origin; stripe states are real and
+    even/odd in x as sin / cos."""
+    n, h = 41, 0.4
+    psi = I.vortex_state_2d(n, n, h, h, (-1, 0, 2))
+    assert abs(np.sum(abs(psi) ** 2) * h * h - 1) < 1e-13
+    x = I.grid_x(n, h)
+    t = np.linspace(0, 2 * np.pi, 400, endpoint=False)
+    ix = np.rint(2.0 * np.cos(t) / h).astype(int) + n // 2
+    iy = np.rint(2.0 * np.sin(t) / h).astype(int) + n // 2
+    for j, L in enumerate((-1, 0, 2)):
+        ph = np.angle(psi[j, iy, ix])
+        wind = np.sum(np.angle(np.exp(1j * np.diff(np.append(ph, ph[0]))))) / (2 * np.pi)
+        assert round(wind) == L
+    s = I.stripe_state_2d(n, n, h, h, 0.5)
+    assert np.allclose(s.imag, 0) and np.allclose(s[0], s[2])
+    assert np.allclose(s[0][:, n // 2], 0) and abs(np.sum(abs(s) ** 2) * h * h - 1) < 1e-13
