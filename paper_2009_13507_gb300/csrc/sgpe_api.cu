@@ -39,7 +39,10 @@ Geometry make_geometry(int dim, int nx, int ny, int esz) {
     // kLongMaxWarps warps), long_warps(ny) warps per column
     g.reg_y = ny <= kRegMaxN;
     const int nwy = long_warps(ny);
-    g.wy = g.reg_y ? 1 : std::max(1, std::min(32 / esz, kLongMaxWarps / nwy));
+    // a power of two (the kernel splits a staging index into row and column by shift and mask)
+    int wy = std::max(1, std::min(32 / esz, kLongMaxWarps / nwy));
+    while (wy & (wy - 1)) wy &= wy - 1;
+    g.wy = g.reg_y ? 1 : wy;
     g.smem_y = g.reg_y ? 0 : (size_t)g.wy * (32 * nwy * (kLongC + 1) + long_col_pad(esz, g.wy)) * esz;
     g.blocks_y = dim == 2 ? 3 * ceil_div(nx, g.reg_y ? cny_cols_per_warp(chunk_len(ny), esz) : g.wy) : 0;
     g.blocks_obs = ceil_div(nx, 32) * ceil_div(ny, 4);

@@ -809,8 +809,8 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps) k_cn_y(const typename V2<R
     const int col0 = (blockIdx.x - j * ncb) * kc;
     const size_t base = (size_t)j * p.nx * p.ny;
     cx<R>* lines = reinterpret_cast<cx<R>*>(smem_raw);  // [kc][span padded]
-    // complex64 tiles of 4 columns: the columns start 8 elements (8 banks pairs) apart
-    // modulo 16, so the 4 threads that stage one row segment use different banks
+    // complex64 tiles of 4 columns: the columns start 4 elements (4 bank pairs) apart
+    // modulo 16, so the threads that stage one row segment use different banks
     const size_t lstride = (size_t)(span / kLongC) * kLongS + long_col_pad(sizeof(cx<R>), kc);
     const int lkc = kc == 4 ? 2 : kc == 2 ? 1 : 0;  // kc is 1, 2 or 4
     // the block's 32 nw kc threads stage span * kc = 16 * blockDim values: all 16 loads
@@ -849,6 +849,85 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps) k_cn_y(const typename V2<R
             for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
             part[blockIdx.x] = s;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The complex64 y sweep of columns longer than 1024 points, double-buffered: one
+// persistent block per SM takes the tiles b = blockIdx.x, + gridDim.x, ... and
+// copies the next tile into its second shared-memory buffer with cp.async (no
+// registers held, out-of-range elements zero-filled) while it solves the current
+// one, so the column loads of one tile overlap the line solves of the other.
+// Same tiles, arithmetic and norm partials (part[b], b the tile) as k_cn_y.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gsrc), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <bool IMAG>
+__global__ void __launch_bounds__(32 * kLongMaxWarps) k_cn_y_pipe(const float2* in, float2* out, KParams p, Tabs<float> t,
+                                                                  int kc, int ntiles, double* part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ cx<float> seg[4 * kLongMaxWarps];
+    __shared__ double red[kLongMaxWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = (blockDim.x >> 5) / kc;
+    const int n = p.ny, span = 32 * kLongC * nw;
+    const int ncb = (p.nx + kc - 1) / kc;
+    const int lkc = kc == 4 ? 2 : kc == 2 ? 1 : 0;  // kc is 1, 2 or 4
+    const size_t lstride = (size_t)(span / kLongC) * kLongS + long_col_pad(8, kc);
+    const size_t bufsz = (size_t)kc * lstride;
+    cx<float>* buf = reinterpret_cast<cx<float>*>(smem_raw);  // two buffers of bufsz elements
+    const int c = warp / nw;
+    pdl_wait();
+    // the 16 copies of this thread for tile b into buffer dst (span * kc = 16 * blockDim values)
+    auto issue = [&](int b, cx<float>* dst) {
+        const int j = b / ncb, col0 = (b - j * ncb) * kc;
+        const size_t base = (size_t)j * p.nx * p.ny;
+#pragma unroll
+        for (int k = 0; k < kLongC; k++) {
+            const int q = threadIdx.x + k * (int)blockDim.x;
+            const int i = q >> lkc, cc = q & (kc - 1), col = col0 + cc;
+            const bool ok = i < n && col < p.nx;
+            cp_async8(dst + cc * lstride + long_slot(i), ok ? (const void*)(in + base + (size_t)i * p.nx + col)
+                                                            : (const void*)in, ok);
+        }
+    };
+    int b = blockIdx.x, k = 0;
+    if (b < ntiles) issue(b, buf);
+    cp_async_commit();
+    for (; b < ntiles; b += gridDim.x, k ^= 1) {
+        cx<float>* cur = buf + k * bufsz;
+        const int bn = b + gridDim.x;
+        if (bn < ntiles) issue(bn, buf + (k ^ 1) * bufsz);
+        cp_async_commit();
+        cp_async_wait_prev();  // this tile's copies (every group but the newest) have landed
+        __syncthreads();
+        double acc = long_line<float, IMAG>(cur + c * lstride, n, t, warp - c * nw, nw, seg + 4 * nw * c);
+        __syncthreads();
+        const int j = b / ncb, col0 = (b - j * ncb) * kc;
+        const size_t base = (size_t)j * p.nx * p.ny;
+        for (int q = threadIdx.x; q < n * kc; q += blockDim.x) {
+            const int i = q >> lkc, cc = q & (kc - 1);
+            const int col = col0 + cc;
+            if (col < p.nx) st<float>(out, base + (size_t)i * p.nx + col, cur[cc * lstride + long_slot(i)]);
+        }
+        if (part) {
+            if (col0 + c >= p.nx) acc = 0.0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if (lane == 0) red[warp] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double sum = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); w++) sum += red[w];
+                part[b] = sum;
+            }
+        }
+        __syncthreads();  // cur is refilled by the copies issued in the next iteration but one
     }
 }
 

@@ -122,6 +122,7 @@ __device__ __forceinline__ void sincos_small(double x, double* s, double* c) {
 }
 __device__ __forceinline__ void sincos_small(float x, float* s, float* c) { sincosf(x, s, c); }
 
+
 // Coefficients of exp(-z A) = I - s_z A + k_z A^2 for the HERM matrix A
 // (A^3 = C^2 A since A has eigenvalues C, 0, -C):
 //   imaginary time (z = dt):  s = sinh(dt C)/C,  k = (cosh(dt C) - 1)/C^2
@@ -271,7 +272,7 @@ constexpr int kLongC = 16;
 constexpr int kLongMaxWarps = 16;
 // Extra elements between the staged columns of a y tile of lines longer than
 // 1024 points (complex64 tiles of 4 columns; see k_cn_y).
-__host__ __device__ constexpr int long_col_pad(int elem_bytes, int kc) { return (elem_bytes == 8 && kc == 4) ? 8 : 0; }
+__host__ __device__ constexpr int long_col_pad(int elem_bytes, int kc) { return (elem_bytes == 8 && kc == 4) ? 4 : 0; }
 
 template <typename R> __device__ __forceinline__ R kc(const KParams& p, int i);
 template <> __device__ __forceinline__ double kc<double>(const KParams& p, int i) { return p.kd[i]; }

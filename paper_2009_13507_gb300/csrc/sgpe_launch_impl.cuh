@@ -1,6 +1,7 @@
 // sgpe_launch_impl.cuh -- launchers of the step / observable kernels for one
 // storage precision; included once per precision translation unit.
 #pragma once
+#include <algorithm>
 #include "sgpe_cn.cuh"
 #include "sgpe_kernels.cuh"
 #include "sgpe_launch.h"
@@ -192,8 +193,20 @@ cudaError_t Launcher<R>::coef_skew(cudaStream_t s, void* fa, void* fg, void* fp,
     return cudaGetLastError();
 }
 
+// Multiprocessor count of the current device (the persistent y sweep's grid).
+static int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return sms;
+}
+
 template <typename R> cudaError_t Launcher<R>::setup() {
     cudaError_t e;
+    if constexpr (std::is_same<R, float>::value) {
+        if ((e = allow_smem(k_cn_y_pipe<true>))) return e;
+        if ((e = allow_smem(k_cn_y_pipe<false>))) return e;
+    }
     if ((e = socn_allow<R, 16>())) return e;
     if ((e = socn_allow<R, 32>())) return e;
     if ((e = step1d_allow_all<R, true>())) return e;
@@ -277,8 +290,24 @@ cudaError_t Launcher<R>::cn_y(cudaStream_t s, bool imag, const void* in, void* o
                           finalize ? partials : nullptr, head_scale ? sc : nullptr, renorm, advance);
         return cudaGetLastError();
     }
+    // tiles of 1, 2 or 4 columns within the block limit (the kernel splits its staging
+    // index by shift and mask)
+    if ((g.wy & (g.wy - 1)) || g.wy > 4 || g.wy * long_warps(p.ny) > kLongMaxWarps) return cudaErrorInvalidValue;
     const dim3 block(32 * g.wy * long_warps(p.ny)), grid(g.blocks_y);
     double* part = finalize ? partials : nullptr;
+    if constexpr (std::is_same<R, float>::value) {
+        // complex64: one persistent double-buffered block per SM
+        const int sms = sm_count();
+        if (sms > 0) {
+            const dim3 pgrid(std::min(g.blocks_y, sms));
+            const size_t smem = 2 * g.smem_y;
+            if (imag)
+                k_cn_y_pipe<true><<<pgrid, block, smem, s>>>((const float2*)in, (float2*)out, p, t, g.wy, g.blocks_y, part);
+            else
+                k_cn_y_pipe<false><<<pgrid, block, smem, s>>>((const float2*)in, (float2*)out, p, t, g.wy, g.blocks_y, part);
+            return cudaGetLastError();
+        }
+    }
     if (imag)
         k_cn_y<R, true><<<grid, block, g.smem_y, s>>>((const T*)in, (T*)out, p, t, g.wy, part);
     else

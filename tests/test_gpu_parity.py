@@ -222,3 +222,21 @@ def test_precision_form_max_line(nx, ny):
     s.set_state(psi)
     s.step_real(2)
     assert relerr(s.get_state(), O.step(prob, psi, 2, False)) < 1e-5
+
+
+@pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("nx,ny", [(9, 2048), (13, 1500), (8, 4100), (5, 2300)])
+def test_precision_form_long_columns(nx, ny, imag):
+    """complex64 columns longer than 1024 points: the y sweep's tiles of up to 8
+    adjacent columns (64-byte row segments, a group of ceil(n/512) warps per
+    column), ragged last tile (9 and 13 columns), ragged last warp (1500, 4100,
+    2300: a group of 5 warps, tiles of 4 columns)."""
+    phys = dict(PHYS_2D, dt=4.0 * 0.01 * 0.01 * 0.5)
+    prob, s = make_pair(2, nx, ny, dx=0.1, dy=0.01, precision="c64", **phys)
+    psi = _rand(prob, nx + ny, env=2.0)
+    s.set_state(psi)
+    s.substep("cn_y", imag)
+    assert relerr(s.get_state(), O.substep(prob, psi, "cn_y", imag)) < 2e-6
+    s.set_state(psi)
+    (s.step_imag(3) if imag else s.step_real(3))
+    assert relerr(s.get_state(), O.step(prob, psi, 3, imag)) < 1e-5
