@@ -359,6 +359,61 @@ __global__ void __launch_bounds__(128) k_pointwise(const typename V2<R>::T* __re
     pointwise_at<R, IMAG>(A, B, p, sc, Ot, ix, iy, mask);
 }
 
+// The same substeps for the complex64 state, two neighbouring points (ix, ix + 1)
+// a thread (nx even): the three values of both points and their y neighbours
+// come in 16-byte loads, the x neighbours from the pair itself and one 8-byte
+// load on each side, the results go out in 16-byte stores; the arithmetic per
+// point is pointwise_apply's, as in k_pointwise. The complex64 pointwise kernel
+// is bound by instruction issue, half of it loads and their index arithmetic.
+template <bool IMAG>
+__global__ void __launch_bounds__(128) k_pointwise2(const float2* __restrict__ A, float2* __restrict__ B, KParams p,
+                                                    const DevScalars* __restrict__ sc,
+                                                    const double* __restrict__ omega_tab, int mask) {
+    const int ix = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    pdl_wait();
+    if (ix >= p.nx || iy >= p.ny) return;
+    const float Ot = omega_tab ? to_r<float>(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440)
+                               : kc<float>(p, KC_OMEGA);
+    const size_t plane = (size_t)p.nx * p.ny;
+    const size_t c = (size_t)iy * p.nx + ix;
+    const bool ns = (mask & kMaskNoScale) != 0;
+    const float ds[3] = {ns ? 1.0f : scale_of<float>(sc, 0), ns ? 1.0f : scale_of<float>(sc, 1),
+                         ns ? 1.0f : scale_of<float>(sc, 2)};
+    const bool so = (mask & 1) && p.so_case;
+    const cx<float> zero = {0.0f, 0.0f};
+    const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    PointIn<float> in0, in1;
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(A + j * plane + c));
+        in0.u[j] = {v.x, v.y};
+        in1.u[j] = {v.z, v.w};
+        in0.X[j] = in0.Y[j] = in1.X[j] = in1.Y[j] = zero;
+    }
+    if (so) {
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const cx<float> xm = ix > 0 ? ld<float>(A, j * plane + c - 1) : zero;
+            const cx<float> xp = ix + 2 < p.nx ? ld<float>(A, j * plane + c + 2) : zero;
+            in0.X[j] = sub(in1.u[j], xm);
+            in1.X[j] = sub(xp, in0.u[j]);
+            if (p.dim == 2) {
+                const float4 ym = iy > 0 ? __ldg(reinterpret_cast<const float4*>(A + j * plane + c - p.nx)) : z4;
+                const float4 yp = iy + 1 < p.ny ? __ldg(reinterpret_cast<const float4*>(A + j * plane + c + p.nx)) : z4;
+                in0.Y[j] = sub(cx<float>{yp.x, yp.y}, cx<float>{ym.x, ym.y});
+                in1.Y[j] = sub(cx<float>{yp.z, yp.w}, cx<float>{ym.z, ym.w});
+            }
+        }
+    }
+    cx<float> u0[3], u1[3];
+    pointwise_apply<float, IMAG>(in0, p, ds, Ot, ix, iy, mask, u0);
+    pointwise_apply<float, IMAG>(in1, p, ds, Ot, ix + 1, iy, mask, u1);
+#pragma unroll
+    for (int j = 0; j < 3; j++)
+        *reinterpret_cast<float4*>(B + j * plane + c) = make_float4(u0[j].re, u0[j].im, u1[j].re, u1[j].im);
+}
+
 // ---------------------------------------------------------------------------
 // End of a step: one block of 3 warps; warp j sums the m partial norms of
 // component j (partials[j*m .. j*m + m), fixed order), then thread 0 publishes

@@ -230,6 +230,18 @@ cudaError_t Launcher<R>::pointwise(cudaStream_t s, bool imag, const void* A, voi
     dim3 grid(ceil_div(p.nx, 32), p.dim == 2 ? ceil_div(p.ny, 2) : 1);
     KParams q = p;
     fill_derived(q);
+    if constexpr (std::is_same<R, float>::value) {
+        // complex64, even rows: two points a thread, 16-byte loads and stores (16-byte aligned:
+        // every buffer starts 16-byte aligned and every row has an even number of points)
+        if (p.nx % 2 == 0) {
+            const dim3 grid2(ceil_div(p.nx, 64), grid.y);
+            if (imag)
+                launch_pdl(k_pointwise2<true>, grid2, block, 0, s, (const float2*)A, (float2*)B, q, sc, omega_tab, mask);
+            else
+                launch_pdl(k_pointwise2<false>, grid2, block, 0, s, (const float2*)A, (float2*)B, q, sc, omega_tab, mask);
+            return cudaGetLastError();
+        }
+    }
     if (imag)
         launch_pdl(k_pointwise<R, true>, grid, block, 0, s, (const T*)A, (T*)B, q, sc, omega_tab, mask);
     else
