@@ -320,19 +320,19 @@ static cudaError_t adj_forward_step(const CtxView& v, const void* in, void* out,
         // x in one kernel (real time: the pending scale is 1, flushed at entry and
         // kept by the y sweep). Same bits as the two kernels; 256^2, 500 steps:
         // 28.4 -> 27.6 ms per gradient (complex128 measured 101.1 -> 102.0, kept unfused).
-        if ((e = Launcher<R>::pwx(v.stream, false, in, v.mid, k, v.sc, nullptr, v.tabs_real, nullptr, 0, 0)))
+        if ((e = Launcher<R>::pwx(v.stream, false, in, v.mid, k, v.sc, nullptr, v.tabs_real[0].t, nullptr, 0, 0)))
             return e;
-        return Launcher<R>::cn_y(v.stream, false, v.mid, out, k, v.tabs_real + 4, *v.geo, v.partials, v.sc, 0, 0, 0);
+        return Launcher<R>::cn_y(v.stream, false, v.mid, out, k, v.tabs_real[1], *v.geo, v.partials, v.sc, 0, 0, 0);
     }
     e = Launcher<R>::pointwise(v.stream, false, in, v.mid, k, v.sc, nullptr, 7);
     if (e) return e;
     if (v.dim == 2) {
-        if ((e = Launcher<R>::cn_x(v.stream, false, false, v.mid, v.mid, k, v.tabs_real, *v.geo, v.partials, v.sc, 0,
+        if ((e = Launcher<R>::cn_x(v.stream, false, false, v.mid, v.mid, k, v.tabs_real[0], *v.geo, v.partials, v.sc, 0,
                                    0)))
             return e;
-        return Launcher<R>::cn_y(v.stream, false, v.mid, out, k, v.tabs_real + 4, *v.geo, v.partials, v.sc, 0, 0, 0);
+        return Launcher<R>::cn_y(v.stream, false, v.mid, out, k, v.tabs_real[1], *v.geo, v.partials, v.sc, 0, 0, 0);
     }
-    return Launcher<R>::cn_x(v.stream, false, false, v.mid, out, k, v.tabs_real, *v.geo, v.partials, v.sc, 0, 0);
+    return Launcher<R>::cn_x(v.stream, false, false, v.mid, out, k, v.tabs_real[0], *v.geo, v.partials, v.sc, 0, 0);
 }
 
 // Marks the workspace as holding the checkpoints of a forward pass of nsteps
@@ -395,8 +395,8 @@ static cudaError_t adj_reverse(const CtxView& v, int nsteps, const double* omega
         for (int k2 = 0; k2 + 1 < s1 - s0 && !e; k2++) e = adj_forward_step<R>(v, seg(k2), seg(k2 + 1), omega_host[s0 + k2]);
         for (int n = s1 - 1; n >= s0 && !e; n--) {
             if (v.dim == 2)
-                e = Launcher<R>::cn_y(s, false, G, G, v.kp, v.tabs_adj + 4, *v.geo, v.partials, v.sc, 0, 0, 0);
-            if (!e) e = Launcher<R>::cn_x(s, false, false, G, G, v.kp, v.tabs_adj, *v.geo, v.partials, v.sc, 0, 0);
+                e = Launcher<R>::cn_y(s, false, G, G, v.kp, v.tabs_adj[1], *v.geo, v.partials, v.sc, 0, 0, 0);
+            if (!e) e = Launcher<R>::cn_x(s, false, false, G, G, v.kp, v.tabs_adj[0], *v.geo, v.partials, v.sc, 0, 0);
             if (!e) {
                 ka_pointwise<R><<<grd, blk, 0, s>>>((const T*)seg(n - s0), G, v.kp, omega_host[n] * 0.70710678118654752440,
                                                     part);

@@ -81,7 +81,8 @@ struct sgpe_ctx {
     // workspace carve-up
     DevScalars* sc;
     void* mid;
-    void* tabs[3][2][4];  // [mode: 0 imag, 1 real, 2 real with -dt (adjoint)][axis: 0 x, 1 y][fa, fg, fp, fq]
+    TabSet tabs[3][2];  // [mode: 0 imag, 1 real, 2 real with -dt (adjoint)][axis: 0 x, 1 y]
+    void* us[3][2];     // the start corrections of the constant-factor form (long lines)
     double* partials;
     // SO by Crank-Nicolson (params.so_mode = 1): skew tables [mode: 0 imag, 1 real][axis][m: +1, -1][4]
     // and the line families [mode][axis]
@@ -129,7 +130,7 @@ static sgpe_status cuda_fail(sgpe_ctx* c, cudaError_t e, const char* where) {
     } while (0)
 
 struct Layout {
-    size_t sc, mid, tabs[3][2][4], tabs_so[2][2][2][4], partials, total;
+    size_t sc, mid, tabs[3][2][4], us[3][2], tabs_so[2][2][2][4], partials, total;
 };
 
 static Layout layout_of(const sgpe_ctx* c) {
@@ -146,6 +147,8 @@ static Layout layout_of(const sgpe_ctx* c) {
                 L.tabs[m][a][k] = off;
                 off = align256(off + (size_t)table_len(n) * c->esz);
             }
+            L.us[m][a] = off;
+            off = align256(off + (size_t)(n > kRegMaxN ? kUniMaxS : 1) * c->esz);
         }
     for (int m = 0; m < 2; m++)
         for (int a = 0; a < 2; a++) {
@@ -364,8 +367,11 @@ sgpe_status sgpe_bind(sgpe_ctx* c, void* psi_dev, void* workspace_dev) {
     c->sc = (DevScalars*)(c->work + L.sc);
     c->mid = c->work + L.mid;
     for (int m = 0; m < 3; m++)
-        for (int a = 0; a < 2; a++)
-            for (int k = 0; k < 4; k++) c->tabs[m][a][k] = c->work + L.tabs[m][a][k];
+        for (int a = 0; a < 2; a++) {
+            for (int k = 0; k < 4; k++) c->tabs[m][a].t[k] = c->work + L.tabs[m][a][k];
+            c->tabs[m][a].u = UniHost{};
+            c->us[m][a] = c->work + L.us[m][a];
+        }
     for (int m = 0; m < 2; m++)
         for (int a = 0; a < 2; a++)
             for (int q = 0; q < 2; q++)
@@ -397,11 +403,19 @@ sgpe_status sgpe_set_params(sgpe_ctx* c, const sgpe_params* p) {
             int n = a == 0 ? c->nx : c->ny;
             double b = p->dt / (4.0 * h * h);
             double bre = m == 0 ? b : 0.0, bim = m == 0 ? 0.0 : (m == 1 ? b : -b);
-            void** t = c->tabs[m][a];
+            void** t = c->tabs[m][a].t;
             cudaError_t e = with_prec(c->prec, [&](auto r) {
                 return Launcher<decltype(r)>::coef(c->stream, t[0], t[1], t[2], t[3], n, bre, bim);
             });
             CK(e, "COEF kernel");
+            // lines longer than kRegMaxN: the constant-factor form of the same solve
+            c->tabs[m][a].u = UniHost{};
+            if (n > kRegMaxN) {
+                e = with_prec(c->prec, [&](auto r) {
+                    return Launcher<decltype(r)>::uni(c->stream, n, bre, bim, c->us[m][a], &c->tabs[m][a].u);
+                });
+                CK(e, "constant-factor form");
+            }
         }
     c->have_params = true;
     return SGPE_OK;
@@ -421,15 +435,16 @@ static bool general_path(const sgpe_ctx* c) { return c->params.split != 0 || c->
 
 static bool head_scale(const sgpe_ctx* c) { return c->geo.fused && c->geo.reg_y && !general_path(c); }
 
-// The register y sweep of the complex64 and double-float forms leaves its norm
-// partials as double-float pairs (summed on the FP32 pipe).
-static int y_parts_df(const sgpe_ctx* c) { return c->dim == 2 && c->geo.reg_y && c->prec != SGPE_C128; }
+// The y sweeps (2D) and the long x sweep (1D) of the complex64 and double-float
+// forms leave their norm partials as double-float pairs (summed on the FP32
+// pipe); the 1D register x sweep and every complex128 sweep leave FP64 sums.
+static int parts_df(const sgpe_ctx* c) { return c->prec != SGPE_C128 && (c->dim == 2 || !c->geo.reg_x); }
 
 static cudaError_t end_steps(sgpe_ctx* c, bool imag) {
     if (!head_scale(c)) return cudaSuccess;
     const int renorm = imag ? c->params.renorm : 0;
     return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 0, c->sc,
-                         y_parts_df(c));
+                         parts_df(c));
 }
 
 // The SO substep by Crank-Nicolson on the line families of the grid, in -> out:
@@ -500,7 +515,7 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
     const int renorm = imag ? c->params.renorm : 0;
     if (general_path(c)) return enqueue_step_general<R>(c, imag, omega_tab);
     if (c->geo.fused) {
-        if ((e = Launcher<R>::pwx(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, c->tabs[mode][0],
+        if ((e = Launcher<R>::pwx(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, c->tabs[mode][0].t,
                                   c->partials, c->geo.blocks_y / 3, renorm)))
             return e;
         const bool head = head_scale(c);
@@ -509,7 +524,7 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
             return e;
         if (head) return cudaSuccess;  // the next head kernel (or end_steps) takes the scale from the partials
         return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 1, c->sc,
-                             y_parts_df(c));
+                             parts_df(c));
     }
     if ((e = Launcher<R>::pointwise(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, 7))) return e;
     if (c->dim == 2) {
@@ -520,13 +535,13 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
                                    c->sc, renorm, 1, 1)))
             return e;
         return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 1, c->sc,
-                             y_parts_df(c));
+                             parts_df(c));
     }
     if ((e = Launcher<R>::cn_x(c->stream, imag, true, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo, c->partials,
                                c->sc, renorm, 1)))
         return e;
     // 1D: one partial per line (3 lines)
-    return finalize_step(c->stream, c->partials, 3 * c->ny, c->kp.cell, renorm, c->kp.mag, 1, c->sc, 0);
+    return finalize_step(c->stream, c->partials, 3 * c->ny, c->kp.cell, renorm, c->kp.mag, 1, c->sc, parts_df(c));
 }
 
 static cudaError_t enqueue_steps(sgpe_ctx* c, int n, bool imag, const double* omega_tab) {
@@ -554,7 +569,7 @@ static sgpe_status run_steps(sgpe_ctx* c, int nsteps, bool imag, const double* o
         const int mode = imag ? 0 : 1;
         const int renorm = imag ? c->params.renorm : 0;
         cudaError_t e = with_prec(c->prec, [&](auto r) {
-            return Launcher<decltype(r)>::step1d(c->stream, imag, c->psi, c->kp, c->sc, omega_tab, c->tabs[mode][0],
+            return Launcher<decltype(r)>::step1d(c->stream, imag, c->psi, c->kp, c->sc, omega_tab, c->tabs[mode][0].t,
                                                  nsteps, renorm);
         });
         CK(e, "1D step loop");
@@ -824,7 +839,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
         if (!e && fused)
             e = with_prec(c->prec, [&](auto r) {
                 return Launcher<decltype(r)>::pwx(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr,
-                                                  c->tabs[mode][0], c->partials, c->geo.blocks_y / 3, renorm);
+                                                  c->tabs[mode][0].t, c->partials, c->geo.blocks_y / 3, renorm);
             });
         if (!e && !fused)
             e = with_prec(c->prec, [&](auto r) {
@@ -846,7 +861,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
         if (!e) e = cudaEventRecord(ev[3], c->stream);
         if (!e && !head)
             e = finalize_step(c->stream, c->partials, two ? c->geo.blocks_y : 3 * c->ny, c->kp.cell, renorm,
-                              c->kp.mag, 1, c->sc, two ? y_parts_df(c) : 0);
+                              c->kp.mag, 1, c->sc, parts_df(c));
         if (!e) e = cudaEventRecord(ev[4], c->stream);
       }
       if (!e) e = cudaEventSynchronize(evs[nb - 1][4]);
@@ -911,8 +926,8 @@ bool ctx_view(sgpe_ctx* c, CtxView* v) {
     v->psi = c->psi;
     v->mid = c->mid;
     v->sc = c->sc;
-    v->tabs_real = (const void* const*)&c->tabs[1][0][0];
-    v->tabs_adj = (const void* const*)&c->tabs[2][0][0];
+    v->tabs_real = &c->tabs[1][0];
+    v->tabs_adj = &c->tabs[2][0];
     v->geo = &c->geo;
     v->kp = c->kp;
     v->partials = c->partials;

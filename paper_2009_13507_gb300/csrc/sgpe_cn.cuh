@@ -699,13 +699,257 @@ __device__ __forceinline__ void group_solve(cx<R> (&v)[kLongC], const Tabs<R>& t
     for (int m = 0; m < kLongC; m++) v[m] = tfma<IMAG>(tld<R>(t.fq, m * G + g), cb, v[m]);
 }
 
+// ---------------------------------------------------------------------------
+// Constant-factor solve of a long line (Tabs::uks > 0). The coefficient is
+// real in imaginary time and complex in real time; complex64 pairs go through
+// the packed FP32x2 instructions (two FP32 operations each, rounded as the two
+// scalar ones would be).
+// ---------------------------------------------------------------------------
+template <bool IMAG, typename R> struct UCoef { using T = cx<R>; };
+template <typename R> struct UCoef<true, R> { using T = R; };
+template <bool IMAG, typename R> __device__ __forceinline__ typename UCoef<IMAG, R>::T ucoef(cx<R> v) {
+    if constexpr (IMAG)
+        return v.re;
+    else
+        return v;
+}
+template <typename R> __device__ __forceinline__ cx<R> gcx(R a) { return cx<R>{a, R(0)}; }
+template <typename R> __device__ __forceinline__ cx<R> gcx(cx<R> a) { return a; }
+template <typename R> __device__ __forceinline__ R gzero(R) { return R(0); }
+template <typename R> __device__ __forceinline__ cx<R> gzero(cx<R>) { return cx<R>{R(0), R(0)}; }
+// g y + x
+template <typename R> __device__ __forceinline__ cx<R> gfma(R g, cx<R> y, cx<R> x) { return axpy(g, y, x); }
+template <typename R> __device__ __forceinline__ cx<R> gfma(cx<R> g, cx<R> y, cx<R> x) { return caxpy(g, y, x); }
+template <typename R> __device__ __forceinline__ cx<R> gmul(R g, cx<R> y) { return scl(g, y); }
+template <typename R> __device__ __forceinline__ cx<R> gmul(cx<R> g, cx<R> y) { return mul(g, y); }
+template <typename R> __device__ __forceinline__ R gprod(R a, R b) { return a * b; }
+template <typename R> __device__ __forceinline__ cx<R> gprod(cx<R> a, cx<R> b) { return mul(a, b); }
+// g y - x
+template <typename R> __device__ __forceinline__ cx<R> gfms(R g, cx<R> y, cx<R> x) {
+    return {fma(g, y.re, -x.re), fma(g, y.im, -x.im)};
+}
+template <typename R> __device__ __forceinline__ cx<R> gfms(cx<R> g, cx<R> y, cx<R> x) {
+    return caxpy(g, y, cx<R>{-x.re, -x.im});
+}
+template <typename R> __device__ __forceinline__ cx<R> gadd(cx<R> a, cx<R> b) { return add(a, b); }
+template <typename R> __device__ __forceinline__ cx<R> gsub(cx<R> a, cx<R> b) { return sub(a, b); }
+template <typename R> __device__ __forceinline__ R gshup(R a, int off) { return shfl_up_r(a, off); }
+template <typename R> __device__ __forceinline__ cx<R> gshup(cx<R> a, int off) { return shup(a, off); }
+template <typename R> __device__ __forceinline__ R gshdn(R a, int off) { return shfl_dn_r(a, off); }
+template <typename R> __device__ __forceinline__ cx<R> gshdn(cx<R> a, int off) { return shdn(a, off); }
+template <typename R> __device__ __forceinline__ bool gtiny(R a) { return tiny_carry(a); }
+template <typename R> __device__ __forceinline__ bool gtiny(cx<R> a) { return tiny_carry(a.re) && tiny_carry(a.im); }
+__device__ __forceinline__ float2 f2(cx<float> a) { return make_float2(a.re, a.im); }
+__device__ __forceinline__ cx<float> fc(float2 a) { return cx<float>{a.x, a.y}; }
+__device__ __forceinline__ cx<float> gfma(float g, cx<float> y, cx<float> x) {
+    return fc(__ffma2_rn(make_float2(g, g), f2(y), f2(x)));
+}
+__device__ __forceinline__ cx<float> gmul(float g, cx<float> y) { return fc(__fmul2_rn(make_float2(g, g), f2(y))); }
+__device__ __forceinline__ cx<float> gadd(cx<float> a, cx<float> b) { return fc(__fadd2_rn(f2(a), f2(b))); }
+// a - b = fma(b, -1, a), exactly rounded once
+__device__ __forceinline__ cx<float> gsub(cx<float> a, cx<float> b) {
+    return fc(__ffma2_rn(f2(b), make_float2(-1.0f, -1.0f), f2(a)));
+}
+// pw y + x with a chunk carry weight pw (Tabs::upow: in imaginary time the
+// real power in both halves, which complex64 uses as the packed pair)
+template <bool IMAG, typename R> __device__ __forceinline__ cx<R> pfma(cx<R> pw, cx<R> y, cx<R> x) {
+    if constexpr (IMAG && std::is_same<R, float>::value)
+        return fc(__ffma2_rn(f2(pw), f2(y), f2(x)));
+    else if constexpr (IMAG)
+        return axpy(pw.re, y, x);
+    else
+        return caxpy(pw, y, x);
+}
+__device__ __forceinline__ double shfl0(double v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ float shfl0(float v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ df shfl0(df v) {
+    return df(__shfl_sync(0xffffffffu, v.hi, 0), __shfl_sync(0xffffffffu, v.lo, 0));
+}
+
+// Solve the lane's chunk v (in: the right-hand side r of its 16 points i0 ..
+// i0 + 15; out: q = w / ua with T w = r) for the group's line of n points.
+// Forward z_i = r_i + g z_(i-1), backward q_i = z_i + g q_(i+1) with the same
+// chunk scans and cross-warp carries as group_solve; a chunk that reaches past n
+// has the chunk factor 0 and zeros past n (the tables hold fg = 0 there), and
+// the first unks points take the correction of the first diagonal entry.
+template <typename R, bool IMAG>
+__device__ __forceinline__ void group_solve_uni(cx<R> (&v)[kLongC], const Tabs<R>& t, int part, int nw, cx<R>* seg,
+                                                int n, int i0) {
+    using G = typename UCoef<IMAG, R>::T;
+    const int lane = threadIdx.x & 31;
+    const cx<R> zero = {R(0), R(0)};
+    const G g = ucoef<IMAG>(t.ug), g16 = ucoef<IMAG>(t.ug16), gz = gzero(g);
+    const bool full = i0 + kLongC <= n;
+    const int nlev = t.unlev;
+    cx<R> z = zero;
+#pragma unroll
+    for (int m = 0; m < kLongC; m++) {
+        z = gfma(g, z, v[m]);
+        v[m] = z;
+    }
+    G A = full ? g16 : gz;
+    cx<R> B = full ? z : zero;
+    for (int l = 0, off = 1; l < nlev; l++, off <<= 1) {
+        const G Ap = gshup(A, off);
+        const cx<R> Bp = shup(B, off);
+        if (lane >= off) {
+            B = gfma(A, Bp, B);
+            A = gprod(A, Ap);
+        }
+    }
+    if (lane == 31) {
+        seg[part] = gcx(A);
+        seg[nw + part] = B;
+    }
+    __syncthreads();
+    cx<R> cw = zero;
+    if (part > 0) {
+        cw = seg[nw + part - 1];
+        G wgt = ucoef<IMAG>(seg[part - 1]);
+        for (int r = part - 2; r >= 0; r--) {
+            if (gtiny(wgt)) break;
+            cw = gfma(wgt, seg[nw + r], cw);
+            wgt = gprod(wgt, ucoef<IMAG>(seg[r]));
+        }
+    }
+    {
+        const G Au = gshup(A, 1);
+        const cx<R> Bu = shup(B, 1);
+        const cx<R> cin = lane == 0 ? cw : gfma(Au, cw, Bu);
+        // z_m += g^(m+1) cin
+#pragma unroll
+        for (int m = 0; m < kLongC; m++) v[m] = pfma<IMAG>(t.upow[m], cin, v[m]);
+    }
+    if (!full) {
+#pragma unroll
+        for (int m = 0; m < kLongC; m++)
+            if (i0 + m >= n) v[m] = zero;
+    }
+    cx<R> q = zero;
+#pragma unroll
+    for (int m = kLongC - 1; m >= 0; m--) {
+        q = gfma(g, q, v[m]);
+        v[m] = q;
+    }
+    A = full ? g16 : gz;
+    B = q;
+    for (int l = 0, off = 1; l < nlev; l++, off <<= 1) {
+        const G An = gshdn(A, off);
+        const cx<R> Bn = shdn(B, off);
+        if (lane + off < 32) {
+            B = gfma(A, Bn, B);
+            A = gprod(A, An);
+        }
+    }
+    if (lane == 0) {
+        seg[2 * nw + part] = gcx(A);
+        seg[3 * nw + part] = B;
+    }
+    __syncthreads();
+    cx<R> cbw = zero;
+    if (part + 1 < nw) {
+        cbw = seg[3 * nw + part + 1];
+        G wgt = ucoef<IMAG>(seg[2 * nw + part + 1]);
+        for (int r = part + 2; r < nw; r++) {
+            if (gtiny(wgt)) break;
+            cbw = gfma(wgt, seg[3 * nw + r], cbw);
+            wgt = gprod(wgt, ucoef<IMAG>(seg[2 * nw + r]));
+        }
+    }
+    {
+        const G An = gshdn(A, 1);
+        const cx<R> Bn = shdn(B, 1);
+        const cx<R> cb = lane == 31 ? cbw : gfma(An, cbw, Bn);
+        // q_m += g^(16 - m) cb
+#pragma unroll
+        for (int m = 0; m < kLongC; m++) v[m] = pfma<IMAG>(t.upow[kLongC - 1 - m], cb, v[m]);
+    }
+    if (part == 0) {
+        const cx<R> q0 = {shfl0(v[0].re), shfl0(v[0].im)};
+        if (i0 < t.uks) {
+            const cx<R> cq = mul(t.uc, q0);
+#pragma unroll
+            for (int m = 0; m < kLongC; m++)
+                if (i0 + m < t.uks) v[m] = sub(v[m], mul(cq, tld<R>(t.us, i0 + m)));
+        }
+    }
+}
+
+// Per-lane |o|^2 sum of the complex64 state on the packed FP32x2 instructions:
+// the same error-free square split and two-sum as NormAcc<float>, with the real
+// and imaginary squares in the two halves.
+struct NormAccF2 {
+    float2 hi = {0.0f, 0.0f}, lo = {0.0f, 0.0f};
+    __device__ __forceinline__ void add(cx<float> o) {
+        const float2 m1 = make_float2(-1.0f, -1.0f);
+        const float2 x = f2(o);
+        const float2 p = __fmul2_rn(x, x);
+        const float2 e = __ffma2_rn(x, x, __fmul2_rn(p, m1));
+        const float2 s = __fadd2_rn(hi, p);
+        const float2 bp = __ffma2_rn(hi, m1, s);
+        const float2 r = __fadd2_rn(__ffma2_rn(__ffma2_rn(bp, m1, s), m1, hi), __ffma2_rn(bp, m1, p));
+        lo = __fadd2_rn(lo, __fadd2_rn(r, e));
+        hi = s;
+    }
+    __device__ __forceinline__ df dfvalue() const {
+        return fast_two_sum(hi.x, lo.x) + fast_two_sum(hi.y, lo.y);
+    }
+};
+
+// The constant-factor variant of long_line (below): the right-hand side is
+// L x (increment form) or x, the solve gives q, and the result is x + uk q or
+// uk q - x.
+template <typename R, bool IMAG>
+__device__ __forceinline__ typename PartT<R>::T long_line_uni(cx<R>* line, int n, const Tabs<R>& t, int part, int nw,
+                                                              cx<R>* seg) {
+    const int i0 = (part * 32 + (threadIdx.x & 31)) * kLongC;
+    constexpr bool INC = sizeof(R) == 4;
+    const cx<R> zero = {R(0), R(0)};
+    cx<R> v[kLongC];
+#pragma unroll
+    for (int m = 0; m < kLongC; m++) v[m] = line[long_slot(i0 + m)];
+    if constexpr (INC) {
+        cx<R> prev = i0 > 0 ? line[long_slot(i0 - 1)] : zero;
+        const cx<R> last = i0 + kLongC < n ? line[long_slot(i0 + kLongC)] : zero;
+#pragma unroll
+        for (int m = 0; m < kLongC; m++) {
+            const cx<R> cur = v[m];
+            const cx<R> nxt = m + 1 < kLongC ? v[m + 1] : last;
+            v[m] = i0 + m < n ? gadd(gsub(prev, cur), gsub(nxt, cur)) : zero;
+            prev = cur;
+        }
+    }
+    group_solve_uni<R, IMAG>(v, t, part, nw, seg, n, i0);
+    const auto k = ucoef<IMAG>(t.uk);
+    typename std::conditional<INC && IMAG, NormAccF2, NormAcc<R>>::type acc;
+#pragma unroll
+    for (int m = 0; m < kLongC; m++) {
+        if (i0 + m < n) {
+            const cx<R> x = line[long_slot(i0 + m)];
+            cx<R> o;
+            if constexpr (INC)
+                o = gfma(k, v[m], x);
+            else
+                o = gfms(k, v[m], x);
+            line[long_slot(i0 + m)] = o;
+            acc.add(o);
+        }
+    }
+    if constexpr (INC && IMAG)
+        return acc.dfvalue();
+    else
+        return acc_value<typename PartT<R>::T>(acc);
+}
+
 // The sweep of one staged line: lane chunk in from shared memory (line, padded
 // layout), solve, and the result o written back to the lane's own slots.
 // complex64: increment form o = x + 2 e, T e = bt L x (the differences of
 // neighbouring values exact); otherwise o = 2 w - x. Returns |o|^2 summed over
 // the lane's points (for the norm partials).
-template <typename R, bool IMAG>
-__device__ __forceinline__ double long_line(cx<R>* line, int n, const Tabs<R>& t, int part, int nw, cx<R>* seg) {
+template <typename R, bool IMAG, bool UNI>
+__device__ __forceinline__ typename PartT<R>::T long_line(cx<R>* line, int n, const Tabs<R>& t, int part, int nw,
+                                                          cx<R>* seg) {
+    if constexpr (UNI) return long_line_uni<R, IMAG>(line, n, t, part, nw, seg);
     const int i0 = (part * 32 + (threadIdx.x & 31)) * kLongC;
     constexpr bool INC = sizeof(R) == 4;
     const cx<R> zero = {R(0), R(0)};
@@ -744,21 +988,43 @@ __device__ __forceinline__ double long_line(cx<R>* line, int n, const Tabs<R>& t
             acc.add(o);
         }
     }
-    return acc.value();
+    return acc_value<typename PartT<R>::T>(acc);
+}
+
+// The block's norm partial from each thread's lane sum v (every thread of the
+// block calls it; fixed order: warps by shuffles, then the warps in index
+// order by thread 0, which returns the sum). FP64 for complex128, a
+// double-float pair on the FP32 pipe otherwise.
+template <typename P> __device__ __forceinline__ P block_part(P v, P* red) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    P s = red[0];
+    if (threadIdx.x == 0)
+        for (int w = 1; w < nw; w++) s = s + red[w];
+    return s;
 }
 
 // CN along x for lines of 1025..8192 points: one block of nw warps per line
 // (line l = j*ny + iy, row iy of component j). in may equal out. With part
-// non-null (1D: the step's last pass) the block writes the FP64 norm of its
-// line to part[line].
-template <typename R, bool IMAG>
-__global__ void __launch_bounds__(32 * kLongMaxWarps) k_cn_x(const typename V2<R>::T* in, typename V2<R>::T* out,
+// non-null (1D: the step's last pass) the block writes the norm of its line to
+// part[line] (PartT<R>: FP64 for complex128, a double-float pair otherwise).
+// UNI: the constant-factor solve (Tabs::uks > 0; complex64 and double-float)
+// instead of the tables; the two are separate instantiations so that neither
+// carries the other's registers.
+template <typename R, bool UNI> constexpr int long_min_blocks() { return (UNI && sizeof(R) == 4) ? 2 : 1; }
+
+template <typename R, bool IMAG, bool UNI>
+__global__ void __launch_bounds__(32 * kLongMaxWarps, long_min_blocks<R, UNI>())
+    k_cn_x(const typename V2<R>::T* in, typename V2<R>::T* out,
                                                              KParams p, Tabs<R> t, double* part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R>* line = reinterpret_cast<cx<R>*>(smem_raw);
+    using P = typename PartT<R>::T;
     __shared__ cx<R> seg[4 * kLongMaxWarps];
-    __shared__ double red[kLongMaxWarps];
-    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ P red[kLongMaxWarps];
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
     const int n = p.nx;
     const size_t base = (size_t)blockIdx.x * n;
     // the block's 32 nw threads stage the span = 16 * 32 nw points: all 16 loads of a
@@ -774,34 +1040,29 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps) k_cn_x(const typename V2<R
         for (int k = 0; k < kLongC; k++) line[long_slot(threadIdx.x + k * (int)blockDim.x)] = tmp[k];
     }
     __syncthreads();
-    double acc = long_line<R, IMAG>(line, n, t, warp, nw, seg);
+    const P acc = long_line<R, IMAG, UNI>(line, n, t, warp, nw, seg);
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) st<R>(out, base + i, line[long_slot(i)]);
     if (part) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (lane == 0) red[warp] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int w = 0; w < nw; w++) s += red[w];
-            part[blockIdx.x] = s;
-        }
+        const P sum = block_part(acc, red);
+        if (threadIdx.x == 0) reinterpret_cast<P*>(part)[blockIdx.x] = sum;
     }
 }
 
 // CN along y for columns of 1025..8192 points: one block per tile of kc (1, 2
 // or 4) adjacent columns [col0, col0 + kc) of component j, staged in shared memory (row
 // segments of kc elements), nw warps per column. With part non-null the block
-// writes the FP64 norm of its tile to part[blockIdx.x] (the blocks of
-// component j are contiguous).
-template <typename R, bool IMAG>
-__global__ void __launch_bounds__(32 * kLongMaxWarps) k_cn_y(const typename V2<R>::T* in, typename V2<R>::T* out,
+// writes the norm of its tile to part[blockIdx.x] (the blocks of component j are
+// contiguous; PartT<R> as for k_cn_x).
+template <typename R, bool IMAG, bool UNI>
+__global__ void __launch_bounds__(32 * kLongMaxWarps, long_min_blocks<R, UNI>())
+    k_cn_y(const typename V2<R>::T* in, typename V2<R>::T* out,
                                                              KParams p, Tabs<R> t, int kc, double* part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    using P = typename PartT<R>::T;
     __shared__ cx<R> seg[4 * kLongMaxWarps];
-    __shared__ double red[kLongMaxWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ P red[kLongMaxWarps];
+    const int warp = threadIdx.x >> 5;
     const int nw = (blockDim.x >> 5) / kc;
     const int n = p.ny, span = 32 * kLongC * nw;
     const int ncb = (p.nx + kc - 1) / kc;
@@ -813,121 +1074,38 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps) k_cn_y(const typename V2<R
     // modulo 16, so the threads that stage one row segment use different banks
     const size_t lstride = (size_t)(span / kLongC) * kLongS + long_col_pad(sizeof(cx<R>), kc);
     const int lkc = kc == 4 ? 2 : kc == 2 ? 1 : 0;  // kc is 1, 2 or 4
+    // thread -> (row it0 + k rs, column cc) of the tile: blockDim is a multiple of
+    // 16 kc, so rs = blockDim / kc is a multiple of 16 and the padded slot of row
+    // it0 + k rs is long_slot(it0) + k (rs / 16) kLongS
+    const int cc = threadIdx.x & (kc - 1), it0 = threadIdx.x >> lkc, rs = blockDim.x >> lkc;
+    const int col = col0 + cc, sstep = (rs >> 4) * kLongS;
+    const bool colok = col < p.nx;
+    const size_t gstep = (size_t)rs * p.nx;
+    cx<R>* tcol = lines + cc * lstride + long_slot(it0);
     // the block's 32 nw kc threads stage span * kc = 16 * blockDim values: all 16 loads
     // of a thread in flight before the shared-memory stores
     {
         cx<R> tmp[kLongC];
+        size_t g = base + (size_t)it0 * p.nx + col;
 #pragma unroll
-        for (int k = 0; k < kLongC; k++) {
-            const int q = threadIdx.x + k * (int)blockDim.x;
-            const int i = q >> lkc, col = col0 + (q & (kc - 1));
-            tmp[k] = (i < n && col < p.nx) ? ldc<R>(in, base + (size_t)i * p.nx + col) : cx<R>{R(0), R(0)};
-        }
+        for (int k = 0; k < kLongC; k++, g += gstep)
+            tmp[k] = (it0 + k * rs < n && colok) ? ldc<R>(in, g) : cx<R>{R(0), R(0)};
 #pragma unroll
-        for (int k = 0; k < kLongC; k++) {
-            const int q = threadIdx.x + k * (int)blockDim.x;
-            lines[(q & (kc - 1)) * lstride + long_slot(q >> lkc)] = tmp[k];
-        }
+        for (int k = 0; k < kLongC; k++) tcol[k * sstep] = tmp[k];
     }
     __syncthreads();
     const int c = warp / nw;
-    double acc = long_line<R, IMAG>(lines + c * lstride, n, t, warp - c * nw, nw, seg + 4 * nw * c);
+    P acc = long_line<R, IMAG, UNI>(lines + c * lstride, n, t, warp - c * nw, nw, seg + 4 * nw * c);
     __syncthreads();
-    for (int q = threadIdx.x; q < n * kc; q += blockDim.x) {
-        const int i = q >> lkc, cc = q & (kc - 1);
-        const int col = col0 + cc;
-        if (col < p.nx) st<R>(out, base + (size_t)i * p.nx + col, lines[cc * lstride + long_slot(i)]);
+    if (colok) {
+        size_t g = base + (size_t)it0 * p.nx + col;
+        const cx<R>* src = tcol;
+        for (int i = it0; i < n; i += rs, g += gstep, src += sstep) st<R>(out, g, *src);
     }
     if (part) {
-        if (col0 + c >= p.nx) acc = 0.0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (lane == 0) red[warp] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
-            part[blockIdx.x] = s;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// The complex64 y sweep of columns longer than 1024 points, double-buffered: one
-// persistent block per SM takes the tiles b = blockIdx.x, + gridDim.x, ... and
-// copies the next tile into its second shared-memory buffer with cp.async (no
-// registers held, out-of-range elements zero-filled) while it solves the current
-// one, so the column loads of one tile overlap the line solves of the other.
-// Same tiles, arithmetic and norm partials (part[b], b the tile) as k_cn_y.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, bool valid) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gsrc), "r"(valid ? 8 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-template <bool IMAG>
-__global__ void __launch_bounds__(32 * kLongMaxWarps) k_cn_y_pipe(const float2* in, float2* out, KParams p, Tabs<float> t,
-                                                                  int kc, int ntiles, double* part) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ cx<float> seg[4 * kLongMaxWarps];
-    __shared__ double red[kLongMaxWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nw = (blockDim.x >> 5) / kc;
-    const int n = p.ny, span = 32 * kLongC * nw;
-    const int ncb = (p.nx + kc - 1) / kc;
-    const int lkc = kc == 4 ? 2 : kc == 2 ? 1 : 0;  // kc is 1, 2 or 4
-    const size_t lstride = (size_t)(span / kLongC) * kLongS + long_col_pad(8, kc);
-    const size_t bufsz = (size_t)kc * lstride;
-    cx<float>* buf = reinterpret_cast<cx<float>*>(smem_raw);  // two buffers of bufsz elements
-    const int c = warp / nw;
-    pdl_wait();
-    // the 16 copies of this thread for tile b into buffer dst (span * kc = 16 * blockDim values)
-    auto issue = [&](int b, cx<float>* dst) {
-        const int j = b / ncb, col0 = (b - j * ncb) * kc;
-        const size_t base = (size_t)j * p.nx * p.ny;
-#pragma unroll
-        for (int k = 0; k < kLongC; k++) {
-            const int q = threadIdx.x + k * (int)blockDim.x;
-            const int i = q >> lkc, cc = q & (kc - 1), col = col0 + cc;
-            const bool ok = i < n && col < p.nx;
-            cp_async8(dst + cc * lstride + long_slot(i), ok ? (const void*)(in + base + (size_t)i * p.nx + col)
-                                                            : (const void*)in, ok);
-        }
-    };
-    int b = blockIdx.x, k = 0;
-    if (b < ntiles) issue(b, buf);
-    cp_async_commit();
-    for (; b < ntiles; b += gridDim.x, k ^= 1) {
-        cx<float>* cur = buf + k * bufsz;
-        const int bn = b + gridDim.x;
-        if (bn < ntiles) issue(bn, buf + (k ^ 1) * bufsz);
-        cp_async_commit();
-        cp_async_wait_prev();  // this tile's copies (every group but the newest) have landed
-        __syncthreads();
-        double acc = long_line<float, IMAG>(cur + c * lstride, n, t, warp - c * nw, nw, seg + 4 * nw * c);
-        __syncthreads();
-        const int j = b / ncb, col0 = (b - j * ncb) * kc;
-        const size_t base = (size_t)j * p.nx * p.ny;
-        for (int q = threadIdx.x; q < n * kc; q += blockDim.x) {
-            const int i = q >> lkc, cc = q & (kc - 1);
-            const int col = col0 + cc;
-            if (col < p.nx) st<float>(out, base + (size_t)i * p.nx + col, cur[cc * lstride + long_slot(i)]);
-        }
-        if (part) {
-            if (col0 + c >= p.nx) acc = 0.0;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-            if (lane == 0) red[warp] = acc;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double sum = 0.0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); w++) sum += red[w];
-                part[b] = sum;
-            }
-        }
-        __syncthreads();  // cur is refilled by the copies issued in the next iteration but one
+        if (col0 + c >= p.nx) acc = P(0);
+        const P sum = block_part(acc, red);
+        if (threadIdx.x == 0) reinterpret_cast<P*>(part)[blockIdx.x] = sum;
     }
 }
 

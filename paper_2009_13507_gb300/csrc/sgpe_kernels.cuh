@@ -44,11 +44,28 @@ struct DevScalars {
 // and the step's Crank-Nicolson result is 2 w - x  (= T^{-1}(I + bt L) x).
 // A warp solves a line in 32 chunks of C consecutive points; fp_i / fq_i are the
 // products of fg over the chunk up to / from point i (carry propagation).
+//
+// Lines longer than 1024 points with uks > 0 skip the tables. The pivots u_i
+// converge to the root u of u^2 - (1 + 2bt) u + bt^2 = 0 with |u| > |bt| (a
+// contraction: |bt/u|^2 < 1). T' = T with its first diagonal entry replaced by u
+// has the constant factors ua = 1/u, ug = bt/u at every point; T = T' + delta
+// e_0 e_0^T with delta = 1 + 2bt - u, so (Sherman-Morrison) T^{-1} r = w - uc w_0 s
+// with w = T'^{-1} r, s = T'^{-1} e_0 and uc = delta / (1 + delta s_0). s decays
+// like ug^i: its first uks entries (us) are the ones above 2^-64 / |uc|. unlev:
+// carry-scan levels after which the composed chunk factor ug^(16 2^L) is below
+// 2^-64 (the cut of tiny_carry). uk: the factor that turns the solve's scaled
+// unknown q = w / ua into the sweep's result (2 ua for 2w - x, 2 bt ua for the
+// increment form x + 2e). upow[k] = ug^(k+1), k < 16 (imaginary time: the
+// real power in both halves), the chunk carry weights.
 template <typename R> struct Tabs {
     const typename V2<R>::T* fa;
     const typename V2<R>::T* fg;
     const typename V2<R>::T* fp;
     const typename V2<R>::T* fq;
+    cx<R> ug, ug16, uc, uk;
+    cx<R> upow[16];
+    const typename V2<R>::T* us;
+    int uks, unlev;
 };
 
 

@@ -90,6 +90,24 @@ struct Geometry {
 
 Geometry make_geometry(int dim, int nx, int ny, int esz);
 
+// Constant-factor form of a long line's Crank-Nicolson solve (Tabs::uks),
+// computed on the host in FP64 when the parameters are set.
+struct UniHost {
+    double gr, gi, g16r, g16i;  // ug, ug^16
+    double cr, ci, kr, ki;      // uc, uk
+    double pr[16], pi[16];      // ug^(k+1) (imaginary time: pi = pr)
+    int ks;                     // entries of s (0: the line uses the tables)
+    int nlev;                   // carry-scan levels
+    const void* s;              // device: s_i, i < ks, in the state's element type
+};
+// The coefficient tables of one axis and time mode, and their constant-factor form.
+struct TabSet {
+    void* t[4];  // device: fa, fg, fp, fq
+    UniHost u;
+};
+// Longest start correction of the constant-factor form (entries of s).
+constexpr int kUniMaxS = 512;
+
 template <typename R> struct Launcher {
     static cudaError_t setup();
     static cudaError_t pointwise(cudaStream_t s, bool imag, const void* A, void* B, const KParams& p,
@@ -108,15 +126,19 @@ template <typename R> struct Launcher {
     // cn_x / cn_y write per-block FP64 norm partials when last / finalize is set
     // (the step's final sweep); finalize_step then reduces them.
     static cudaError_t cn_x(cudaStream_t s, bool imag, bool last, const void* in, void* out, const KParams& p,
-                            const void* const* tabs, const Geometry& g, double* partials, DevScalars* sc, int renorm,
+                            const TabSet& tabs, const Geometry& g, double* partials, DevScalars* sc, int renorm,
                             int advance);
     // head_scale (register y sweep of the fused 2D step): the next step's head
     // kernel derives the pending scale from this sweep's partials; the sweep
     // marks that and advances the step counter by advance (no finalize_step).
     static cudaError_t cn_y(cudaStream_t s, bool imag, const void* in, void* out, const KParams& p,
-                            const void* const* tabs, const Geometry& g, double* partials, DevScalars* sc, int renorm,
+                            const TabSet& tabs, const Geometry& g, double* partials, DevScalars* sc, int renorm,
                             int advance, int finalize, bool head_scale = false);
     static cudaError_t coef(cudaStream_t s, void* fa, void* fg, void* fp, void* fq, int n, double bre, double bim);
+    // The constant-factor form of an n-point line with bt = bre + i bim (n > kRegMaxN):
+    // fills u and copies s to s_dev (kUniMaxS entries of room); u->ks = 0 where the
+    // correction would be longer than that.
+    static cudaError_t uni(cudaStream_t s, int n, double bre, double bim, void* s_dev, UniHost* u);
     static cudaError_t flush(cudaStream_t s, void* A, size_t plane, const DevScalars* sc);
     // advance: also move the step counter on (the last kernel of a step).
     static cudaError_t norms(cudaStream_t s, const void* A, size_t plane, double cell, int renorm, double mag,
@@ -159,8 +181,8 @@ struct CtxView {
     void* psi;
     void* mid;
     DevScalars* sc;
-    const void* const* tabs_real;  // [axis][4], bt = i dt/(4h^2)
-    const void* const* tabs_adj;   // [axis][4], bt = -i dt/(4h^2)
+    const TabSet* tabs_real;  // [axis], bt = i dt/(4h^2)
+    const TabSet* tabs_adj;   // [axis], bt = -i dt/(4h^2)
     const Geometry* geo;
     KParams kp;
     double* partials;

@@ -2,6 +2,9 @@
 // storage precision; included once per precision translation unit.
 #pragma once
 #include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
 #include "sgpe_cn.cuh"
 #include "sgpe_kernels.cuh"
 #include "sgpe_launch.h"
@@ -10,9 +13,44 @@
 
 namespace sgpe {
 
+// The constant-factor form serves the forms on the FP32 pipe; complex128 keeps
+// the tables (their loads cost nothing next to its FP64 arithmetic, measured).
+template <typename R> constexpr bool kUniForm = !std::is_same<R, double>::value;
+
 template <typename R> static Tabs<R> make_tabs(const void* const* t) {
     using T = typename V2<R>::T;
-    return Tabs<R>{(const T*)t[0], (const T*)t[1], (const T*)t[2], (const T*)t[3]};
+    Tabs<R> r{};
+    r.fa = (const T*)t[0];
+    r.fg = (const T*)t[1];
+    r.fp = (const T*)t[2];
+    r.fq = (const T*)t[3];
+    r.uks = 0;
+    r.unlev = 5;
+    return r;
+}
+
+static inline double2 pack_host(cx<double> a) { return make_double2(a.re, a.im); }
+static inline float2 pack_host(cx<float> a) { return make_float2(a.re, a.im); }
+static inline float4 pack_host(cx<df> a) { return make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
+// A host double pair as the device complex type R (double-float: hi + lo split).
+template <typename R> static cx<R> host_cx(double re, double im) { return cx<R>{(R)re, (R)im}; }
+template <> cx<df> host_cx<df>(double re, double im) { return cx<df>{df_from(re), df_from(im)}; }
+template <typename R> static typename V2<R>::T host_elem(double re, double im) { return pack_host(host_cx<R>(re, im)); }
+
+template <typename R> static Tabs<R> make_tabs(const TabSet& ts) {
+    Tabs<R> r = make_tabs<R>((const void* const*)ts.t);
+    const UniHost& u = ts.u;
+    if (u.ks > 0) {
+        r.ug = host_cx<R>(u.gr, u.gi);
+        r.ug16 = host_cx<R>(u.g16r, u.g16i);
+        r.uc = host_cx<R>(u.cr, u.ci);
+        r.uk = host_cx<R>(u.kr, u.ki);
+        for (int k = 0; k < 16; k++) r.upow[k] = host_cx<R>(u.pr[k], u.pi[k]);
+        r.us = (const typename V2<R>::T*)u.s;
+        r.uks = u.ks;
+        r.unlev = u.nlev;
+    }
+    return r;
 }
 
 template <typename R, int C>
@@ -193,19 +231,13 @@ cudaError_t Launcher<R>::coef_skew(cudaStream_t s, void* fa, void* fg, void* fp,
     return cudaGetLastError();
 }
 
-// Multiprocessor count of the current device (the persistent y sweep's grid).
-static int sm_count() {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return 0;
-    return sms;
-}
-
 template <typename R> cudaError_t Launcher<R>::setup() {
     cudaError_t e;
-    if constexpr (std::is_same<R, float>::value) {
-        if ((e = allow_smem(k_cn_y_pipe<true>))) return e;
-        if ((e = allow_smem(k_cn_y_pipe<false>))) return e;
+    if constexpr (kUniForm<R>) {
+        if ((e = allow_smem(k_cn_x<R, true, true>))) return e;
+        if ((e = allow_smem(k_cn_x<R, false, true>))) return e;
+        if ((e = allow_smem(k_cn_y<R, true, true>))) return e;
+        if ((e = allow_smem(k_cn_y<R, false, true>))) return e;
     }
     if ((e = socn_allow<R, 16>())) return e;
     if ((e = socn_allow<R, 32>())) return e;
@@ -213,10 +245,10 @@ template <typename R> cudaError_t Launcher<R>::setup() {
     if ((e = step1d_allow_all<R, false>())) return e;
     if ((e = pwx_allow_all<R, true>())) return e;
     if ((e = pwx_allow_all<R, false>())) return e;
-    if ((e = allow_smem(k_cn_x<R, true>))) return e;
-    if ((e = allow_smem(k_cn_x<R, false>))) return e;
-    if ((e = allow_smem(k_cn_y<R, true>))) return e;
-    if ((e = allow_smem(k_cn_y<R, false>))) return e;
+    if ((e = allow_smem(k_cn_x<R, true, false>))) return e;
+    if ((e = allow_smem(k_cn_x<R, false, false>))) return e;
+    if ((e = allow_smem(k_cn_y<R, true, false>))) return e;
+    if ((e = allow_smem(k_cn_y<R, false, false>))) return e;
     return cudaSuccess;
 }
 
@@ -273,7 +305,7 @@ cudaError_t Launcher<R>::pwx(cudaStream_t s, bool imag, const void* A, void* B, 
 
 template <typename R>
 cudaError_t Launcher<R>::cn_x(cudaStream_t s, bool imag, bool last, const void* in, void* out, const KParams& p,
-                              const void* const* tabs, const Geometry& g, double* partials, DevScalars* sc,
+                              const TabSet& tabs, const Geometry& g, double* partials, DevScalars* sc,
                               int renorm, int advance) {
     using T = typename V2<R>::T;
     Tabs<R> t = make_tabs<R>(tabs);
@@ -284,16 +316,18 @@ cudaError_t Launcher<R>::cn_x(cudaStream_t s, bool imag, bool last, const void* 
     }
     const dim3 block(32 * g.wx), grid(g.blocks_x);
     double* part = last ? partials : nullptr;
-    if (imag)
-        k_cn_x<R, true><<<grid, block, g.smem_x, s>>>((const T*)in, (T*)out, p, t, part);
-    else
-        k_cn_x<R, false><<<grid, block, g.smem_x, s>>>((const T*)in, (T*)out, p, t, part);
+    auto go = [&](auto kern) { kern<<<grid, block, g.smem_x, s>>>((const T*)in, (T*)out, p, t, part); };
+    if (kUniForm<R> && t.uks > 0) {
+        if constexpr (kUniForm<R>) imag ? go(k_cn_x<R, true, true>) : go(k_cn_x<R, false, true>);
+    } else {
+        imag ? go(k_cn_x<R, true, false>) : go(k_cn_x<R, false, false>);
+    }
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t Launcher<R>::cn_y(cudaStream_t s, bool imag, const void* in, void* out, const KParams& p,
-                              const void* const* tabs, const Geometry& g, double* partials, DevScalars* sc,
+                              const TabSet& tabs, const Geometry& g, double* partials, DevScalars* sc,
                               int renorm, int advance, int finalize, bool head_scale) {
     using T = typename V2<R>::T;
     Tabs<R> t = make_tabs<R>(tabs);
@@ -307,23 +341,13 @@ cudaError_t Launcher<R>::cn_y(cudaStream_t s, bool imag, const void* in, void* o
     if ((g.wy & (g.wy - 1)) || g.wy > 4 || g.wy * long_warps(p.ny) > kLongMaxWarps) return cudaErrorInvalidValue;
     const dim3 block(32 * g.wy * long_warps(p.ny)), grid(g.blocks_y);
     double* part = finalize ? partials : nullptr;
-    if constexpr (std::is_same<R, float>::value) {
-        // complex64: one persistent double-buffered block per SM
-        const int sms = sm_count();
-        if (sms > 0) {
-            const dim3 pgrid(std::min(g.blocks_y, sms));
-            const size_t smem = 2 * g.smem_y;
-            if (imag)
-                k_cn_y_pipe<true><<<pgrid, block, smem, s>>>((const float2*)in, (float2*)out, p, t, g.wy, g.blocks_y, part);
-            else
-                k_cn_y_pipe<false><<<pgrid, block, smem, s>>>((const float2*)in, (float2*)out, p, t, g.wy, g.blocks_y, part);
-            return cudaGetLastError();
-        }
+    const bool uni = kUniForm<R> && t.uks > 0;
+    auto go = [&](auto kern) { kern<<<grid, block, g.smem_y, s>>>((const T*)in, (T*)out, p, t, g.wy, part); };
+    if (uni) {
+        if constexpr (kUniForm<R>) imag ? go(k_cn_y<R, true, true>) : go(k_cn_y<R, false, true>);
+    } else {
+        imag ? go(k_cn_y<R, true, false>) : go(k_cn_y<R, false, false>);
     }
-    if (imag)
-        k_cn_y<R, true><<<grid, block, g.smem_y, s>>>((const T*)in, (T*)out, p, t, g.wy, part);
-    else
-        k_cn_y<R, false><<<grid, block, g.smem_y, s>>>((const T*)in, (T*)out, p, t, g.wy, part);
     return cudaGetLastError();
 }
 
@@ -333,6 +357,72 @@ cudaError_t Launcher<R>::coef(cudaStream_t s, void* fa, void* fg, void* fp, void
     k_coef<R><<<1, 32, 0, s>>>((T*)fa, (T*)fg, (T*)fp, (T*)fq, n, chunk_len(n), table_len(n), n > kRegMaxN ? 1 : 0,
                                bre, bim);
     return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launcher<R>::uni(cudaStream_t s, int n, double bre, double bim, void* s_dev, UniHost* u) {
+    using C = std::complex<double>;
+    *u = UniHost{};
+    const C b(bre, bim), d = 1.0 + 2.0 * b;
+    // the pivot limit: the root of u^2 - d u + b^2 with |u| > |b|, polished by the
+    // contraction u <- d - b^2 / u itself
+    const C disc = std::sqrt(d * d - 4.0 * b * b);
+    C piv = (d + disc) * 0.5, alt = (d - disc) * 0.5;
+    if (std::abs(alt) > std::abs(piv)) piv = alt;
+    for (int k = 0; k < 8; k++) piv = d - b * b / piv;
+    const C a = 1.0 / piv, g = b / piv;
+    if (!kUniForm<R> || !(std::abs(g) < 1.0) || n <= kRegMaxN) return cudaSuccess;
+    C g16 = g;
+    for (int k = 0; k < 4; k++) g16 = g16 * g16;
+    // s = T'^{-1} e_0: forward z_0 = 1, z_i = g z_{i-1}; backward q_{n-1} = z_{n-1},
+    // q_i = z_i + g q_{i+1}; s = a q
+    std::vector<C> z(n), q(n);
+    z[0] = 1.0;
+    for (int i = 1; i < n; i++) z[i] = g * z[i - 1];
+    q[n - 1] = z[n - 1];
+    for (int i = n - 2; i >= 0; i--) q[i] = z[i] + g * q[i + 1];
+    const C delta = d - piv;
+    const C s0 = a * q[0];
+    const C c = delta / (1.0 + delta * s0);
+    const double cut = std::ldexp(1.0, -64);
+    int ks = 0;
+    for (int i = 0; i < n; i++)
+        if (std::abs(c * a * q[i]) >= cut) ks = i + 1;
+    if (ks > kUniMaxS) return cudaSuccess;
+    ks = std::max(ks, 1);
+    int nlev = 0;
+    for (double f = std::abs(g16); nlev < 5 && !(f < cut); f *= f) nlev++;
+    // the sweep's result from q = w / a: 2 a q - x, or x + 2 bt a q (increment form, complex64)
+    const C k = is_f32<R>() ? 2.0 * b * a : 2.0 * a;
+    using T = typename V2<R>::T;
+    std::vector<T> hs(ks);
+    for (int i = 0; i < ks; i++) {
+        const C si = a * q[i];
+        hs[i] = host_elem<R>(si.real(), si.imag());
+    }
+    cudaError_t e = cudaMemcpyAsync(s_dev, hs.data(), sizeof(T) * ks, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    // pageable source: the copy is staged before cudaMemcpyAsync returns; keep the
+    // stream order with the kernels that read s
+    *u = UniHost{};
+    u->gr = g.real();
+    u->gi = g.imag();
+    u->g16r = g16.real();
+    u->g16i = g16.imag();
+    u->cr = c.real();
+    u->ci = c.imag();
+    u->kr = k.real();
+    u->ki = k.imag();
+    C pw = 1.0;
+    for (int j = 0; j < 16; j++) {
+        pw *= g;
+        u->pr[j] = pw.real();
+        u->pi[j] = bim == 0.0 ? pw.real() : pw.imag();
+    }
+    u->ks = ks;
+    u->nlev = nlev;
+    u->s = s_dev;
+    return cudaSuccess;
 }
 
 template <typename R> cudaError_t Launcher<R>::flush(cudaStream_t s, void* A, size_t plane, const DevScalars* sc) {

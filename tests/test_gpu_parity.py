@@ -58,22 +58,50 @@ def test_cn_sweeps_across_bt(bt, which, imag):
     assert relerr(s.get_state(), O.substep(prob, psi, which, imag)) < 1e-13
 
 
-@pytest.mark.parametrize("precision,tol", [("c128", 1e-13), ("cdf", 1e-12)])
+# complex64: FP32 factors and state; the error grows with the condition of T (about 1 + 4 bt)
+LONG_TOL = {("c128", 0.02): 1e-13, ("c128", 50.0): 1e-13, ("c128", 500.0): 1e-12,
+            ("cdf", 0.02): 1e-12, ("cdf", 50.0): 1e-12, ("cdf", 500.0): 1e-11,
+            ("c64", 0.02): 2e-6, ("c64", 50.0): 1e-4, ("c64", 500.0): 1e-3}
+
+
+@pytest.mark.parametrize("precision", ["c128", "cdf", "c64"])
 @pytest.mark.parametrize("imag", [True, False])
 @pytest.mark.parametrize("which,nx,ny", [("cn_x", 1500, 7), ("cn_y", 7, 1500), ("cn_x", 4096, 3),
-                                         ("cn_y", 3, 2100)])
-@pytest.mark.parametrize("bt", [0.02, 50.0])
-def test_cn_long_lines(bt, which, nx, ny, imag, precision, tol):
+                                         ("cn_y", 3, 2100), ("cn_x", 1025, 3), ("cn_y", 4, 4095)])
+@pytest.mark.parametrize("bt", [0.02, 50.0, 500.0])
+def test_cn_long_lines(bt, which, nx, ny, imag, precision):
     """Lines longer than 1024 points: a group of ceil(n/512) warps per line, 16
     points a lane, the warps' chunk maps composed through shared memory (cut
-    once negligible at small bt, all of them at bt = 50); ragged last warp."""
+    once negligible at small bt, all of them at bt = 50); ragged last warp and
+    ragged last chunk (1025, 1500, 2100, 4095 points). The complex64 and
+    double-float forms take the constant-factor solve with the start correction
+    (its length: 10 points at bt = 0.02, 312 at bt = 50 in imaginary time, 442
+    in real time); at bt = 500 the correction would exceed 512 points and they
+    take the tables, as complex128 always does."""
     dx = 0.1
     phys = dict(PHYS_2D, dt=4.0 * dx * dx * bt)
     prob, s = make_pair(2, nx, ny, dx=dx, precision=precision, **phys)
     psi = _rand(prob, 29, env=3.0)
     s.set_state(psi)
     s.substep(which, imag)
-    assert relerr(s.get_state(), O.substep(prob, psi, which, imag)) < tol
+    assert relerr(s.get_state(), O.substep(prob, psi, which, imag)) < LONG_TOL[(precision, bt)]
+
+
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("cdf", 1e-10), ("c64", 2e-5)])
+@pytest.mark.parametrize("nx", [1025, 3000])
+def test_1d_long_lines_full_steps(nx, precision, tol):
+    """1D lines longer than 1024 points: the pointwise kernel, the warp-group x
+    sweep with the step's norm partials (FP64 for complex128, double-float pairs
+    otherwise) and the finalize block; imaginary then real time, with the
+    observables."""
+    prob, s = make_pair(1, nx, 1, dx=0.01, precision=precision, **PHYS_1D)
+    psi = I.gaussian_jitter_1d(nx, 0.01, seed=nx)
+    s.set_state(psi)
+    s.step_imag(4)
+    s.step_real(3)
+    ref = O.step(prob, O.step(prob, psi, 4, True), 3, False)
+    assert relerr(s.get_state(), ref) < tol
+    assert obs_relerr(s.energy(), O.observables(prob, ref)) < tol
 
 
 @pytest.mark.parametrize("so", [0, 1, 2, 3])
@@ -227,10 +255,10 @@ def test_precision_form_max_line(nx, ny):
 @pytest.mark.parametrize("imag", [True, False])
 @pytest.mark.parametrize("nx,ny", [(9, 2048), (13, 1500), (8, 4100), (5, 2300)])
 def test_precision_form_long_columns(nx, ny, imag):
-    """complex64 columns longer than 1024 points: the y sweep's tiles of up to 8
-    adjacent columns (64-byte row segments, a group of ceil(n/512) warps per
+    """complex64 columns longer than 1024 points: the y sweep's tiles of up to 4
+    adjacent columns (32-byte row segments, a group of ceil(n/512) warps per
     column), ragged last tile (9 and 13 columns), ragged last warp (1500, 4100,
-    2300: a group of 5 warps, tiles of 4 columns)."""
+    2300: groups of 3, 9 and 5 warps, tiles of 1 to 4 columns)."""
     phys = dict(PHYS_2D, dt=4.0 * 0.01 * 0.01 * 0.5)
     prob, s = make_pair(2, nx, ny, dx=0.1, dy=0.01, precision="c64", **phys)
     psi = _rand(prob, nx + ny, env=2.0)
