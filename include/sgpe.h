@@ -246,6 +246,16 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* ctx, int nsteps, int imag, double* ms_o
 sgpe_status sgpe_measure_fp64_rate(void* cuda_stream, double* tflops_out);
 
 /*
+ * Check aid (no counterpart in the paper): y[i] = exp(x[i]) - 1 by the FP32
+ * routine of the complex64 CALCNU substep (Sec. 3's exp(-z mu) factor, applied
+ * as u + (exp(-dt mu) - 1) u in imaginary time), for comparison with other
+ * implementations. x_dev, y_dev: device arrays of n floats (caller-owned; they
+ * may be the same array). Asynchronous on cuda_stream. Returns SGPE_EINVAL for
+ * n < 0 or a null array with n > 0, SGPE_ECUDA if the launch fails.
+ */
+sgpe_status sgpe_eval_expm1f(void* cuda_stream, const float* x_dev, float* y_dev, int n);
+
+/*
  * sgpe_observables_noalloc -- the SGPE_NOBS observables of sgpe_energy for a
  * state given by pointer, without a context and without any device memory from
  * the caller beyond its input and output. The paper has no counterpart: this is

@@ -45,6 +45,7 @@ Geometry make_geometry(int dim, int nx, int ny, int esz) {
     g.wy = g.reg_y ? 1 : wy;
     g.smem_y = g.reg_y ? 0 : (size_t)g.wy * (32 * nwy * (kLongC + 1) + long_col_pad(esz, g.wy)) * esz;
     g.blocks_y = dim == 2 ? 3 * ceil_div(nx, g.reg_y ? cny_cols_per_warp(chunk_len(ny), esz) : g.wy) : 0;
+    g.blocks_yt = dim == 2 && !g.reg_y ? 3 * ceil_div(nx, 32) * ceil_div(ny, kTileRows) : 0;
     g.blocks_obs = ceil_div(nx, 32) * ceil_div(ny, 4);
     g.blocks_norm = kNormBlocks;
     return g;
@@ -162,9 +163,9 @@ static Layout layout_of(const sgpe_ctx* c) {
     L.partials = off;
     size_t np = 0;
     const Geometry& g = c->geo;
-    size_t cand[4] = {(size_t)g.blocks_x * 3, (size_t)g.blocks_y * 3, (size_t)g.blocks_obs * kObsAcc,
-                      (size_t)g.blocks_norm * 3};
-    for (int i = 0; i < 4; i++)
+    size_t cand[5] = {(size_t)g.blocks_x * 3, (size_t)g.blocks_y * 3, (size_t)g.blocks_obs * kObsAcc,
+                      (size_t)g.blocks_norm * 3, (size_t)g.blocks_yt * 3};
+    for (int i = 0; i < 5; i++)
         if (cand[i] > np) np = cand[i];
     off = align256(off + np * sizeof(double));
     L.total = off;
@@ -523,8 +524,8 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
                                    c->sc, renorm, 1, 1, head)))
             return e;
         if (head) return cudaSuccess;  // the next head kernel (or end_steps) takes the scale from the partials
-        return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 1, c->sc,
-                             parts_df(c));
+        return finalize_step(c->stream, c->partials, y_parts(c->geo, c->tabs[mode][1], c->mid, c->psi), c->kp.cell,
+                             renorm, c->kp.mag, 1, c->sc, parts_df(c));
     }
     if ((e = Launcher<R>::pointwise(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, 7))) return e;
     if (c->dim == 2) {
@@ -534,8 +535,8 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
         if ((e = Launcher<R>::cn_y(c->stream, imag, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials,
                                    c->sc, renorm, 1, 1)))
             return e;
-        return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 1, c->sc,
-                             parts_df(c));
+        return finalize_step(c->stream, c->partials, y_parts(c->geo, c->tabs[mode][1], c->mid, c->psi), c->kp.cell,
+                             renorm, c->kp.mag, 1, c->sc, parts_df(c));
     }
     if ((e = Launcher<R>::cn_x(c->stream, imag, true, c->mid, c->psi, c->kp, c->tabs[mode][0], c->geo, c->partials,
                                c->sc, renorm, 1)))
@@ -860,7 +861,8 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
             });
         if (!e) e = cudaEventRecord(ev[3], c->stream);
         if (!e && !head)
-            e = finalize_step(c->stream, c->partials, two ? c->geo.blocks_y : 3 * c->ny, c->kp.cell, renorm,
+            e = finalize_step(c->stream, c->partials,
+                              two ? y_parts(c->geo, c->tabs[mode][1], c->mid, c->psi) : 3 * c->ny, c->kp.cell, renorm,
                               c->kp.mag, 1, c->sc, parts_df(c));
         if (!e) e = cudaEventRecord(ev[4], c->stream);
       }
@@ -1002,5 +1004,27 @@ extern "C" sgpe_status sgpe_measure_fp64_rate(void* cuda_stream, double* tflops_
         return SGPE_ECUDA;
     }
     *tflops_out = best;
+    return SGPE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Check aid: the FP32 exp(x) - 1 of the complex64 CALCNU substep on device data.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void k_eval_expm1(const float* x, float* y, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = expm1_cw(x[i]);
+}
+}  // namespace
+
+extern "C" sgpe_status sgpe_eval_expm1f(void* cuda_stream, const float* x_dev, float* y_dev, int n) {
+    if (n < 0 || (n > 0 && (!x_dev || !y_dev))) return SGPE_EINVAL;
+    if (n == 0) return SGPE_OK;
+    k_eval_expm1<<<(n + 255) / 256, 256, 0, (cudaStream_t)cuda_stream>>>(x_dev, y_dev, n);
+    const cudaError_t e = cudaGetLastError();
+    if (e) {
+        set_thread_error(cudaGetErrorString(e));
+        return SGPE_ECUDA;
+    }
     return SGPE_OK;
 }

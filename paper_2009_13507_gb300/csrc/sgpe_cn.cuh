@@ -901,7 +901,7 @@ struct NormAccF2 {
 // uk q - x.
 template <typename R, bool IMAG>
 __device__ __forceinline__ typename PartT<R>::T long_line_uni(cx<R>* line, int n, const Tabs<R>& t, int part, int nw,
-                                                              cx<R>* seg) {
+                                                              cx<R>* seg, bool want_norm = true) {
     const int i0 = (part * 32 + (threadIdx.x & 31)) * kLongC;
     constexpr bool INC = sizeof(R) == 4;
     const cx<R> zero = {R(0), R(0)};
@@ -922,18 +922,24 @@ __device__ __forceinline__ typename PartT<R>::T long_line_uni(cx<R>* line, int n
     group_solve_uni<R, IMAG>(v, t, part, nw, seg, n, i0);
     const auto k = ucoef<IMAG>(t.uk);
     typename std::conditional<INC && IMAG, NormAccF2, NormAcc<R>>::type acc;
+    auto result = [&](int m) {
+        const cx<R> x = line[long_slot(i0 + m)];
+        cx<R> o;
+        if constexpr (INC)
+            o = gfma(k, v[m], x);
+        else
+            o = gfms(k, v[m], x);
+        line[long_slot(i0 + m)] = o;
+        return o;
+    };
+    if (want_norm) {
 #pragma unroll
-    for (int m = 0; m < kLongC; m++) {
-        if (i0 + m < n) {
-            const cx<R> x = line[long_slot(i0 + m)];
-            cx<R> o;
-            if constexpr (INC)
-                o = gfma(k, v[m], x);
-            else
-                o = gfms(k, v[m], x);
-            line[long_slot(i0 + m)] = o;
-            acc.add(o);
-        }
+        for (int m = 0; m < kLongC; m++)
+            if (i0 + m < n) acc.add(result(m));
+    } else {
+        // (points past n: their slots are never stored)
+#pragma unroll
+        for (int m = 0; m < kLongC; m++) result(m);
     }
     if constexpr (INC && IMAG)
         return acc.dfvalue();
@@ -948,8 +954,8 @@ __device__ __forceinline__ typename PartT<R>::T long_line_uni(cx<R>* line, int n
 // the lane's points (for the norm partials).
 template <typename R, bool IMAG, bool UNI>
 __device__ __forceinline__ typename PartT<R>::T long_line(cx<R>* line, int n, const Tabs<R>& t, int part, int nw,
-                                                          cx<R>* seg) {
-    if constexpr (UNI) return long_line_uni<R, IMAG>(line, n, t, part, nw, seg);
+                                                          cx<R>* seg, bool want_norm = true) {
+    if constexpr (UNI) return long_line_uni<R, IMAG>(line, n, t, part, nw, seg, want_norm);
     const int i0 = (part * 32 + (threadIdx.x & 31)) * kLongC;
     constexpr bool INC = sizeof(R) == 4;
     const cx<R> zero = {R(0), R(0)};
@@ -1028,21 +1034,27 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps, long_min_blocks<R, UNI>())
     const int n = p.nx;
     const size_t base = (size_t)blockIdx.x * n;
     // the block's 32 nw threads stage the span = 16 * 32 nw points: all 16 loads of a
-    // thread in flight before the shared-memory stores
+    // thread in flight before the shared-memory stores. Point threadIdx.x + k blockDim
+    // sits at slot long_slot(threadIdx.x) + k sstep (blockDim is a multiple of 16).
+    const int sstep = ((int)blockDim.x >> 4) * kLongS;
+    const typename V2<R>::T* src = in + base + threadIdx.x;
+    typename V2<R>::T* dst = out + base + threadIdx.x;
+    cx<R>* slot = line + long_slot(threadIdx.x);
+    const int rem = n - (int)threadIdx.x;  // point k is in the line when k blockDim < rem
     {
         cx<R> tmp[kLongC];
 #pragma unroll
-        for (int k = 0; k < kLongC; k++) {
-            const int i = threadIdx.x + k * (int)blockDim.x;
-            tmp[k] = i < n ? ldc<R>(in, base + i) : cx<R>{R(0), R(0)};
-        }
+        for (int k = 0; k < kLongC; k++)
+            tmp[k] = k * (int)blockDim.x < rem ? ldc<R>(src, (size_t)k * blockDim.x) : cx<R>{R(0), R(0)};
 #pragma unroll
-        for (int k = 0; k < kLongC; k++) line[long_slot(threadIdx.x + k * (int)blockDim.x)] = tmp[k];
+        for (int k = 0; k < kLongC; k++) slot[k * sstep] = tmp[k];
     }
     __syncthreads();
-    const P acc = long_line<R, IMAG, UNI>(line, n, t, warp, nw, seg);
+    const P acc = long_line<R, IMAG, UNI>(line, n, t, warp, nw, seg, part != nullptr);
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) st<R>(out, base + i, line[long_slot(i)]);
+#pragma unroll
+    for (int k = 0; k < kLongC; k++)
+        if (k * (int)blockDim.x < rem) st<R>(dst, (size_t)k * blockDim.x, slot[k * sstep]);
     if (part) {
         const P sum = block_part(acc, red);
         if (threadIdx.x == 0) reinterpret_cast<P*>(part)[blockIdx.x] = sum;
@@ -1105,6 +1117,175 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps, long_min_blocks<R, UNI>())
     if (part) {
         if (col0 + c >= p.nx) acc = P(0);
         const P sum = block_part(acc, red);
+        if (threadIdx.x == 0) reinterpret_cast<P*>(part)[blockIdx.x] = sum;
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// CN along y in row tiles, for the constant-factor solve (Tabs::uks > 0) when
+// a chunk's carries reach at most kTileMaxHalo chunks: |g^16|^hc < 2^-64 (the
+// small bt of the workloads, where g = bt / u is about 0.02). A block holds
+// a tile of 32 adjacent columns, one per lane, so that every warp load and
+// store is one contiguous row segment (256 bytes in complex64), and the rows
+// [y0 - 16 hc, y0 + 16 (kTileReal + hc)): kTileReal chunks of 16 rows that it
+// writes, and hc chunks above and below that only feed their carries. Warp w
+// holds the chunk of rows i0 = y0 + 16 (w - hc) .. i0 + 15 of its lane's
+// column in registers; the forward and backward carries of the hc nearest
+// chunks are composed through shared memory (a chunk further away weighs less
+// than 2^-64). The top tile applies the start correction of the first uks
+// rows (uks <= 16 kTileReal). The arithmetic per point is that of
+// long_line_uni. in != out: the halos read other tiles' input rows.
+// ---------------------------------------------------------------------------
+
+template <typename R, int HC> constexpr int tile_min_blocks() { return sizeof(R) == 4 ? (HC == 1 ? 3 : 2) : 1; }
+
+template <typename R, bool IMAG, int HC>
+__global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<R, HC>()))
+    k_cn_y_tile(const typename V2<R>::T* __restrict__ in, typename V2<R>::T* __restrict__ out, KParams p, Tabs<R> t,
+                double* part) {
+    using G = typename UCoef<IMAG, R>::T;
+    using P = typename PartT<R>::T;
+    using T = typename V2<R>::T;
+    constexpr bool INC = sizeof(R) == 4;
+    constexpr int NW = kTileReal + 2 * HC;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<R>* xs = reinterpret_cast<cx<R>*>(smem_raw);  // [warp][m][lane]: the loaded values
+    __shared__ cx<R> fend[NW][32], bend[NW][32];      // chunk ends of the two passes
+    __shared__ cx<R> q0s[32];
+    __shared__ P red[NW];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int n = p.ny, nx = p.nx;
+    const int nrt = (n + kTileRows - 1) / kTileRows, nct = (nx + 31) >> 5;
+    const int rt = blockIdx.x % nrt, rest = blockIdx.x / nrt;
+    const int ct = rest % nct, j = rest / nct;
+    const int y0 = rt * kTileRows, i0 = y0 + 16 * (w - HC);
+    const int col = ct * 32 + lane;
+    const bool colok = col < nx;
+    // a lane past the last column reads column nx - 1 (in bounds) and stores nothing:
+    // the columns are independent
+    const size_t cbase = (size_t)j * nx * n + (colok ? col : nx - 1);
+    const cx<R> zero = {R(0), R(0)};
+    cx<R>* xw = xs + (size_t)w * kLongC * 32 + lane;
+    // warp-uniform: the chunk and the rows next to it lie inside the column
+    const bool inner = i0 >= 1 && i0 + kLongC < n;
+    const T* src = in + cbase + (ptrdiff_t)i0 * nx;
+    cx<R> v[kLongC];
+    {
+        cx<R> x[kLongC];
+        cx<R> prev, last;
+        if (inner) {
+#pragma unroll
+            for (int m = 0; m < kLongC; m++) x[m] = ldc<R>(src, (size_t)m * nx);
+            prev = ldc<R>(src - nx, 0);
+            last = ldc<R>(src, (size_t)kLongC * nx);
+        } else {
+#pragma unroll
+            for (int m = 0; m < kLongC; m++) {
+                const int i = i0 + m;
+                x[m] = (i >= 0 && i < n) ? ldc<R>(in, cbase + (size_t)i * nx) : zero;
+            }
+            // the neighbours of the chunk's end rows (outside the tile they count as
+            // zero: they feed the halo's carries only)
+            const int im = i0 - 1, ip = i0 + kLongC;
+            prev = (im >= 0 && im < n) ? ldc<R>(in, cbase + (size_t)im * nx) : zero;
+            last = (ip >= 0 && ip < n) ? ldc<R>(in, cbase + (size_t)ip * nx) : zero;
+        }
+        if constexpr (INC) {
+            // right-hand side L x, zero outside the column
+#pragma unroll
+            for (int m = 0; m < kLongC; m++) {
+                const cx<R> cur = x[m];
+                const cx<R> nxt = m + 1 < kLongC ? x[m + 1] : last;
+                const cx<R> r = gadd(gsub(prev, cur), gsub(nxt, cur));
+                v[m] = (inner || (i0 + m >= 0 && i0 + m < n)) ? r : zero;
+                prev = cur;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < kLongC; m++) v[m] = x[m];
+        }
+#pragma unroll
+        for (int m = 0; m < kLongC; m++) xw[m * 32] = x[m];
+    }
+    const G g = ucoef<IMAG>(t.ug), g16 = ucoef<IMAG>(t.ug16);
+    // forward z_i = r_i + g z_(i-1): the chunk from a zero start, then the carry
+    cx<R> z = zero;
+#pragma unroll
+    for (int m = 0; m < kLongC; m++) {
+        z = gfma(g, z, v[m]);
+        v[m] = z;
+    }
+    fend[w][lane] = z;
+    __syncthreads();
+    {
+        cx<R> cin = zero;
+#pragma unroll
+        for (int k = HC; k >= 1; k--)
+            if (w - k >= 0) cin = gfma(g16, cin, fend[w - k][lane]);
+        // z_m += g^(m+1) cin
+#pragma unroll
+        for (int m = 0; m < kLongC; m++) v[m] = pfma<IMAG>(t.upow[m], cin, v[m]);
+    }
+    if (i0 + kLongC > n) {
+#pragma unroll
+        for (int m = 0; m < kLongC; m++)
+            if (i0 + m >= n) v[m] = zero;
+    }
+    // backward q_i = z_i + g q_(i+1)
+    cx<R> q = zero;
+#pragma unroll
+    for (int m = kLongC - 1; m >= 0; m--) {
+        q = gfma(g, q, v[m]);
+        v[m] = q;
+    }
+    bend[w][lane] = q;
+    __syncthreads();
+    {
+        cx<R> cb = zero;
+#pragma unroll
+        for (int k = HC; k >= 1; k--)
+            if (w + k < NW) cb = gfma(g16, cb, bend[w + k][lane]);
+        // q_m += g^(16 - m) cb
+#pragma unroll
+        for (int m = 0; m < kLongC; m++) v[m] = pfma<IMAG>(t.upow[kLongC - 1 - m], cb, v[m]);
+    }
+    if (y0 == 0) {  // the start correction: rows i < uks (block-uniform branch)
+        if (w == HC) q0s[lane] = v[0];
+        __syncthreads();
+        if (w >= HC && i0 < t.uks) {
+            const cx<R> cq = mul(t.uc, q0s[lane]);
+#pragma unroll
+            for (int m = 0; m < kLongC; m++)
+                if (i0 + m < t.uks) v[m] = sub(v[m], mul(cq, tld<R>(t.us, i0 + m)));
+        }
+    }
+    const auto k = ucoef<IMAG>(t.uk);
+    typename std::conditional<INC && IMAG, NormAccF2, NormAcc<R>>::type acc;
+    if (w >= HC && w < HC + kTileReal && colok) {
+        T* dst = out + cbase + (ptrdiff_t)i0 * nx;
+        const bool full = i0 + kLongC <= n;
+#pragma unroll
+        for (int m = 0; m < kLongC; m++) {
+            if (full || i0 + m < n) {
+                const cx<R> x = xw[m * 32];
+                cx<R> o;
+                if constexpr (INC)
+                    o = gfma(k, v[m], x);
+                else
+                    o = gfms(k, v[m], x);
+                st<R>(dst, (size_t)m * nx, o);
+                acc.add(o);
+            }
+        }
+    }
+    if (part) {
+        P a;
+        if constexpr (INC && IMAG)
+            a = acc.dfvalue();
+        else
+            a = acc_value<P>(acc);
+        const P sum = block_part(a, red);
         if (threadIdx.x == 0) reinterpret_cast<P*>(part)[blockIdx.x] = sum;
     }
 }

@@ -104,6 +104,33 @@ __device__ __forceinline__ double exp_small(double x) {
 }
 __device__ __forceinline__ float exp_small(float x) { return expf(x); }
 
+// exp(x) - 1 in FP32 for the complex64 CALCNU factor, written out from the
+// mathematics: Cody-Waite reduction x = k ln2 + r with |r| <= ln2/2 (ln2 split
+// into a 12-bit head, whose product with k is exact for |k| < 2^12, and the
+// rest), the Taylor series of expm1(r) through r^8/8! (the omitted terms stay
+// below 6e-10 |r|, 0.01 ulp), and expm1(x) = 2^k expm1(r) + (2^k - 1) in one
+// fused multiply-add (2^k - 1 is exact for |k| <= 24; k = 0 returns the series
+// itself). The argument is clamped to [-87.3, 89] so that 2^k stays a normal
+// number or becomes infinity (x > 88.72: the true result overflows too); the
+// clamp compares, so a NaN argument stays NaN.
+__device__ __forceinline__ float expm1_cw(float x) {
+    x = x < -87.3f ? -87.3f : x;
+    x = x > 89.0f ? 89.0f : x;
+    const float kf = rintf(x * 1.44269504088896341f);  // nearest integer to x / ln2
+    float r = fmaf(-kf, 0.693145751953125f, x);         // ln2 head: 2839 / 4096
+    r = fmaf(-kf, 1.42860682030941723e-6f, r);          // ln2 - head
+    float q = 1.0f / 40320.0f;
+    q = fmaf(q, r, 1.0f / 5040.0f);
+    q = fmaf(q, r, 1.0f / 720.0f);
+    q = fmaf(q, r, 1.0f / 120.0f);
+    q = fmaf(q, r, 1.0f / 24.0f);
+    q = fmaf(q, r, 1.0f / 6.0f);
+    q = fmaf(q, r, 0.5f);
+    const float e = fmaf(q, r * r, r);  // expm1(r)
+    const float t = __int_as_float(((int)kf + 127) << 23);  // 2^k
+    return fmaf(t, e, t - 1.0f);
+}
+
 __device__ __forceinline__ void sincos_small(double x, double* s, double* c) {
     if (small_arg(x)) {
         double t = x * x;
@@ -270,6 +297,11 @@ inline void fill_derived(KParams& k) {
 // Lines longer than 1024 points: 16 points a lane, at most 16 warps a block.
 constexpr int kLongC = 16;
 constexpr int kLongMaxWarps = 16;
+// Row tiles of the y sweep of long columns (k_cn_y_tile): chunks of kLongC rows
+// a tile writes, the most halo chunks above and below, rows written per tile.
+constexpr int kTileReal = 8, kTileMaxHalo = 2;
+constexpr int kTileMaxWarps = kTileReal + 2 * kTileMaxHalo;
+constexpr int kTileRows = kLongC * kTileReal;
 // Extra elements between the staged columns of a y tile of lines longer than
 // 1024 points (complex64 tiles of 4 columns; see k_cn_y).
 __host__ __device__ constexpr int long_col_pad(int elem_bytes, int kc) { return (elem_bytes == 8 && kc == 4) ? 4 : 0; }
@@ -354,7 +386,7 @@ __device__ __forceinline__ void calcnu_point(cx<R> (&u)[3], R V, R c0, R c2, R d
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             if (IMAG) {
-                u[j] = axpy((R)expm1f((float)(-dt * mu[j])), u[j], u[j]);
+                u[j] = axpy((R)expm1_cw((float)(-dt * mu[j])), u[j], u[j]);
             } else {
                 float sh, ch;
                 sincosf((float)(0.5f * dt * mu[j]), &sh, &ch);

@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(128) k_pointwise(const typename V2<R>::T* __re
 // point is pointwise_apply's, as in k_pointwise. The complex64 pointwise kernel
 // is bound by instruction issue, half of it loads and their index arithmetic.
 template <bool IMAG>
-__global__ void __launch_bounds__(128) k_pointwise2(const float2* __restrict__ A, float2* __restrict__ B, KParams p,
+__global__ void __launch_bounds__(256) k_pointwise2(const float2* __restrict__ A, float2* __restrict__ B, KParams p,
                                                     const DevScalars* __restrict__ sc,
                                                     const double* __restrict__ omega_tab, int mask) {
     const int ix = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -409,17 +409,34 @@ __global__ void __launch_bounds__(128) k_pointwise2(const float2* __restrict__ A
         in0.X[j] = in0.Y[j] = in1.X[j] = in1.Y[j] = zero;
     }
     if (so) {
+        // every neighbour inside the grid (2D): loads without the zero ghosts
+        const bool inner = p.dim == 2 && ix > 0 && ix + 2 < p.nx && iy > 0 && iy + 1 < p.ny;
+        if (inner) {
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-            const cx<float> xm = ix > 0 ? ld<float>(A, j * plane + c - 1) : zero;
-            const cx<float> xp = ix + 2 < p.nx ? ld<float>(A, j * plane + c + 2) : zero;
-            in0.X[j] = sub(in1.u[j], xm);
-            in1.X[j] = sub(xp, in0.u[j]);
-            if (p.dim == 2) {
-                const float4 ym = iy > 0 ? __ldg(reinterpret_cast<const float4*>(A + j * plane + c - p.nx)) : z4;
-                const float4 yp = iy + 1 < p.ny ? __ldg(reinterpret_cast<const float4*>(A + j * plane + c + p.nx)) : z4;
+            for (int j = 0; j < 3; j++) {
+                const float2* a = A + j * plane + c;
+                const cx<float> xm = unpack(__ldg(a - 1)), xp = unpack(__ldg(a + 2));
+                in0.X[j] = sub(in1.u[j], xm);
+                in1.X[j] = sub(xp, in0.u[j]);
+                const float4 ym = __ldg(reinterpret_cast<const float4*>(a - p.nx));
+                const float4 yp = __ldg(reinterpret_cast<const float4*>(a + p.nx));
                 in0.Y[j] = sub(cx<float>{yp.x, yp.y}, cx<float>{ym.x, ym.y});
                 in1.Y[j] = sub(cx<float>{yp.z, yp.w}, cx<float>{ym.z, ym.w});
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const cx<float> xm = ix > 0 ? ld<float>(A, j * plane + c - 1) : zero;
+                const cx<float> xp = ix + 2 < p.nx ? ld<float>(A, j * plane + c + 2) : zero;
+                in0.X[j] = sub(in1.u[j], xm);
+                in1.X[j] = sub(xp, in0.u[j]);
+                if (p.dim == 2) {
+                    const float4 ym = iy > 0 ? __ldg(reinterpret_cast<const float4*>(A + j * plane + c - p.nx)) : z4;
+                    const float4 yp =
+                        iy + 1 < p.ny ? __ldg(reinterpret_cast<const float4*>(A + j * plane + c + p.nx)) : z4;
+                    in0.Y[j] = sub(cx<float>{yp.x, yp.y}, cx<float>{ym.x, ym.y});
+                    in1.Y[j] = sub(cx<float>{yp.z, yp.w}, cx<float>{ym.z, ym.w});
+                }
             }
         }
     }
@@ -508,6 +525,35 @@ __device__ __forceinline__ void scale_from_df_sums(const df (&S)[3], double cell
     for (int j = 0; j < 3; j++) f[j] = df_from(d[j]);
 }
 
+// Thread 0: N_j, the next pending scale and the step counter from the three
+// component sums (FP64 sums, or double-float pairs when part_df).
+__device__ __forceinline__ void finalize_publish(const double (&red)[3], const df (&red_df)[3], double cell,
+                                                 int renorm, double mag, int advance_step, DevScalars* sc,
+                                                 int part_df) {
+    double N[3], d[3];
+    bool finite;
+    if (part_df) {
+        const df S[3] = {red_df[0], red_df[1], red_df[2]};
+        df f[3];
+        scale_from_df_sums(S, cell, renorm, mag, f, d, N, finite);
+    } else {
+        N[0] = red[0] * cell;
+        N[1] = red[1] * cell;
+        N[2] = red[2] * cell;
+        finite = isfinite(N[0]) && isfinite(N[1]) && isfinite(N[2]);
+        renorm_factors(N, finite ? renorm : 0, mag, d);
+    }
+    for (int q3 = 0; q3 < 3; q3++) {
+        sc->norms[q3] = N[q3];
+        sc->scale[q3] = d[q3];
+        sc->scale_f[q3] = (float)d[q3];
+        sc->scale_l[q3] = (float)(d[q3] - (double)sc->scale_f[q3]);
+    }
+    if (!finite) sc->err |= 1;
+    if (advance_step) sc->step_idx += 1;
+    sc->scale_src = 0;
+}
+
 // part_df: the partials are double-float pairs (see sum_partials_warp above).
 static __global__ void __launch_bounds__(96) k_finalize(const double* partials, int m, double cell, int renorm,
                                                  double mag, int advance_step, DevScalars* sc, int part_df) {
@@ -525,28 +571,73 @@ static __global__ void __launch_bounds__(96) k_finalize(const double* partials, 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double N[3], d[3];
-        bool finite;
-        if (part_df) {
-            const df S[3] = {red_df[0], red_df[1], red_df[2]};
-            df f[3];
-            scale_from_df_sums(S, cell, renorm, mag, f, d, N, finite);
-        } else {
-            N[0] = red[0] * cell;
-            N[1] = red[1] * cell;
-            N[2] = red[2] * cell;
-            finite = isfinite(N[0]) && isfinite(N[1]) && isfinite(N[2]);
-            renorm_factors(N, finite ? renorm : 0, mag, d);
+        double r[3] = {red[0], red[1], red[2]};
+        df rd[3] = {red_df[0], red_df[1], red_df[2]};
+        finalize_publish(r, rd, cell, renorm, mag, advance_step, sc, part_df);
+    }
+}
+
+// The same for more than 256 partials per component (the row-tiled sweeps of
+// large grids): kFinWarps warps per component, warp s summing the partials
+// s * 32 + lane + 256 k in batches of eight loads in flight (a pairwise tree
+// per batch, the batches in order), then the warps' sums in index order. The
+// order depends on m only: the same sums on every run.
+constexpr int kFinWarps = 8;
+template <typename P> __device__ __forceinline__ P fin_load(const P* q, int i, int m);
+template <> __device__ __forceinline__ double fin_load<double>(const double* q, int i, int m) {
+    return i < m ? __ldcg(q + i) : 0.0;
+}
+template <> __device__ __forceinline__ df fin_load<df>(const df* q, int i, int m) {
+    if (i >= m) return df(0.0f, 0.0f);
+    const float2 e = __ldcg(reinterpret_cast<const float2*>(q) + i);
+    return df(e.x, e.y);
+}
+__device__ __forceinline__ double fin_xor(double v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ df fin_xor(df v, int off) { return df_shfl_xor(v, off); }
+
+template <typename P> __device__ __forceinline__ P sum_partials_wide(const P* q, int m, int sub) {
+    const int lane = threadIdx.x & 31;
+    P s = P(0);
+    for (int b0 = sub * 32 + lane; b0 < m; b0 += 8 * 32 * kFinWarps) {
+        P v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = fin_load(q, b0 + k * 32 * kFinWarps, m);
+        s = s + (((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s = s + fin_xor(s, off);
+    return s;
+}
+
+static __global__ void __launch_bounds__(96 * kFinWarps) k_finalize_wide(const double* partials, int m, double cell,
+                                                                      int renorm, double mag, int advance_step,
+                                                                      DevScalars* sc, int part_df) {
+    __shared__ double red[3][kFinWarps];
+    __shared__ df red_df[3][kFinWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = warp / kFinWarps, sub = warp % kFinWarps;
+    pdl_trigger();
+    pdl_wait();
+    if (part_df) {
+        const df s = sum_partials_wide(reinterpret_cast<const df*>(partials) + (size_t)j * m, m, sub);
+        if (lane == 0) red_df[j][sub] = s;
+    } else {
+        const double s = sum_partials_wide(partials + (size_t)j * m, m, sub);
+        if (lane == 0) red[j][sub] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r[3];
+        df rd[3];
+        for (int c = 0; c < 3; c++) {
+            r[c] = red[c][0];
+            rd[c] = red_df[c][0];
+            for (int w = 1; w < kFinWarps; w++) {
+                r[c] += red[c][w];
+                rd[c] = rd[c] + red_df[c][w];
+            }
         }
-        for (int q3 = 0; q3 < 3; q3++) {
-            sc->norms[q3] = N[q3];
-            sc->scale[q3] = d[q3];
-            sc->scale_f[q3] = (float)d[q3];
-            sc->scale_l[q3] = (float)(d[q3] - (double)sc->scale_f[q3]);
-        }
-        if (!finite) sc->err |= 1;
-        if (advance_step) sc->step_idx += 1;
-        sc->scale_src = 0;
+        finalize_publish(r, rd, cell, renorm, mag, advance_step, sc, part_df);
     }
 }
 

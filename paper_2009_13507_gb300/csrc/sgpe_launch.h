@@ -86,6 +86,7 @@ struct Geometry {
     bool fused;         // 2D with register x lines: pointwise + CN-x in one kernel
     size_t smem_x, smem_y;
     int blocks_x, blocks_y, blocks_obs, blocks_norm;
+    int blocks_yt;  // long columns: blocks (= norm partials) of the row-tiled y sweep
 };
 
 Geometry make_geometry(int dim, int nx, int ny, int esz);
@@ -98,6 +99,7 @@ struct UniHost {
     double pr[16], pi[16];      // ug^(k+1) (imaginary time: pi = pr)
     int ks;                     // entries of s (0: the line uses the tables)
     int nlev;                   // carry-scan levels
+    int hc;                     // halo chunks of the row-tiled y sweep (0: not applicable)
     const void* s;              // device: s_i, i < ks, in the state's element type
 };
 // The coefficient tables of one axis and time mode, and their constant-factor form.
@@ -105,6 +107,16 @@ struct TabSet {
     void* t[4];  // device: fa, fg, fp, fq
     UniHost u;
 };
+
+// Whether the y sweep of these tables runs in row tiles (k_cn_y_tile: long
+// columns, the constant-factor form with a short carry reach, in != out).
+inline bool y_tiled(const Geometry& g, const TabSet& ty, const void* in, const void* out) {
+    return g.dim == 2 && !g.reg_y && ty.u.ks > 0 && ty.u.hc > 0 && in != out;
+}
+// Norm partials that the step's y sweep (in -> out) leaves.
+inline int y_parts(const Geometry& g, const TabSet& ty, const void* in, const void* out) {
+    return y_tiled(g, ty, in, out) ? g.blocks_yt : g.blocks_y;
+}
 // Longest start correction of the constant-factor form (entries of s).
 constexpr int kUniMaxS = 512;
 

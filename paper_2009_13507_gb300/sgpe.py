@@ -29,7 +29,8 @@ SUBSTEP = {"so": 0, "calcnu": 1, "herm": 2, "cn_x": 3, "cn_y": 4, "renorm": 5, "
 # Every symbol include/sgpe.h declares (checked by the CPU test suite).
 EXPORTS = ("sgpe_init_grid", "sgpe_workspace_bytes", "sgpe_bind", "sgpe_set_params", "sgpe_step_imag",
            "sgpe_step_real", "sgpe_normalize", "sgpe_energy", "sgpe_set_state", "sgpe_get_state", "sgpe_load_state",
-           "sgpe_substep", "sgpe_profile_steps", "sgpe_measure_fp64_rate", "sgpe_observables_noalloc", "sgpe_launches_per_step",
+           "sgpe_substep", "sgpe_profile_steps", "sgpe_measure_fp64_rate", "sgpe_eval_expm1f",
+           "sgpe_observables_noalloc", "sgpe_launches_per_step",
            "sgpe_last_error", "sgpe_destroy", "sgpe_adjoint_workspace_bytes", "sgpe_adjoint_loss_grad",
            "sgpe_adjoint_forward", "sgpe_adjoint_step",
            "sgpe_batch_create", "sgpe_batch_sizes", "sgpe_batch_offsets", "sgpe_batch_bind",
@@ -77,6 +78,7 @@ def load():
         "sgpe_substep": (I, [P, I, I, D]),
         "sgpe_profile_steps": (I, [P, I, I, P, P]),
         "sgpe_measure_fp64_rate": (I, [P, P]),
+        "sgpe_eval_expm1f": (I, [P, P, P, I]),
         "sgpe_observables_noalloc": (I, [P, I, I, I, D, D, I, ctypes.POINTER(Params), P, P]),
         "sgpe_launches_per_step": (I, [P]),
         "sgpe_last_error": (ctypes.c_char_p, [P]),
@@ -309,6 +311,24 @@ class Solver:
         self._check(self.lib.sgpe_adjoint_step(self.ctx, n, om.data_ptr(), tape["K"], tape["ws"].data_ptr(),
                                                g.data_ptr(), dom.data_ptr(), dw.ctypes.data))
         return g, dom, (float(dw[0]), float(dw[1]))
+
+
+def eval_expm1f(x):
+    """exp(x) - 1 of a float32 CUDA tensor by the library's FP32 routine (sgpe_eval_expm1f)."""
+    import torch
+
+    lib = load()
+    x = x.contiguous()
+    if x.dtype != torch.float32 or not x.is_cuda:
+        raise ValueError("eval_expm1f takes a float32 CUDA tensor")
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream(x.device)
+    rc = lib.sgpe_eval_expm1f(ctypes.c_void_p(stream.cuda_stream), ctypes.c_void_p(x.data_ptr()),
+                              ctypes.c_void_p(y.data_ptr()), int(x.numel()))
+    if rc != OK:
+        msg = lib.sgpe_last_error(None)
+        raise SgpeError(rc, msg.decode() if msg else "sgpe_eval_expm1f")
+    return y
 
 
 def measure_fp64_rate(stream=None) -> float:

@@ -87,6 +87,33 @@ def test_cn_long_lines(bt, which, nx, ny, imag, precision):
     assert relerr(s.get_state(), O.substep(prob, psi, which, imag)) < LONG_TOL[(precision, bt)]
 
 
+@pytest.mark.parametrize("precision", ["c64", "cdf"])
+@pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("nx,ny", [(33, 1100), (64, 2048), (5, 1025), (70, 1300)])
+@pytest.mark.parametrize("bt", [0.02, 0.3])
+def test_cn_y_row_tiles(bt, nx, ny, imag, precision):
+    """Columns longer than 1024 points in the constant-factor forms at small bt:
+    the y sweep in row tiles of 32 columns x 128 rows with one (bt = 0.02) or two
+    (bt = 0.3) halo chunks of 16 rows above and below; ragged last column tile
+    (33, 70 and 5 columns), ragged last row tile (1100, 1025, 1300 rows), the
+    start correction in the top tile. Then full steps in both time modes, whose
+    norm partials come from the tiles (1024 of them per component at 64 x 2048:
+    the wide finalize block)."""
+    dy = 0.1
+    phys = dict(PHYS_2D, dt=4.0 * dy * dy * bt)
+    prob, s = make_pair(2, nx, ny, dx=0.1, dy=dy, precision=precision, **phys)
+    psi = _rand(prob, 31 + nx, env=3.0)
+    s.set_state(psi)
+    s.substep("cn_y", imag)
+    tol = {"c64": 5e-6, "cdf": 1e-12}[precision]
+    assert relerr(s.get_state(), O.substep(prob, psi, "cn_y", imag)) < tol
+    s.set_state(psi)
+    (s.step_imag(3) if imag else s.step_real(3))
+    ref = O.step(prob, psi, 3, imag)
+    assert relerr(s.get_state(), ref) < (1e-5 if precision == "c64" else 1e-10)
+    assert obs_relerr(s.energy(), O.observables(prob, ref)) < (1e-5 if precision == "c64" else 1e-10)
+
+
 @pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("cdf", 1e-10), ("c64", 2e-5)])
 @pytest.mark.parametrize("nx", [1025, 3000])
 def test_1d_long_lines_full_steps(nx, precision, tol):
