@@ -1041,6 +1041,7 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps, long_min_blocks<R, UNI>())
     typename V2<R>::T* dst = out + base + threadIdx.x;
     cx<R>* slot = line + long_slot(threadIdx.x);
     const int rem = n - (int)threadIdx.x;  // point k is in the line when k blockDim < rem
+    pdl_wait();
     {
         cx<R> tmp[kLongC];
 #pragma unroll
@@ -1051,6 +1052,7 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps, long_min_blocks<R, UNI>())
     }
     __syncthreads();
     const P acc = long_line<R, IMAG, UNI>(line, n, t, warp, nw, seg, part != nullptr);
+    pdl_trigger();  // the next sweep's blocks may take the slots this grid frees
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kLongC; k++)
@@ -1171,10 +1173,17 @@ __global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<R,
     const bool inner = i0 >= 1 && i0 + kLongC < n;
     const T* src = in + cbase + (ptrdiff_t)i0 * nx;
     cx<R> v[kLongC];
-    {
+    pdl_wait();
+    // with norm partials the next launch is the finalize block, which may become
+    // resident now (it waits for this grid); otherwise the next kernel launches at the end
+    if (part) pdl_trigger();
+    // the chunk's values x (kept in shared memory for the result) and the right-hand
+    // side: L x (increment form) or x. IN: no row checks (inner chunk).
+    auto load_rhs = [&](auto in_tag) {
+        constexpr bool IN = decltype(in_tag)::value;
         cx<R> x[kLongC];
         cx<R> prev, last;
-        if (inner) {
+        if constexpr (IN) {
 #pragma unroll
             for (int m = 0; m < kLongC; m++) x[m] = ldc<R>(src, (size_t)m * nx);
             prev = ldc<R>(src - nx, 0);
@@ -1192,13 +1201,16 @@ __global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<R,
             last = (ip >= 0 && ip < n) ? ldc<R>(in, cbase + (size_t)ip * nx) : zero;
         }
         if constexpr (INC) {
-            // right-hand side L x, zero outside the column
+            // L x, zero outside the column
 #pragma unroll
             for (int m = 0; m < kLongC; m++) {
                 const cx<R> cur = x[m];
                 const cx<R> nxt = m + 1 < kLongC ? x[m + 1] : last;
                 const cx<R> r = gadd(gsub(prev, cur), gsub(nxt, cur));
-                v[m] = (inner || (i0 + m >= 0 && i0 + m < n)) ? r : zero;
+                if constexpr (IN)
+                    v[m] = r;
+                else
+                    v[m] = (i0 + m >= 0 && i0 + m < n) ? r : zero;
                 prev = cur;
             }
         } else {
@@ -1207,7 +1219,11 @@ __global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<R,
         }
 #pragma unroll
         for (int m = 0; m < kLongC; m++) xw[m * 32] = x[m];
-    }
+    };
+    if (inner)
+        load_rhs(std::true_type{});
+    else
+        load_rhs(std::false_type{});
     const G g = ucoef<IMAG>(t.ug), g16 = ucoef<IMAG>(t.ug16);
     // forward z_i = r_i + g z_(i-1): the chunk from a zero start, then the carry
     cx<R> z = zero;
@@ -1264,19 +1280,23 @@ __global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<R,
     typename std::conditional<INC && IMAG, NormAccF2, NormAcc<R>>::type acc;
     if (w >= HC && w < HC + kTileReal && colok) {
         T* dst = out + cbase + (ptrdiff_t)i0 * nx;
-        const bool full = i0 + kLongC <= n;
+        auto result = [&](int m) {
+            const cx<R> x = xw[m * 32];
+            cx<R> o;
+            if constexpr (INC)
+                o = gfma(k, v[m], x);
+            else
+                o = gfms(k, v[m], x);
+            st<R>(dst, (size_t)m * nx, o);
+            acc.add(o);
+        };
+        if (i0 + kLongC <= n) {
 #pragma unroll
-        for (int m = 0; m < kLongC; m++) {
-            if (full || i0 + m < n) {
-                const cx<R> x = xw[m * 32];
-                cx<R> o;
-                if constexpr (INC)
-                    o = gfma(k, v[m], x);
-                else
-                    o = gfms(k, v[m], x);
-                st<R>(dst, (size_t)m * nx, o);
-                acc.add(o);
-            }
+            for (int m = 0; m < kLongC; m++) result(m);
+        } else {
+#pragma unroll
+            for (int m = 0; m < kLongC; m++)
+                if (i0 + m < n) result(m);
         }
     }
     if (part) {

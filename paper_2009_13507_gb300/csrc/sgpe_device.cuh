@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "sgpe_df.cuh"
 
 namespace sgpe {
@@ -131,6 +133,62 @@ __device__ __forceinline__ float expm1_cw(float x) {
     return fmaf(t, e, t - 1.0f);
 }
 
+// Two FP32 numbers as one operand of the packed FP32x2 instructions (add, sub,
+// mul and fma on both lanes at once, each lane rounded as the scalar
+// instruction rounds it). The complex64 pointwise kernel evaluates its two grid
+// points (ix, ix + 1) as one pair, so each arithmetic instruction of the
+// substeps serves both points.
+struct f32x2 {
+    float2 v;
+    f32x2() = default;
+    __device__ __forceinline__ f32x2(float2 a) : v(a) {}
+    __device__ __forceinline__ f32x2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ explicit f32x2(float a) : v(make_float2(a, a)) {}
+    __device__ __forceinline__ explicit f32x2(int a) : v(make_float2((float)a, (float)a)) {}
+};
+template <typename R> constexpr bool is_pair() { return std::is_same<R, f32x2>::value; }
+__device__ __forceinline__ f32x2 operator+(f32x2 a, f32x2 b) { return __fadd2_rn(a.v, b.v); }
+__device__ __forceinline__ f32x2 operator*(f32x2 a, f32x2 b) { return __fmul2_rn(a.v, b.v); }
+__device__ __forceinline__ f32x2 operator-(f32x2 a, f32x2 b) {
+    unsigned long long ra, rb, rd;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.v.x), "f"(a.v.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.v.x), "f"(b.v.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(rd));
+    return f32x2(x, y);
+}
+// -a, an exact sign change of both lanes
+__device__ __forceinline__ f32x2 operator-(f32x2 a) { return __fmul2_rn(a.v, make_float2(-1.0f, -1.0f)); }
+__device__ __forceinline__ f32x2 fma(f32x2 a, f32x2 b, f32x2 c) { return __ffma2_rn(a.v, b.v, c.v); }
+
+// expm1_cw on both lanes: the clamps, the rounding to the nearest integer and the
+// exponent of 2^k per lane, the rest on the packed instructions (each lane the
+// same operations in the same order as expm1_cw).
+__device__ __forceinline__ f32x2 expm1_cw(f32x2 x) {
+    float a = x.v.x, b = x.v.y;
+    a = a < -87.3f ? -87.3f : a;
+    a = a > 89.0f ? 89.0f : a;
+    b = b < -87.3f ? -87.3f : b;
+    b = b > 89.0f ? 89.0f : b;
+    const f32x2 xc(a, b);
+    const f32x2 kx = xc * f32x2(1.44269504088896341f);
+    const float ka = rintf(kx.v.x), kb = rintf(kx.v.y);
+    const f32x2 nk(-ka, -kb);
+    f32x2 r = fma(nk, f32x2(0.693145751953125f), xc);
+    r = fma(nk, f32x2(1.42860682030941723e-6f), r);
+    f32x2 q(1.0f / 40320.0f);
+    q = fma(q, r, f32x2(1.0f / 5040.0f));
+    q = fma(q, r, f32x2(1.0f / 720.0f));
+    q = fma(q, r, f32x2(1.0f / 120.0f));
+    q = fma(q, r, f32x2(1.0f / 24.0f));
+    q = fma(q, r, f32x2(1.0f / 6.0f));
+    q = fma(q, r, f32x2(0.5f));
+    const f32x2 e = fma(q, r * r, r);
+    const f32x2 t(__int_as_float(((int)ka + 127) << 23), __int_as_float(((int)kb + 127) << 23));
+    return fma(t, e, t - f32x2(1.0f));
+}
+
 __device__ __forceinline__ void sincos_small(double x, double* s, double* c) {
     if (small_arg(x)) {
         double t = x * x;
@@ -225,6 +283,28 @@ __device__ __forceinline__ void herm_coeffs(float C2, float dt, float* s, float*
     }
 }
 
+// herm_coeffs on a pair of points: the series on the packed instructions when
+// both lanes are in its range, otherwise lane by lane.
+template <bool IMAG>
+__device__ __forceinline__ void herm_coeffs_pair(f32x2 C2, f32x2 dt, f32x2* s, f32x2* k) {
+    const f32x2 w = dt * dt * C2;
+    if (w.v.x <= 1.0f / 256.0f && w.v.y <= 1.0f / 256.0f) {
+        const f32x2 v = IMAG ? w : -w;
+        f32x2 ps = fma(fma(f32x2(1.0f / 5040.0f), v, f32x2(1.0f / 120.0f)), v, f32x2(1.0f / 6.0f));
+        ps = fma(ps, v, f32x2(1.0f));
+        f32x2 pk = fma(fma(f32x2(1.0f / 40320.0f), v, f32x2(1.0f / 720.0f)), v, f32x2(1.0f / 24.0f));
+        pk = fma(pk, v, f32x2(0.5f));
+        *s = dt * ps;
+        *k = (IMAG ? dt * dt : -dt * dt) * pk;
+        return;
+    }
+    float s0, k0, s1, k1;
+    herm_coeffs<IMAG>(C2.v.x, dt.v.x, &s0, &k0);
+    herm_coeffs<IMAG>(C2.v.y, dt.v.y, &s1, &k1);
+    *s = f32x2(s0, s1);
+    *k = f32x2(k0, k1);
+}
+
 // Multiply by z/dt: 1 in imaginary time, i in real time.
 template <bool IMAG, typename R> __device__ __forceinline__ cx<R> zunit(cx<R> a) {
     if (IMAG) return a;
@@ -310,6 +390,7 @@ template <typename R> __device__ __forceinline__ R kc(const KParams& p, int i);
 template <> __device__ __forceinline__ double kc<double>(const KParams& p, int i) { return p.kd[i]; }
 template <> __device__ __forceinline__ float kc<float>(const KParams& p, int i) { return p.kf[i]; }
 template <> __device__ __forceinline__ df kc<df>(const KParams& p, int i) { return df(p.kf[i], p.kl[i]); }
+template <> __device__ __forceinline__ f32x2 kc<f32x2>(const KParams& p, int i) { return f32x2(p.kf[i]); }
 
 // Programmatic dependent launch (sm_90+). The step kernels are launched with
 // programmatic stream serialization, so a kernel's blocks may be scheduled
@@ -378,7 +459,25 @@ __device__ __forceinline__ void calcnu_point(cx<R> (&u)[3], R V, R c0, R c2, R d
     R mup = fma(c2, rp - rm + r0, base);
     R mu0 = fma(c2, rp + rm, base);
     R mum = fma(c2, rm - rp + r0, base);
-    if (sizeof(R) == 4) {
+    if constexpr (is_pair<R>()) {
+        // the complex64 form below on a pair of points
+        const R mu[3] = {mup, mu0, mum};
+        const R ndt = -dt, hdt = R(0.5f) * dt;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            if (IMAG) {
+                u[j] = axpy(expm1_cw(ndt * mu[j]), u[j], u[j]);
+            } else {
+                const R t = hdt * mu[j];
+                float s0, c0_, s1, c1_;
+                sincosf(t.v.x, &s0, &c0_);
+                sincosf(t.v.y, &s1, &c1_);
+                const R sh(s0, s1), ch(c0_, c1_), m2 = R(-2.0f) * sh;
+                const cx<R> fm1 = {m2 * sh, m2 * ch};  // exp(-i t) - 1
+                u[j] = add(u[j], mul(fm1, u[j]));
+            }
+        }
+    } else if constexpr (sizeof(R) == 4) {
         // complex64 state: apply the factor as u + (f - 1) u with f - 1 formed
         // without cancellation, so that rounding the factor cannot bias |u|
         // the same way every step (expm1; cos t - 1 = -2 sin^2(t/2)).
@@ -484,7 +583,9 @@ __device__ __forceinline__ void herm_point(cx<R> (&u)[3], R c2, R Ot, R dt, cons
     R na = nrm(a), nb = nrm(b);
     R C2 = na + nb;
     R s, k;
-    if constexpr (is_f32<R>()) {
+    if constexpr (is_pair<R>()) {
+        herm_coeffs_pair<IMAG>(C2, dt, &s, &k);
+    } else if constexpr (is_f32<R>()) {
         herm_coeffs<IMAG>(C2, dt, &s, &k);
     } else {
         herm_coeffs_dt<IMAG>(C2, *kp, &s, &k);

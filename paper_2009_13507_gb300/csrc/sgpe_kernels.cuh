@@ -283,16 +283,20 @@ __device__ __forceinline__ void pointwise_load(const typename V2<R>::T* __restri
 
 // The pointwise substeps at one loaded grid point; u: the three updated values.
 // ds: the pending scale per component (3 values); mask as for pointwise_point.
-template <typename R, bool IMAG>
+// STD: the full step of a 2D grid (mask 7, SO case 4) known at compile time.
+template <typename R, bool IMAG, bool STD = false>
 __device__ __forceinline__ void pointwise_apply(const PointIn<R>& in, const KParams& p, const R* ds, R Ot, int ix,
-                                                int iy, int mask, cx<R> (&u)[3]) {
+                                                int iy, int mask_rt, cx<R> (&u)[3]) {
+    const int mask = STD ? 7 : mask_rt;
+    const int so_case = STD ? 4 : p.so_case;
+    const int dim = STD ? 2 : p.dim;
     R d[3];
 #pragma unroll
     for (int j = 0; j < 3; j++) d[j] = ds[j];
 #pragma unroll
     for (int j = 0; j < 3; j++) u[j] = scl(d[j], in.u[j]);
     const R dt = kc<R>(p, KC_DT);
-    if ((mask & 1) && p.so_case) {
+    if ((mask & 1) && so_case) {
         R gx[3], gy[3];
         if (p.renorm != 2) {
             // one scale for all components (DJ2, or none): the same products, formed once
@@ -309,17 +313,23 @@ __device__ __forceinline__ void pointwise_apply(const PointIn<R>& in, const KPar
                 gy[j] = kc<R>(p, KC_HY) * d[j];
             }
         }
-        so_point<IMAG>(u, in.X, in.Y, gx, gy, p.so_case);
+        so_point<IMAG>(u, in.X, in.Y, gx, gy, so_case);
     }
     auto calcnu = [&]() {
         // V = wx^2 x^2/2 + wy^2 y^2/2 with x = kx dx: kx^2 is an exact integer
         const int kx = ix - p.nx / 2, ky = iy - p.ny / 2;
-        if constexpr (!is_f32<R>()) {
+        if constexpr (is_pair<R>()) {
+            // the pair's points are (ix, ix + 1)
+            const int kx1 = kx + 1;
+            R V = kc<R>(p, KC_VX) * R((float)(kx * kx), (float)(kx1 * kx1)) +
+                  (dim == 2 ? kc<R>(p, KC_VY) * R((float)(ky * ky)) : R(0));
+            calcnu_point<IMAG>(u, V, kc<R>(p, KC_C0), kc<R>(p, KC_C2), dt);
+        } else if constexpr (!is_f32<R>()) {
             // complex128 / double-float: -dt folded into the coefficients (exponent -dt mu directly)
-            R Vn = kc<R>(p, KC_NVX) * R(kx * kx) + (p.dim == 2 ? kc<R>(p, KC_NVY) * R(ky * ky) : R(0));
+            R Vn = kc<R>(p, KC_NVX) * R(kx * kx) + (dim == 2 ? kc<R>(p, KC_NVY) * R(ky * ky) : R(0));
             calcnu_point_dt<IMAG>(u, Vn, p);
         } else {
-            R V = kc<R>(p, KC_VX) * R(kx * kx) + (p.dim == 2 ? kc<R>(p, KC_VY) * R(ky * ky) : R(0));
+            R V = kc<R>(p, KC_VX) * R(kx * kx) + (dim == 2 ? kc<R>(p, KC_VY) * R(ky * ky) : R(0));
             calcnu_point<IMAG>(u, V, kc<R>(p, KC_C0), kc<R>(p, KC_C2), dt);
         }
     };
@@ -382,7 +392,7 @@ __global__ void __launch_bounds__(128) k_pointwise(const typename V2<R>::T* __re
 // load on each side, the results go out in 16-byte stores; the arithmetic per
 // point is pointwise_apply's, as in k_pointwise. The complex64 pointwise kernel
 // is bound by instruction issue, half of it loads and their index arithmetic.
-template <bool IMAG>
+template <bool IMAG, bool STD>
 __global__ void __launch_bounds__(256) k_pointwise2(const float2* __restrict__ A, float2* __restrict__ B, KParams p,
                                                     const DevScalars* __restrict__ sc,
                                                     const double* __restrict__ omega_tab, int mask) {
@@ -390,62 +400,59 @@ __global__ void __launch_bounds__(256) k_pointwise2(const float2* __restrict__ A
     const int iy = blockIdx.y * blockDim.y + threadIdx.y;
     pdl_wait();
     if (ix >= p.nx || iy >= p.ny) return;
-    const float Ot = omega_tab ? to_r<float>(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440)
-                               : kc<float>(p, KC_OMEGA);
+    float Ot = kc<float>(p, KC_OMEGA);
+    if (omega_tab) Ot = to_r<float>(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440);
     const size_t plane = (size_t)p.nx * p.ny;
     const size_t c = (size_t)iy * p.nx + ix;
     const bool ns = (mask & kMaskNoScale) != 0;
-    const float ds[3] = {ns ? 1.0f : scale_of<float>(sc, 0), ns ? 1.0f : scale_of<float>(sc, 1),
-                         ns ? 1.0f : scale_of<float>(sc, 2)};
-    const bool so = (mask & 1) && p.so_case;
-    const cx<float> zero = {0.0f, 0.0f};
+    const f32x2 ds[3] = {f32x2(ns ? 1.0f : scale_of<float>(sc, 0)), f32x2(ns ? 1.0f : scale_of<float>(sc, 1)),
+                         f32x2(ns ? 1.0f : scale_of<float>(sc, 2))};
+    const bool so = STD || ((mask & 1) && p.so_case);
     const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    PointIn<float> in0, in1;
+    const float2 z2 = make_float2(0.0f, 0.0f);
+    // lane 0 of every pair: point ix, lane 1: point ix + 1
+    PointIn<f32x2> in;
+    float4 v[3];
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(A + j * plane + c));
-        in0.u[j] = {v.x, v.y};
-        in1.u[j] = {v.z, v.w};
-        in0.X[j] = in0.Y[j] = in1.X[j] = in1.Y[j] = zero;
+        v[j] = __ldg(reinterpret_cast<const float4*>(A + j * plane + c));
+        in.u[j] = {f32x2(v[j].x, v[j].z), f32x2(v[j].y, v[j].w)};
+        in.X[j] = in.Y[j] = {f32x2(0.0f), f32x2(0.0f)};
     }
     if (so) {
+        // X = psi(x + 1) - psi(x - 1), Y = psi(y + 1) - psi(y - 1), zero ghosts
+        auto diffs = [&](int j, float2 xm, float2 xp, float4 ym, float4 yp) {
+            in.X[j] = {f32x2(v[j].z, xp.x) - f32x2(xm.x, v[j].x), f32x2(v[j].w, xp.y) - f32x2(xm.y, v[j].y)};
+            in.Y[j] = {f32x2(yp.x, yp.z) - f32x2(ym.x, ym.z), f32x2(yp.y, yp.w) - f32x2(ym.y, ym.w)};
+        };
         // every neighbour inside the grid (2D): loads without the zero ghosts
-        const bool inner = p.dim == 2 && ix > 0 && ix + 2 < p.nx && iy > 0 && iy + 1 < p.ny;
+        const bool inner = (STD || p.dim == 2) && ix > 0 && ix + 2 < p.nx && iy > 0 && iy + 1 < p.ny;
         if (inner) {
 #pragma unroll
             for (int j = 0; j < 3; j++) {
                 const float2* a = A + j * plane + c;
-                const cx<float> xm = unpack(__ldg(a - 1)), xp = unpack(__ldg(a + 2));
-                in0.X[j] = sub(in1.u[j], xm);
-                in1.X[j] = sub(xp, in0.u[j]);
-                const float4 ym = __ldg(reinterpret_cast<const float4*>(a - p.nx));
-                const float4 yp = __ldg(reinterpret_cast<const float4*>(a + p.nx));
-                in0.Y[j] = sub(cx<float>{yp.x, yp.y}, cx<float>{ym.x, ym.y});
-                in1.Y[j] = sub(cx<float>{yp.z, yp.w}, cx<float>{ym.z, ym.w});
+                diffs(j, __ldg(a - 1), __ldg(a + 2), __ldg(reinterpret_cast<const float4*>(a - p.nx)),
+                      __ldg(reinterpret_cast<const float4*>(a + p.nx)));
             }
         } else {
+            const bool two = STD || p.dim == 2;
 #pragma unroll
             for (int j = 0; j < 3; j++) {
-                const cx<float> xm = ix > 0 ? ld<float>(A, j * plane + c - 1) : zero;
-                const cx<float> xp = ix + 2 < p.nx ? ld<float>(A, j * plane + c + 2) : zero;
-                in0.X[j] = sub(in1.u[j], xm);
-                in1.X[j] = sub(xp, in0.u[j]);
-                if (p.dim == 2) {
-                    const float4 ym = iy > 0 ? __ldg(reinterpret_cast<const float4*>(A + j * plane + c - p.nx)) : z4;
-                    const float4 yp =
-                        iy + 1 < p.ny ? __ldg(reinterpret_cast<const float4*>(A + j * plane + c + p.nx)) : z4;
-                    in0.Y[j] = sub(cx<float>{yp.x, yp.y}, cx<float>{ym.x, ym.y});
-                    in1.Y[j] = sub(cx<float>{yp.z, yp.w}, cx<float>{ym.z, ym.w});
-                }
+                const float2* a = A + j * plane + c;
+                const float2 xm = ix > 0 ? __ldg(a - 1) : z2;
+                const float2 xp = ix + 2 < p.nx ? __ldg(a + 2) : z2;
+                const float4 ym = two && iy > 0 ? __ldg(reinterpret_cast<const float4*>(a - p.nx)) : z4;
+                const float4 yp = two && iy + 1 < p.ny ? __ldg(reinterpret_cast<const float4*>(a + p.nx)) : z4;
+                diffs(j, xm, xp, ym, yp);
             }
         }
     }
-    cx<float> u0[3], u1[3];
-    pointwise_apply<float, IMAG>(in0, p, ds, Ot, ix, iy, mask, u0);
-    pointwise_apply<float, IMAG>(in1, p, ds, Ot, ix + 1, iy, mask, u1);
+    cx<f32x2> u[3];
+    pointwise_apply<f32x2, IMAG, STD>(in, p, ds, f32x2(Ot), ix, iy, mask, u);
+    pdl_trigger();  // the next kernel's blocks may take the slots this grid frees
 #pragma unroll
     for (int j = 0; j < 3; j++)
-        *reinterpret_cast<float4*>(B + j * plane + c) = make_float4(u0[j].re, u0[j].im, u1[j].re, u1[j].im);
+        *reinterpret_cast<float4*>(B + j * plane + c) = make_float4(u[j].re.v.x, u[j].im.v.x, u[j].re.v.y, u[j].im.v.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -616,8 +623,10 @@ static __global__ void __launch_bounds__(96 * kFinWarps) k_finalize_wide(const d
     __shared__ df red_df[3][kFinWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = warp / kFinWarps, sub = warp % kFinWarps;
-    pdl_trigger();
+    // the y sweep lets this block become resident early; the next step's first
+    // kernel launches once the sweep is done
     pdl_wait();
+    pdl_trigger();
     if (part_df) {
         const df s = sum_partials_wide(reinterpret_cast<const df*>(partials) + (size_t)j * m, m, sub);
         if (lane == 0) red_df[j][sub] = s;

@@ -274,12 +274,15 @@ cudaError_t Launcher<R>::pointwise(cudaStream_t s, bool imag, const void* A, voi
             // loaded by the block itself (L1 hits; measured faster than 32 x 2 and 32 x 4)
             const dim3 block2(32, p.dim == 2 ? 8 : 1);
             const dim3 grid2(ceil_div(p.nx, 64), p.dim == 2 ? ceil_div(p.ny, 8) : 1);
-            if (imag)
-                launch_pdl(k_pointwise2<true>, grid2, block2, 0, s, (const float2*)A, (float2*)B, q, sc, omega_tab,
-                           mask);
+            // the full step of a 2D grid with SO as its own instantiation (no runtime case tests)
+            const bool std2d = mask == 7 && p.dim == 2 && q.so_case == 4;
+            auto go = [&](auto kern) {
+                launch_pdl(kern, grid2, block2, 0, s, (const float2*)A, (float2*)B, q, sc, omega_tab, mask);
+            };
+            if (std2d)
+                imag ? go(k_pointwise2<true, true>) : go(k_pointwise2<false, true>);
             else
-                launch_pdl(k_pointwise2<false>, grid2, block2, 0, s, (const float2*)A, (float2*)B, q, sc, omega_tab,
-                           mask);
+                imag ? go(k_pointwise2<true, false>) : go(k_pointwise2<false, false>);
             return cudaGetLastError();
         }
     }
@@ -325,7 +328,7 @@ cudaError_t Launcher<R>::cn_x(cudaStream_t s, bool imag, bool last, const void* 
     }
     const dim3 block(32 * g.wx), grid(g.blocks_x);
     double* part = last ? partials : nullptr;
-    auto go = [&](auto kern) { kern<<<grid, block, g.smem_x, s>>>((const T*)in, (T*)out, p, t, part); };
+    auto go = [&](auto kern) { launch_pdl(kern, grid, block, g.smem_x, s, (const T*)in, (T*)out, p, t, part); };
     if (kUniForm<R> && t.uks > 0) {
         if constexpr (kUniForm<R>) imag ? go(k_cn_x<R, true, true>) : go(k_cn_x<R, false, true>);
     } else {
@@ -354,7 +357,7 @@ cudaError_t Launcher<R>::cn_y(cudaStream_t s, bool imag, const void* in, void* o
             const int hc = tabs.u.hc;
             const dim3 tb(32 * (kTileReal + 2 * hc)), tg(g.blocks_yt);
             const size_t sm = (size_t)(kTileReal + 2 * hc) * kLongC * 32 * sizeof(cx<R>);
-            auto go = [&](auto kern) { kern<<<tg, tb, sm, s>>>((const T*)in, (T*)out, p, t, part); };
+            auto go = [&](auto kern) { launch_pdl(kern, tg, tb, sm, s, (const T*)in, (T*)out, p, t, part); };
             if (hc == 1)
                 imag ? go(k_cn_y_tile<R, true, 1>) : go(k_cn_y_tile<R, false, 1>);
             else
