@@ -229,7 +229,9 @@ sgpe_status sgpe_substep(sgpe_ctx* ctx, int which, int imag, double omega);
  * with lines of at most 1024 points kind 0 is the fused kernel (pending scale,
  * pointwise substeps and the x sweep), kind 1 has no launches, and the end of
  * step runs inside kinds 0 and 2 (kind 3 has no launches; one untimed
- * end-of-steps launch follows the last step).
+ * end-of-steps launch follows the last step). On complex64 2D grids with even
+ * rows of 1025..2048 points kind 0 is the fused pointwise + x-sweep kernel too
+ * and kind 1 has no launches.
  * Advances the state exactly like the step functions. Synchronises the stream.
  */
 sgpe_status sgpe_profile_steps(sgpe_ctx* ctx, int nsteps, int imag, double* ms_out, int* launches_out);

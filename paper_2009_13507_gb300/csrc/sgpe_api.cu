@@ -527,11 +527,18 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
         return finalize_step(c->stream, c->partials, y_parts(c->geo, c->tabs[mode][1], c->mid, c->psi), c->kp.cell,
                              renorm, c->kp.mag, 1, c->sc, parts_df(c));
     }
-    if ((e = Launcher<R>::pointwise(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, 7))) return e;
-    if (c->dim == 2) {
-        if ((e = Launcher<R>::cn_x(c->stream, imag, false, c->mid, c->mid, c->kp, c->tabs[mode][0], c->geo,
-                                   c->partials, c->sc, renorm, 1)))
+    if (pwx_long_fits(c->geo, c->tabs[mode][0])) {
+        // complex64 rows of 1025..2048 points: pointwise substeps and x sweep in one kernel
+        if ((e = Launcher<R>::pwx_long(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, c->tabs[mode][0],
+                                       7)))
             return e;
+    } else {
+        if ((e = Launcher<R>::pointwise(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, 7))) return e;
+        if (c->dim == 2 && (e = Launcher<R>::cn_x(c->stream, imag, false, c->mid, c->mid, c->kp, c->tabs[mode][0],
+                                                  c->geo, c->partials, c->sc, renorm, 1)))
+            return e;
+    }
+    if (c->dim == 2) {
         if ((e = Launcher<R>::cn_y(c->stream, imag, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials,
                                    c->sc, renorm, 1, 1)))
             return e;
@@ -829,6 +836,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
     int cnt[4] = {0, 0, 0, 0};
     const bool two = c->dim == 2;
     const bool fused = c->geo.fused;
+    const bool long_fused = !general_path(c) && pwx_long_fits(c->geo, c->tabs[mode][0]);
     const bool head = head_scale(c);
     sgpe_status out = SGPE_OK;
     for (int i0 = 0; i0 < nsteps && out == SGPE_OK; i0 += kBatch) {
@@ -842,13 +850,18 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
                 return Launcher<decltype(r)>::pwx(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr,
                                                   c->tabs[mode][0].t, c->partials, c->geo.blocks_y / 3, renorm);
             });
-        if (!e && !fused)
+        if (!e && long_fused)
+            e = with_prec(c->prec, [&](auto r) {
+                return Launcher<decltype(r)>::pwx_long(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr,
+                                                       c->tabs[mode][0], 7);
+            });
+        if (!e && !fused && !long_fused)
             e = with_prec(c->prec, [&](auto r) {
                 return Launcher<decltype(r)>::pointwise(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr, 7);
             });
         if (!e) e = cudaEventRecord(ev[1], c->stream);
         void* xout = two ? c->mid : c->psi;
-        if (!e && !fused)
+        if (!e && !fused && !long_fused)
             e = with_prec(c->prec, [&](auto r) {
                 return Launcher<decltype(r)>::cn_x(c->stream, im, !two, c->mid, xout, c->kp, c->tabs[mode][0], c->geo,
                                                    c->partials, c->sc, renorm, 1);
@@ -873,7 +886,7 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
       }
       for (int bi = 0; bi < nb; bi++)
           for (int k = 0; k < 4; k++) {
-              if ((k == 2 && !two) || (k == 1 && fused) || (k == 3 && head)) continue;
+              if ((k == 2 && !two) || (k == 1 && (fused || long_fused)) || (k == 3 && head)) continue;
               float ms = 0.f;
               cudaEventElapsedTime(&ms, evs[bi][k], evs[bi][k + 1]);
               acc[k] += ms;

@@ -1063,6 +1063,56 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps, long_min_blocks<R, UNI>())
     }
 }
 
+// Pointwise substeps and CN along x of one row of a 2D complex64 grid with
+// 1025..2048 points (nx even; the constant-factor solve, Tabs::uks > 0): one
+// block per row, 3 groups of nwl = ceil(nx / 512) warps (one group per
+// component line). The threads evaluate the row's point pairs (pair_substeps)
+// into the padded chunk layout of the three lines in shared memory (slots past
+// nx zero), then group j solves line j (long_line_uni) and the block stores the
+// three lines to B. Each step then streams the state twice (A -> B here, B -> A
+// in the y sweep) instead of three times.
+constexpr int kPwxLongMaxGroupWarps = 4;
+template <bool IMAG, bool STD>
+__global__ void __launch_bounds__(96 * kPwxLongMaxGroupWarps, 2)
+    k_pwx_long(const float2* __restrict__ A, float2* __restrict__ B, KParams p, const DevScalars* __restrict__ sc,
+               const double* __restrict__ omega_tab, Tabs<float> t, int mask) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<float>* lines = reinterpret_cast<cx<float>*>(smem_raw);  // [3][32 nwl kLongS]
+    __shared__ cx<float> seg[3][4 * kPwxLongMaxGroupWarps];
+    const int nwl = blockDim.x / 96;
+    const int warp = threadIdx.x >> 5;
+    const int nx = p.nx, iy = blockIdx.x;
+    const int span = 32 * kLongC * nwl, S = 32 * nwl * kLongS;
+    pdl_wait();
+    f32x2 ds[3];
+    float Ot;
+    pair_constants(p, sc, omega_tab, mask, ds, Ot);
+    for (int q = threadIdx.x; 2 * q < nx; q += blockDim.x) {
+        cx<f32x2> u[3];
+        pair_substeps<IMAG, STD>(A, p, ds, Ot, mask, 2 * q, iy, u);
+        const int s0 = long_slot(2 * q);  // 2q is even: 2q + 1 sits in the next slot of the same chunk
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            lines[j * S + s0] = cx<float>{u[j].re.v.x, u[j].im.v.x};
+            lines[j * S + s0 + 1] = cx<float>{u[j].re.v.y, u[j].im.v.y};
+        }
+    }
+    for (int i = nx + threadIdx.x; i < span; i += blockDim.x)
+#pragma unroll
+        for (int j = 0; j < 3; j++) lines[j * S + long_slot(i)] = cx<float>{0.0f, 0.0f};
+    __syncthreads();
+    const int j = warp / nwl;
+    long_line_uni<float, IMAG>(lines + j * S, nx, t, warp - j * nwl, nwl, seg[j], false);
+    pdl_trigger();  // the y sweep's blocks may take the slots this grid frees
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float2* dst = B + ((size_t)c * p.ny + iy) * nx;
+        const cx<float>* src = lines + c * S;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) dst[i] = make_float2(src[long_slot(i)].re, src[long_slot(i)].im);
+    }
+}
+
 // CN along y for columns of 1025..8192 points: one block per tile of kc (1, 2
 // or 4) adjacent columns [col0, col0 + kc) of component j, staged in shared memory (row
 // segments of kc elements), nw warps per column. With part non-null the block

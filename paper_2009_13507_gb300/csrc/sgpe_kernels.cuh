@@ -392,25 +392,18 @@ __global__ void __launch_bounds__(128) k_pointwise(const typename V2<R>::T* __re
 // load on each side, the results go out in 16-byte stores; the arithmetic per
 // point is pointwise_apply's, as in k_pointwise. The complex64 pointwise kernel
 // is bound by instruction issue, half of it loads and their index arithmetic.
+// The pointwise substeps of the two neighbouring points (ix, ix + 1) of row iy
+// (complex64, nx even) as one f32x2 pair (lane 0: ix, lane 1: ix + 1): the
+// 16-byte loads of each component's pair, the x and y neighbours (zero ghosts;
+// inner points without the selects), then pointwise_apply.
 template <bool IMAG, bool STD>
-__global__ void __launch_bounds__(256) k_pointwise2(const float2* __restrict__ A, float2* __restrict__ B, KParams p,
-                                                    const DevScalars* __restrict__ sc,
-                                                    const double* __restrict__ omega_tab, int mask) {
-    const int ix = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
-    pdl_wait();
-    if (ix >= p.nx || iy >= p.ny) return;
-    float Ot = kc<float>(p, KC_OMEGA);
-    if (omega_tab) Ot = to_r<float>(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440);
+__device__ __forceinline__ void pair_substeps(const float2* __restrict__ A, const KParams& p, const f32x2 (&ds)[3],
+                                              float Ot, int mask, int ix, int iy, cx<f32x2> (&u)[3]) {
     const size_t plane = (size_t)p.nx * p.ny;
     const size_t c = (size_t)iy * p.nx + ix;
-    const bool ns = (mask & kMaskNoScale) != 0;
-    const f32x2 ds[3] = {f32x2(ns ? 1.0f : scale_of<float>(sc, 0)), f32x2(ns ? 1.0f : scale_of<float>(sc, 1)),
-                         f32x2(ns ? 1.0f : scale_of<float>(sc, 2))};
     const bool so = STD || ((mask & 1) && p.so_case);
     const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     const float2 z2 = make_float2(0.0f, 0.0f);
-    // lane 0 of every pair: point ix, lane 1: point ix + 1
     PointIn<f32x2> in;
     float4 v[3];
 #pragma unroll
@@ -447,9 +440,35 @@ __global__ void __launch_bounds__(256) k_pointwise2(const float2* __restrict__ A
             }
         }
     }
-    cx<f32x2> u[3];
     pointwise_apply<f32x2, IMAG, STD>(in, p, ds, f32x2(Ot), ix, iy, mask, u);
+}
+
+// The pending scale (complex64 copy) and the Rabi coupling of this step for the pair kernels.
+__device__ __forceinline__ void pair_constants(const KParams& p, const DevScalars* sc, const double* omega_tab, int mask,
+                                               f32x2 (&ds)[3], float& Ot) {
+    Ot = kc<float>(p, KC_OMEGA);
+    if (omega_tab) Ot = to_r<float>(__ldg(omega_tab + sc->step_idx) * 0.70710678118654752440);
+    const bool ns = (mask & kMaskNoScale) != 0;
+#pragma unroll
+    for (int j = 0; j < 3; j++) ds[j] = f32x2(ns ? 1.0f : scale_of<float>(sc, j));
+}
+
+template <bool IMAG, bool STD>
+__global__ void __launch_bounds__(256) k_pointwise2(const float2* __restrict__ A, float2* __restrict__ B, KParams p,
+                                                    const DevScalars* __restrict__ sc,
+                                                    const double* __restrict__ omega_tab, int mask) {
+    const int ix = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    pdl_wait();
+    if (ix >= p.nx || iy >= p.ny) return;
+    f32x2 ds[3];
+    float Ot;
+    pair_constants(p, sc, omega_tab, mask, ds, Ot);
+    cx<f32x2> u[3];
+    pair_substeps<IMAG, STD>(A, p, ds, Ot, mask, ix, iy, u);
     pdl_trigger();  // the next kernel's blocks may take the slots this grid frees
+    const size_t plane = (size_t)p.nx * p.ny;
+    const size_t c = (size_t)iy * p.nx + ix;
 #pragma unroll
     for (int j = 0; j < 3; j++)
         *reinterpret_cast<float4*>(B + j * plane + c) = make_float4(u[j].re.v.x, u[j].im.v.x, u[j].re.v.y, u[j].im.v.y);

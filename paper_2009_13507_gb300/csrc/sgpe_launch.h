@@ -117,6 +117,12 @@ inline bool y_tiled(const Geometry& g, const TabSet& ty, const void* in, const v
 inline int y_parts(const Geometry& g, const TabSet& ty, const void* in, const void* out) {
     return y_tiled(g, ty, in, out) ? g.blocks_yt : g.blocks_y;
 }
+// Whether the 2D step of a complex64 grid runs its pointwise substeps and x sweep
+// in one kernel on rows longer than kRegMaxN (k_pwx_long: even rows of at most
+// 2048 points, the constant-factor x solve).
+inline bool pwx_long_fits(const Geometry& g, const TabSet& tx) {
+    return g.dim == 2 && g.esz == 8 && !g.reg_x && g.nx % 2 == 0 && long_warps(g.nx) <= 4 && tx.u.ks > 0;
+}
 // Longest start correction of the constant-factor form (entries of s).
 constexpr int kUniMaxS = 512;
 
@@ -146,6 +152,10 @@ template <typename R> struct Launcher {
     static cudaError_t cn_y(cudaStream_t s, bool imag, const void* in, void* out, const KParams& p,
                             const TabSet& tabs, const Geometry& g, double* partials, DevScalars* sc, int renorm,
                             int advance, int finalize, bool head_scale = false);
+    // Fused pointwise substeps + CN along x of a 2D complex64 grid with rows of
+    // 1025..2048 points (pwx_long_fits): A -> B.
+    static cudaError_t pwx_long(cudaStream_t s, bool imag, const void* A, void* B, const KParams& p,
+                                const DevScalars* sc, const double* omega_tab, const TabSet& tabs_x, int mask);
     static cudaError_t coef(cudaStream_t s, void* fa, void* fg, void* fp, void* fq, int n, double bre, double bim);
     // The constant-factor form of an n-point line with bt = bre + i bim (n > kRegMaxN):
     // fills u and copies s to s_dev (kUniMaxS entries of room); u->ks = 0 where the

@@ -238,6 +238,12 @@ template <typename R> cudaError_t Launcher<R>::setup() {
         if ((e = allow_smem(k_cn_x<R, false, true>))) return e;
         if ((e = allow_smem(k_cn_y<R, true, true>))) return e;
         if ((e = allow_smem(k_cn_y<R, false, true>))) return e;
+        if constexpr (std::is_same<R, float>::value) {
+            if ((e = allow_smem(k_pwx_long<true, true>))) return e;
+            if ((e = allow_smem(k_pwx_long<false, true>))) return e;
+            if ((e = allow_smem(k_pwx_long<true, false>))) return e;
+            if ((e = allow_smem(k_pwx_long<false, false>))) return e;
+        }
         if ((e = allow_smem(k_cn_y_tile<R, true, 1>))) return e;
         if ((e = allow_smem(k_cn_y_tile<R, false, 1>))) return e;
         if ((e = allow_smem(k_cn_y_tile<R, true, 2>))) return e;
@@ -313,6 +319,32 @@ cudaError_t Launcher<R>::pwx(cudaStream_t s, bool imag, const void* A, void* B, 
         default: pwx_c<R, 32>(imag, p.ny, s, a, b, q, sc, omega_tab, t, partials, m, renorm); break;
     }
     return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launcher<R>::pwx_long(cudaStream_t s, bool imag, const void* A, void* B, const KParams& p,
+                                  const DevScalars* sc, const double* omega_tab, const TabSet& tabs_x, int mask) {
+    if constexpr (!std::is_same<R, float>::value) {
+        return cudaErrorNotSupported;
+    } else {
+        const int nwl = long_warps(p.nx);
+        if (p.dim != 2 || p.nx <= kRegMaxN || p.nx % 2 || nwl > kPwxLongMaxGroupWarps || tabs_x.u.ks <= 0)
+            return cudaErrorInvalidValue;
+        const Tabs<float> t = make_tabs<float>(tabs_x);
+        KParams q = p;
+        fill_derived(q);
+        const size_t smem = (size_t)3 * 32 * nwl * kLongS * sizeof(cx<float>);
+        const bool std2d = mask == 7 && q.so_case == 4;
+        auto go = [&](auto kern) {
+            launch_pdl(kern, dim3(p.ny), dim3(96 * nwl), smem, s, (const float2*)A, (float2*)B, q, sc, omega_tab, t,
+                       mask);
+        };
+        if (std2d)
+            imag ? go(k_pwx_long<true, true>) : go(k_pwx_long<false, true>);
+        else
+            imag ? go(k_pwx_long<true, false>) : go(k_pwx_long<false, false>);
+        return cudaGetLastError();
+    }
 }
 
 template <typename R>

@@ -280,6 +280,27 @@ def test_precision_form_max_line(nx, ny):
 
 
 @pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("nx,ny", [(1026, 5), (1500, 6), (2048, 4), (1501, 5)])
+def test_precision_form_fused_long_rows(nx, ny, imag):
+    """complex64 rows of 1025..2048 points, even: the pointwise substeps and the x
+    sweep in one kernel (three warp groups of 3 or 4 warps, point pairs on FP32x2,
+    slots past the row's end zero); 1501 points (odd) take the separate kernels.
+    Full steps with the observables against the oracle, then the per-kernel
+    profile, which must advance the state exactly as the step does."""
+    prob, s = make_pair(2, nx, ny, dx=0.02, precision="c64", **PHYS_2D)
+    psi = _rand(prob, nx + 7 * ny, env=2.0)
+    s.set_state(psi)
+    (s.step_imag(3) if imag else s.step_real(3))
+    ref = O.step(prob, psi, 3, imag)
+    got = s.get_state()
+    assert relerr(got, ref) < 1e-5
+    assert obs_relerr(s.energy(), O.observables(prob, ref)) < 1e-5
+    s.set_state(psi)
+    s.profile_steps(3, imag=imag)
+    assert relerr(s.get_state(), got) < 1e-6
+
+
+@pytest.mark.parametrize("imag", [True, False])
 @pytest.mark.parametrize("nx,ny", [(9, 2048), (13, 1500), (8, 4100), (5, 2300)])
 def test_precision_form_long_columns(nx, ny, imag):
     """complex64 columns longer than 1024 points: the y sweep's tiles of up to 4
