@@ -280,11 +280,12 @@ def test_precision_form_max_line(nx, ny):
 
 
 @pytest.mark.parametrize("imag", [True, False])
-@pytest.mark.parametrize("nx,ny", [(1026, 5), (1500, 6), (2048, 4), (1501, 5)])
+@pytest.mark.parametrize("nx,ny", [(1026, 5), (1500, 6), (2048, 4), (3000, 3), (4096, 3), (1501, 5)])
 def test_precision_form_fused_long_rows(nx, ny, imag):
     """complex64 rows of 1025..2048 points, even: the pointwise substeps and the x
     sweep in one kernel (three warp groups of 3 or 4 warps, point pairs on FP32x2,
-    slots past the row's end zero); 1501 points (odd) take the separate kernels.
+    slots past the row's end zero); 1501 points (odd), 3000 and 4096 take the
+    separate kernels.
     Full steps with the observables against the oracle, then the per-kernel
     profile, which must advance the state exactly as the step does."""
     prob, s = make_pair(2, nx, ny, dx=0.02, precision="c64", **PHYS_2D)
