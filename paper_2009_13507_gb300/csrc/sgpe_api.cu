@@ -45,7 +45,8 @@ Geometry make_geometry(int dim, int nx, int ny, int esz) {
     g.wy = g.reg_y ? 1 : wy;
     g.smem_y = g.reg_y ? 0 : (size_t)g.wy * (32 * nwy * (kLongC + 1) + long_col_pad(esz, g.wy)) * esz;
     g.blocks_y = dim == 2 ? 3 * ceil_div(nx, g.reg_y ? cny_cols_per_warp(chunk_len(ny), esz) : g.wy) : 0;
-    g.blocks_yt = dim == 2 && !g.reg_y ? 3 * ceil_div(nx, 32) * ceil_div(ny, kTileRows) : 0;
+    g.tiled = dim == 2 && esz == 8 && nx % 2 == 0 && nx >= kMidMinN && ny >= kMidMinN && g.reg_x && g.reg_y;
+    g.blocks_yt = dim == 2 && (!g.reg_y || g.tiled) ? 3 * ceil_div(nx, 32) * ceil_div(ny, kTileRows) : 0;
     g.blocks_obs = ceil_div(nx, 32) * ceil_div(ny, 4);
     g.blocks_norm = kNormBlocks;
     return g;
@@ -149,7 +150,7 @@ static Layout layout_of(const sgpe_ctx* c) {
                 off = align256(off + (size_t)table_len(n) * c->esz);
             }
             L.us[m][a] = off;
-            off = align256(off + (size_t)(n > kRegMaxN ? kUniMaxS : 1) * c->esz);
+            off = align256(off + (size_t)(n > kRegMaxN || c->geo.tiled ? kUniMaxS : 1) * c->esz);
         }
     for (int m = 0; m < 2; m++)
         for (int a = 0; a < 2; a++) {
@@ -409,9 +410,10 @@ sgpe_status sgpe_set_params(sgpe_ctx* c, const sgpe_params* p) {
                 return Launcher<decltype(r)>::coef(c->stream, t[0], t[1], t[2], t[3], n, bre, bim);
             });
             CK(e, "COEF kernel");
-            // lines longer than kRegMaxN: the constant-factor form of the same solve
+            // lines longer than kRegMaxN (and the lines of a tiled grid): the constant-factor
+            // form of the same solve
             c->tabs[m][a].u = UniHost{};
-            if (n > kRegMaxN) {
+            if (n > kRegMaxN || c->geo.tiled) {
                 e = with_prec(c->prec, [&](auto r) {
                     return Launcher<decltype(r)>::uni(c->stream, n, bre, bim, c->us[m][a], &c->tabs[m][a].u);
                 });
@@ -434,7 +436,13 @@ sgpe_status sgpe_set_params(sgpe_ctx* c, const sgpe_params* p) {
 // enqueue_step_general.
 static bool general_path(const sgpe_ctx* c) { return c->params.split != 0 || c->params.so_mode != 0; }
 
-static bool head_scale(const sgpe_ctx* c) { return c->geo.fused && c->geo.reg_y && !general_path(c); }
+// A tiled grid's step in the given time mode (0 imaginary, 1 real) on the kernels of long lines.
+static bool tiled_mode(const sgpe_ctx* c, int mode) {
+    return c->geo.tiled && !general_path(c) && tiled_step(c->geo, c->tabs[mode][0], c->tabs[mode][1]);
+}
+static bool head_scale(const sgpe_ctx* c, int mode) {
+    return c->geo.fused && c->geo.reg_y && !general_path(c) && !tiled_mode(c, mode);
+}
 
 // The y sweeps (2D) and the long x sweep (1D) of the complex64 and double-float
 // forms leave their norm partials as double-float pairs (summed on the FP32
@@ -442,7 +450,7 @@ static bool head_scale(const sgpe_ctx* c) { return c->geo.fused && c->geo.reg_y 
 static int parts_df(const sgpe_ctx* c) { return c->prec != SGPE_C128 && (c->dim == 2 || !c->geo.reg_x); }
 
 static cudaError_t end_steps(sgpe_ctx* c, bool imag) {
-    if (!head_scale(c)) return cudaSuccess;
+    if (!head_scale(c, imag ? 0 : 1)) return cudaSuccess;
     const int renorm = imag ? c->params.renorm : 0;
     return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 0, c->sc,
                          parts_df(c));
@@ -515,11 +523,11 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
     const int mode = imag ? 0 : 1;
     const int renorm = imag ? c->params.renorm : 0;
     if (general_path(c)) return enqueue_step_general<R>(c, imag, omega_tab);
-    if (c->geo.fused) {
+    if (c->geo.fused && !tiled_mode(c, mode)) {
         if ((e = Launcher<R>::pwx(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, c->tabs[mode][0].t,
                                   c->partials, c->geo.blocks_y / 3, renorm)))
             return e;
-        const bool head = head_scale(c);
+        const bool head = head_scale(c, mode);
         if ((e = Launcher<R>::cn_y(c->stream, imag, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials,
                                    c->sc, renorm, 1, 1, head)))
             return e;
@@ -835,9 +843,9 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
     double acc[4] = {0, 0, 0, 0};
     int cnt[4] = {0, 0, 0, 0};
     const bool two = c->dim == 2;
-    const bool fused = c->geo.fused;
-    const bool long_fused = !general_path(c) && pwx_long_fits(c->geo, c->tabs[mode][0]);
-    const bool head = head_scale(c);
+    const bool fused = c->geo.fused && !tiled_mode(c, mode);
+    const bool long_fused = !general_path(c) && !fused && pwx_long_fits(c->geo, c->tabs[mode][0]);
+    const bool head = head_scale(c, mode);
     sgpe_status out = SGPE_OK;
     for (int i0 = 0; i0 < nsteps && out == SGPE_OK; i0 += kBatch) {
       const int nb = nsteps - i0 < kBatch ? nsteps - i0 : kBatch;
@@ -911,8 +919,9 @@ int sgpe_launches_per_step(const sgpe_ctx* c) {
         return so + 1 + sweeps + (c->params.split ? 1 + (so ? so : 1) : 0) + 1;
     }
     if (one_block_1d(c)) return 0;  // one launch per step call
-    if (head_scale(c)) return 2;  // plus one end-of-steps launch per step call
-    if (c->geo.fused) return 3;
+    if (head_scale(c, 0)) return 2;  // plus one end-of-steps launch per step call
+    if (c->geo.fused && !tiled_mode(c, 0)) return 3;
+    if (c->dim == 2 && pwx_long_fits(c->geo, c->tabs[0][0])) return 3;
     return c->dim == 2 ? 4 : 3;
 }
 

@@ -86,8 +86,13 @@ struct Geometry {
     bool fused;         // 2D with register x lines: pointwise + CN-x in one kernel
     size_t smem_x, smem_y;
     int blocks_x, blocks_y, blocks_obs, blocks_norm;
-    int blocks_yt;  // long columns: blocks (= norm partials) of the row-tiled y sweep
+    int blocks_yt;  // long columns (and tiled grids): blocks (= norm partials) of the row-tiled y sweep
+    bool tiled;     // complex64 2D grid of kMidMinN..kRegMaxN points an axis, even rows: its steps may take the
+                    // kernels of long lines (fused pointwise + x sweep, row-tiled y sweep) when the
+                    // constant-factor form applies
 };
+// Shortest axis of a grid that the tiled step serves.
+constexpr int kMidMinN = 384;
 
 Geometry make_geometry(int dim, int nx, int ny, int esz);
 
@@ -111,17 +116,23 @@ struct TabSet {
 // Whether the y sweep of these tables runs in row tiles (k_cn_y_tile: long
 // columns, the constant-factor form with a short carry reach, in != out).
 inline bool y_tiled(const Geometry& g, const TabSet& ty, const void* in, const void* out) {
-    return g.dim == 2 && !g.reg_y && ty.u.ks > 0 && ty.u.hc > 0 && in != out;
+    return g.dim == 2 && (!g.reg_y || g.tiled) && ty.u.ks > 0 && ty.u.hc > 0 && in != out;
 }
 // Norm partials that the step's y sweep (in -> out) leaves.
 inline int y_parts(const Geometry& g, const TabSet& ty, const void* in, const void* out) {
     return y_tiled(g, ty, in, out) ? g.blocks_yt : g.blocks_y;
 }
 // Whether the 2D step of a complex64 grid runs its pointwise substeps and x sweep
-// in one kernel on rows longer than kRegMaxN (k_pwx_long: even rows of at most
-// 2048 points, the constant-factor x solve).
+// in one kernel (k_pwx_long: even rows longer than kRegMaxN and of at most 2048
+// points, or the rows of a tiled grid; the constant-factor x solve).
 inline bool pwx_long_fits(const Geometry& g, const TabSet& tx) {
-    return g.dim == 2 && g.esz == 8 && !g.reg_x && g.nx % 2 == 0 && long_warps(g.nx) <= 4 && tx.u.ks > 0;
+    return g.dim == 2 && g.esz == 8 && (!g.reg_x || g.tiled) && g.nx % 2 == 0 && long_warps(g.nx) <= 4 &&
+           tx.u.ks > 0;
+}
+// A step of a tiled grid (Geometry::tiled) on the kernels of long lines: both axes
+// in the constant-factor form (x: pwx_long_fits; y: the row tiles reach).
+inline bool tiled_step(const Geometry& g, const TabSet& tx, const TabSet& ty) {
+    return g.tiled && pwx_long_fits(g, tx) && ty.u.ks > 0 && ty.u.hc > 0;
 }
 // Longest start correction of the constant-factor form (entries of s).
 constexpr int kUniMaxS = 512;

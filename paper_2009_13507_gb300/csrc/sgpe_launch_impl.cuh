@@ -328,7 +328,7 @@ cudaError_t Launcher<R>::pwx_long(cudaStream_t s, bool imag, const void* A, void
         return cudaErrorNotSupported;
     } else {
         const int nwl = long_warps(p.nx);
-        if (p.dim != 2 || p.nx <= kRegMaxN || p.nx % 2 || nwl > kPwxLongMaxGroupWarps || tabs_x.u.ks <= 0)
+        if (p.dim != 2 || p.nx % 2 || nwl > kPwxLongMaxGroupWarps || tabs_x.u.ks <= 0)
             return cudaErrorInvalidValue;
         const Tabs<float> t = make_tabs<float>(tabs_x);
         KParams q = p;
@@ -375,14 +375,6 @@ cudaError_t Launcher<R>::cn_y(cudaStream_t s, bool imag, const void* in, void* o
                               int renorm, int advance, int finalize, bool head_scale) {
     using T = typename V2<R>::T;
     Tabs<R> t = make_tabs<R>(tabs);
-    if (g.reg_y) {
-        launch_cny_reg<R>(chunk_len(p.ny), imag, dim3(g.blocks_y), s, (const T*)in, (T*)out, p, t,
-                          finalize ? partials : nullptr, head_scale ? sc : nullptr, renorm, advance);
-        return cudaGetLastError();
-    }
-    // tiles of 1, 2 or 4 columns within the block limit (the kernel splits its staging
-    // index by shift and mask)
-    if ((g.wy & (g.wy - 1)) || g.wy > 4 || g.wy * long_warps(p.ny) > kLongMaxWarps) return cudaErrorInvalidValue;
     double* part = finalize ? partials : nullptr;
     if (y_tiled(g, tabs, in, out)) {
         if constexpr (kUniForm<R>) {
@@ -397,6 +389,14 @@ cudaError_t Launcher<R>::cn_y(cudaStream_t s, bool imag, const void* in, void* o
             return cudaGetLastError();
         }
     }
+    if (g.reg_y) {
+        launch_cny_reg<R>(chunk_len(p.ny), imag, dim3(g.blocks_y), s, (const T*)in, (T*)out, p, t,
+                          finalize ? partials : nullptr, head_scale ? sc : nullptr, renorm, advance);
+        return cudaGetLastError();
+    }
+    // tiles of 1, 2 or 4 columns within the block limit (the kernel splits its staging
+    // index by shift and mask)
+    if ((g.wy & (g.wy - 1)) || g.wy > 4 || g.wy * long_warps(p.ny) > kLongMaxWarps) return cudaErrorInvalidValue;
     const dim3 block(32 * g.wy * long_warps(p.ny)), grid(g.blocks_y);
     const bool uni = kUniForm<R> && t.uks > 0;
     auto go = [&](auto kern) { kern<<<grid, block, g.smem_y, s>>>((const T*)in, (T*)out, p, t, g.wy, part); };
@@ -428,7 +428,7 @@ cudaError_t Launcher<R>::uni(cudaStream_t s, int n, double bre, double bim, void
     if (std::abs(alt) > std::abs(piv)) piv = alt;
     for (int k = 0; k < 8; k++) piv = d - b * b / piv;
     const C a = 1.0 / piv, g = b / piv;
-    if (!kUniForm<R> || !(std::abs(g) < 1.0) || n <= kRegMaxN) return cudaSuccess;
+    if (!kUniForm<R> || !(std::abs(g) < 1.0)) return cudaSuccess;
     C g16 = g;
     for (int k = 0; k < 4; k++) g16 = g16 * g16;
     // s = T'^{-1} e_0: forward z_0 = 1, z_i = g z_{i-1}; backward q_{n-1} = z_{n-1},

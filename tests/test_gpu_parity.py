@@ -280,6 +280,35 @@ def test_precision_form_max_line(nx, ny):
 
 
 @pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("nx,ny", [(384, 600), (512, 512), (1024, 386), (600, 1024), (382, 512)])
+def test_precision_form_tiled_grids(nx, ny, imag):
+    """complex64 grids of 384..1024 points an axis (even rows) step on the kernels of
+    long lines when the constant-factor form applies (the fused pointwise + x-sweep
+    kernel with groups of one or two warps a line, the row-tiled y sweep with its
+    norm partials and the finalize block); 382 rows take the register kernels.
+    Full steps with the observables against the oracle, step calls of both time
+    modes in turn (the pending scale handed between the two step paths), and the
+    per-kernel profile."""
+    prob, s = make_pair(2, nx, ny, dx=0.04, precision="c64", **PHYS_2D)
+    psi = _rand(prob, nx * 3 + ny, env=3.0)
+    s.set_state(psi)
+    (s.step_imag(3) if imag else s.step_real(3))
+    ref = O.step(prob, psi, 3, imag)
+    got = s.get_state()
+    assert relerr(got, ref) < 1e-5
+    assert obs_relerr(s.energy(), O.observables(prob, ref)) < 1e-5
+    s.set_state(psi)
+    s.step_imag(2)
+    s.step_real(2)
+    s.step_imag(1)
+    ref2 = O.step(prob, O.step(prob, O.step(prob, psi, 2, True), 2, False), 1, True)
+    assert relerr(s.get_state(), ref2) < 1e-5
+    s.set_state(psi)
+    s.profile_steps(3, imag=imag)
+    assert relerr(s.get_state(), got) < 1e-6
+
+
+@pytest.mark.parametrize("imag", [True, False])
 @pytest.mark.parametrize("nx,ny", [(1026, 5), (1500, 6), (2048, 4), (3000, 3), (4096, 3), (1501, 5)])
 def test_precision_form_fused_long_rows(nx, ny, imag):
     """complex64 rows of 1025..2048 points, even: the pointwise substeps and the x
