@@ -31,8 +31,8 @@ Geometry make_geometry(int dim, int nx, int ny, int esz) {
     // shared memory (32 * nw chunks of kLongC + 1 entries)
     g.reg_x = nx <= kRegMaxN;
     g.fused = dim == 2 && g.reg_x;
-    g.wx = g.reg_x ? 1 : long_warps(nx);
-    g.smem_x = g.reg_x ? 0 : (size_t)32 * g.wx * (kLongC + 1) * esz;
+    g.wx = long_warps(nx);  // (the register kernels take one warp a line)
+    g.smem_x = (size_t)32 * g.wx * (kLongC + 1) * esz;
     g.blocks_x = 3 * ny;
     // y sweep: register kernel up to kRegMaxN points; longer columns: tiles of wy
     // adjacent columns (a 32-byte row segment where the block stays within
@@ -45,7 +45,7 @@ Geometry make_geometry(int dim, int nx, int ny, int esz) {
     g.wy = g.reg_y ? 1 : wy;
     g.smem_y = g.reg_y ? 0 : (size_t)g.wy * (32 * nwy * (kLongC + 1) + long_col_pad(esz, g.wy)) * esz;
     g.blocks_y = dim == 2 ? 3 * ceil_div(nx, g.reg_y ? cny_cols_per_warp(chunk_len(ny), esz) : g.wy) : 0;
-    g.tiled = dim == 2 && esz == 8 && nx % 2 == 0 && nx >= kMidMinN && ny >= kMidMinN && g.reg_x && g.reg_y;
+    g.tiled = dim == 2 && nx >= kMidMinN && ny >= kMidMinN && g.reg_x && g.reg_y;
     g.blocks_yt = dim == 2 && (!g.reg_y || g.tiled) ? 3 * ceil_div(nx, 32) * ceil_div(ny, kTileRows) : 0;
     g.blocks_obs = ceil_div(nx, 32) * ceil_div(ny, 4);
     g.blocks_norm = kNormBlocks;
@@ -535,8 +535,8 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
         return finalize_step(c->stream, c->partials, y_parts(c->geo, c->tabs[mode][1], c->mid, c->psi), c->kp.cell,
                              renorm, c->kp.mag, 1, c->sc, parts_df(c));
     }
-    if (pwx_long_fits(c->geo, c->tabs[mode][0])) {
-        // complex64 rows of 1025..2048 points: pointwise substeps and x sweep in one kernel
+    if (pwx_long_fits(c->geo, c->tabs[mode][0]) && (!c->geo.reg_x || tiled_mode(c, mode))) {
+        // complex64 rows of 1025..2048 points, and tiled grids: pointwise substeps and x sweep in one kernel
         if ((e = Launcher<R>::pwx_long(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, c->tabs[mode][0],
                                        7)))
             return e;
@@ -844,7 +844,8 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
     int cnt[4] = {0, 0, 0, 0};
     const bool two = c->dim == 2;
     const bool fused = c->geo.fused && !tiled_mode(c, mode);
-    const bool long_fused = !general_path(c) && !fused && pwx_long_fits(c->geo, c->tabs[mode][0]);
+    const bool long_fused = !general_path(c) && !fused && pwx_long_fits(c->geo, c->tabs[mode][0]) &&
+                            (!c->geo.reg_x || tiled_mode(c, mode));
     const bool head = head_scale(c, mode);
     sgpe_status out = SGPE_OK;
     for (int i0 = 0; i0 < nsteps && out == SGPE_OK; i0 += kBatch) {
@@ -921,7 +922,7 @@ int sgpe_launches_per_step(const sgpe_ctx* c) {
     if (one_block_1d(c)) return 0;  // one launch per step call
     if (head_scale(c, 0)) return 2;  // plus one end-of-steps launch per step call
     if (c->geo.fused && !tiled_mode(c, 0)) return 3;
-    if (c->dim == 2 && pwx_long_fits(c->geo, c->tabs[0][0])) return 3;
+    if (c->dim == 2 && pwx_long_fits(c->geo, c->tabs[0][0]) && (!c->geo.reg_x || tiled_mode(c, 0))) return 3;
     return c->dim == 2 ? 4 : 3;
 }
 

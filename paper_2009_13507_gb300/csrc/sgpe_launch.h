@@ -87,9 +87,10 @@ struct Geometry {
     size_t smem_x, smem_y;
     int blocks_x, blocks_y, blocks_obs, blocks_norm;
     int blocks_yt;  // long columns (and tiled grids): blocks (= norm partials) of the row-tiled y sweep
-    bool tiled;     // complex64 2D grid of kMidMinN..kRegMaxN points an axis, even rows: its steps may take the
-                    // kernels of long lines (fused pointwise + x sweep, row-tiled y sweep) when the
-                    // constant-factor form applies
+    bool tiled;     // 2D grid of kMidMinN..kRegMaxN points an axis: its steps take the kernels of long
+                    // lines (complex64: fused pointwise + x sweep; double-float: pointwise kernel and the
+                    // constant-factor x sweep; then the row-tiled y sweep) where the constant-factor form
+                    // applies
 };
 // Shortest axis of a grid that the tiled step serves.
 constexpr int kMidMinN = 384;
@@ -130,10 +131,13 @@ inline bool pwx_long_fits(const Geometry& g, const TabSet& tx) {
            tx.u.ks > 0;
 }
 // A step of a tiled grid (Geometry::tiled) on the kernels of long lines: both axes
-// in the constant-factor form (x: pwx_long_fits; y: the row tiles reach).
+// in the constant-factor form (which complex128 never takes), the row tiles reaching
+// the y carries.
 inline bool tiled_step(const Geometry& g, const TabSet& tx, const TabSet& ty) {
-    return g.tiled && pwx_long_fits(g, tx) && ty.u.ks > 0 && ty.u.hc > 0;
+    return g.tiled && tx.u.ks > 0 && ty.u.ks > 0 && ty.u.hc > 0;
 }
+// The x sweep of a tiled grid on the constant-factor long-line kernel.
+inline bool x_tiled(const Geometry& g, const TabSet& tx) { return g.dim == 2 && g.tiled && tx.u.ks > 0; }
 // Longest start correction of the constant-factor form (entries of s).
 constexpr int kUniMaxS = 512;
 

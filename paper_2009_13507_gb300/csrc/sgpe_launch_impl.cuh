@@ -353,7 +353,7 @@ cudaError_t Launcher<R>::cn_x(cudaStream_t s, bool imag, bool last, const void* 
                               int renorm, int advance) {
     using T = typename V2<R>::T;
     Tabs<R> t = make_tabs<R>(tabs);
-    if (g.reg_x) {
+    if (g.reg_x && !(kUniForm<R> && x_tiled(g, tabs))) {
         launch_cnx_reg<R>(chunk_len(p.nx), imag, dim3(g.blocks_x), s, (const T*)in, (T*)out, p, t,
                           last ? partials : nullptr);
         return cudaGetLastError();

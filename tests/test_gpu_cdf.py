@@ -76,6 +76,31 @@ def test_full_step_parity_2d_cdf(imag):
 
 
 @pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("nx,ny", [(512, 400), (386, 1024), (1023, 384)])
+def test_tiled_grids_cdf(nx, ny, imag):
+    """Double-float grids of 384..1024 points an axis on the kernels of long lines:
+    the pointwise kernel, the constant-factor x sweep with one or two warps a line,
+    the row-tiled y sweep (one halo chunk), its norm partials and the finalize
+    block; both time modes in turn, then the per-kernel profile."""
+    prob, s = make_pair(2, nx, ny, dx=0.04, precision="cdf", **PHYS_2D)
+    psi = _rand(prob, nx + 5 * ny, env=3.0)
+    s.set_state(psi)
+    (s.step_imag(3) if imag else s.step_real(3))
+    ref = O.step(prob, psi, 3, imag)
+    got = s.get_state()
+    assert relerr(got, ref) < 1e-10
+    assert obs_relerr(s.energy(), O.observables(prob, ref)) < 1e-10
+    s.set_state(psi)
+    s.step_imag(2)
+    s.step_real(1)
+    ref2 = O.step(prob, O.step(prob, psi, 2, True), 1, False)
+    assert relerr(s.get_state(), ref2) < 1e-10
+    s.set_state(psi)
+    s.profile_steps(3, imag=imag)
+    assert relerr(s.get_state(), got) < 1e-13
+
+
+@pytest.mark.parametrize("imag", [True, False])
 def test_full_step_parity_1d_cdf(imag):
     prob, s = make_pair(1, 256, 1, dx=0.05, precision="cdf", **PHYS_1D)
     psi = I.gaussian_jitter_1d(256, 0.05, seed=0)
