@@ -440,8 +440,14 @@ static bool general_path(const sgpe_ctx* c) { return c->params.split != 0 || c->
 static bool tiled_mode(const sgpe_ctx* c, int mode) {
     return c->geo.tiled && !general_path(c) && tiled_step(c->geo, c->tabs[mode][0], c->tabs[mode][1]);
 }
+// The fused head kernel of a tiled complex64 step forms the pending scale from the
+// row tiles' partials itself (at most 256 a component) instead of a finalize block.
+static bool tiled_head(const sgpe_ctx* c, int mode) {
+    return tiled_mode(c, mode) && pwx_long_fits(c->geo, c->tabs[mode][0]) && c->geo.blocks_yt / 3 <= 256;
+}
 static bool head_scale(const sgpe_ctx* c, int mode) {
-    return c->geo.fused && c->geo.reg_y && !general_path(c) && !tiled_mode(c, mode);
+    if (general_path(c)) return false;
+    return (c->geo.fused && c->geo.reg_y && !tiled_mode(c, mode)) || tiled_head(c, mode);
 }
 
 // The y sweeps (2D) and the long x sweep (1D) of the complex64 and double-float
@@ -450,10 +456,11 @@ static bool head_scale(const sgpe_ctx* c, int mode) {
 static int parts_df(const sgpe_ctx* c) { return c->prec != SGPE_C128 && (c->dim == 2 || !c->geo.reg_x); }
 
 static cudaError_t end_steps(sgpe_ctx* c, bool imag) {
-    if (!head_scale(c, imag ? 0 : 1)) return cudaSuccess;
+    const int mode = imag ? 0 : 1;
+    if (!head_scale(c, mode)) return cudaSuccess;
     const int renorm = imag ? c->params.renorm : 0;
-    return finalize_step(c->stream, c->partials, c->geo.blocks_y, c->kp.cell, renorm, c->kp.mag, 0, c->sc,
-                         parts_df(c));
+    return finalize_step(c->stream, c->partials, y_parts(c->geo, c->tabs[mode][1], c->mid, c->psi), c->kp.cell,
+                         renorm, c->kp.mag, 0, c->sc, parts_df(c));
 }
 
 // The SO substep by Crank-Nicolson on the line families of the grid, in -> out:
@@ -534,6 +541,15 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
         if (head) return cudaSuccess;  // the next head kernel (or end_steps) takes the scale from the partials
         return finalize_step(c->stream, c->partials, y_parts(c->geo, c->tabs[mode][1], c->mid, c->psi), c->kp.cell,
                              renorm, c->kp.mag, 1, c->sc, parts_df(c));
+    }
+    if (tiled_head(c, mode)) {
+        // tiled complex64 grid: the fused kernel forms the pending scale from the row
+        // tiles' partials, the y sweep marks them and moves the step counter on
+        if ((e = Launcher<R>::pwx_long(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, c->tabs[mode][0], 7,
+                                       c->partials, c->geo.blocks_yt / 3, renorm)))
+            return e;
+        return Launcher<R>::cn_y(c->stream, imag, c->mid, c->psi, c->kp, c->tabs[mode][1], c->geo, c->partials,
+                                 c->sc, renorm, 1, 1, true);
     }
     if (pwx_long_fits(c->geo, c->tabs[mode][0]) && (!c->geo.reg_x || tiled_mode(c, mode))) {
         // complex64 rows of 1025..2048 points, and tiled grids: pointwise substeps and x sweep in one kernel
@@ -862,7 +878,8 @@ sgpe_status sgpe_profile_steps(sgpe_ctx* c, int nsteps, int imag, double* ms_out
         if (!e && long_fused)
             e = with_prec(c->prec, [&](auto r) {
                 return Launcher<decltype(r)>::pwx_long(c->stream, im, c->psi, c->mid, c->kp, c->sc, nullptr,
-                                                       c->tabs[mode][0], 7);
+                                                       c->tabs[mode][0], 7, head ? c->partials : nullptr,
+                                                       c->geo.blocks_yt / 3, renorm);
             });
         if (!e && !fused && !long_fused)
             e = with_prec(c->prec, [&](auto r) {

@@ -1075,10 +1075,13 @@ constexpr int kPwxLongMaxGroupWarps = 4;
 template <bool IMAG, bool STD>
 __global__ void __launch_bounds__(96 * kPwxLongMaxGroupWarps, 2)
     k_pwx_long(const float2* __restrict__ A, float2* __restrict__ B, KParams p, const DevScalars* __restrict__ sc,
-               const double* __restrict__ omega_tab, Tabs<float> t, int mask) {
+               const double* __restrict__ omega_tab, Tabs<float> t, int mask, const double* __restrict__ partials,
+               int m, int renorm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<float>* lines = reinterpret_cast<cx<float>*>(smem_raw);  // [3][32 nwl kLongS]
     __shared__ cx<float> seg[3][4 * kPwxLongMaxGroupWarps];
+    __shared__ df red_df[3];
+    __shared__ float dsh[3];
     const int nwl = blockDim.x / 96;
     const int warp = threadIdx.x >> 5;
     const int nx = p.nx, iy = blockIdx.x;
@@ -1087,6 +1090,27 @@ __global__ void __launch_bounds__(96 * kPwxLongMaxGroupWarps, 2)
     f32x2 ds[3];
     float Ot;
     pair_constants(p, sc, omega_tab, mask, ds, Ot);
+    if (partials && *(volatile const int*)&sc->scale_src) {
+        // the previous y sweep left its norm partials (m per component, double-float
+        // pairs): every block forms the pending scale from them, in the same order
+        if (warp < 3) {
+            const df sm = sum_partials_warp(reinterpret_cast<const df*>(partials) + (size_t)warp * m, m);
+            if ((threadIdx.x & 31) == 0) red_df[warp] = sm;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const df S3[3] = {red_df[0], red_df[1], red_df[2]};
+            df f[3];
+            double d[3], N[3];
+            bool finite;
+            scale_from_df_sums(S3, p.cell, renorm, p.mag, f, d, N, finite);
+#pragma unroll
+            for (int j = 0; j < 3; j++) dsh[j] = to_r_df<float>(f[j]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 3; j++) ds[j] = f32x2(dsh[j]);
+    }
     for (int q = threadIdx.x; 2 * q < nx; q += blockDim.x) {
         cx<f32x2> u[3];
         pair_substeps<IMAG, STD>(A, p, ds, Ot, mask, 2 * q, iy, u);
@@ -1192,10 +1216,13 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps, long_min_blocks<R, UNI>())
 
 template <typename R, int HC> constexpr int tile_min_blocks() { return sizeof(R) == 4 ? (HC == 1 ? 3 : 2) : 1; }
 
+// sc (nullable): the tiled step whose next head kernel forms the pending scale from
+// these partials (as k_cny_reg: block 0 marks that, or stores the scale 1 when
+// renorm == 0, and moves the step counter on if advance).
 template <typename R, bool IMAG, int HC>
 __global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<R, HC>()))
     k_cn_y_tile(const typename V2<R>::T* __restrict__ in, typename V2<R>::T* __restrict__ out, KParams p, Tabs<R> t,
-                double* part) {
+                double* part, DevScalars* sc, int renorm, int advance) {
     using G = typename UCoef<IMAG, R>::T;
     using P = typename PartT<R>::T;
     using T = typename V2<R>::T;
@@ -1224,9 +1251,20 @@ __global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<R,
     const T* src = in + cbase + (ptrdiff_t)i0 * nx;
     cx<R> v[kLongC];
     pdl_wait();
-    // with norm partials the next launch is the finalize block, which may become
-    // resident now (it waits for this grid); otherwise the next kernel launches at the end
-    if (part) pdl_trigger();
+    // with norm partials and no head scale the next launch is the finalize block, which
+    // may become resident now (it waits for this grid); otherwise the next kernel
+    // launches at the end
+    if (part && !sc) pdl_trigger();
+    if (sc && blockIdx.x == 0 && threadIdx.x < 3) {
+        if (renorm) {
+            if (threadIdx.x == 0) sc->scale_src = 1;
+        } else {
+            sc->scale[threadIdx.x] = 1.0;
+            sc->scale_f[threadIdx.x] = 1.0f;
+            sc->scale_l[threadIdx.x] = 0.0f;
+        }
+        if (advance && threadIdx.x == 0) sc->step_idx += 1;
+    }
     // the chunk's values x (kept in shared memory for the result) and the right-hand
     // side: L x (increment form) or x. IN: no row checks (inner chunk).
     auto load_rhs = [&](auto in_tag) {

@@ -167,10 +167,12 @@ template <typename R> struct Launcher {
     static cudaError_t cn_y(cudaStream_t s, bool imag, const void* in, void* out, const KParams& p,
                             const TabSet& tabs, const Geometry& g, double* partials, DevScalars* sc, int renorm,
                             int advance, int finalize, bool head_scale = false);
-    // Fused pointwise substeps + CN along x of a 2D complex64 grid with rows of
-    // 1025..2048 points (pwx_long_fits): A -> B.
+    // Fused pointwise substeps + CN along x of a 2D complex64 grid (pwx_long_fits):
+    // A -> B. partials (nullable) / m / renorm: the previous row-tiled y sweep's norm
+    // partials (m per component) for the pending scale (DevScalars::scale_src).
     static cudaError_t pwx_long(cudaStream_t s, bool imag, const void* A, void* B, const KParams& p,
-                                const DevScalars* sc, const double* omega_tab, const TabSet& tabs_x, int mask);
+                                const DevScalars* sc, const double* omega_tab, const TabSet& tabs_x, int mask,
+                                const double* partials = nullptr, int m = 0, int renorm = 0);
     static cudaError_t coef(cudaStream_t s, void* fa, void* fg, void* fp, void* fq, int n, double bre, double bim);
     // The constant-factor form of an n-point line with bt = bre + i bim (n > kRegMaxN):
     // fills u and copies s to s_dev (kUniMaxS entries of room); u->ks = 0 where the

@@ -323,7 +323,8 @@ cudaError_t Launcher<R>::pwx(cudaStream_t s, bool imag, const void* A, void* B, 
 
 template <typename R>
 cudaError_t Launcher<R>::pwx_long(cudaStream_t s, bool imag, const void* A, void* B, const KParams& p,
-                                  const DevScalars* sc, const double* omega_tab, const TabSet& tabs_x, int mask) {
+                                  const DevScalars* sc, const double* omega_tab, const TabSet& tabs_x, int mask,
+                                  const double* partials, int m, int renorm) {
     if constexpr (!std::is_same<R, float>::value) {
         return cudaErrorNotSupported;
     } else {
@@ -337,7 +338,7 @@ cudaError_t Launcher<R>::pwx_long(cudaStream_t s, bool imag, const void* A, void
         const bool std2d = mask == 7 && q.so_case == 4;
         auto go = [&](auto kern) {
             launch_pdl(kern, dim3(p.ny), dim3(96 * nwl), smem, s, (const float2*)A, (float2*)B, q, sc, omega_tab, t,
-                       mask);
+                       mask, partials, m, renorm);
         };
         if (std2d)
             imag ? go(k_pwx_long<true, true>) : go(k_pwx_long<false, true>);
@@ -381,7 +382,10 @@ cudaError_t Launcher<R>::cn_y(cudaStream_t s, bool imag, const void* in, void* o
             const int hc = tabs.u.hc;
             const dim3 tb(32 * (kTileReal + 2 * hc)), tg(g.blocks_yt);
             const size_t sm = (size_t)(kTileReal + 2 * hc) * kLongC * 32 * sizeof(cx<R>);
-            auto go = [&](auto kern) { launch_pdl(kern, tg, tb, sm, s, (const T*)in, (T*)out, p, t, part); };
+            DevScalars* hs = head_scale ? sc : nullptr;
+            auto go = [&](auto kern) {
+                launch_pdl(kern, tg, tb, sm, s, (const T*)in, (T*)out, p, t, part, hs, renorm, advance);
+            };
             if (hc == 1)
                 imag ? go(k_cn_y_tile<R, true, 1>) : go(k_cn_y_tile<R, false, 1>);
             else
