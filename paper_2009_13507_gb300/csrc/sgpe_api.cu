@@ -45,7 +45,8 @@ Geometry make_geometry(int dim, int nx, int ny, int esz) {
     g.wy = g.reg_y ? 1 : wy;
     g.smem_y = g.reg_y ? 0 : (size_t)g.wy * (32 * nwy * (kLongC + 1) + long_col_pad(esz, g.wy)) * esz;
     g.blocks_y = dim == 2 ? 3 * ceil_div(nx, g.reg_y ? cny_cols_per_warp(chunk_len(ny), esz) : g.wy) : 0;
-    g.tiled = dim == 2 && nx >= kMidMinN && ny >= kMidMinN && g.reg_x && g.reg_y;
+    const int mid_min = esz == 8 ? kMidMinN : kMidMinN16;
+    g.tiled = dim == 2 && nx >= mid_min && ny >= mid_min && g.reg_x && g.reg_y;
     g.blocks_yt = dim == 2 && (!g.reg_y || g.tiled) ? 3 * ceil_div(nx, 32) * ceil_div(ny, kTileRows) : 0;
     g.blocks_obs = ceil_div(nx, 32) * ceil_div(ny, 4);
     g.blocks_norm = kNormBlocks;

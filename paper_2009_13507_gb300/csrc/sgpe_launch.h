@@ -87,13 +87,15 @@ struct Geometry {
     size_t smem_x, smem_y;
     int blocks_x, blocks_y, blocks_obs, blocks_norm;
     int blocks_yt;  // long columns (and tiled grids): blocks (= norm partials) of the row-tiled y sweep
-    bool tiled;     // 2D grid of kMidMinN..kRegMaxN points an axis: its steps take the kernels of long
+    bool tiled;     // 2D grid of kMidMinN (kMidMinN16)..kRegMaxN points an axis: its steps take the kernels of long
                     // lines (complex64: fused pointwise + x sweep; double-float: pointwise kernel and the
                     // constant-factor x sweep; then the row-tiled y sweep) where the constant-factor form
                     // applies
 };
-// Shortest axis of a grid that the tiled step serves.
-constexpr int kMidMinN = 384;
+// Shortest axis of a grid that the tiled step serves: complex64 (8-byte elements)
+// and double-float (16-byte; its register path measured faster on 256-point lines).
+constexpr int kMidMinN = 256;
+constexpr int kMidMinN16 = 320;
 
 Geometry make_geometry(int dim, int nx, int ny, int esz);
 

@@ -76,9 +76,10 @@ def test_full_step_parity_2d_cdf(imag):
 
 
 @pytest.mark.parametrize("imag", [True, False])
-@pytest.mark.parametrize("nx,ny", [(512, 400), (386, 1024), (1023, 384)])
+@pytest.mark.parametrize("nx,ny", [(512, 400), (386, 1024), (1023, 320), (320, 319)])
 def test_tiled_grids_cdf(nx, ny, imag):
-    """Double-float grids of 384..1024 points an axis on the kernels of long lines:
+    """Double-float grids of 320..1024 points an axis on the kernels of long lines
+    (319 rows: the register kernels):
     the pointwise kernel, the constant-factor x sweep with one or two warps a line,
     the row-tiled y sweep (one halo chunk), its norm partials and the finalize
     block; both time modes in turn, then the per-kernel profile."""

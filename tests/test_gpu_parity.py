@@ -280,13 +280,14 @@ def test_precision_form_max_line(nx, ny):
 
 
 @pytest.mark.parametrize("imag", [True, False])
-@pytest.mark.parametrize("nx,ny", [(384, 600), (512, 512), (1024, 386), (600, 1024), (385, 400), (382, 512)])
+@pytest.mark.parametrize("nx,ny", [(256, 256), (384, 600), (512, 512), (1024, 386), (600, 1024), (385, 400), (254, 512)])
 def test_precision_form_tiled_grids(nx, ny, imag):
-    """complex64 grids of 384..1024 points an axis (even rows) step on the kernels of
-    long lines when the constant-factor form applies (the fused pointwise + x-sweep
-    kernel with groups of one or two warps a line, the row-tiled y sweep with its
-    norm partials and the finalize block); odd rows (385) the pointwise kernel and
-    the constant-factor x sweep; 382 rows take the register kernels.
+    """complex64 grids of 256..1024 points an axis step on the kernels of long lines
+    when the constant-factor form applies: even rows on the fused pointwise + x-sweep
+    kernel (groups of one or two warps a line), which forms the pending scale from
+    the row-tiled y sweep's norm partials (no finalize block); odd rows (385) on the
+    pointwise kernel and the constant-factor x sweep, then the y tiles and the
+    finalize block; 254-point rows take the register kernels.
     Full steps with the observables against the oracle, step calls of both time
     modes in turn (the pending scale handed between the two step paths), and the
     per-kernel profile."""
