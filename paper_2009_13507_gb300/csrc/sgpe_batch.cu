@@ -153,6 +153,38 @@ __global__ void kb_cny(typename V2<R>::T* A, const typename V2<R>::T* B, const B
     cny_cols<R, IMAG, C>(B + I.off, A + I.off, I.p, t, e.y, e.z, partials + e.w);
 }
 
+// Tiled instances (complex64 2D grids of 256..1024 points an axis with even rows,
+// the constant-factor form in both time modes): the kernels of the single-grid
+// tiled step through work lists. uni holds the instances' constant-factor forms as
+// Tabs, [instance][mode][axis].
+// Row entry: (instance, row, -, -); one launch per warps-a-line count (blockDim 96 nwl).
+template <bool IMAG>
+__global__ void __launch_bounds__(96 * kPwxLongMaxGroupWarps, 2)
+    kb_pwx_long(const float2* __restrict__ A, float2* __restrict__ B, const BInst* __restrict__ insts,
+                const Tabs<float>* __restrict__ uni, const int4* __restrict__ rows,
+                const DevScalars* __restrict__ scs) {
+    const int4 e = rows[blockIdx.x];
+    const BInst& I = insts[e.x];
+    f32x2 ds[3];
+    float Ot;
+    pair_constants(I.p, scs + e.x, nullptr, 7, ds, Ot);
+    const Tabs<float> t = uni[4 * e.x + (IMAG ? 0 : 2)];
+    pwx_long_row<IMAG, false>(A + I.off, B + I.off, I.p, ds, Ot, t, 7, e.y);
+}
+
+// Tile entry: (instance, component j + 4 column tile, row tile, partial slot); one
+// launch per halo depth HC. The tile's norm goes to its FP64 partial slot.
+template <bool IMAG, int HC>
+__global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<float, HC>()))
+    kb_cny_tile(float2* __restrict__ A, const float2* __restrict__ B, const BInst* __restrict__ insts,
+                const Tabs<float>* __restrict__ uni, const int4* __restrict__ work, double* partials) {
+    const int4 e = work[blockIdx.x];
+    const BInst& I = insts[e.x];
+    const Tabs<float> t = uni[4 * e.x + (IMAG ? 0 : 2) + 1];
+    const df sum = cny_tile<float, IMAG, HC>(B + I.off, A + I.off, I.p, t, e.y & 3, e.y >> 2, e.z, true);
+    if (threadIdx.x == 0) partials[e.w] = (double)sum.hi + (double)sum.lo;
+}
+
 // One block per instance: sum its partial slots in order, publish norms and the
 // next pending scale (imaginary time with renorm != 0), advance its step count.
 __global__ void __launch_bounds__(128) kb_finalize(const BInst* __restrict__ insts, const double* partials,
@@ -261,14 +293,19 @@ struct sgpe_batch {
     cudaStream_t stream;
     std::vector<sgpe_instance> inst;
     std::vector<BInst> hinst;
-    std::vector<int2> tiles;
+    std::vector<int2> tiles;    // every instance's tiles (flush, observables)
+    std::vector<int2> pwtiles;  // the tiles of the pointwise kernel (instances on the register path)
     std::map<int, std::vector<int4>> cnx, cny, rows;  // work lists by chunk length (rows: the fused x part)
+    // tiled instances (complex64): row entries by warps a line, tile entries by halo depth
+    std::vector<char> tiled;
+    std::map<int, std::vector<int4>> rows_t, ytile;
     size_t state_elems;
     long long tab_elems;
     int nslots;
     // workspace layout (byte offsets)
     size_t o_inst, o_sc, o_tiles, o_part, o_tab, o_mid, total;
-    std::map<int, size_t> o_cnx, o_cny, o_rows;
+    size_t o_pwtiles, o_uni, o_us;
+    std::map<int, size_t> o_cnx, o_cny, o_rows, o_rows_t, o_ytile;
     // bound buffers
     void* psi;
     unsigned char* work;
@@ -344,8 +381,18 @@ static cudaError_t benqueue_step(sgpe_batch* b) {
                 default: kb_pwx_c<R, IMAG, 32>(grid, block, b->stream, A, B, I, pool, w, sc, part); break;
             }
         }
-    } else {
-        kb_pointwise<R, IMAG><<<(unsigned)b->tiles.size(), 128, 0, b->stream>>>(A, B, I, tiles, sc);
+    } else if (!b->pwtiles.empty()) {
+        const int2* pwt = (const int2*)(b->work + b->o_pwtiles);
+        kb_pointwise<R, IMAG><<<(unsigned)b->pwtiles.size(), 128, 0, b->stream>>>(A, B, I, pwt, sc);
+    }
+    if constexpr (std::is_same<R, float>::value) {
+        const Tabs<float>* uni = (const Tabs<float>*)(b->work + b->o_uni);
+        for (auto& kv : b->rows_t) {
+            const int4* w = (const int4*)(b->work + b->o_rows_t[kv.first]);
+            const size_t sm = (size_t)3 * 32 * kv.first * kLongS * sizeof(cx<float>);
+            kb_pwx_long<IMAG><<<(unsigned)kv.second.size(), 96 * kv.first, sm, b->stream>>>(
+                (const float2*)A, (float2*)B, I, uni, w, sc);
+        }
     }
     for (auto& kv : b->cnx) {
         if (b->wx == 0) break;  // fused into kb_pwx
@@ -372,6 +419,19 @@ static cudaError_t benqueue_step(sgpe_batch* b) {
             case 8: kb_cny<R, IMAG, 8><<<grid, block, 0, b->stream>>>(A, B, I, pool, w, nw, part); break;
             case 16: kb_cny<R, IMAG, 16><<<grid, block, 0, b->stream>>>(A, B, I, pool, w, nw, part); break;
             default: kb_cny<R, IMAG, 32><<<grid, block, 0, b->stream>>>(A, B, I, pool, w, nw, part); break;
+        }
+    }
+    if constexpr (std::is_same<R, float>::value) {
+        const Tabs<float>* uni = (const Tabs<float>*)(b->work + b->o_uni);
+        for (auto& kv : b->ytile) {
+            const int4* w = (const int4*)(b->work + b->o_ytile[kv.first]);
+            const int hc = kv.first;
+            const size_t sm = (size_t)(kTileReal + 2 * hc) * kLongC * 32 * sizeof(cx<float>);
+            const dim3 grid((unsigned)kv.second.size()), block(32 * (kTileReal + 2 * hc));
+            if (hc == 1)
+                kb_cny_tile<IMAG, 1><<<grid, block, sm, b->stream>>>((float2*)A, (const float2*)B, I, uni, w, part);
+            else
+                kb_cny_tile<IMAG, 2><<<grid, block, sm, b->stream>>>((float2*)A, (const float2*)B, I, uni, w, part);
         }
     }
     kb_finalize<<<b->n, 128, 0, b->stream>>>(I, part, sc, IMAG ? 1 : 0);
@@ -513,10 +573,39 @@ sgpe_status sgpe_batch_create(sgpe_batch** out, int n, const sgpe_instance* inst
         tab += 2LL * 4 * (I.lenx + I.leny);
         I.tile0 = (int)b->tiles.size();
         I.ntile = q.dim == 2 ? ceil_div(q.nx, 32) * ceil_div(q.ny, 4) : ceil_div(q.nx, 128);
-        for (int t = 0; t < I.ntile; t++) b->tiles.push_back(make_int2(i, t));
+        // complex64 2D instances of 256..1024 points an axis with even rows take the tiled
+        // step when both axes have the constant-factor form in both time modes
+        bool tl = prec == SGPE_C64 && q.dim == 2 && q.nx % 2 == 0 && q.nx >= kMidMinN && q.ny >= kMidMinN;
+        int hcmax = 0;
+        for (int m = 0; m < 2 && tl; m++)
+            for (int a = 0; a < 2 && tl; a++) {
+                const double h = a == 0 ? q.dx : q.dy, bt = q.params.dt / (4.0 * h * h);
+                UniHost u;
+                if (Launcher<float>::uni(nullptr, a == 0 ? q.nx : q.ny, m == 0 ? bt : 0.0, m == 0 ? 0.0 : bt, nullptr,
+                                         &u) != cudaSuccess ||
+                    u.ks <= 0 || (a == 1 && u.hc <= 0))
+                    tl = false;
+                else if (a == 1)
+                    hcmax = std::max(hcmax, u.hc);
+            }
+        b->tiled.push_back(tl ? 1 : 0);
+        for (int t = 0; t < I.ntile; t++) {
+            b->tiles.push_back(make_int2(i, t));
+            if (!tl) b->pwtiles.push_back(make_int2(i, t));
+        }
         const int Cx = chunk_len(q.nx);
         I.slot0 = slot;
-        if (q.dim == 1) {
+        if (tl) {
+            const int nwl = long_warps(q.nx);
+            for (int r = 0; r < q.ny; r++) b->rows_t[nwl].push_back(make_int4(i, r, 0, 0));
+            const int nct = ceil_div(q.nx, 32), nrt = ceil_div(q.ny, kTileRows);
+            for (int j = 0; j < 3; j++)
+                for (int ct = 0; ct < nct; ct++)
+                    for (int rt = 0; rt < nrt; rt++)
+                        b->ytile[hcmax].push_back(make_int4(i, j + 4 * ct, rt, slot + (j * nct + ct) * nrt + rt));
+            I.nslot = 3 * nct * nrt;
+            slot += I.nslot;
+        } else if (q.dim == 1) {
             I.nslot = 3;
             for (int l = 0; l < 3; l++) b->cnx[Cx].push_back(make_int4(i, l, slot + l, 0));
             b->rows[Cx].push_back(make_int4(i, 0, slot, 0));
@@ -544,6 +633,21 @@ sgpe_status sgpe_batch_create(sgpe_batch** out, int n, const sgpe_instance* inst
     o = al256(o + sizeof(DevScalars) * n);
     b->o_tiles = o;
     o = al256(o + sizeof(int2) * b->tiles.size());
+    b->o_pwtiles = o;
+    o = al256(o + sizeof(int2) * b->pwtiles.size());
+    for (auto& kv : b->rows_t) {
+        b->o_rows_t[kv.first] = o;
+        o = al256(o + sizeof(int4) * kv.second.size());
+    }
+    for (auto& kv : b->ytile) {
+        b->o_ytile[kv.first] = o;
+        o = al256(o + sizeof(int4) * kv.second.size());
+    }
+    // the constant-factor forms of tiled instances: [instance][mode][axis] Tabs and start corrections
+    b->o_uni = o;
+    o = al256(o + (prec == SGPE_C64 ? sizeof(Tabs<float>) * 4 * (size_t)n : 0));
+    b->o_us = o;
+    o = al256(o + (prec == SGPE_C64 ? sizeof(float2) * kUniMaxS * 4 * (size_t)n : 0));
     for (auto& kv : b->cnx) {
         b->o_cnx[kv.first] = o;
         o = al256(o + sizeof(int4) * kv.second.size());
@@ -603,6 +707,57 @@ sgpe_status sgpe_batch_bind(sgpe_batch* b, void* psi_dev, void* workspace_dev) {
     for (auto& kv : b->rows)
         BCK(cudaMemcpyAsync(b->work + b->o_rows[kv.first], kv.second.data(), sizeof(int4) * kv.second.size(),
                             cudaMemcpyHostToDevice, s), "copy");
+    if (!b->pwtiles.empty())
+        BCK(cudaMemcpyAsync(b->work + b->o_pwtiles, b->pwtiles.data(), sizeof(int2) * b->pwtiles.size(),
+                            cudaMemcpyHostToDevice, s), "copy");
+    for (auto& kv : b->rows_t)
+        BCK(cudaMemcpyAsync(b->work + b->o_rows_t[kv.first], kv.second.data(), sizeof(int4) * kv.second.size(),
+                            cudaMemcpyHostToDevice, s), "copy");
+    for (auto& kv : b->ytile)
+        BCK(cudaMemcpyAsync(b->work + b->o_ytile[kv.first], kv.second.data(), sizeof(int4) * kv.second.size(),
+                            cudaMemcpyHostToDevice, s), "copy");
+    if (b->prec == SGPE_C64) {
+        // tiled instances: the constant-factor forms (start corrections into the workspace)
+        std::vector<Tabs<float>> ut(4 * (size_t)b->n);
+        memset(ut.data(), 0, sizeof(Tabs<float>) * ut.size());
+        for (int i = 0; i < b->n; i++) {
+            if (!b->tiled[i]) continue;
+            const BInst& I = b->hinst[i];
+            for (int m = 0; m < 2; m++)
+                for (int a = 0; a < 2; a++) {
+                    const size_t k = 4 * (size_t)i + 2 * m + a;
+                    const double h = a == 0 ? I.p.dx : I.p.dy, bt = I.p.dt / (4.0 * h * h);
+                    void* sdev = b->work + b->o_us + sizeof(float2) * kUniMaxS * k;
+                    UniHost u;
+                    BCK(Launcher<float>::uni(s, a == 0 ? I.p.nx : I.p.ny, m == 0 ? bt : 0.0, m == 0 ? 0.0 : bt, sdev,
+                                             &u),
+                        "constant-factor form");
+                    Tabs<float>& t = ut[k];
+                    t.ug = {(float)u.gr, (float)u.gi};
+                    t.ug16 = {(float)u.g16r, (float)u.g16i};
+                    t.uc = {(float)u.cr, (float)u.ci};
+                    t.uk = {(float)u.kr, (float)u.ki};
+                    for (int q = 0; q < 16; q++) t.upow[q] = {(float)u.pr[q], (float)u.pi[q]};
+                    t.us = (const float2*)u.s;
+                    t.uks = u.ks;
+                    t.unlev = u.nlev;
+                }
+        }
+        BCK(cudaMemcpyAsync(b->work + b->o_uni, ut.data(), sizeof(Tabs<float>) * ut.size(), cudaMemcpyHostToDevice,
+                            s),
+            "copy");
+        BCK(cudaStreamSynchronize(s), "sync");  // the host tables must outlive the copy
+        for (int imag = 0; imag < 2; imag++) {
+            const size_t sm1 = (size_t)(kTileReal + 2) * kLongC * 32 * sizeof(cx<float>);
+            const size_t sm2 = (size_t)(kTileReal + 4) * kLongC * 32 * sizeof(cx<float>);
+            BCK(cudaFuncSetAttribute(imag ? kb_cny_tile<true, 1> : kb_cny_tile<false, 1>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1),
+                "kernel attributes");
+            BCK(cudaFuncSetAttribute(imag ? kb_cny_tile<true, 2> : kb_cny_tile<false, 2>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2),
+                "kernel attributes");
+        }
+    }
     if (b->prec == SGPE_C128) {
         BCK((kb_pwx_allow<double, true>()), "kernel attributes");
         BCK((kb_pwx_allow<double, false>()), "kernel attributes");
@@ -743,8 +898,9 @@ sgpe_status sgpe_batch_set_tiles(sgpe_batch* b, int x, int y) {
 
 int sgpe_batch_launches_per_step(const sgpe_batch* b) {
     if (!b) return 0;
-    if (b->wx == 0) return 1 + (int)b->rows.size() + (int)b->cny.size();
-    return 2 + (int)b->cnx.size() + (int)b->cny.size();
+    const int t = (int)b->rows_t.size() + (int)b->ytile.size();
+    if (b->wx == 0) return 1 + (int)b->rows.size() + (int)b->cny.size() + t;
+    return 1 + (b->pwtiles.empty() ? 0 : 1) + (int)b->cnx.size() + (int)b->cny.size() + t;
 }
 
 const char* sgpe_batch_last_error(const sgpe_batch* b) { return b ? b->err : "null batch"; }

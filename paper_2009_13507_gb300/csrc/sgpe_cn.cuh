@@ -1063,6 +1063,47 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps, long_min_blocks<R, UNI>())
     }
 }
 
+constexpr int kPwxLongMaxGroupWarps = 4;
+// The row iy of k_pwx_long once the pending scale ds and Omega are known: the
+// point pairs into the three lines' chunk layout in shared memory, the three line
+// solves by the block's warp groups (blockDim = 96 nwl), the lines to B. Every
+// thread of the block calls it.
+template <bool IMAG, bool STD>
+__device__ __forceinline__ void pwx_long_row(const float2* __restrict__ A, float2* __restrict__ B, const KParams& p,
+                                             const f32x2 (&ds)[3], float Ot, const Tabs<float>& t, int mask, int iy) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<float>* lines = reinterpret_cast<cx<float>*>(smem_raw);  // [3][32 nwl kLongS]
+    __shared__ cx<float> seg[3][4 * kPwxLongMaxGroupWarps];
+    const int nwl = blockDim.x / 96;
+    const int warp = threadIdx.x >> 5;
+    const int nx = p.nx;
+    const int span = 32 * kLongC * nwl, S = 32 * nwl * kLongS;
+    for (int q = threadIdx.x; 2 * q < nx; q += blockDim.x) {
+        cx<f32x2> u[3];
+        pair_substeps<IMAG, STD>(A, p, ds, Ot, mask, 2 * q, iy, u);
+        const int s0 = long_slot(2 * q);  // 2q is even: 2q + 1 sits in the next slot of the same chunk
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            lines[j * S + s0] = cx<float>{u[j].re.v.x, u[j].im.v.x};
+            lines[j * S + s0 + 1] = cx<float>{u[j].re.v.y, u[j].im.v.y};
+        }
+    }
+    for (int i = nx + threadIdx.x; i < span; i += blockDim.x)
+#pragma unroll
+        for (int j = 0; j < 3; j++) lines[j * S + long_slot(i)] = cx<float>{0.0f, 0.0f};
+    __syncthreads();
+    const int j = warp / nwl;
+    long_line_uni<float, IMAG>(lines + j * S, nx, t, warp - j * nwl, nwl, seg[j], false);
+    pdl_trigger();  // the y sweep's blocks may take the slots this grid frees
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float2* dst = B + ((size_t)c * p.ny + iy) * nx;
+        const cx<float>* src = lines + c * S;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) dst[i] = make_float2(src[long_slot(i)].re, src[long_slot(i)].im);
+    }
+}
+
 // Pointwise substeps and CN along x of one row of a 2D complex64 grid with
 // 1025..2048 points (nx even; the constant-factor solve, Tabs::uks > 0): one
 // block per row, 3 groups of nwl = ceil(nx / 512) warps (one group per
@@ -1071,21 +1112,15 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps, long_min_blocks<R, UNI>())
 // nx zero), then group j solves line j (long_line_uni) and the block stores the
 // three lines to B. Each step then streams the state twice (A -> B here, B -> A
 // in the y sweep) instead of three times.
-constexpr int kPwxLongMaxGroupWarps = 4;
 template <bool IMAG, bool STD>
 __global__ void __launch_bounds__(96 * kPwxLongMaxGroupWarps, 2)
     k_pwx_long(const float2* __restrict__ A, float2* __restrict__ B, KParams p, const DevScalars* __restrict__ sc,
                const double* __restrict__ omega_tab, Tabs<float> t, int mask, const double* __restrict__ partials,
                int m, int renorm) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<float>* lines = reinterpret_cast<cx<float>*>(smem_raw);  // [3][32 nwl kLongS]
-    __shared__ cx<float> seg[3][4 * kPwxLongMaxGroupWarps];
     __shared__ df red_df[3];
     __shared__ float dsh[3];
-    const int nwl = blockDim.x / 96;
     const int warp = threadIdx.x >> 5;
-    const int nx = p.nx, iy = blockIdx.x;
-    const int span = 32 * kLongC * nwl, S = 32 * nwl * kLongS;
+    const int iy = blockIdx.x;
     pdl_wait();
     f32x2 ds[3];
     float Ot;
@@ -1111,30 +1146,7 @@ __global__ void __launch_bounds__(96 * kPwxLongMaxGroupWarps, 2)
 #pragma unroll
         for (int j = 0; j < 3; j++) ds[j] = f32x2(dsh[j]);
     }
-    for (int q = threadIdx.x; 2 * q < nx; q += blockDim.x) {
-        cx<f32x2> u[3];
-        pair_substeps<IMAG, STD>(A, p, ds, Ot, mask, 2 * q, iy, u);
-        const int s0 = long_slot(2 * q);  // 2q is even: 2q + 1 sits in the next slot of the same chunk
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            lines[j * S + s0] = cx<float>{u[j].re.v.x, u[j].im.v.x};
-            lines[j * S + s0 + 1] = cx<float>{u[j].re.v.y, u[j].im.v.y};
-        }
-    }
-    for (int i = nx + threadIdx.x; i < span; i += blockDim.x)
-#pragma unroll
-        for (int j = 0; j < 3; j++) lines[j * S + long_slot(i)] = cx<float>{0.0f, 0.0f};
-    __syncthreads();
-    const int j = warp / nwl;
-    long_line_uni<float, IMAG>(lines + j * S, nx, t, warp - j * nwl, nwl, seg[j], false);
-    pdl_trigger();  // the y sweep's blocks may take the slots this grid frees
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        float2* dst = B + ((size_t)c * p.ny + iy) * nx;
-        const cx<float>* src = lines + c * S;
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) dst[i] = make_float2(src[long_slot(i)].re, src[long_slot(i)].im);
-    }
+    pwx_long_row<IMAG, STD>(A, B, p, ds, Ot, t, mask, iy);
 }
 
 // CN along y for columns of 1025..8192 points: one block per tile of kc (1, 2
@@ -1216,13 +1228,14 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps, long_min_blocks<R, UNI>())
 
 template <typename R, int HC> constexpr int tile_min_blocks() { return sizeof(R) == 4 ? (HC == 1 ? 3 : 2) : 1; }
 
-// sc (nullable): the tiled step whose next head kernel forms the pending scale from
-// these partials (as k_cny_reg: block 0 marks that, or stores the scale 1 when
-// renorm == 0, and moves the step counter on if advance).
+// One tile of the row-tiled y sweep: columns [32 ct, 32 ct + 32) of component j,
+// rows [128 rt, 128 rt + 128) written (see k_cn_y_tile). Every thread of the block
+// calls it after the dependency wait; with want_norm it returns the tile's |o|^2
+// sum in thread 0 (PartT<R>), otherwise zero.
 template <typename R, bool IMAG, int HC>
-__global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<R, HC>()))
-    k_cn_y_tile(const typename V2<R>::T* __restrict__ in, typename V2<R>::T* __restrict__ out, KParams p, Tabs<R> t,
-                double* part, DevScalars* sc, int renorm, int advance) {
+__device__ __forceinline__ typename PartT<R>::T cny_tile(const typename V2<R>::T* __restrict__ in,
+                                                         typename V2<R>::T* __restrict__ out, const KParams& p,
+                                                         const Tabs<R>& t, int j, int ct, int rt, bool want_norm) {
     using G = typename UCoef<IMAG, R>::T;
     using P = typename PartT<R>::T;
     using T = typename V2<R>::T;
@@ -1235,9 +1248,6 @@ __global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<R,
     __shared__ P red[NW];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int n = p.ny, nx = p.nx;
-    const int nrt = (n + kTileRows - 1) / kTileRows, nct = (nx + 31) >> 5;
-    const int rt = blockIdx.x % nrt, rest = blockIdx.x / nrt;
-    const int ct = rest % nct, j = rest / nct;
     const int y0 = rt * kTileRows, i0 = y0 + 16 * (w - HC);
     const int col = ct * 32 + lane;
     const bool colok = col < nx;
@@ -1250,21 +1260,6 @@ __global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<R,
     const bool inner = i0 >= 1 && i0 + kLongC < n;
     const T* src = in + cbase + (ptrdiff_t)i0 * nx;
     cx<R> v[kLongC];
-    pdl_wait();
-    // with norm partials and no head scale the next launch is the finalize block, which
-    // may become resident now (it waits for this grid); otherwise the next kernel
-    // launches at the end
-    if (part && !sc) pdl_trigger();
-    if (sc && blockIdx.x == 0 && threadIdx.x < 3) {
-        if (renorm) {
-            if (threadIdx.x == 0) sc->scale_src = 1;
-        } else {
-            sc->scale[threadIdx.x] = 1.0;
-            sc->scale_f[threadIdx.x] = 1.0f;
-            sc->scale_l[threadIdx.x] = 0.0f;
-        }
-        if (advance && threadIdx.x == 0) sc->step_idx += 1;
-    }
     // the chunk's values x (kept in shared memory for the result) and the right-hand
     // side: L x (increment form) or x. IN: no row checks (inner chunk).
     auto load_rhs = [&](auto in_tag) {
@@ -1387,15 +1382,44 @@ __global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<R,
                 if (i0 + m < n) result(m);
         }
     }
-    if (part) {
-        P a;
-        if constexpr (INC && IMAG)
-            a = acc.dfvalue();
-        else
-            a = acc_value<P>(acc);
-        const P sum = block_part(a, red);
-        if (threadIdx.x == 0) reinterpret_cast<P*>(part)[blockIdx.x] = sum;
+    if (!want_norm) return P(0);
+    P a;
+    if constexpr (INC && IMAG)
+        a = acc.dfvalue();
+    else
+        a = acc_value<P>(acc);
+    return block_part(a, red);
+}
+
+
+// sc (nullable): the tiled step whose next head kernel forms the pending scale from
+// these partials (as k_cny_reg: block 0 marks that, or stores the scale 1 when
+// renorm == 0, and moves the step counter on if advance).
+template <typename R, bool IMAG, int HC>
+__global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<R, HC>()))
+    k_cn_y_tile(const typename V2<R>::T* __restrict__ in, typename V2<R>::T* __restrict__ out, KParams p, Tabs<R> t,
+                double* part, DevScalars* sc, int renorm, int advance) {
+    using P = typename PartT<R>::T;
+    const int nrt = (p.ny + kTileRows - 1) / kTileRows, nct = (p.nx + 31) >> 5;
+    const int rt = blockIdx.x % nrt, rest = blockIdx.x / nrt;
+    const int ct = rest % nct, j = rest / nct;
+    pdl_wait();
+    // with norm partials and no head scale the next launch is the finalize block, which
+    // may become resident now (it waits for this grid); otherwise the next kernel
+    // launches at the end
+    if (part && !sc) pdl_trigger();
+    if (sc && blockIdx.x == 0 && threadIdx.x < 3) {
+        if (renorm) {
+            if (threadIdx.x == 0) sc->scale_src = 1;
+        } else {
+            sc->scale[threadIdx.x] = 1.0;
+            sc->scale_f[threadIdx.x] = 1.0f;
+            sc->scale_l[threadIdx.x] = 0.0f;
+        }
+        if (advance && threadIdx.x == 0) sc->step_idx += 1;
     }
+    const P sum = cny_tile<R, IMAG, HC>(in, out, p, t, j, ct, rt, part != nullptr);
+    if (part && threadIdx.x == 0) reinterpret_cast<P*>(part)[blockIdx.x] = sum;
 }
 
 }  // namespace sgpe

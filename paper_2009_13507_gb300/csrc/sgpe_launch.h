@@ -176,9 +176,9 @@ template <typename R> struct Launcher {
                                 const DevScalars* sc, const double* omega_tab, const TabSet& tabs_x, int mask,
                                 const double* partials = nullptr, int m = 0, int renorm = 0);
     static cudaError_t coef(cudaStream_t s, void* fa, void* fg, void* fp, void* fq, int n, double bre, double bim);
-    // The constant-factor form of an n-point line with bt = bre + i bim (n > kRegMaxN):
-    // fills u and copies s to s_dev (kUniMaxS entries of room); u->ks = 0 where the
-    // correction would be longer than that.
+    // The constant-factor form of an n-point line with bt = bre + i bim: fills u and
+    // copies s to s_dev (kUniMaxS entries of room; s_dev null: no copy); u->ks = 0
+    // where the correction would be longer than that (and always for complex128).
     static cudaError_t uni(cudaStream_t s, int n, double bre, double bim, void* s_dev, UniHost* u);
     static cudaError_t flush(cudaStream_t s, void* A, size_t plane, const DevScalars* sc);
     // advance: also move the step counter on (the last kernel of a step).

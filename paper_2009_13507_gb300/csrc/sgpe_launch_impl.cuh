@@ -461,8 +461,11 @@ cudaError_t Launcher<R>::uni(cudaStream_t s, int n, double bre, double bim, void
         const C si = a * q[i];
         hs[i] = host_elem<R>(si.real(), si.imag());
     }
-    cudaError_t e = cudaMemcpyAsync(s_dev, hs.data(), sizeof(T) * ks, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
+    // (s_dev null: the host figures only, nothing copied)
+    if (s_dev) {
+        cudaError_t e = cudaMemcpyAsync(s_dev, hs.data(), sizeof(T) * ks, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
     // pageable source: the copy is staged before cudaMemcpyAsync returns; keep the
     // stream order with the kernels that read s
     *u = UniHost{};

@@ -59,6 +59,38 @@ def test_small_uneven_batch_matches_oracle(precision, tiles):
     torch.cuda.synchronize()
 
 
+TILED = [
+    dict(dim=2, nx=256, ny=300, dx=0.05, c0=40.0, c2=1.0, so_type=1, gamma=0.8, omega=0.5, dt=2e-4),
+    dict(dim=2, nx=384, ny=256, dx=0.02, c0=20.0, c2=-1.0, so_type=2, gamma=0.5, omega=0.3, dt=2e-4),
+    dict(dim=2, nx=257, ny=300, dx=0.05, c0=40.0, c2=1.0, so_type=1, gamma=0.8, omega=0.5, dt=2e-4),
+    dict(dim=2, nx=100, ny=80, dx=0.15, c0=30.0, c2=0.5, so_type=3, gamma=0.6, omega=0.9, dt=1e-3),
+    dict(dim=1, nx=400, dx=0.05, c0=60.0, c2=0.7, so_type=1, gamma=0.9, omega=0.6, dt=1e-3),
+]
+
+
+@pytest.mark.parametrize("tiles", [(0, 1), (2, 2)])
+def test_tiled_instances_in_a_batch(tiles):
+    """complex64 instances of 256..1024 points an axis with even rows take the tiled
+    step inside the batch (the fused row kernel and the row tiles through work
+    lists; one halo chunk at bt = 0.02, two at bt = 0.125), next to instances on the
+    register path (odd rows, small grids, 1D) and with either x part of those."""
+    bs = sgpe.BatchSolver(TILED, precision="c64")
+    bs.set_tiles(*tiles)
+    states = [_initial(s, 40 + i) for i, s in enumerate(bs.specs)]
+    bs.load_state(bs.pack(states))
+    bs.step_imag(20)
+    bs.step_real(5)
+    obs = bs.energy()
+    got = bs.states()
+    for i, spec in enumerate(bs.specs):
+        prob = _problem(spec)
+        ref = O.step(prob, O.step(prob, states[i], 20, True), 5, False)
+        assert relerr(got[i], ref) < 1e-4, i
+        ro = O.observables_array(prob, ref)
+        for k in (0, 1, 2, 3, 5, 6, 7, 8, 9):
+            assert abs(obs[i, k] - ro[k]) <= 1e-5 * max(abs(ro[k]), 1e-3), (i, k, obs[i, k], ro[k])
+
+
 def test_batch_workload_sampled_against_oracle():
     """The batched workload at full size: 32 1D instances (nx ~ U{128..1024}) and
     32 2D instances (n ~ U{128..384}), (gamma, Omega, c0, c2) drawn per instance,
