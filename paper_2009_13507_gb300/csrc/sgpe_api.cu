@@ -441,10 +441,19 @@ static bool general_path(const sgpe_ctx* c) { return c->params.split != 0 || c->
 static bool tiled_mode(const sgpe_ctx* c, int mode) {
     return c->geo.tiled && !general_path(c) && tiled_step(c->geo, c->tabs[mode][0], c->tabs[mode][1]);
 }
-// The fused head kernel of a tiled complex64 step forms the pending scale from the
-// row tiles' partials itself (at most 256 a component) instead of a finalize block.
+// The fused head kernel of a complex64 step on the long-line kernels (tiled grids,
+// or rows of 1025..2048 points) forms the pending scale from the row tiles' partials
+// itself instead of a finalize block: with renormalisation, where there are at most
+// kHeadMaxParts partials a component (2048^2, 1024 a component: every block summing
+// them measured 108.5 -> 126.4 us/step); without it (real time) the y tiles store
+// the scale 1 and nothing is summed (2048^2 real time 126.5 -> 124.9).
+constexpr int kHeadMaxParts = 256;
 static bool tiled_head(const sgpe_ctx* c, int mode) {
-    return tiled_mode(c, mode) && pwx_long_fits(c->geo, c->tabs[mode][0]) && c->geo.blocks_yt / 3 <= 256;
+    if (general_path(c) || !pwx_long_fits(c->geo, c->tabs[mode][0])) return false;
+    if (c->geo.tiled ? !tiled_mode(c, mode) : c->geo.reg_x) return false;
+    const int renorm = mode == 0 ? c->params.renorm : 0;
+    return y_tiled(c->geo, c->tabs[mode][1], c->mid, c->psi) &&
+           (renorm == 0 || c->geo.blocks_yt / 3 <= kHeadMaxParts);
 }
 static bool head_scale(const sgpe_ctx* c, int mode) {
     if (general_path(c)) return false;
