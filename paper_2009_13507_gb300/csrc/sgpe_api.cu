@@ -47,7 +47,8 @@ Geometry make_geometry(int dim, int nx, int ny, int esz) {
     g.blocks_y = dim == 2 ? 3 * ceil_div(nx, g.reg_y ? cny_cols_per_warp(chunk_len(ny), esz) : g.wy) : 0;
     const int mid_min = esz == 8 ? kMidMinN : kMidMinN16;
     g.tiled = dim == 2 && nx >= mid_min && ny >= mid_min && g.reg_x && g.reg_y;
-    g.blocks_yt = dim == 2 && (!g.reg_y || g.tiled) ? 3 * ceil_div(nx, 32) * ceil_div(ny, kTileRows) : 0;
+    g.tile_rt = ny <= kTileShortMaxN ? kTileRealShort : kTileReal;
+    g.blocks_yt = dim == 2 && (!g.reg_y || g.tiled) ? 3 * ceil_div(nx, 32) * ceil_div(ny, kLongC * g.tile_rt) : 0;
     g.blocks_obs = ceil_div(nx, 32) * ceil_div(ny, 4);
     g.blocks_norm = kNormBlocks;
     return g;

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<fl
     const int4 e = work[blockIdx.x];
     const BInst& I = insts[e.x];
     const Tabs<float> t = uni[4 * e.x + (IMAG ? 0 : 2) + 1];
-    const df sum = cny_tile<float, IMAG, HC>(B + I.off, A + I.off, I.p, t, e.y & 3, e.y >> 2, e.z, true);
+    const df sum = cny_tile<float, IMAG, HC, kTileReal>(B + I.off, A + I.off, I.p, t, e.y & 3, e.y >> 2, e.z, true);
     if (threadIdx.x == 0) partials[e.w] = (double)sum.hi + (double)sum.lo;
 }
 

@@ -1226,13 +1226,15 @@ __global__ void __launch_bounds__(32 * kLongMaxWarps, long_min_blocks<R, UNI>())
 // long_line_uni. in != out: the halos read other tiles' input rows.
 // ---------------------------------------------------------------------------
 
-template <typename R, int HC> constexpr int tile_min_blocks() { return sizeof(R) == 4 ? (HC == 1 ? 3 : 2) : 1; }
+template <typename R, int HC, int RT = kTileReal> constexpr int tile_min_blocks() {
+    return RT == kTileReal ? (sizeof(R) == 4 ? (HC == 1 ? 3 : 2) : 1) : (sizeof(R) == 4 ? (HC == 1 ? 5 : 4) : 2);
+}
 
 // One tile of the row-tiled y sweep: columns [32 ct, 32 ct + 32) of component j,
 // rows [128 rt, 128 rt + 128) written (see k_cn_y_tile). Every thread of the block
 // calls it after the dependency wait; with want_norm it returns the tile's |o|^2
 // sum in thread 0 (PartT<R>), otherwise zero.
-template <typename R, bool IMAG, int HC>
+template <typename R, bool IMAG, int HC, int RT = kTileReal>
 __device__ __forceinline__ typename PartT<R>::T cny_tile(const typename V2<R>::T* __restrict__ in,
                                                          typename V2<R>::T* __restrict__ out, const KParams& p,
                                                          const Tabs<R>& t, int j, int ct, int rt, bool want_norm) {
@@ -1240,7 +1242,7 @@ __device__ __forceinline__ typename PartT<R>::T cny_tile(const typename V2<R>::T
     using P = typename PartT<R>::T;
     using T = typename V2<R>::T;
     constexpr bool INC = sizeof(R) == 4;
-    constexpr int NW = kTileReal + 2 * HC;
+    constexpr int NW = RT + 2 * HC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R>* xs = reinterpret_cast<cx<R>*>(smem_raw);  // [warp][m][lane]: the loaded values
     __shared__ cx<R> fend[NW][32], bend[NW][32];      // chunk ends of the two passes
@@ -1248,7 +1250,7 @@ __device__ __forceinline__ typename PartT<R>::T cny_tile(const typename V2<R>::T
     __shared__ P red[NW];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int n = p.ny, nx = p.nx;
-    const int y0 = rt * kTileRows, i0 = y0 + 16 * (w - HC);
+    const int y0 = rt * kLongC * RT, i0 = y0 + 16 * (w - HC);
     const int col = ct * 32 + lane;
     const bool colok = col < nx;
     // a lane past the last column reads column nx - 1 (in bounds) and stores nothing:
@@ -1361,7 +1363,7 @@ __device__ __forceinline__ typename PartT<R>::T cny_tile(const typename V2<R>::T
     }
     const auto k = ucoef<IMAG>(t.uk);
     typename std::conditional<INC && IMAG, NormAccF2, NormAcc<R>>::type acc;
-    if (w >= HC && w < HC + kTileReal && colok) {
+    if (w >= HC && w < HC + RT && colok) {
         T* dst = out + cbase + (ptrdiff_t)i0 * nx;
         auto result = [&](int m) {
             const cx<R> x = xw[m * 32];
@@ -1395,12 +1397,12 @@ __device__ __forceinline__ typename PartT<R>::T cny_tile(const typename V2<R>::T
 // sc (nullable): the tiled step whose next head kernel forms the pending scale from
 // these partials (as k_cny_reg: block 0 marks that, or stores the scale 1 when
 // renorm == 0, and moves the step counter on if advance).
-template <typename R, bool IMAG, int HC>
-__global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<R, HC>()))
+template <typename R, bool IMAG, int HC, int RT>
+__global__ void __launch_bounds__(32 * (RT + 2 * HC), (tile_min_blocks<R, HC, RT>()))
     k_cn_y_tile(const typename V2<R>::T* __restrict__ in, typename V2<R>::T* __restrict__ out, KParams p, Tabs<R> t,
                 double* part, DevScalars* sc, int renorm, int advance) {
     using P = typename PartT<R>::T;
-    const int nrt = (p.ny + kTileRows - 1) / kTileRows, nct = (p.nx + 31) >> 5;
+    const int nrt = (p.ny + kLongC * RT - 1) / (kLongC * RT), nct = (p.nx + 31) >> 5;
     const int rt = blockIdx.x % nrt, rest = blockIdx.x / nrt;
     const int ct = rest % nct, j = rest / nct;
     pdl_wait();
@@ -1418,7 +1420,7 @@ __global__ void __launch_bounds__(32 * (kTileReal + 2 * HC), (tile_min_blocks<R,
         }
         if (advance && threadIdx.x == 0) sc->step_idx += 1;
     }
-    const P sum = cny_tile<R, IMAG, HC>(in, out, p, t, j, ct, rt, part != nullptr);
+    const P sum = cny_tile<R, IMAG, HC, RT>(in, out, p, t, j, ct, rt, part != nullptr);
     if (part && threadIdx.x == 0) reinterpret_cast<P*>(part)[blockIdx.x] = sum;
 }
 

@@ -379,7 +379,10 @@ constexpr int kLongC = 16;
 constexpr int kLongMaxWarps = 16;
 // Row tiles of the y sweep of long columns (k_cn_y_tile): chunks of kLongC rows
 // a tile writes, the most halo chunks above and below, rows written per tile.
+// (kTileReal: the tall tiles; grids of at most kTileShortMaxN rows take tiles of
+// kTileRealShort chunks, which gives short columns more tiles)
 constexpr int kTileReal = 8, kTileMaxHalo = 2;
+constexpr int kTileRealShort = 4, kTileShortMaxN = 512;
 constexpr int kTileMaxWarps = kTileReal + 2 * kTileMaxHalo;
 constexpr int kTileRows = kLongC * kTileReal;
 // Extra elements between the staged columns of a y tile of lines longer than

@@ -87,6 +87,7 @@ struct Geometry {
     size_t smem_x, smem_y;
     int blocks_x, blocks_y, blocks_obs, blocks_norm;
     int blocks_yt;  // long columns (and tiled grids): blocks (= norm partials) of the row-tiled y sweep
+    int tile_rt;    // chunks of 16 rows that a y tile writes (kTileReal, or kTileRealShort on short columns)
     bool tiled;     // 2D grid of kMidMinN (kMidMinN16)..kRegMaxN points an axis: its steps take the kernels of long
                     // lines (complex64: fused pointwise + x sweep; double-float: pointwise kernel and the
                     // constant-factor x sweep; then the row-tiled y sweep) where the constant-factor form
@@ -119,7 +120,8 @@ struct TabSet {
 // Whether the y sweep of these tables runs in row tiles (k_cn_y_tile: long
 // columns, the constant-factor form with a short carry reach, in != out).
 inline bool y_tiled(const Geometry& g, const TabSet& ty, const void* in, const void* out) {
-    return g.dim == 2 && (!g.reg_y || g.tiled) && ty.u.ks > 0 && ty.u.hc > 0 && in != out;
+    return g.dim == 2 && (!g.reg_y || g.tiled) && ty.u.ks > 0 && ty.u.hc > 0 && ty.u.ks <= kLongC * g.tile_rt &&
+           in != out;
 }
 // Norm partials that the step's y sweep (in -> out) leaves.
 inline int y_parts(const Geometry& g, const TabSet& ty, const void* in, const void* out) {
@@ -136,7 +138,7 @@ inline bool pwx_long_fits(const Geometry& g, const TabSet& tx) {
 // in the constant-factor form (which complex128 never takes), the row tiles reaching
 // the y carries.
 inline bool tiled_step(const Geometry& g, const TabSet& tx, const TabSet& ty) {
-    return g.tiled && tx.u.ks > 0 && ty.u.ks > 0 && ty.u.hc > 0;
+    return g.tiled && tx.u.ks > 0 && ty.u.ks > 0 && ty.u.hc > 0 && ty.u.ks <= kLongC * g.tile_rt;
 }
 // The x sweep of a tiled grid on the constant-factor long-line kernel.
 inline bool x_tiled(const Geometry& g, const TabSet& tx) { return g.dim == 2 && g.tiled && tx.u.ks > 0; }

@@ -244,10 +244,14 @@ template <typename R> cudaError_t Launcher<R>::setup() {
             if ((e = allow_smem(k_pwx_long<true, false>))) return e;
             if ((e = allow_smem(k_pwx_long<false, false>))) return e;
         }
-        if ((e = allow_smem(k_cn_y_tile<R, true, 1>))) return e;
-        if ((e = allow_smem(k_cn_y_tile<R, false, 1>))) return e;
-        if ((e = allow_smem(k_cn_y_tile<R, true, 2>))) return e;
-        if ((e = allow_smem(k_cn_y_tile<R, false, 2>))) return e;
+        if ((e = allow_smem(k_cn_y_tile<R, true, 1, kTileReal>))) return e;
+        if ((e = allow_smem(k_cn_y_tile<R, false, 1, kTileReal>))) return e;
+        if ((e = allow_smem(k_cn_y_tile<R, true, 2, kTileReal>))) return e;
+        if ((e = allow_smem(k_cn_y_tile<R, false, 2, kTileReal>))) return e;
+        if ((e = allow_smem(k_cn_y_tile<R, true, 1, kTileRealShort>))) return e;
+        if ((e = allow_smem(k_cn_y_tile<R, false, 1, kTileRealShort>))) return e;
+        if ((e = allow_smem(k_cn_y_tile<R, true, 2, kTileRealShort>))) return e;
+        if ((e = allow_smem(k_cn_y_tile<R, false, 2, kTileRealShort>))) return e;
     }
     if ((e = socn_allow<R, 16>())) return e;
     if ((e = socn_allow<R, 32>())) return e;
@@ -379,17 +383,24 @@ cudaError_t Launcher<R>::cn_y(cudaStream_t s, bool imag, const void* in, void* o
     double* part = finalize ? partials : nullptr;
     if (y_tiled(g, tabs, in, out)) {
         if constexpr (kUniForm<R>) {
-            const int hc = tabs.u.hc;
-            const dim3 tb(32 * (kTileReal + 2 * hc)), tg(g.blocks_yt);
-            const size_t sm = (size_t)(kTileReal + 2 * hc) * kLongC * 32 * sizeof(cx<R>);
+            const int hc = tabs.u.hc, rtc = g.tile_rt;
+            const dim3 tb(32 * (rtc + 2 * hc)), tg(g.blocks_yt);
+            const size_t sm = (size_t)(rtc + 2 * hc) * kLongC * 32 * sizeof(cx<R>);
             DevScalars* hs = head_scale ? sc : nullptr;
             auto go = [&](auto kern) {
                 launch_pdl(kern, tg, tb, sm, s, (const T*)in, (T*)out, p, t, part, hs, renorm, advance);
             };
-            if (hc == 1)
-                imag ? go(k_cn_y_tile<R, true, 1>) : go(k_cn_y_tile<R, false, 1>);
-            else
-                imag ? go(k_cn_y_tile<R, true, 2>) : go(k_cn_y_tile<R, false, 2>);
+            if (rtc == kTileReal) {
+                if (hc == 1)
+                    imag ? go(k_cn_y_tile<R, true, 1, kTileReal>) : go(k_cn_y_tile<R, false, 1, kTileReal>);
+                else
+                    imag ? go(k_cn_y_tile<R, true, 2, kTileReal>) : go(k_cn_y_tile<R, false, 2, kTileReal>);
+            } else {
+                if (hc == 1)
+                    imag ? go(k_cn_y_tile<R, true, 1, kTileRealShort>) : go(k_cn_y_tile<R, false, 1, kTileRealShort>);
+                else
+                    imag ? go(k_cn_y_tile<R, true, 2, kTileRealShort>) : go(k_cn_y_tile<R, false, 2, kTileRealShort>);
+            }
             return cudaGetLastError();
         }
     }
