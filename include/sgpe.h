@@ -429,11 +429,15 @@ const char* sgpe_batch_last_error(const sgpe_batch* b);
 sgpe_status sgpe_batch_destroy(sgpe_batch* b);
 
 /*
- * Number of kernel launches one step enqueues (for launch accounting): 2 on 2D
- * grids with lines of at most 1024 points (plus one end-of-steps launch per
- * sgpe_step_imag / sgpe_step_real call), 3 or 4 for longer lines; 0 on 1D grids
- * whose whole step loop is one launch per call (lines of at most 1024 points in
- * SGPE_C64 and SGPE_CDF, at most 256 in SGPE_C128), 3 on other 1D grids.
+ * Number of kernel launches one imaginary-time step enqueues (for launch
+ * accounting): 2 on 2D grids with lines of at most 1024 points whose step needs
+ * no finalize launch (the register path; the tiled complex64 path of grids of
+ * 256..1024 points an axis), plus one end-of-steps launch per sgpe_step_imag /
+ * sgpe_step_real call; 3 on complex64 grids with even rows of 1025..2048 points
+ * (fused pointwise + x sweep, row-tiled y sweep, finalize) and 4 on other 2D
+ * paths (double-float tiled grids, longer lines); 0 on 1D grids whose whole step
+ * loop is one launch per call (lines of at most 1024 points in SGPE_C64 and
+ * SGPE_CDF, at most 256 in SGPE_C128), 3 on other 1D grids.
  */
 int sgpe_launches_per_step(const sgpe_ctx* ctx);
 
