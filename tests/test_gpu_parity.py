@@ -213,6 +213,24 @@ def test_real_time_omega_table():
     assert relerr(s.get_state(), ref) < 1e-10
 
 
+@pytest.mark.parametrize("nx,ny", [(256, 300), (1026, 5)])
+def test_real_time_omega_table_fused_kernels(nx, ny):
+    """complex64 real-time steps with a per-step Omega(t) table on the kernels of long
+    lines: a tiled grid (the y tiles move the step counter that indexes the table,
+    no finalize block) and long rows (the finalize block moves it); 37 steps, a
+    graph of 32 and 5 more, after imaginary-time steps that leave a pending scale."""
+    import torch
+    phys = dict(PHYS_2D)
+    prob, s = make_pair(2, nx, ny, dx=0.05, precision="c64", **phys)
+    psi = _rand(prob, nx + ny, env=2.0)
+    om = 0.5 * np.cos(np.linspace(0, 3, 37)) + 0.1 * I.uniform(11, 37)
+    s.set_state(psi)
+    s.step_imag(3)
+    s.step_real(37, torch.tensor(om, dtype=torch.float64, device="cuda:0"))
+    ref = O.step(prob, O.step(prob, psi, 3, True), 37, False, omega_t=om)
+    assert relerr(s.get_state(), ref) < 1e-5
+
+
 @pytest.mark.parametrize("mag", [0.0, 0.3])
 def test_fixed_magnetisation_renorm(mag):
     phys = dict(c0=30.0, c2=2.0, so_type=0, gamma=0.0, omega=0.0, dt=1e-3, renorm=2, mag=mag)
