@@ -226,12 +226,13 @@ sgpe_status sgpe_substep(sgpe_ctx* ctx, int which, int imag, double omega);
  * each kernel kind to ms_out[0..3] (0 pointwise SO/CALCNU/HERM, 1 Crank-Nicolson
  * along x, 2 along y, 3 end-of-step norm reduction and renormalisation scale;
  * unused kinds 0) and the launch counts to launches_out[0..3]. On 2D grids
- * with lines of at most 1024 points kind 0 is the fused kernel (pending scale,
- * pointwise substeps and the x sweep), kind 1 has no launches, and the end of
- * step runs inside kinds 0 and 2 (kind 3 has no launches; one untimed
+ * with lines of at most 1024 points (except double-float grids of 320..1024
+ * points an axis, which launch all four kinds) kind 0 is a fused kernel (pending
+ * scale, pointwise substeps and the x sweep), kind 1 has no launches, and the end
+ * of step runs inside kinds 0 and 2 (kind 3 has no launches; one untimed
  * end-of-steps launch follows the last step). On complex64 2D grids with even
  * rows of 1025..2048 points kind 0 is the fused pointwise + x-sweep kernel too
- * and kind 1 has no launches.
+ * and kind 1 has no launches (kind 3 only in imaginary time).
  * Advances the state exactly like the step functions. Synchronises the stream.
  */
 sgpe_status sgpe_profile_steps(sgpe_ctx* ctx, int nsteps, int imag, double* ms_out, int* launches_out);

@@ -563,7 +563,8 @@ static cudaError_t enqueue_step(sgpe_ctx* c, bool imag, const double* omega_tab)
                                  c->sc, renorm, 1, 1, true);
     }
     if (pwx_long_fits(c->geo, c->tabs[mode][0]) && (!c->geo.reg_x || tiled_mode(c, mode))) {
-        // complex64 rows of 1025..2048 points, and tiled grids: pointwise substeps and x sweep in one kernel
+        // complex64 rows of 1025..2048 points (and tiled grids outside the head path): pointwise
+        // substeps and x sweep in one kernel
         if ((e = Launcher<R>::pwx_long(c->stream, imag, c->psi, c->mid, c->kp, c->sc, omega_tab, c->tabs[mode][0],
                                        7)))
             return e;

@@ -1104,14 +1104,16 @@ __device__ __forceinline__ void pwx_long_row(const float2* __restrict__ A, float
     }
 }
 
-// Pointwise substeps and CN along x of one row of a 2D complex64 grid with
-// 1025..2048 points (nx even; the constant-factor solve, Tabs::uks > 0): one
-// block per row, 3 groups of nwl = ceil(nx / 512) warps (one group per
-// component line). The threads evaluate the row's point pairs (pair_substeps)
-// into the padded chunk layout of the three lines in shared memory (slots past
-// nx zero), then group j solves line j (long_line_uni) and the block stores the
-// three lines to B. Each step then streams the state twice (A -> B here, B -> A
-// in the y sweep) instead of three times.
+// Pointwise substeps and CN along x of one row of a 2D complex64 grid with even
+// rows of at most 2048 points (1025..2048, or the rows of a tiled grid; the
+// constant-factor solve, Tabs::uks > 0): one block per row, 3 groups of nwl =
+// ceil(nx / 512) warps (one group per component line). The threads evaluate the
+// row's point pairs (pair_substeps) into the padded chunk layout of the three
+// lines in shared memory (slots past nx zero), then group j solves line j
+// (long_line_uni) and the block stores the three lines to B. Each step then
+// streams the state twice (A -> B here, B -> A in the y sweep) instead of three
+// times. With partials (the tiled step) every block first forms the pending
+// scale from the previous y tiles' norm partials, as k_pwx does.
 template <bool IMAG, bool STD>
 __global__ void __launch_bounds__(96 * kPwxLongMaxGroupWarps, 2)
     k_pwx_long(const float2* __restrict__ A, float2* __restrict__ B, KParams p, const DevScalars* __restrict__ sc,
