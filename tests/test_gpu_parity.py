@@ -297,6 +297,20 @@ def test_precision_form_max_line(nx, ny):
     assert relerr(s.get_state(), O.step(prob, psi, 2, False)) < 1e-5
 
 
+@pytest.mark.parametrize("precision,tol", [("c64", 5e-6), ("cdf", 1e-12)])
+@pytest.mark.parametrize("imag", [True, False])
+@pytest.mark.parametrize("which", ["cn_x", "cn_y"])
+def test_tiled_grid_sweeps(which, imag, precision, tol):
+    """Single sweeps on a tiled grid (512 x 400: 64-row tiles, one halo chunk): the
+    constant-factor x sweep with one warp a line and the row-tiled y sweep, against
+    the oracle's Thomas solves."""
+    prob, s = make_pair(2, 512, 400, dx=0.05, precision=precision, **PHYS_2D)
+    psi = _rand(prob, 77, env=3.0)
+    s.set_state(psi)
+    s.substep(which, imag)
+    assert relerr(s.get_state(), O.substep(prob, psi, which, imag)) < tol
+
+
 @pytest.mark.parametrize("imag", [True, False])
 @pytest.mark.parametrize("nx,ny", [(256, 256), (384, 600), (512, 512), (1024, 386), (600, 1024), (385, 400), (254, 512)])
 def test_precision_form_tiled_grids(nx, ny, imag):
