@@ -70,7 +70,7 @@ TILED = [
 
 @pytest.mark.parametrize("tiles", [(0, 1), (2, 2)])
 def test_tiled_instances_in_a_batch(tiles):
-    """complex64 instances of 256..1024 points an axis with even rows take the tiled
+    """complex64 instances of 128..1024 points an axis with even rows take the tiled
     step inside the batch (the fused row kernel and the row tiles through work
     lists; one halo chunk at bt = 0.02, two at bt = 0.125), next to instances on the
     register path (odd rows, small grids, 1D) and with either x part of those."""
