@@ -259,6 +259,26 @@ def test_fixed_magnetisation_renorm_2d(precision, tol):
     assert abs(o["N"] - 1) < 1e-12 and abs(o["mag"] - 0.3) < 1e-12
 
 
+@pytest.mark.parametrize("precision,nx,ny,tol", [("c64", 256, 300, 1e-5), ("cdf", 320, 384, 1e-10),
+                                                  ("c64", 1026, 6, 1e-5)])
+def test_fixed_magnetisation_renorm_tiled(precision, nx, ny, tol):
+    """Eq. (DJ) on the kernels of long lines: a tiled complex64 grid (the fused head
+    kernel forms the per-component scale from the y tiles' partials), a tiled
+    double-float grid and complex64 long rows (the finalize block forms it). N and
+    m are exact to the storage precision: 1e-12 in double-float, 1e-6 for the
+    FP32-rounded complex64 state."""
+    phys = dict(c0=30.0, c2=2.0, so_type=1, gamma=0.5, omega=0.0, dt=5e-4, renorm=2, mag=0.3)
+    prob, s = make_pair(2, nx, ny, dx=0.05, precision=precision, **phys)
+    psi = _rand(prob, 5 + nx, env=2.0)
+    s.set_state(psi)
+    s.step_imag(20)
+    ref = O.step(prob, psi, 20, True)
+    assert relerr(s.get_state(), ref) < tol
+    o = s.energy()
+    nt = 1e-6 if precision == "c64" else 1e-12
+    assert abs(o["N"] - 1) < nt and abs(o["mag"] - 0.3) < nt
+
+
 @pytest.mark.parametrize("dim,nx,ny", [(2, 3, 3), (2, 5, 7), (2, 17, 3), (2, 33, 65), (1, 3, 1), (1, 32, 1),
                                        (1, 33, 1), (1, 224, 1), (1, 256, 1), (1, 257, 1), (1, 1000, 1),
                                        (2, 1500, 4), (2, 2560, 3), (2, 4096, 3), (2, 3, 4096)])
