@@ -433,7 +433,7 @@ sgpe_status sgpe_batch_destroy(sgpe_batch* b);
  * Number of kernel launches one imaginary-time step enqueues (for launch
  * accounting): 2 on 2D grids with lines of at most 1024 points whose step needs
  * no finalize launch (the register path; the tiled complex64 path of grids of
- * 256..1024 points an axis), plus one end-of-steps launch per sgpe_step_imag /
+ * 129..1024 points an axis), plus one end-of-steps launch per sgpe_step_imag /
  * sgpe_step_real call; 3 on complex64 grids with even rows of 1025..2048 points
  * (fused pointwise + x sweep, row-tiled y sweep, finalize) and 4 on other 2D
  * paths (double-float tiled grids, longer lines); 0 on 1D grids whose whole step

@@ -93,9 +93,12 @@ struct Geometry {
                     // constant-factor x sweep; then the row-tiled y sweep) where the constant-factor form
                     // applies
 };
-// Shortest axis of a grid that the tiled step serves: complex64 (8-byte elements)
-// and double-float (16-byte; its register path measured faster on 256-point lines).
-constexpr int kMidMinN = 256;
+// Shortest axis of a grid that the tiled step serves: complex64 (8-byte elements;
+// lines of more than 128 points take 8-point register chunks, slower than the tiles:
+// measured at 160, 192 and 224 points, while 128 points stay faster on the register
+// kernels) and double-float (16-byte; its register path measured faster on
+// 256-point lines).
+constexpr int kMidMinN = 129;
 constexpr int kMidMinN16 = 320;
 
 Geometry make_geometry(int dim, int nx, int ny, int esz);

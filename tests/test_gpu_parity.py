@@ -332,14 +332,15 @@ def test_tiled_grid_sweeps(which, imag, precision, tol):
 
 
 @pytest.mark.parametrize("imag", [True, False])
-@pytest.mark.parametrize("nx,ny", [(256, 256), (384, 600), (512, 512), (1024, 386), (600, 1024), (385, 400), (254, 512)])
+@pytest.mark.parametrize("nx,ny", [(256, 256), (160, 200), (384, 600), (512, 512), (1024, 386), (600, 1024), (385, 400),
+                                   (128, 512)])
 def test_precision_form_tiled_grids(nx, ny, imag):
-    """complex64 grids of 256..1024 points an axis step on the kernels of long lines
+    """complex64 grids of 129..1024 points an axis step on the kernels of long lines
     when the constant-factor form applies: even rows on the fused pointwise + x-sweep
     kernel (groups of one or two warps a line), which forms the pending scale from
     the row-tiled y sweep's norm partials (no finalize block); odd rows (385) on the
     pointwise kernel and the constant-factor x sweep, then the y tiles and the
-    finalize block; 254-point rows take the register kernels.
+    finalize block; 128-point rows take the register kernels.
     Full steps with the observables against the oracle, step calls of both time
     modes in turn (the pending scale handed between the two step paths), and the
     per-kernel profile."""
