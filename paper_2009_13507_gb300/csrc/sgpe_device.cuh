@@ -43,7 +43,6 @@ template <typename R> constexpr bool is_f32() { return sizeof(R) == 4; }
 template <typename R> __device__ __forceinline__ R to_r_df(df x) { return (R)df_to(x); }
 template <> __device__ __forceinline__ df to_r_df<df>(df x) { return x; }
 
-template <typename R> __device__ __forceinline__ cx<R> mk(R a, R b) { return cx<R>{a, b}; }
 template <typename R> __device__ __forceinline__ cx<R> add(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
 template <typename R> __device__ __forceinline__ cx<R> sub(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
 template <typename R> __device__ __forceinline__ cx<R> scl(R s, cx<R> a) { return {s * a.re, s * a.im}; }

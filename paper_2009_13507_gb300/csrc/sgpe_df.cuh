@@ -73,8 +73,6 @@ __device__ __forceinline__ df fma(df a, df b, df c) {
     return fast_two_sum(s.hi, s.lo + (e + c.lo));
 }
 
-__device__ __forceinline__ bool df_isfinite(df a) { return isfinite(a.hi); }
-
 // 1/sqrt(a) for a > 0: FP32 estimate, then two Newton steps y <- y (3 - a y^2)/2
 // in double-float (error ~2^-23, then ~2^-45, then the format's ~2^-48).
 __device__ __forceinline__ df df_rsqrt(df a) {
