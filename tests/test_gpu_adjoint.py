@@ -107,15 +107,17 @@ def test_differentiation_workload_against_central_differences():
     assert abs(fdy - dw[1]) < 1e-4 * abs(fdy) + floor
 
 
-def test_adjoint_precision_form_moderate_size():
+@pytest.mark.parametrize("n,nsteps,tol_om", [(64, 50, 1e-3), (160, 20, 5e-3)])
+def test_adjoint_precision_form_moderate_size(n, nsteps, tol_om):
     """The complex64 adjoint (FP32 state, FP64 gradient sums) against the oracle
-    adjoint at 64 x 64, 50 real-time steps with the workload's physics (c0 = 50,
-    c2 = 1, Rashba gamma = 0.8) and a varying Omega(t), checkpoint every 10 steps:
-    its error against the exact FP64 derivative is the stated error of the form
-    (measured on GB300: loss 1.6e-6, dL/dOmega 7.0e-4 of its largest entry,
-    dL/dw 1.0e-5)."""
+    adjoint with the workload's physics (c0 = 50, c2 = 1, Rashba gamma = 0.8) and a
+    varying Omega(t), checkpoint every 10 steps: its error against the exact FP64
+    derivative is the stated error of the form. Measured on GB300: 64 x 64, 50
+    real-time steps: loss 1.6e-6, dL/dOmega 7.0e-4 of its largest entry, dL/dw
+    1.0e-5; 160 x 160 (the forward y sweeps on row tiles), 20 steps: loss 9.9e-7,
+    dL/dOmega 2.2e-3, dL/dw 3.5e-6 (complex128 there: 1.9e-8 for dL/dOmega)."""
     phys = dict(c0=50.0, c2=1.0, so_type=1, gamma=0.8, omega=0.5, wx=1.0, wy=1.0, dt=1e-3, renorm=0)
-    n, dx, nsteps = 64, 0.2, 50
+    dx = 0.2
     prob, s = make_pair(2, n, n, dx=dx, precision="c64", **phys)
     psi0 = I.gaussian_phase_2d(n, n, dx, dx, seed=6)
     tgt = I.gaussian_target(n, n, dx, dx, seed=8)
@@ -128,7 +130,7 @@ def test_adjoint_precision_form_moderate_size():
     e_w = max(abs(dw[0] - g_wx) / abs(g_wx), abs(dw[1] - g_wy) / abs(g_wy))
     print("complex64 adjoint vs oracle: loss %.2e, dL/dOmega %.2e, dL/dw %.2e" % (e_L, e_om, e_w))
     assert e_L < 1e-5
-    assert e_om < 1e-3
+    assert e_om < tol_om
     assert e_w < 1e-3
 
 
