@@ -360,6 +360,58 @@ def test_table4_energies(oracle, row):
     assert abs(o["E"] - E_paper) < 1e-4
 
 
+def _table3_1d_converged():
+    rows = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "tables_3_4.txt")):
+        if line.strip() and not line.startswith("#"):
+            t, dim, ph, c0, c2, g, dx, E = line.split()
+            if t == "T3" and dim == "1" and float(dx) == 0.0:
+                rows[ph] = (float(c0), float(c2), float(g), float(E))
+    return rows
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("phase", ["ferro", "polar"])
+def test_table3_1d_converged_energy(oracle, phase):
+    """Table 3's converged 1D SO energies (5 printed decimals) from the oracle on its
+    own grids: DX = 0.1 and 0.05 on [-16, 16), DT = DX^2 / 10 (the imaginary-time
+    step of Sec. 4), each run to |dE| < 1e-10 E over tau = 2. The R5 stencils leave
+    an O(dx^2) error (DT scales with it), so the Richardson value E_0.05 -
+    (E_0.1 - E_0.05) / 3 is the continuum one; it must reach the printed value to
+    its last decimal, and both grid energies lie above it."""
+    c0, c2, g, E_paper = _table3_1d_converged()[phase]
+    threads = min(4, os.cpu_count() or 1)
+    E = {}
+    try:
+        oracle.set_threads(threads)
+        for dx in (0.1, 0.05):
+            nx, dt = int(round(32.0 / dx)), dx * dx * 0.1
+            prob = oracle.Problem(dim=1, nx=nx, dx=dx, dt=dt, c0=c0, c2=c2, so_type=1, gamma=g, renorm=1)
+            x = I.grid_x(nx, dx)
+            w = 4.0 if phase == "polar" else 6.0
+            env = np.exp(-x**2 / (2 * w * w))
+            if phase == "polar":
+                psi = np.stack([1j * np.sin(g * x) / SQ2, -np.cos(g * x), 1j * np.sin(g * x) / SQ2]) * env
+            else:
+                psi = np.stack([np.full(nx, 0.5), np.full(nx, -1 / SQ2), np.full(nx, 0.5)]) * np.exp(1j * g * x) * env
+            psi = psi[:, None, :] / np.sqrt(np.sum(abs(psi) ** 2) * dx)
+            chunk, steps, e_old = int(round(2.0 / dt)), 0, None
+            while steps * dt < 60.0:
+                psi = oracle.step(prob, psi, chunk, imag=True)
+                steps += chunk
+                e = oracle.observables(prob, psi)["E"]
+                if e_old is not None and steps * dt > 10.0 and abs(e - e_old) < 1e-10 * e:
+                    break
+                e_old = e
+            assert abs(e - e_old) < 1e-10 * e  # converged in imaginary time
+            E[dx] = e
+    finally:
+        oracle.set_threads(1)
+    limit = E[0.05] - (E[0.1] - E[0.05]) / 3.0
+    assert abs(limit - E_paper) < 3e-5
+    assert E[0.1] > E[0.05] > limit
+
+
 # ---------------------------------------------------------------------------
 # rms sizes (LENGTH / RADIUS) and the chemical potential: closed forms and the
 # GP Hamiltonian built independently from the spin matrices
